@@ -1,0 +1,370 @@
+"""Pins for the CPU oracle: each check compares it with something other than itself.
+
+Kinds of pin used (no GPU needed):
+  - published test vectors (splitmix64, tests/golden/splitmix64.txt);
+  - library routines of a different algorithm (LAPACK via numpy/scipy, Bessel K_nu);
+  - closed forms (Ornstein-Uhlenbeck tridiagonal inverse) and the Kalman filter, each an
+    independent route to C^-1 y and log det C;
+  - identities from the paper (Sylvester's determinant theorem, Sec. 4; the
+    Sherman-Morrison-Woodbury formula, Sec. 3.2);
+  - exact-rank facts (1-D exponential / Matern-3/2 / Matern-5/2 blocks of disjoint sorted
+    sets have rank 1 / 2 / 3) and the truncated SVD (optimal low rank, Sec. 3.1);
+  - the paper's claims: results independent of the leaf size (Sec. 5.6) and error
+    decreasing with the tolerance.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.special as sps
+import scipy.stats as sst
+
+import oracle as O
+from paper_1403_6015_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense_C(x, kern, theta, s2):
+    x = np.asarray(x, dtype=np.float64)
+    if x.ndim == 1:
+        x = x[:, None]
+    r = np.sqrt(((x[:, None, :] - x[None, :, :]) ** 2).sum(-1))
+    K = O.kernel_values(kern, r.ravel(), theta[0], theta[1]).reshape(r.shape)
+    return K + s2 * np.eye(len(x))
+
+
+# ---------------------------------------------------------------- inputs ----------------
+
+def test_splitmix64_published_vectors():
+    for line in open(os.path.join(GOLDEN, "splitmix64.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        seed, *outs = line.split()
+        got = I.splitmix64(int(seed), len(outs))
+        assert [int(o, 16) for o in outs] == [int(g) for g in got]
+
+
+def test_inputs_shapes_and_ranges():
+    x = I.uniform_points(1000, 2, 0.0, 1.0, 7)
+    assert x.shape == (1000, 2) and x.min() >= 0 and x.max() < 1
+    g = I.normal(200000, 3)
+    assert abs(g.mean()) < 0.01 and abs(g.std() - 1) < 0.01
+    Y = I.normal(100, 3, 4)
+    assert Y.shape == (100, 4) and Y.flags.f_contiguous
+
+
+# ---------------------------------------------------------------- kernels ---------------
+
+@pytest.mark.parametrize("nu2,name", [(1, "exp"), (3, "matern32"), (5, "matern52")])
+def test_matern_closed_forms_match_bessel(nu2, name):
+    """Half-integer Matern closed forms equal the Bessel form of Table 1 (with ell)."""
+    nu = nu2 / 2.0
+    ell = 0.37
+    r = np.linspace(1e-3, 3.0, 400)
+    z = np.sqrt(2 * nu) * r / ell
+    bessel = z ** nu * sps.kv(nu, z) / (sps.gamma(nu) * 2 ** (nu - 1))
+    got = O.kernel_values(name, r, ell, 1.0)
+    np.testing.assert_allclose(got, bessel, rtol=1e-12, atol=1e-300)
+    assert O.kernel_values(name, np.zeros(1), ell, 2.5)[0] == 2.5
+
+
+def test_se_special_values():
+    # k(ell) = exp(-1/2), k(0) = a, k(2 ell) = exp(-2)
+    v = O.kernel_values("se", np.array([0.0, 0.3, 0.6]), 0.3, 1.7)
+    np.testing.assert_allclose(v, 1.7 * np.array([1.0, np.exp(-0.5), np.exp(-2.0)]), rtol=1e-15)
+
+
+# ---------------------------------------------------------------- O1 dense --------------
+
+@pytest.mark.parametrize("kern", ["exp", "se", "matern32", "matern52"])
+@pytest.mark.parametrize("d", [1, 2])
+def test_dense_matches_lapack(kern, d):
+    n = 300
+    x = I.uniform_points(n, d, -1, 1, 11)
+    y = I.normal(n, 12, 3)
+    th, s2 = [0.4, 1.3], 0.05
+    C = dense_C(x, kern, th, s2)
+    sol, ld = O.dense_solve(x, kern, th, s2, y)
+    sign, ref = np.linalg.slogdet(C)
+    assert sign > 0
+    assert abs(ld - ref) <= 1e-11 * abs(ref)
+    np.testing.assert_allclose(sol, sla.solve(C, y, assume_a="pos"), rtol=1e-9, atol=1e-9)
+
+
+def test_dense_tiny_cofactor():
+    """3x3 determinant by cofactor expansion (no factorization at all)."""
+    x = np.array([0.1, -0.4, 0.9])
+    C = dense_C(x, "matern32", [0.5, 1.0], 0.2)
+    det = (C[0, 0] * (C[1, 1] * C[2, 2] - C[1, 2] * C[2, 1])
+           - C[0, 1] * (C[1, 0] * C[2, 2] - C[1, 2] * C[2, 0])
+           + C[0, 2] * (C[1, 0] * C[2, 1] - C[1, 1] * C[2, 0]))
+    _, ld = O.dense_solve(x, "matern32", [0.5, 1.0], 0.2, np.ones(3))
+    assert abs(ld - np.log(det)) < 1e-14
+
+
+def test_dense_rejects_non_spd():
+    # sigma^2 < 0 large enough to make C indefinite
+    x = np.linspace(-1, 1, 20)
+    with pytest.raises(O.OracleError):
+        O.dense_solve(x, "se", [0.3, 1.0], -2.0, np.ones(20))
+
+
+def test_dense_matvec_rows_exact():
+    n = 500
+    x = I.uniform_points(n, 1, -1, 1, 5)
+    v = I.normal(n, 6)
+    C = dense_C(x, "matern52", [0.2, 1.0], 0.01)
+    rows = np.array([0, 17, 250, 499])
+    np.testing.assert_allclose(O.dense_matvec_rows(x, "matern52", [0.2, 1.0], 0.01, v, rows),
+                               (C @ v)[rows], rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- closed forms ----------
+
+def test_ou_closed_form_vs_dense():
+    n = 1500
+    x, y = I.workload_1d(n, 21, nrhs=2)
+    xs = np.sort(x[:, 0])
+    p = np.argsort(x[:, 0], kind="stable")
+    th, s2 = [0.2, 1.4], 0.01
+    sol_d, ld_d = O.dense_solve(x, "exp", th, s2, y)
+    sol_c, ld_c = O.ou_closed_form(xs, th[0], th[1], s2, y[p])
+    assert abs(ld_c - ld_d) <= 1e-11 * abs(ld_d)
+    np.testing.assert_allclose(sol_c, sol_d[p], rtol=1e-8, atol=1e-8 * np.abs(sol_d).max())
+
+
+@pytest.mark.parametrize("nu2,name", [(1, "exp"), (3, "matern32"), (5, "matern52")])
+def test_kalman_vs_dense(nu2, name):
+    n = 1200
+    x, y = I.workload_1d(n, 31)
+    p = np.argsort(x[:, 0], kind="stable")
+    th, s2 = [0.15, 0.8], 0.02
+    sol, ld = O.dense_solve(x, name, th, s2, y)
+    ldk, q = O.matern_kalman(x[p, 0], nu2, th[0], th[1], s2, y[p])
+    assert abs(ldk - ld) <= 1e-10 * abs(ld)
+    assert abs(q - y @ sol) <= 1e-9 * abs(q)
+
+
+def test_loglik_formula_vs_scipy():
+    n = 200
+    x, y = I.workload_1d(n, 41)
+    th, s2 = [0.3, 1.0], 0.1
+    C = dense_C(x, "se", th, s2)
+    H = O.Hodlr(x, "se", th, s2, 16, 1e-14)
+    ref = sst.multivariate_normal(mean=np.zeros(n), cov=C).logpdf(y)
+    assert abs(H.loglik(y) - ref) <= 1e-9 * abs(ref)
+
+
+# ---------------------------------------------------------------- identities ------------
+
+def test_sylvester_identity():
+    """det(I_m + A B) = det(I_n + B A) (Sec. 4), through the oracle's LU."""
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((80, 5)) * 0.3
+    B = rng.standard_normal((5, 80)) * 0.3
+    big, s1 = O.lu_logdet(np.eye(80) + A @ B)
+    small, s2 = O.lu_logdet(np.eye(5) + B @ A)
+    assert s1 == s2 and abs(big - small) < 1e-12
+    ref = np.linalg.slogdet(np.eye(80) + A @ B)
+    assert abs(big - ref[1]) < 1e-12 and s1 == ref[0]
+
+
+def test_smw_identity():
+    """(A + L S R)^-1 b = A^-1 b - A^-1 L (S^-1 + R A^-1 L)^-1 R A^-1 b (Sec. 3.2)."""
+    rng = np.random.default_rng(1)
+    m, r = 60, 4
+    A = np.eye(m) * 3 + rng.standard_normal((m, m)) * 0.1
+    L = rng.standard_normal((m, r))
+    S = np.eye(r) + rng.standard_normal((r, r)) * 0.1
+    R = rng.standard_normal((r, m))
+    b = rng.standard_normal(m)
+    direct = O.lu_solve(A + L @ S @ R, b)
+    Ainv_b = O.lu_solve(A, b)
+    AinvL = np.column_stack([O.lu_solve(A, L[:, k]) for k in range(r)])
+    inner = np.linalg.inv(S) + R @ AinvL
+    smw = Ainv_b - AinvL @ O.lu_solve(inner, R @ Ainv_b)
+    np.testing.assert_allclose(smw, direct, rtol=1e-12, atol=1e-12)
+
+
+def test_lu_negative_determinant_sign():
+    A = np.diag([1.0, -2.0, 3.0])
+    ld, sg = O.lu_logdet(A)
+    assert sg == -1 and abs(ld - np.log(6.0)) < 1e-15
+
+
+# ---------------------------------------------------------------- ordering --------------
+
+def test_tree_order_1d_is_stable_sort():
+    x = I.uniform_points(5000, 1, -1, 1, 3)
+    x[100] = x[200]  # a tie: the lower original index comes first
+    np.testing.assert_array_equal(O.tree_order(x, 32), np.argsort(x[:, 0], kind="stable"))
+
+
+def test_tree_order_2d_kd_invariant():
+    n, leaf = 3000, 20
+    x = I.uniform_points(n, 2, 0, 1, 4)
+    perm = O.tree_order(x, leaf)
+    assert sorted(perm.tolist()) == list(range(n))
+    xs = x[perm]
+    kap = O.kappa(n, leaf)
+
+    def check(b, m, depth):
+        if depth >= kap:
+            return
+        dim = depth % 2
+        ml = m // 2
+        assert xs[b:b + ml, dim].max() <= xs[b + ml:b + m, dim].min()
+        check(b, ml, depth + 1)
+        check(b + ml, m - ml, depth + 1)
+
+    check(0, n, 0)
+
+
+def test_kappa_reading():
+    assert O.kappa(1 << 20, 128) == 13
+    assert O.kappa(4096, 64) == 6
+    assert O.kappa(100, 128) == 0
+    assert O.kappa(129, 128) == 1
+    assert O.kappa(4097, 64) == 7
+
+
+# ---------------------------------------------------------------- compression -----------
+
+@pytest.mark.parametrize("name,rank", [("exp", 1), ("matern32", 2), ("matern52", 3)])
+def test_aca_exact_ranks(name, rank):
+    x, _ = I.workload_1d(4096, 51)
+    H = O.Hodlr(x, name, [0.1, 1.0], 0.01, 64, 1e-12)
+    assert set(H.ranks().tolist()) == {rank}
+
+
+def test_aca_se_error_vs_svd():
+    """ACA block error is at the tolerance's scale and its rank is near the SVD eps-rank."""
+    n, eps = 1024, 1e-10
+    x, _ = I.workload_1d(n, 61)
+    th = [0.3, 1.0]
+    H = O.Hodlr(x, "se", th, 0.1, 64, eps)
+    xs = x[H.perm(), 0]
+    for node in range(3):
+        (bl, ml), (br, mr) = H.node_range(2 * node + 1), H.node_range(2 * node + 2)
+        B = dense_C(xs, "se", th, 0.0)[bl:bl + ml, br:br + mr]
+        U, V = H.node_factors(node)
+        err = np.linalg.norm(B - U @ V.T) / np.linalg.norm(B)
+        assert err <= 100 * eps
+        s = np.linalg.svd(B, compute_uv=False)
+        svd_rank = int(np.sum(s > eps * s[0]))
+        assert svd_rank - 2 <= U.shape[1] <= svd_rank + 4
+
+
+def test_aca_rank_cap_reports():
+    x, _ = I.workload_1d(512, 71)
+    with pytest.raises(O.OracleError):
+        O.Hodlr(x, "se", [0.5, 1.0], 0.1, 16, 1e-14, max_rank=2)
+    H = O.Hodlr(x, "se", [0.5, 1.0], 0.1, 16, 1e-14, max_rank=2, allow_rank_cap=True)
+    assert H.status == 4 and H.ranks().max() == 2
+
+
+# ---------------------------------------------------------------- O2 vs O1 --------------
+
+def rel_residual(x, kern, th, s2, sol, y):
+    C = dense_C(x, kern, th, s2)
+    return np.linalg.norm(C @ sol - y) / np.linalg.norm(y)
+
+
+def test_hodlr_small_se_vs_dense():
+    """The small squared-exponential workload: n=4096, ell=0.5, sigma^2=0.1, leaf 64."""
+    x, y = I.workload_small_se()
+    th, s2 = [0.5, 1.0], 0.1
+    sol_d, ld_d = O.dense_solve(x, "se", th, s2, y)
+    H = O.Hodlr(x, "se", th, s2, 64, 1e-12)
+    sol = H.factor_solve(y)
+    assert abs(H.logdet() - ld_d) <= 1e-10 * abs(ld_d)
+    # ACA meets eps per block; the residual scales as eps |K| |C^-1| (about 1.0e-10 here),
+    # so the 1e-10 residual bar is checked at eps = 3e-13 and eps = 1e-12 gets 2e-10.
+    assert rel_residual(x, "se", th, s2, sol, y) <= 2e-10
+    np.testing.assert_allclose(H.solve(y), sol, rtol=0, atol=1e-12 * np.abs(sol).max())
+    H2 = O.Hodlr(x, "se", th, s2, 64, 3e-13)
+    assert rel_residual(x, "se", th, s2, H2.factor_solve(y), y) <= 1e-10
+
+
+@pytest.mark.parametrize("n,leaf", [(8, 2), (37, 3), (100, 7), (257, 16), (512, 16)])
+@pytest.mark.parametrize("kern", ["exp", "se", "matern32", "matern52"])
+def test_hodlr_brute_force_small(n, leaf, kern):
+    x, y = I.workload_1d(n, 80 + n)
+    th, s2 = [0.3, 1.0], 0.05
+    sol_d, ld_d = O.dense_solve(x, kern, th, s2, y)
+    H = O.Hodlr(x, kern, th, s2, leaf, 1e-14)
+    sol = H.factor_solve(y)
+    assert abs(H.logdet() - ld_d) <= 1e-11 * max(1.0, abs(ld_d))
+    np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-10 * np.abs(sol_d).max())
+
+
+def test_hodlr_2d_vs_dense():
+    n = 1500
+    x, y = I.workload_2d(n, 91)
+    th, s2 = [0.1, 1.0], 0.01
+    sol_d, ld_d = O.dense_solve(x, "se", th, s2, y)
+    H = O.Hodlr(x, "se", th, s2, 32, 1e-12, max_rank=1000)
+    sol = H.factor_solve(y)
+    assert abs(H.logdet() - ld_d) <= 1e-10 * abs(ld_d)
+    assert rel_residual(x, "se", th, s2, sol, y) <= 1e-9
+
+
+def test_hodlr_matvec_matches_dense():
+    n = 800
+    x, y = I.workload_1d(n, 95)
+    th, s2 = [0.2, 1.0], 0.01
+    H = O.Hodlr(x, "matern32", th, s2, 32, 1e-12)
+    C = dense_C(x, "matern32", th, s2)
+    np.testing.assert_allclose(H.matvec(y), C @ y, rtol=0, atol=1e-12 * np.abs(C @ y).max())
+
+
+@pytest.mark.parametrize("leaf", [16, 32, 64, 128])
+def test_leaf_size_invariance(leaf):
+    """Sec. 5.6: the leaf size changes the time, not the result."""
+    x, y = I.workload_1d(2048, 97)
+    th, s2 = [0.25, 1.0], 0.01
+    sol_d, ld_d = O.dense_solve(x, "matern52", th, s2, y)
+    H = O.Hodlr(x, "matern52", th, s2, leaf, 1e-13)
+    sol = H.factor_solve(y)
+    assert abs(H.logdet() - ld_d) <= 1e-11 * abs(ld_d)
+    np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-9 * np.abs(sol_d).max())
+
+
+def test_error_decreases_with_eps():
+    x, y = I.workload_1d(1024, 99)
+    th, s2 = [0.3, 1.0], 0.1
+    _, ld_d = O.dense_solve(x, "se", th, s2, y)
+    errs = []
+    for eps in [1e-4, 1e-7, 1e-10]:
+        H = O.Hodlr(x, "se", th, s2, 32, eps)
+        H.factor()
+        errs.append(abs(H.logdet() - ld_d))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[0] < 1e-1 and errs[2] < 1e-6
+
+
+def test_ou_large_vs_hodlr():
+    """Exponential kernel at n=2^15: O2 against the closed form (independent)."""
+    n = 1 << 15
+    x, y = I.workload_1d(n, 1002)
+    th, s2 = [0.2, 1.0], 1e-2
+    H = O.Hodlr(x, "exp", th, s2, 128, 1e-12)
+    sol = H.factor_solve(y)
+    p = H.perm()
+    sol_c, ld_c = O.ou_closed_form(x[p, 0], th[0], th[1], s2, y[p])
+    assert abs(H.logdet() - ld_c) <= 1e-10 * abs(ld_c)
+    np.testing.assert_allclose(sol[p], sol_c, rtol=0, atol=1e-8 * np.abs(sol_c).max())
+
+
+def test_matern32_large_vs_kalman():
+    n = 1 << 15
+    x, y = I.workload_1d(n, 1003)
+    th, s2 = [0.1, 1.0], 1e-2
+    H = O.Hodlr(x, "matern32", th, s2, 128, 1e-12)
+    sol = H.factor_solve(y)
+    p = H.perm()
+    ldk, q = O.matern_kalman(x[p, 0], 3, th[0], th[1], s2, y[p])
+    assert abs(H.logdet() - ldk) <= 1e-10 * abs(ldk)
+    assert abs(y @ sol - q) <= 1e-9 * abs(q)
