@@ -1,0 +1,325 @@
+"""Benchmark: GP log-likelihood evaluations per second at n = 2^20 on one GB300.
+
+Workload (the paper's 1-D covariance experiments, Sec. 5, in the n = 2^20 form): 2^20
+points uniform on [-1, 1] (seed 1002), y ~ N(0, 1) (seed 1003), sigma^2 = 1e-2, leaf 128,
+eps = 1e-12, nrhs = 1, two kernels: Matern-3/2 with ell = 0.1 and exponential with
+ell = 0.2. One step = one log-likelihood evaluation of each kernel for its hyperparameters
+on the fixed points: recompression (ACA) + factorization with the solve fused + log det +
+y^T C^-1 y. The ordering of the points depends on x only and is done once, outside the
+timed region (as in a hyperparameter sweep). Every result is checked after timing against
+the exact O(n) oracles (Kalman filter, Ornstein-Uhlenbeck closed form) and exact residual
+rows; the accuracy is reported in the JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 1 << 20
+LEAF = 128
+EPS = 1e-12
+SIGMA2 = 1e-2
+KERNELS = [("matern32", 0.1), ("exp", 0.2)]
+SEED = 1002
+METRIC = "GP log-likelihood evals/sec (solve+logdet) at n=2^20, 1 GB300, at 1e-10 rel err"
+FP64_PEAK = 152 * 2 * 2 * 2.07e9  # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
+
+# DRAM bytes (read + write) of one launch of the leaf kernel from the ncu capture summarised
+# in profiles/leaf_kernel_n2p20.md; None until that capture matches the current kernel.
+LEAF_TRAFFIC_BYTES = None
+
+
+def config():
+    return {"workload": "1-D GP, n=2^20 U[-1,1], Matern-3/2 ell=0.1 + exponential ell=0.2, "
+                        "sigma^2=1e-2, leaf 128, eps=1e-12, nrhs=1",
+            "n": N, "leaf": LEAF, "eps": EPS, "sigma2": SIGMA2,
+            "kernels": [f"{k}:ell={e}" for k, e in KERNELS],
+            "evals_per_step": len(KERNELS),
+            "l2": "inputs larger than L2 (1 GB leaf factors + 0.2 GB panels per eval)"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def leaf_flops(ctx_info):
+    """Algorithmic FP64 flops of one leaf-kernel launch: per leaf of p points, Cholesky
+    p^3/3, two triangular solves 2 p^2 W on W = R + nrhs columns, and the level-(kappa-1)
+    partial products 2 p r W. Kernel-function evaluations are not counted."""
+    p = N >> ctx_info["kappa"]
+    W = ctx_info["R"] + 1
+    nleaf = 1 << ctx_info["kappa"]
+    return nleaf * (p ** 3 / 3.0 + 2.0 * p * p * W + 2.0 * p * ctx_info["r_last"] * W)
+
+
+def accuracy(x, y, perm, kern, ell, ll, logdet, sol):
+    """Relative errors against exact O(n) oracles (no HODLR involved)."""
+    import oracle as O
+    xs, ys = x[perm, 0], y[perm]
+    if kern == "exp":
+        sol_c, ld_c = O.ou_closed_form(xs, ell, 1.0, SIGMA2, ys)
+        q_c = float(ys @ sol_c)
+    else:
+        ld_c, q_c = O.matern_kalman(xs, 3, ell, 1.0, SIGMA2, ys)
+    ll_c = -0.5 * q_c - 0.5 * ld_c - 0.5 * N * np.log(2 * np.pi)
+    rows = np.unique(np.linspace(0, N - 1, 32).astype(np.int64))
+    Cx = O.dense_matvec_rows(x, kern, [ell, 1.0], SIGMA2, sol, rows)
+    return {"logdet": abs(logdet - ld_c) / abs(ld_c), "loglik": abs(ll - ll_c) / abs(ll_c),
+            "residual_rows": float(np.abs(Cx - y[rows]).max() / np.abs(y).max())}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1403_6015_gb300 import build_lib
+    from paper_1403_6015_gb300 import hodlr as H
+    from paper_1403_6015_gb300 import inputs as I
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build_lib.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    # replicas: every rank evaluates its own copy of the workload (independent problems)
+    x, y = I.workload_1d(N, SEED + 1000 * rank)
+    xd = torch.from_numpy(x).to(dev)
+    yd = torch.from_numpy(y).to(dev)
+    ctxs = []
+    for kern, ell in KERNELS:
+        ctxs.append(H.Hodlr(xd, kern, [ell, 1.0], SIGMA2, LEAF, EPS, max_rank=16, max_nrhs=1,
+                            stream=stream.cuda_stream))
+    outs = torch.zeros(len(KERNELS), dtype=torch.float64, device=dev)
+
+    def step(leaf_ms=None):
+        for i, (h, (kern, ell)) in enumerate(zip(ctxs, KERNELS)):
+            h.rebuild([ell, 1.0], SIGMA2)
+            h.loglik(yd, out=outs[i:i + 1])
+            if leaf_ms is not None:
+                leaf_ms.append(h.phase_ms()["leaf_kernel"])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = sum(h.counters()["launches"] for h in ctxs)
+    leaf_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(leaf_ms)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = sum(h.counters()["launches"] for h in ctxs) - launches0
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    evals = args.steps * len(KERNELS) * world
+    value = evals / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: pinned y in, host scalar out
+    y_pin = torch.from_numpy(y).pin_memory()
+    y_host = y_pin.numpy()
+    host_out = np.zeros(len(KERNELS))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for i, (h, (kern, ell)) in enumerate(zip(ctxs, KERNELS)):
+            h.rebuild([ell, 1.0], SIGMA2)
+            host_out[i] = h.loglik(y_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = args.steps * len(KERNELS) * world / e2e_s
+
+    # roofline of the dominant kernel (the leaf kernel, FP64-ALU bound)
+    h0 = ctxs[0]
+    ranks = h0.ranks()
+    kappa = h0.tree()[0]
+    R = 0
+    for j in range(kappa):
+        R += int(ranks[(1 << j) - 1:(1 << (j + 1)) - 1].max())
+    r_last = int(ranks[(1 << (kappa - 1)) - 1:].max())
+    info = {"kappa": kappa, "R": R, "r_last": r_last}
+    lm = float(np.mean(leaf_ms[0::len(KERNELS)]))  # Matern-3/2 launches
+    achieved = leaf_flops(info) / (lm / 1e3) / 1e12
+    step_ms = ms / args.steps
+    phases = h0.phase_ms()
+
+    # accuracy (outside the timed region)
+    acc = {}
+    if rank == 0:
+        for i, (h, (kern, ell)) in enumerate(zip(ctxs, KERNELS)):
+            h.rebuild([ell, 1.0], SIGMA2)
+            sol = h.factor_solve(y)
+            ld = h.logdet()
+            _, perm = h.tree()
+            acc[kern] = accuracy(x, y, perm, kern, ell, float(outs[i].item()), ld, sol)
+        acc["host_vs_device_loglik"] = float(np.max(np.abs(host_out - outs.cpu().numpy())))
+    cpu = cpu_baseline(x, y) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded splitmix64 points and N(0,1) right-hand side)",
+            "config": config(),
+            "e2e": {"value": e2e_value, "unit": "evals/s",
+                    "h2d_bytes_per_step": len(KERNELS) * N * 8,
+                    "d2h_bytes_per_step": len(KERNELS) * 8},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK / 1e12,
+                         "unit": "TFLOP/s", "frac": achieved * 1e12 / FP64_PEAK,
+                         "traffic": LEAF_TRAFFIC_BYTES, "kernel": "k_leaf<true> (leaf build + "
+                         "Cholesky + panel solve)", "kernel_ms": lm,
+                         "peak_note": "FP64 derived: 152 SMs x 2 FMA/clk x 2.07 GHz"},
+            "phase_ms": phases,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "accuracy": acc,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(x, y):
+    """The oracle (plain FP64 CPU HODLR, OpenMP over the nodes of a level) on one full step
+    of the same workload: one log-likelihood evaluation of each kernel at n = 2^20."""
+    import oracle as O
+    t0 = time.perf_counter()
+    for kern, ell in KERNELS:
+        O.Hodlr(x, kern, [ell, 1.0], SIGMA2, LEAF, EPS).loglik(y)
+    dt = time.perf_counter() - t0
+    return {"value": len(KERNELS) / dt, "unit": "evals/s", "cores": O.num_threads(),
+            "kind": "oracle", "sample": "one full step: one loglik per kernel at n=2^20 "
+                                        f"({dt:.1f} s)"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm, on rank 0 only; each step is one full-size step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1403_6015_gb300 import inputs as I
+    x, y = I.workload_1d(N, SEED)
+    O.build()
+
+    def step():
+        for kern, ell in KERNELS:
+            O.Hodlr(x, kern, [ell, 1.0], SIGMA2, LEAF, EPS).loglik(y)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = args.steps * len(KERNELS) / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(),
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": O.num_threads(),
+                             "kind": "oracle", "sample": "full workload, every step"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,153 @@
+/*
+ * hodlr.h — C ABI of the GB300 (sm_103a) HODLR Gaussian-process solver.
+ *
+ * The library factors the covariance matrix C = sigma^2 I + K, K_ij = k(x_i, x_j), of a
+ * Gaussian process into the hierarchical product C = K_kappa K_{kappa-1} ... K_1 K_0 of
+ * Ambikasaran et al., "Fast Direct Methods for Gaussian Processes" (arXiv:1403.6015),
+ * Sec. 3.2: K_kappa is block diagonal with the dense leaf blocks of C, and every other
+ * factor is block diagonal with blocks I + [Ut 0; 0 Vt][0 V^T; U^T 0] (low-rank updates of
+ * the identity). From it the library computes C^-1 y (Sherman-Morrison-Woodbury on each
+ * factor, Sec. 3.2), log det C (Sylvester's determinant theorem on each factor, Sec. 4)
+ * and the Gaussian log-likelihood (Sec. 1, Eq. 1).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers to arrays may be host or device (CUDA) pointers; the library asks the CUDA
+ *     runtime which one it was given. Host arrays are copied in and out inside the call,
+ *     and a call that writes a host array returns only after the result is there. Device
+ *     arrays are read and written in stream order on opts.stream and the call may return
+ *     before the GPU is done.
+ *   - Vectors and matrices are FP64. Matrices of right-hand sides and solutions are
+ *     column-major, n rows, nrhs columns, leading dimension ld >= n.
+ *   - y and x are in the caller's point order; the tree permutation is internal.
+ *   - The context owns every buffer it allocates; the caller owns every pointer it passes.
+ *   - Errors are return codes; nothing is thrown across the ABI. hodlr_last_error() gives
+ *     a one-line description of the last failure on that context.
+ *   - Sizes: 1 <= n < 2^31, 1 <= leaf <= 128, d in {1, 2}.
+ */
+#ifndef HODLR_GB300_H
+#define HODLR_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hodlr_ctx hodlr_ctx; /* opaque; owns all device memory of one problem */
+
+typedef enum {
+  HODLR_OK = 0,
+  HODLR_EINVAL = 1,   /* argument out of range or non-finite input */
+  HODLR_ENOMEM = 2,   /* device allocation failed */
+  HODLR_ENOTSPD = 3,  /* a leaf pivot or a factor determinant was not positive */
+  HODLR_ERANK = 4,    /* compression hit opts.max_rank before reaching eps */
+  HODLR_ETIMEOUT = 5, /* a bounded device wait gave up */
+  HODLR_ESTATE = 6,   /* call out of order (e.g. solve before factor) */
+  HODLR_ECUDA = 7     /* a CUDA runtime call failed */
+} hodlr_status;
+
+/* Covariance functions k(r) = a f(r / ell), theta = {ell, a} (Table 1 with a length scale
+ * ell and amplitude a; Matern nu = 3/2 and 5/2 in closed form; nu = 1/2 is HODLR_K_EXP). */
+typedef enum {
+  HODLR_K_EXP = 0,      /* a exp(-r/ell)                              (Ornstein-Uhlenbeck) */
+  HODLR_K_SE = 1,       /* a exp(-r^2/(2 ell^2))                      (Gaussian)           */
+  HODLR_K_MATERN32 = 2, /* a (1 + sqrt3 r/ell) exp(-sqrt3 r/ell)                           */
+  HODLR_K_MATERN52 = 3  /* a (1 + sqrt5 r/ell + 5r^2/(3ell^2)) exp(-sqrt5 r/ell)           */
+} hodlr_kernel;
+
+typedef struct {
+  int precision;       /* 0: FP64 throughout (the only mode in this version)              */
+  int rank_mode;       /* 0: adaptive ACA ranks                                            */
+  int max_rank;        /* cap on the ACA rank of one off-diagonal block (1..64), default 64 */
+  int max_nrhs;        /* right-hand sides carried through a fused factor, default 16     */
+  double refine_tol;   /* reserved (iterative refinement), default 1e-10                  */
+  int refine_maxit;    /* reserved, default 0                                             */
+  void* stream;        /* cudaStream_t for all device work; NULL = legacy default stream  */
+} hodlr_opts;
+
+/* Fill *o with the defaults listed above. */
+void hodlr_default_opts(hodlr_opts* o);
+
+/* Point ordering and compression (paper: the "Assembly" column of Sec. 5).
+ *   x      n points, row-major n x d (host or device). Copied; not kept.
+ *   kernel covariance function; theta = {ell, a} (host pointer, 2 doubles), ell > 0, a > 0.
+ *   sigma2 noise variance on the diagonal (>= 0).
+ *   leaf   largest leaf block; the tree has kappa = ceil(log2(n / leaf)) levels (Sec. 3.2,
+ *          pseudo-code figure, read so that no leaf exceeds `leaf` points).
+ *   eps    ACA tolerance relative to each block's Frobenius norm (Sec. 3.1), > 0.
+ *   o      options (NULL = defaults).
+ * Sorts the points (Sec. 3: split by point count, one dimension at a time), then compresses
+ * every off-diagonal block K[I_left, I_right] ~ U V^T by partial-pivoted adaptive cross
+ * approximation. Synchronises opts.stream once (to size the rank pool).
+ * Errors: EINVAL, ENOMEM, ERANK (rank cap reached; *out is still returned and usable),
+ * ECUDA. On EINVAL/ENOMEM/ECUDA *out is NULL. */
+hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
+                         const double* theta, double sigma2, int leaf, double eps,
+                         const hodlr_opts* o, hodlr_ctx** out);
+
+/* Recompress for new hyperparameters on the same points (the ordering is reused), as in a
+ * hyperparameter sweep (Sec. 2.5). theta as in hodlr_build. Drops any factorization.
+ * Errors: EINVAL, ENOMEM, ERANK, ECUDA. */
+hodlr_status hodlr_rebuild(hodlr_ctx* ctx, const double* theta, double sigma2);
+
+/* Factorization C = K_kappa ... K_0 (Sec. 3.2 and its pseudo-code figure): Cholesky of the
+ * dense leaf blocks, their inverses applied to the ancestors' U/V rows, then level by level
+ * from the finest internal level to the root the 2r x 2r matrices [I, V^T Vt; U^T Ut, I],
+ * their LU factors and log dets. Synchronises once to check pivots.
+ * Errors: ESTATE (already factored), ENOTSPD, ECUDA. */
+hodlr_status hodlr_factor(hodlr_ctx* ctx);
+
+/* Factor as above with nrhs right-hand sides y (n x nrhs, column stride ld) carried through
+ * the same sweep, so that on return x = C^-1 y (the solve fused into the factorization).
+ * nrhs <= opts.max_nrhs. Errors: EINVAL, ESTATE, ENOTSPD, ECUDA. */
+hodlr_status hodlr_factor_solve(hodlr_ctx* ctx, const double* y, double* x, int nrhs,
+                                int64_t ld);
+
+/* x = C^-1 y with the stored factors: C^-1 = K_0^-1 K_1^-1 ... K_kappa^-1 (Sec. 3.2), each
+ * inverse by the Sherman-Morrison-Woodbury formula. y and x may alias.
+ * Errors: ESTATE (not factored), EINVAL, ECUDA. */
+hodlr_status hodlr_solve(hodlr_ctx* ctx, const double* y, double* x, int nrhs, int64_t ld);
+
+/* log det C = sum of the leaf log dets and of log det(I + W L) over all nodes (Sec. 4,
+ * Sylvester's theorem and the product of block determinants), summed in a fixed order.
+ * logdet is a host or device pointer to one double. Errors: ESTATE, ENOTSPD, ECUDA. */
+hodlr_status hodlr_logdet(hodlr_ctx* ctx, double* logdet);
+
+/* Gaussian log-likelihood of y (length n): -y^T C^-1 y / 2 - log det C / 2 - n log(2 pi) / 2
+ * (Sec. 1, Eq. 1, with the normalising constant). If the context is not yet factored the
+ * solve is fused into the factorization. out: host or device pointer to one double.
+ * Errors: ENOTSPD, ECUDA. */
+hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out);
+
+/* Ranks of the 2^kappa - 1 off-diagonal blocks in level order (root first), into a host
+ * array of capacity cap. Returns the number of blocks via *count. Errors: EINVAL. */
+hodlr_status hodlr_ranks(hodlr_ctx* ctx, int32_t* ranks, int64_t cap, int64_t* count);
+
+/* Number of tree levels kappa, and the point permutation (sorted row i holds point
+ * perm[i]) into a host array of n int64. Either output may be NULL. */
+hodlr_status hodlr_tree(hodlr_ctx* ctx, int* kappa, int64_t* perm);
+
+/* C~ x with the compressed operator (dense leaves + U V^T blocks), x and y of length n. */
+hodlr_status hodlr_matvec(hodlr_ctx* ctx, const double* x, double* y);
+
+/* Device time in milliseconds (CUDA events on opts.stream) of the last calls, into a host
+ * array of 6 floats: out[0] ordering, out[1] compression, out[2] factorization (all of
+ * it), out[3] last standalone solve, out[4] the leaf kernel of the last factorization,
+ * out[5] the level sweep and log det of the last factorization. */
+hodlr_status hodlr_phase_ms(hodlr_ctx* ctx, float* out6);
+
+/* Counters since hodlr_build, into a host array of 2 int64: out[0] CUDA kernels this
+ * context launched, out[1] host synchronisations it performed. */
+hodlr_status hodlr_counters(hodlr_ctx* ctx, int64_t* out2);
+
+const char* hodlr_last_error(const hodlr_ctx* ctx);
+const char* hodlr_status_string(hodlr_status s);
+
+/* Frees all device memory of the context. NULL is ignored. */
+void hodlr_destroy(hodlr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HODLR_GB300_H */

@@ -44,41 +44,48 @@ int oracle_num_threads(void) {
  * Covariance functions. k(r) = a f(r / ell), r the Euclidean distance (Table 1 with a
  * length scale ell and amplitude a; Matern nu = 3/2 and 5/2 in their closed forms).
  * ---------------------------------------------------------------------------------- */
-static double orc_kernel_r2(int kind, double r2, double ell, double amp) {
+/* r is the distance, r2 its square (both passed so neither is recomputed from the other). */
+static double orc_kernel(int kind, double r, double r2, double ell, double amp) {
   switch (kind) {
-    case ORC_EXP: return amp * exp(-sqrt(r2) / ell);
+    case ORC_EXP: return amp * exp(-r / ell);
     case ORC_SE: return amp * exp(-0.5 * r2 / (ell * ell));
     case ORC_M32: {
-      double s = sqrt(3.0) * sqrt(r2) / ell;
+      double s = sqrt(3.0) * r / ell;
       return amp * (1.0 + s) * exp(-s);
     }
     case ORC_M52: {
-      double s = sqrt(5.0) * sqrt(r2) / ell;
+      double s = sqrt(5.0) * r / ell;
       return amp * (1.0 + s + s * s / 3.0) * exp(-s);
     }
   }
   return NAN;
 }
 
-static double orc_r2(const double* x, int d, int64_t i, int64_t j) {
+/* k(x_i, x_j): in 1-D r = |x_i - x_j|, otherwise r = sqrt(sum of squared differences). */
+static double orc_kij(const double* x, int d, int kind, double ell, double amp, int64_t i,
+                      int64_t j) {
+  if (d == 1) {
+    double r = fabs(x[i] - x[j]);
+    return orc_kernel(kind, r, r * r, ell, amp);
+  }
   double s = 0.0;
   for (int c = 0; c < d; ++c) {
     double t = x[i * d + c] - x[j * d + c];
     s += t * t;
   }
-  return s;
+  return orc_kernel(kind, sqrt(s), s, ell, amp);
 }
 
 /* Entry of C = sigma^2 I + K (Sec. 5, C_ij = sigma^2 delta_ij + k(r_i, r_j)). */
 static double orc_entry(const double* x, int d, int kind, double ell, double amp, double sigma2,
                         int64_t i, int64_t j) {
-  double v = orc_kernel_r2(kind, orc_r2(x, d, i, j), ell, amp);
+  double v = orc_kij(x, d, kind, ell, amp, i, j);
   return i == j ? v + sigma2 : v;
 }
 
 void oracle_kernel_values(int kind, const double* r, int64_t m, double ell, double amp,
                           double* out) {
-  for (int64_t i = 0; i < m; ++i) out[i] = orc_kernel_r2(kind, r[i] * r[i], ell, amp);
+  for (int64_t i = 0; i < m; ++i) out[i] = orc_kernel(kind, r[i], r[i] * r[i], ell, amp);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -509,7 +516,7 @@ static int orc_aca(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int64
   *ok = 0;
   while (k < rmax) {
     for (int64_t b = 0; b < mr; ++b) {
-      double v = orc_kernel_r2(H->kind, orc_r2(H->xs, H->d, bl + i, br + b), H->ell, H->amp);
+      double v = orc_kij(H->xs, H->d, H->kind, H->ell, H->amp, bl + i, br + b);
       for (int l = 0; l < k; ++l) v -= U[l * ml + i] * V[l * mr + b];
       row[b] = v;
     }
@@ -529,7 +536,7 @@ static int orc_aca(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int64
     }
     for (int64_t b = 0; b < mr; ++b) row[b] /= delta;
     for (int64_t a = 0; a < ml; ++a) {
-      double u = orc_kernel_r2(H->kind, orc_r2(H->xs, H->d, bl + a, br + j), H->ell, H->amp);
+      double u = orc_kij(H->xs, H->d, H->kind, H->ell, H->amp, bl + a, br + j);
       for (int l = 0; l < k; ++l) u -= U[l * ml + a] * V[l * mr + j];
       col[a] = u;
     }

@@ -1,0 +1,431 @@
+// Level-batched adaptive cross approximation (Sec. 3.1: partial-pivoted LU of each
+// off-diagonal block, O(r m) work per block, with the Frobenius-norm estimate as the
+// sub-sampled error check). Every internal node of every level advances together, one
+// cross step per four launches:
+//   A  residual row    R(i,:) = B(i,:) - sum_l u_l(i) v_l        (tile of columns per CTA)
+//   B  pivot column    j = argmax |R(i,:)| (lowest index on ties), delta = R(i,j)
+//   C  residual column u = B(:,j) - sum_l u_l v_l(j), v = R(i,:) / delta, tile dots
+//   D  norm update     |S_k|^2 += 2 sum_l (u_l.u)(v_l.v) + |u|^2 |v|^2; stop (dropping the
+//                      term) when |u||v| <= eps |S_k|; next row = argmax over unused rows
+// The block B = K[I_left, I_right] of node id lives in one column of the level's raw panel:
+// rows of the left child hold u, rows of the right child hold v. All reductions use fixed
+// orders, so results are deterministic.
+#include <cuda_runtime.h>
+
+#include "hodlr_internal.cuh"
+
+namespace hodlr {
+namespace {
+
+constexpr int kAcaThreads = 256;
+constexpr int kPer = kAcaTile / kAcaThreads;  // elements per thread
+
+struct AcaArgs {
+  Pts pts;
+  Cov cov;
+  double eps;
+  const int32_t* nb;   // node begin
+  const int32_t* ns;   // node size
+  const int32_t* item_node;
+  const int32_t* item_start;
+  const int32_t* node_item0;
+  double* raw;
+  int64_t raw_off[32];
+  int32_t *rank, *row, *col, *done, *ok, *zero, *phase, *nused, *used;
+  int used_stride;
+  double *delta, *s2, *part;
+  int part_stride;
+  int max_rank;
+  int32_t* active;
+  int nint;
+};
+
+__device__ __forceinline__ int level_of(int id) { return 31 - __clz(id + 1); }
+
+__device__ __forceinline__ int rmax_of(const AcaArgs& a, int id) {
+  int ml = a.ns[2 * id + 1], mr = a.ns[2 * id + 2];
+  int m = ml < mr ? ml : mr;
+  return m < a.max_rank ? m : a.max_rank;
+}
+
+// Argmax of |v| with the lowest index on ties (idx < 0 means empty).
+__device__ __forceinline__ void amax_merge(double& bv, int& bi, double v, int i) {
+  if (i < 0) return;
+  double av = fabs(v), ab = fabs(bv);
+  if (bi < 0 || av > ab || (av == ab && i < bi)) {
+    bv = v;
+    bi = i;
+  }
+}
+
+__device__ __forceinline__ void warp_amax(double& bv, int& bi) {
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    amax_merge(bv, bi, ov, oi);
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_aca_init(AcaArgs a) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= a.nint) return;
+  a.rank[id] = 0;
+  a.row[id] = 0;
+  a.col[id] = 0;
+  a.done[id] = rmax_of(a, id) <= 0;
+  a.ok[id] = 0;
+  a.zero[id] = 0;
+  a.phase[id] = 0;
+  a.nused[id] = 0;
+  a.s2[id] = 0.0;
+  a.delta[id] = 0.0;
+}
+
+// A: residual row of the current pivot row, stored unnormalised in column k of the V rows.
+__global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
+  int item = blockIdx.x;
+  int id = a.item_node[item];
+  if (a.done[id]) return;
+  __shared__ double uik[kMaxRank];
+  __shared__ double wv[kAcaThreads / 32];
+  __shared__ int wi[kAcaThreads / 32];
+  int k = a.rank[id], i = a.row[id];
+  int bl = a.nb[2 * id + 1], br = a.nb[2 * id + 2], mr = a.ns[2 * id + 2];
+  int64_t n = a.pts.n;
+  double* raw = a.raw + a.raw_off[level_of(id)];
+  if (threadIdx.x < k) uik[threadIdx.x] = raw[threadIdx.x * n + bl + i];
+  __syncthreads();
+  int start = a.item_start[item];
+  double bv = 0.0;
+  int bi = -1;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    int b = start + q * kAcaThreads + threadIdx.x;
+    if (b < mr) {
+      double v = cov_r(a.cov, dist(a.pts, bl + i, br + b));
+      for (int l = 0; l < k; ++l) v -= uik[l] * raw[l * n + br + b];
+      raw[(int64_t)k * n + br + b] = v;
+      amax_merge(bv, bi, v, b);
+    }
+  }
+  warp_amax(bv, bi);
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    wv[w] = bv;
+    wi[w] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double fv = 0.0;
+    int fi = -1;
+    for (int q = 0; q < kAcaThreads / 32; ++q) amax_merge(fv, fi, wv[q], wi[q]);
+    a.part[(int64_t)item * a.part_stride + 0] = fv;
+    a.part[(int64_t)item * a.part_stride + 1] = (double)fi;
+  }
+}
+
+// B: one warp per node picks the pivot column (or handles an all-zero residual row).
+__global__ void k_aca_pivot_row(AcaArgs a) {
+  int id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (id >= a.nint || a.done[id]) return;
+  int i0 = a.node_item0[id], i1 = a.node_item0[id + 1];
+  double bv = 0.0;
+  int bi = -1;
+  for (int it = i0 + lane; it < i1; it += 32) {
+    const double* p = a.part + (int64_t)it * a.part_stride;
+    amax_merge(bv, bi, p[0], (int)p[1]);
+  }
+  warp_amax(bv, bi);
+  if (lane != 0) return;
+  int i = a.row[id];
+  int* used = a.used + (int64_t)id * a.used_stride;
+  int nu = a.nused[id];
+  used[nu++] = i;
+  a.nused[id] = nu;
+  if (bi < 0 || bv == 0.0) {
+    a.phase[id] = 0;
+    int rmax = rmax_of(a, id);
+    if (++a.zero[id] > rmax) {
+      a.done[id] = 1;
+      a.ok[id] = 1;
+      return;
+    }
+    int ml = a.ns[2 * id + 1];
+    int nx = -1;
+    for (int r = 0; r < ml && nx < 0; ++r) {
+      bool u = false;
+      for (int q = 0; q < nu; ++q) u |= used[q] == r;
+      if (!u) nx = r;
+    }
+    if (nx < 0) {
+      a.done[id] = 1;
+      a.ok[id] = 1;
+      return;
+    }
+    a.row[id] = nx;
+    return;
+  }
+  a.col[id] = bi;
+  a.delta[id] = bv;
+  a.phase[id] = 1;
+}
+
+// C: residual column u (stored in column k of the U rows), normalised row v, and this tile's
+// contributions to |u|^2, |v|^2, u_l.u, v_l.v and argmax over unused rows of |u|.
+__global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
+  int item = blockIdx.x;
+  int id = a.item_node[item];
+  if (a.done[id] || !a.phase[id]) return;
+  __shared__ double vjk[kMaxRank];
+  __shared__ int used[2 * kMaxRank + 2];
+  __shared__ double red[2 * kMaxRank + 2][kAcaThreads / 32];
+  __shared__ double wv[kAcaThreads / 32];
+  __shared__ int wi[kAcaThreads / 32];
+  int k = a.rank[id], j = a.col[id];
+  double delta = a.delta[id];
+  int bl = a.nb[2 * id + 1], ml = a.ns[2 * id + 1];
+  int br = a.nb[2 * id + 2], mr = a.ns[2 * id + 2];
+  int nu = a.nused[id];
+  int64_t n = a.pts.n;
+  double* raw = a.raw + a.raw_off[level_of(id)];
+  if (threadIdx.x < k) vjk[threadIdx.x] = raw[threadIdx.x * n + br + j];
+  for (int q = threadIdx.x; q < nu; q += kAcaThreads) used[q] = a.used[(int64_t)id * a.used_stride + q];
+  __syncthreads();
+  int start = a.item_start[item];
+  double uu[kPer], vv[kPer];
+  double nu2 = 0.0, nv2 = 0.0, bv = 0.0;
+  int bi = -1;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    int t = start + q * kAcaThreads + threadIdx.x;
+    uu[q] = 0.0;
+    vv[q] = 0.0;
+    if (t < ml) {
+      double u = cov_r(a.cov, dist(a.pts, bl + t, br + j));
+      for (int l = 0; l < k; ++l) u -= raw[l * n + bl + t] * vjk[l];
+      raw[(int64_t)k * n + bl + t] = u;
+      uu[q] = u;
+      nu2 += u * u;
+      bool isu = false;
+      for (int s = 0; s < nu; ++s) isu |= used[s] == t;
+      if (!isu) amax_merge(bv, bi, u, t);
+    }
+    if (t < mr) {
+      double v = raw[(int64_t)k * n + br + t] / delta;
+      raw[(int64_t)k * n + br + t] = v;
+      vv[q] = v;
+      nv2 += v * v;
+    }
+  }
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  nu2 = warp_sum(nu2);
+  nv2 = warp_sum(nv2);
+  warp_amax(bv, bi);
+  if (lane == 0) {
+    red[0][w] = nu2;
+    red[1][w] = nv2;
+    wv[w] = bv;
+    wi[w] = bi;
+  }
+  for (int l = 0; l < k; ++l) {
+    double du = 0.0, dv = 0.0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      int t = start + q * kAcaThreads + threadIdx.x;
+      if (t < ml) du += raw[l * n + bl + t] * uu[q];
+      if (t < mr) dv += raw[l * n + br + t] * vv[q];
+    }
+    du = warp_sum(du);
+    dv = warp_sum(dv);
+    if (lane == 0) {
+      red[2 + l][w] = du;
+      red[2 + kMaxRank + l][w] = dv;
+    }
+  }
+  __syncthreads();
+  double* out = a.part + (int64_t)item * a.part_stride;
+  int nval = 2 + 2 * kMaxRank;
+  for (int e = threadIdx.x; e < nval; e += kAcaThreads) {
+    bool live = e < 2 || (e - 2 < k) || (e >= 2 + kMaxRank && e - 2 - kMaxRank < k);
+    if (!live) continue;
+    double s = 0.0;
+    for (int q = 0; q < kAcaThreads / 32; ++q) s += red[e][q];
+    // layout: [0] argmax value, [1] argmax index, [2] |u|^2, [3] |v|^2, [4..] u_l.u, v_l.v
+    if (e == 0) out[2] = s;
+    else if (e == 1) out[3] = s;
+    else if (e < 2 + kMaxRank) out[4 + (e - 2)] = s;
+    else out[4 + a.max_rank + (e - 2 - kMaxRank)] = s;
+  }
+  if (threadIdx.x == 0) {
+    double fv = 0.0;
+    int fi = -1;
+    for (int q = 0; q < kAcaThreads / 32; ++q) amax_merge(fv, fi, wv[q], wi[q]);
+    out[0] = fv;
+    out[1] = (double)fi;
+  }
+}
+
+// D: one warp per node combines the tiles, updates the norm estimate and decides.
+__global__ void k_aca_pivot_col(AcaArgs a) {
+  int id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (id >= a.nint || a.done[id]) return;
+  if (!a.phase[id]) {
+    if (lane == 0) atomicAdd(a.active, 1);
+    return;
+  }
+  int k = a.rank[id];
+  int i0 = a.node_item0[id], i1 = a.node_item0[id + 1];
+  double bv = 0.0, nu2 = 0.0, nv2 = 0.0;
+  int bi = -1;
+  for (int it = i0 + lane; it < i1; it += 32) {
+    const double* p = a.part + (int64_t)it * a.part_stride;
+    amax_merge(bv, bi, p[0], (int)p[1]);
+    nu2 += p[2];
+    nv2 += p[3];
+  }
+  warp_amax(bv, bi);
+  nu2 = warp_sum(nu2);
+  nv2 = warp_sum(nv2);
+  double cross = 0.0;
+  for (int l = 0; l < k; ++l) {
+    double du = 0.0, dv = 0.0;
+    for (int it = i0 + lane; it < i1; it += 32) {
+      const double* p = a.part + (int64_t)it * a.part_stride;
+      du += p[4 + l];
+      dv += p[4 + a.max_rank + l];
+    }
+    du = warp_sum(du);
+    dv = warp_sum(dv);
+    cross += du * dv;
+  }
+  if (lane != 0) return;
+  double s2 = a.s2[id] + 2.0 * cross + nu2 * nv2;
+  a.s2[id] = s2;
+  if (sqrt(nu2 * nv2) <= a.eps * sqrt(s2)) {
+    a.done[id] = 1;
+    a.ok[id] = 1;
+    return;
+  }
+  int r = k + 1;
+  a.rank[id] = r;
+  if (bi < 0) {
+    a.done[id] = 1;
+    a.ok[id] = 1;
+    return;
+  }
+  a.row[id] = bi;
+  int rmax = rmax_of(a, id);
+  if (r >= rmax) {
+    int ml = a.ns[2 * id + 1], mr = a.ns[2 * id + 2];
+    a.done[id] = 1;
+    a.ok[id] = rmax == (ml < mr ? ml : mr);
+    return;
+  }
+  atomicAdd(a.active, 1);
+}
+
+// Compact panels: level j's columns [coff_j, coff_j + r_j) of phi and pan take the node's
+// first rank columns of the raw panel and zeros beyond (zero columns leave every product
+// of the factorization unchanged).
+struct PackArgs {
+  const double* raw;
+  int64_t raw_off[32];
+  int coff[33];
+  int rl[32];
+  const int32_t* nb;
+  const int32_t* rank;
+  double* phi;
+  double* pan;
+  int64_t n;
+};
+
+__global__ void k_pack(PackArgs p) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int j = blockIdx.y;
+  if (i >= p.n) return;
+  int id = 0;
+  for (int l = 0; l < j; ++l) id = i < p.nb[2 * id + 2] ? 2 * id + 1 : 2 * id + 2;
+  int r = p.rank[id];
+  const double* src = p.raw + p.raw_off[j];
+  for (int c = 0; c < p.rl[j]; ++c) {
+    double v = c < r ? src[c * p.n + i] : 0.0;
+    int64_t o = (int64_t)(p.coff[j] + c) * p.n + i;
+    p.phi[o] = v;
+    p.pan[o] = v;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_aca(Ctx& c, int* steps_out) {
+  int nint = (1 << c.kappa) - 1;
+  *steps_out = 0;
+  if (nint == 0) return cudaSuccess;
+  AcaArgs a;
+  a.pts = Pts{c.xs, c.n, c.d};
+  a.cov = Cov{c.kind, 1.0 / c.ell, c.amp};
+  a.eps = c.eps;
+  a.nb = c.nodes;
+  a.ns = c.nodes + ((int64_t)2 << c.kappa);
+  a.item_node = c.item_node;
+  a.item_start = c.item_start;
+  a.node_item0 = c.node_item0;
+  a.raw = c.raw;
+  for (int j = 0; j < 32; ++j) a.raw_off[j] = j < c.kappa ? c.h_raw_off[j] : 0;
+  a.rank = c.st_rank; a.row = c.st_row; a.col = c.st_col; a.done = c.st_done; a.ok = c.st_ok;
+  a.zero = c.st_zero; a.phase = c.st_phase; a.nused = c.st_nused; a.used = c.st_used;
+  a.used_stride = 2 * c.max_rank + 2;
+  a.delta = c.st_delta; a.s2 = c.st_s2; a.part = c.aca_part;
+  a.part_stride = 4 + 2 * c.max_rank;
+  a.max_rank = c.max_rank;
+  a.active = c.active;
+  a.nint = nint;
+  k_aca_init<<<(nint + 255) / 256, 256, 0, c.stream>>>(a);
+  ++c.launches;
+  int wblocks = (nint * 32 + 255) / 256;
+  int max_steps = 2 * c.max_rank + 4;
+  for (int s = 0; s < max_steps; ++s) {
+    HODLR_CUDA_TRY(cudaMemsetAsync(c.active, 0, sizeof(int32_t), c.stream));
+    k_aca_row<<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
+    k_aca_pivot_row<<<wblocks, 256, 0, c.stream>>>(a);
+    k_aca_col<<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
+    k_aca_pivot_col<<<wblocks, 256, 0, c.stream>>>(a);
+    c.launches += 4;
+    HODLR_CUDA_TRY(cudaGetLastError());
+    HODLR_CUDA_TRY(cudaMemcpyAsync(c.h_active, c.active, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    HODLR_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    ++c.syncs;
+    *steps_out = s + 1;
+    if (*c.h_active == 0) break;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_pack(Ctx& c) {
+  if (c.kappa == 0 || c.R == 0) return cudaSuccess;
+  PackArgs p;
+  p.raw = c.raw;
+  for (int j = 0; j < 32; ++j) {
+    p.raw_off[j] = j < c.kappa ? c.h_raw_off[j] : 0;
+    p.rl[j] = j < c.kappa ? c.h_rl[j] : 0;
+  }
+  for (int j = 0; j < 33; ++j) p.coff[j] = j <= c.kappa ? c.h_coff[j] : 0;
+  p.nb = c.nodes;
+  p.rank = c.rank_dev;
+  p.phi = c.phi;
+  p.pan = c.pan;
+  p.n = c.n;
+  dim3 g((unsigned)((c.n + 255) / 256), (unsigned)c.kappa);
+  k_pack<<<g, 256, 0, c.stream>>>(p);
+  ++c.launches;
+  return cudaGetLastError();
+}
+
+}  // namespace hodlr

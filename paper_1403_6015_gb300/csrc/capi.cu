@@ -1,0 +1,612 @@
+// C ABI of the GB300 HODLR library (declared in include/hodlr.h): argument checks, the tree
+// of index ranges, device allocation, and the order of the kernel launches for build,
+// factor, solve, log det and log-likelihood.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "hodlr_internal.cuh"
+
+using hodlr::Ctx;
+
+namespace {
+
+hodlr_status fail(Ctx* c, hodlr_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+hodlr_status cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+  cudaGetLastError();
+  return fail(c, e == cudaErrorMemoryAllocation ? HODLR_ENOMEM : HODLR_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define TRY_CUDA(c, expr, where)                         \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, where); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) return cudaSuccess;
+  return cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+int kappa_for(int64_t n, int leaf) {
+  int k = 0;
+  while (((int64_t)leaf << k) < n) ++k;
+  return k;
+}
+
+__global__ void k_check_finite(const double* x, int64_t m, int32_t* flag) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m && !isfinite(x[i])) atomicOr(flag, 1);
+}
+
+void free_factor_buffers(Ctx* c) {
+  dfree(c->phi); dfree(c->pan); dfree(c->part); dfree(c->part2); dfree(c->half); dfree(c->Z);
+  dfree(c->rank_dev);
+  c->R_cap = 0;
+}
+
+void free_all(Ctx* c) {
+  free_factor_buffers(c);
+  dfree(c->nodes); dfree(c->xs); dfree(c->perm);
+  dfree(c->item_node); dfree(c->item_start); dfree(c->node_item0); dfree(c->raw);
+  dfree(c->st_rank); dfree(c->st_row); dfree(c->st_col); dfree(c->st_done); dfree(c->st_ok);
+  dfree(c->st_zero); dfree(c->st_phase); dfree(c->st_nused); dfree(c->st_used);
+  dfree(c->st_delta); dfree(c->st_s2); dfree(c->aca_part); dfree(c->active);
+  dfree(c->Y); dfree(c->ysort); dfree(c->leafL); dfree(c->leaf_logdet); dfree(c->node_logdet);
+  dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->Mlu); dfree(c->Mpiv);
+  if (c->h_active) cudaFreeHost(c->h_active);
+  c->h_active = nullptr;
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+}
+
+// Tree of index ranges (Sec. 3): node (j, k) has id 2^j - 1 + k, left child gets the first
+// floor(m/2) points. Begins in [0, 2^(kappa+1)), sizes in [2^(kappa+1), 2^(kappa+2)).
+void build_tree(Ctx* c) {
+  int64_t tot = (int64_t)2 << c->kappa;
+  c->h_nodes.assign((size_t)(2 * tot), 0);
+  int32_t* nb = c->h_nodes.data();
+  int32_t* ns = nb + tot;
+  nb[0] = 0;
+  ns[0] = (int32_t)c->n;
+  for (int64_t id = 0; id < ((int64_t)1 << c->kappa) - 1; ++id) {
+    int32_t m = ns[id], ml = m / 2;
+    nb[2 * id + 1] = nb[id];
+    ns[2 * id + 1] = ml;
+    nb[2 * id + 2] = nb[id] + ml;
+    ns[2 * id + 2] = m - ml;
+  }
+  int mx = 0;
+  for (int64_t k = 0; k < ((int64_t)1 << c->kappa); ++k)
+    mx = std::max(mx, ns[((int64_t)1 << c->kappa) - 1 + k]);
+  c->max_leaf_size = mx;
+}
+
+hodlr_status setup_aca(Ctx* c) {
+  int K = c->kappa;
+  int nint = (1 << K) - 1;
+  if (nint == 0) return HODLR_OK;
+  const int32_t* nb = c->h_nodes.data();
+  const int32_t* ns = nb + ((int64_t)2 << K);
+  std::vector<int32_t> inode, istart, i0(nint + 1);
+  for (int id = 0; id < nint; ++id) {
+    i0[id] = (int32_t)inode.size();
+    int32_t m = std::max(ns[2 * id + 1], ns[2 * id + 2]);
+    for (int32_t s = 0; s < m; s += hodlr::kAcaTile) {
+      inode.push_back(id);
+      istart.push_back(s);
+    }
+  }
+  i0[nint] = (int32_t)inode.size();
+  c->n_items = (int64_t)inode.size();
+  c->h_raw_off.assign(K, 0);
+  c->h_rcap.assign(K, 0);
+  int64_t off = 0;
+  for (int j = 0; j < K; ++j) {
+    int64_t half = (c->n + ((int64_t)2 << j) - 1) >> (j + 1);
+    c->h_rcap[j] = (int)std::min<int64_t>(c->max_rank, half);
+    c->h_raw_off[j] = off;
+    off += c->n * c->h_rcap[j];
+  }
+  c->raw_elems = off;
+  int us = 2 * c->max_rank + 2;
+  TRY_CUDA(c, dalloc(&c->item_node, c->n_items), "alloc items");
+  TRY_CUDA(c, dalloc(&c->item_start, c->n_items), "alloc items");
+  TRY_CUDA(c, dalloc(&c->node_item0, nint + 1), "alloc items");
+  TRY_CUDA(c, dalloc(&c->raw, c->raw_elems), "alloc raw panel");
+  TRY_CUDA(c, dalloc(&c->st_rank, nint), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->st_row, nint), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->st_col, nint), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->st_done, nint), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->st_ok, nint), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->st_zero, nint), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->st_phase, nint), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->st_nused, nint), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->st_used, (int64_t)nint * us), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->st_delta, nint), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->st_s2, nint), "alloc aca state");
+  TRY_CUDA(c, dalloc(&c->aca_part, c->n_items * (4 + 2 * c->max_rank)), "alloc aca partials");
+  TRY_CUDA(c, cudaMemcpyAsync(c->item_node, inode.data(), 4 * inode.size(), cudaMemcpyHostToDevice, c->stream), "upload");
+  TRY_CUDA(c, cudaMemcpyAsync(c->item_start, istart.data(), 4 * istart.size(), cudaMemcpyHostToDevice, c->stream), "upload");
+  TRY_CUDA(c, cudaMemcpyAsync(c->node_item0, i0.data(), 4 * i0.size(), cudaMemcpyHostToDevice, c->stream), "upload");
+  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "upload");
+  ++c->syncs;
+  return HODLR_OK;
+}
+
+// Compression of all off-diagonal blocks, then the rank-padded compact panels.
+hodlr_status compress(Ctx* c) {
+  int K = c->kappa;
+  int nint = (1 << K) - 1;
+  c->compressed = false;
+  c->factored = false;
+  c->rank_capped = false;
+  cudaEventRecord(c->ev[2], c->stream);
+  int steps = 0;
+  TRY_CUDA(c, hodlr::launch_aca(*c, &steps), "aca");
+  c->h_rank.assign(nint, 0);
+  std::vector<int32_t> ok(nint, 1);
+  if (nint > 0) {
+    TRY_CUDA(c, cudaMemcpyAsync(c->h_rank.data(), c->st_rank, 4 * (size_t)nint, cudaMemcpyDeviceToHost, c->stream), "ranks");
+    TRY_CUDA(c, cudaMemcpyAsync(ok.data(), c->st_ok, 4 * (size_t)nint, cudaMemcpyDeviceToHost, c->stream), "ranks");
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream), "ranks");
+  ++c->syncs;
+  }
+  for (int id = 0; id < nint; ++id)
+    if (!ok[id]) c->rank_capped = true;
+  c->h_rl.assign(K, 0);
+  c->h_coff.assign(K + 1, 0);
+  for (int j = 0; j < K; ++j) {
+    int mx = 0;
+    for (int k = 0; k < (1 << j); ++k) mx = std::max(mx, c->h_rank[(1 << j) - 1 + k]);
+    c->h_rl[j] = mx;
+    c->h_coff[j + 1] = c->h_coff[j] + mx;
+  }
+  c->R = c->h_coff[K];
+  // sizes that depend on the ranks
+  int64_t nleaf = (int64_t)1 << K;
+  int rmax_level = 0;
+  for (int j = 0; j < K; ++j) rmax_level = std::max(rmax_level, c->h_rl[j]);
+  int64_t pstride = std::max<int64_t>(1, (int64_t)rmax_level * (c->R + c->max_nrhs));
+  pstride = std::max<int64_t>(pstride, c->R);  // the matvec stores R partials per leaf
+  int64_t zel = 1, hel = 1, mlu = 0, piv = 0;
+  c->h_mlu_off.assign(K, 0);
+  c->h_piv_off.assign(K, 0);
+  for (int j = 0; j < K; ++j) {
+    int r = c->h_rl[j];
+    zel = std::max<int64_t>(zel, ((int64_t)1 << j) * 2 * r * (c->h_coff[j] + c->max_nrhs));
+    zel = std::max<int64_t>(zel, ((int64_t)2 << j) * c->R);
+    c->h_mlu_off[j] = mlu;
+    c->h_piv_off[j] = piv;
+    mlu += ((int64_t)1 << j) * 4 * r * r;
+    piv += ((int64_t)1 << j) * 2 * r;
+    hel += ((int64_t)2 << j) * r;
+  }
+  hel = std::max<int64_t>(hel, (nleaf + 1) * pstride);
+  bool realloc = c->R_cap < c->R || !c->part || c->part_stride < pstride || c->z_elems < zel ||
+                 c->half_elems < hel;
+  if (realloc) {
+    free_factor_buffers(c);
+    int64_t Rc = std::max<int64_t>(c->R, 1);
+    TRY_CUDA(c, dalloc(&c->phi, c->n * Rc), "alloc panels");
+    TRY_CUDA(c, dalloc(&c->pan, c->n * Rc), "alloc panels");
+    TRY_CUDA(c, dalloc(&c->part, nleaf * pstride), "alloc partials");
+    TRY_CUDA(c, dalloc(&c->part2, std::max<int64_t>(nleaf / 64 + 1, 8) * pstride + 4096), "alloc partials");
+    TRY_CUDA(c, dalloc(&c->half, hel), "alloc partials");
+    TRY_CUDA(c, dalloc(&c->Z, zel), "alloc Z");
+    TRY_CUDA(c, dalloc(&c->rank_dev, std::max(nint, 1)), "alloc ranks");
+    c->R_cap = Rc;
+    c->part_stride = pstride;
+    c->z_elems = zel;
+    c->half_elems = hel;
+  }
+  if (c->mlu_cap < mlu || c->piv_cap < piv) {
+    dfree(c->Mlu);
+    dfree(c->Mpiv);
+    TRY_CUDA(c, dalloc(&c->Mlu, std::max<int64_t>(mlu, 1)), "alloc node LU");
+    TRY_CUDA(c, dalloc(&c->Mpiv, std::max<int64_t>(piv, 1)), "alloc node LU");
+    c->mlu_cap = std::max<int64_t>(mlu, 1);
+    c->piv_cap = std::max<int64_t>(piv, 1);
+  }
+  // the panels keep their own copy of the ranks
+  if (nint > 0)
+    TRY_CUDA(c, cudaMemcpyAsync(c->rank_dev, c->st_rank, 4 * (size_t)nint, cudaMemcpyDeviceToDevice, c->stream), "ranks");
+  TRY_CUDA(c, hodlr::launch_pack(*c), "pack");
+  cudaEventRecord(c->ev[3], c->stream);
+  c->compressed = true;
+  return HODLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hodlr_default_opts(hodlr_opts* o) {
+  if (!o) return;
+  o->precision = 0;
+  o->rank_mode = 0;
+  o->max_rank = hodlr::kMaxRank;
+  o->max_nrhs = 16;
+  o->refine_tol = 1e-10;
+  o->refine_maxit = 0;
+  o->stream = nullptr;
+}
+
+const char* hodlr_status_string(hodlr_status s) {
+  switch (s) {
+    case HODLR_OK: return "OK";
+    case HODLR_EINVAL: return "EINVAL";
+    case HODLR_ENOMEM: return "ENOMEM";
+    case HODLR_ENOTSPD: return "ENOTSPD";
+    case HODLR_ERANK: return "ERANK";
+    case HODLR_ETIMEOUT: return "ETIMEOUT";
+    case HODLR_ESTATE: return "ESTATE";
+    case HODLR_ECUDA: return "ECUDA";
+  }
+  return "UNKNOWN";
+}
+
+const char* hodlr_last_error(const hodlr_ctx* ctx) {
+  const Ctx* c = reinterpret_cast<const Ctx*>(ctx);
+  return c ? c->last_error.c_str() : "null context";
+}
+
+void hodlr_destroy(hodlr_ctx* ctx) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_all(c);
+  delete c;
+}
+
+static bool bad_theta(const double* th) {
+  return !th || !std::isfinite(th[0]) || !std::isfinite(th[1]) || !(th[0] > 0) || !(th[1] > 0);
+}
+
+hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
+                         const double* theta, double sigma2, int leaf, double eps,
+                         const hodlr_opts* o, hodlr_ctx** out) {
+  if (!out) return HODLR_EINVAL;
+  *out = nullptr;
+  hodlr_opts opts;
+  hodlr_default_opts(&opts);
+  if (o) opts = *o;
+  if (!x || n < 1 || n >= ((int64_t)1 << 31) || (d != 1 && d != 2) || leaf < 1 ||
+      leaf > hodlr::kMaxLeaf || !(eps > 0) || !std::isfinite(eps) || !(sigma2 >= 0) ||
+      !std::isfinite(sigma2) || bad_theta(theta) || (int)kernel < 0 || (int)kernel > 3 ||
+      opts.max_rank < 1 || opts.max_rank > hodlr::kMaxRank || opts.max_nrhs < 1 ||
+      opts.precision != 0)
+    return HODLR_EINVAL;
+  Ctx* c = new (std::nothrow) Ctx;
+  if (!c) return HODLR_ENOMEM;
+  c->n = n;
+  c->d = d;
+  c->kind = (int)kernel;
+  c->ell = theta[0];
+  c->amp = theta[1];
+  c->sigma2 = sigma2;
+  c->eps = eps;
+  c->leaf = leaf;
+  c->max_rank = opts.max_rank;
+  c->max_nrhs = opts.max_nrhs;
+  c->stream = (cudaStream_t)opts.stream;
+  c->kappa = kappa_for(n, leaf);
+  auto bail = [&](hodlr_status s) {
+    free_all(c);
+    delete c;
+    return s;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return bail(HODLR_ECUDA);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return bail(HODLR_ECUDA);
+  build_tree(c);
+  int64_t tot = (int64_t)2 << c->kappa;
+  int64_t nleaf = (int64_t)1 << c->kappa;
+  if (dalloc(&c->nodes, 2 * tot) || dalloc(&c->xs, n * d) || dalloc(&c->perm, n) ||
+      dalloc(&c->dflags, 4) || dalloc(&c->scal, 8) || dalloc(&c->active, 1) ||
+      dalloc(&c->Y, n * c->max_nrhs) || dalloc(&c->ysort, n) || dalloc(&c->tmpvec, n * c->max_nrhs) ||
+      dalloc(&c->leaf_logdet, nleaf) || dalloc(&c->node_logdet, std::max<int64_t>(nleaf - 1, 1)) ||
+      dalloc(&c->leafL, nleaf * hodlr::kMaxLeaf * hodlr::kMaxLeaf) ||
+      cudaMallocHost(&c->h_active, sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(HODLR_ENOMEM);
+  }
+  cudaMemcpyAsync(c->nodes, c->h_nodes.data(), 4 * c->h_nodes.size(), cudaMemcpyHostToDevice, c->stream);
+  // points on the device (row-major n x d), finiteness check
+  const double* xd = x;
+  double* xtmp = nullptr;
+  if (!is_device_ptr(x)) {
+    if (dalloc(&xtmp, n * d) != cudaSuccess) return bail(HODLR_ENOMEM);
+    cudaMemcpyAsync(xtmp, x, sizeof(double) * n * d, cudaMemcpyHostToDevice, c->stream);
+    xd = xtmp;
+  }
+  cudaMemsetAsync(c->dflags, 0, 4, c->stream);
+  k_check_finite<<<(unsigned)((n * d + 255) / 256), 256, 0, c->stream>>>(xd, n * d, c->dflags);
+  ++c->launches;
+  int32_t fl = 0;
+  cudaMemcpyAsync(&fl, c->dflags, 4, cudaMemcpyDeviceToHost, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    dfree(xtmp);
+    return bail(HODLR_ECUDA);
+  }
+  if (fl) {
+    dfree(xtmp);
+    return bail(HODLR_EINVAL);
+  }
+  cudaEventRecord(c->ev[0], c->stream);
+  cudaError_t e = d == 1 ? hodlr::launch_sort_1d(*c, xd) : hodlr::launch_sort_kd(*c, xd);
+  cudaEventRecord(c->ev[1], c->stream);
+  cudaStreamSynchronize(c->stream);
+  dfree(xtmp);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bail(e == cudaErrorMemoryAllocation ? HODLR_ENOMEM : HODLR_ECUDA);
+  }
+  hodlr_status s = setup_aca(c);
+  if (s != HODLR_OK) return bail(s);
+  s = compress(c);
+  if (s != HODLR_OK) return bail(s);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(HODLR_ECUDA);
+  cudaEventElapsedTime(&c->phase_ms[0], c->ev[0], c->ev[1]);
+  cudaEventElapsedTime(&c->phase_ms[1], c->ev[2], c->ev[3]);
+  *out = reinterpret_cast<hodlr_ctx*>(c);
+  if (c->rank_capped) {
+    c->last_error = "ACA reached max_rank before eps in at least one block";
+    return HODLR_ERANK;
+  }
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_rebuild(hodlr_ctx* ctx, const double* theta, double sigma2) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  if (bad_theta(theta) || !(sigma2 >= 0) || !std::isfinite(sigma2))
+    return fail(c, HODLR_EINVAL, "rebuild: bad theta or sigma2");
+  c->ell = theta[0];
+  c->amp = theta[1];
+  c->sigma2 = sigma2;
+  hodlr_status s = compress(c);
+  if (s != HODLR_OK) return s;
+  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "rebuild");
+  ++c->syncs;
+  cudaEventElapsedTime(&c->phase_ms[1], c->ev[2], c->ev[3]);
+  if (c->rank_capped) return fail(c, HODLR_ERANK, "ACA reached max_rank before eps in at least one block");
+  return HODLR_OK;
+}
+
+// Stage a (possibly host) n x nrhs column-major input; returns a device pointer and its ld.
+static hodlr_status stage_in(Ctx* c, const double* y, int nrhs, int64_t ld, const double** yd,
+                             int64_t* ldd) {
+  if (is_device_ptr(y)) {
+    *yd = y;
+    *ldd = ld;
+    return HODLR_OK;
+  }
+  TRY_CUDA(c, cudaMemcpy2DAsync(c->tmpvec, sizeof(double) * c->n, y, sizeof(double) * ld,
+                                sizeof(double) * c->n, nrhs, cudaMemcpyHostToDevice, c->stream),
+           "copy y");
+  *yd = c->tmpvec;
+  *ldd = c->n;
+  return HODLR_OK;
+}
+
+static hodlr_status write_out(Ctx* c, double* x, int nrhs, int64_t ld) {
+  if (is_device_ptr(x)) {
+    TRY_CUDA(c, hodlr::launch_scatter_rhs(*c, x, ld, nrhs), "scatter");
+    return HODLR_OK;
+  }
+  TRY_CUDA(c, hodlr::launch_scatter_rhs(*c, c->tmpvec, c->n, nrhs), "scatter");
+  TRY_CUDA(c, cudaMemcpy2DAsync(x, sizeof(double) * ld, c->tmpvec, sizeof(double) * c->n,
+                                sizeof(double) * c->n, nrhs, cudaMemcpyDeviceToHost, c->stream),
+           "copy x");
+  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "copy x");
+  ++c->syncs;
+  return HODLR_OK;
+}
+
+static hodlr_status check_flags(Ctx* c) {
+  int32_t fl = 0;
+  TRY_CUDA(c, cudaMemcpyAsync(&fl, c->dflags, 4, cudaMemcpyDeviceToHost, c->stream), "flags");
+  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "flags");
+  ++c->syncs;
+  if (fl & hodlr::kFlagNotSpd) {
+    c->factored = false;
+    return fail(c, HODLR_ENOTSPD, "a leaf pivot or node determinant was not positive");
+  }
+  return HODLR_OK;
+}
+
+// Factor with nrhs right-hand sides already gathered into c->Y (nrhs may be 0).
+static hodlr_status factor_impl(Ctx* c, int nrhs) {
+  if (!c->compressed) return fail(c, HODLR_ESTATE, "not compressed");
+  if (c->factored) return fail(c, HODLR_ESTATE, "already factored (rebuild first)");
+  c->solve_timed = false;
+  cudaEventRecord(c->ev[4], c->stream);
+  if (c->R > 0 && c->kappa > 0) {
+    // the working panel starts from the original U/V (a previous factor modified it)
+    TRY_CUDA(c, cudaMemcpyAsync(c->pan, c->phi, sizeof(double) * c->n * c->R, cudaMemcpyDeviceToDevice, c->stream), "panel");
+  }
+  TRY_CUDA(c, cudaMemsetAsync(c->dflags, 0, 4, c->stream), "flags");
+  cudaEventRecord(c->ev[6], c->stream);
+  TRY_CUDA(c, hodlr::launch_leaf_factor(*c, nrhs), "leaf factor");
+  cudaEventRecord(c->ev[7], c->stream);
+  TRY_CUDA(c, hodlr::launch_levels(*c, nrhs, true), "levels");
+  TRY_CUDA(c, hodlr::launch_logdet_sum(*c), "logdet");
+  cudaEventRecord(c->ev[5], c->stream);
+  c->factored = true;
+  c->nrhs_fused = nrhs;
+  hodlr_status s = check_flags(c);
+  cudaEventElapsedTime(&c->phase_ms[2], c->ev[4], c->ev[5]);
+  cudaEventElapsedTime(&c->phase_ms[4], c->ev[6], c->ev[7]);
+  cudaEventElapsedTime(&c->phase_ms[5], c->ev[7], c->ev[5]);
+  return s;
+}
+
+hodlr_status hodlr_factor(hodlr_ctx* ctx) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  return factor_impl(c, 0);
+}
+
+hodlr_status hodlr_factor_solve(hodlr_ctx* ctx, const double* y, double* x, int nrhs,
+                                int64_t ld) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  if (!y || !x || nrhs < 1 || nrhs > c->max_nrhs || ld < c->n)
+    return fail(c, HODLR_EINVAL, "factor_solve: bad y/x/nrhs/ld");
+  if (c->factored) return fail(c, HODLR_ESTATE, "already factored (rebuild first)");
+  const double* yd;
+  int64_t ldd;
+  hodlr_status s = stage_in(c, y, nrhs, ld, &yd, &ldd);
+  if (s != HODLR_OK) return s;
+  TRY_CUDA(c, hodlr::launch_gather_rhs(*c, yd, ldd, nrhs), "gather");
+  s = factor_impl(c, nrhs);
+  if (s != HODLR_OK) return s;
+  return write_out(c, x, nrhs, ld);
+}
+
+hodlr_status hodlr_solve(hodlr_ctx* ctx, const double* y, double* x, int nrhs, int64_t ld) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  if (!c->factored) return fail(c, HODLR_ESTATE, "solve before factor");
+  if (!y || !x || nrhs < 1 || ld < c->n) return fail(c, HODLR_EINVAL, "solve: bad y/x/nrhs/ld");
+  for (int c0 = 0; c0 < nrhs; c0 += c->max_nrhs) {
+    int nb = std::min(c->max_nrhs, nrhs - c0);
+    const double* yd;
+    int64_t ldd;
+    hodlr_status s = stage_in(c, y + (int64_t)c0 * ld, nb, ld, &yd, &ldd);
+    if (s != HODLR_OK) return s;
+    cudaEventRecord(c->ev[4], c->stream);
+    TRY_CUDA(c, hodlr::launch_gather_rhs(*c, yd, ldd, nb), "gather");
+    TRY_CUDA(c, hodlr::launch_leaf_solve(*c, nb), "leaf solve");
+    TRY_CUDA(c, hodlr::launch_levels(*c, nb, false), "levels");
+    cudaEventRecord(c->ev[5], c->stream);
+    c->solve_timed = true;
+    s = write_out(c, x + (int64_t)c0 * ld, nb, ld);
+    if (s != HODLR_OK) return s;
+  }
+  return HODLR_OK;
+}
+
+static hodlr_status write_scalar(Ctx* c, const double* src, double* out) {
+  if (is_device_ptr(out)) {
+    TRY_CUDA(c, cudaMemcpyAsync(out, src, sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "out");
+    return HODLR_OK;
+  }
+  TRY_CUDA(c, cudaMemcpyAsync(out, src, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "out");
+  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "out");
+  ++c->syncs;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_logdet(hodlr_ctx* ctx, double* logdet) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !logdet) return HODLR_EINVAL;
+  if (!c->factored) return fail(c, HODLR_ESTATE, "logdet before factor");
+  return write_scalar(c, c->scal, logdet);
+}
+
+hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !y || !out) return HODLR_EINVAL;
+  const double* yd;
+  int64_t ldd;
+  hodlr_status s = stage_in(c, y, 1, c->n, &yd, &ldd);
+  if (s != HODLR_OK) return s;
+  TRY_CUDA(c, hodlr::launch_gather_rhs(*c, yd, ldd, 1), "gather");
+  if (!c->factored) {
+    s = factor_impl(c, 1);
+    if (s != HODLR_OK) return s;
+  } else {
+    TRY_CUDA(c, hodlr::launch_leaf_solve(*c, 1), "leaf solve");
+    TRY_CUDA(c, hodlr::launch_levels(*c, 1, false), "levels");
+  }
+  TRY_CUDA(c, hodlr::launch_quad_loglik(*c), "loglik");
+  return write_scalar(c, c->scal + 2, out);
+}
+
+hodlr_status hodlr_ranks(hodlr_ctx* ctx, int32_t* ranks, int64_t cap, int64_t* count) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  int64_t m = (int64_t)c->h_rank.size();
+  if (count) *count = m;
+  if (ranks)
+    for (int64_t i = 0; i < m && i < cap; ++i) ranks[i] = c->h_rank[i];
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_tree(hodlr_ctx* ctx, int* kappa, int64_t* perm) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  if (kappa) *kappa = c->kappa;
+  if (perm) {
+    std::vector<int32_t> p(c->n);
+    TRY_CUDA(c, cudaMemcpyAsync(p.data(), c->perm, 4 * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream), "perm");
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream), "perm");
+  ++c->syncs;
+    for (int64_t i = 0; i < c->n; ++i) perm[i] = p[i];
+  }
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_matvec(hodlr_ctx* ctx, const double* x, double* y) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !x || !y) return HODLR_EINVAL;
+  if (!c->compressed) return fail(c, HODLR_ESTATE, "matvec before build");
+  const double* xd;
+  int64_t ldd;
+  hodlr_status s = stage_in(c, x, 1, c->n, &xd, &ldd);
+  if (s != HODLR_OK) return s;
+  // sorted x into ysort, product into Y[:, 0], then back to caller order
+  TRY_CUDA(c, hodlr::launch_gather_rhs(*c, xd, ldd, 1), "gather");
+  TRY_CUDA(c, cudaMemcpyAsync(c->ysort, c->Y, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  TRY_CUDA(c, hodlr::launch_matvec(*c, c->ysort, c->Y), "matvec");
+  return write_out(c, y, 1, c->n);
+}
+
+hodlr_status hodlr_phase_ms(hodlr_ctx* ctx, float* out6) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !out6) return HODLR_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  if (c->solve_timed) cudaEventElapsedTime(&c->phase_ms[3], c->ev[4], c->ev[5]);
+  for (int i = 0; i < 6; ++i) out6[i] = c->phase_ms[i];
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_counters(hodlr_ctx* ctx, int64_t* out2) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !out2) return HODLR_EINVAL;
+  out2[0] = c->launches;
+  out2[1] = c->syncs;
+  return HODLR_OK;
+}
+
+}  // extern "C"

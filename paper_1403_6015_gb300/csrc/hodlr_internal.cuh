@@ -1,0 +1,185 @@
+// Internal declarations of the GB300 HODLR library: the problem context, the covariance
+// functions evaluated on the device, and the host-side launch wrappers of every kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/hodlr.h"
+
+namespace hodlr {
+
+constexpr int kMaxLeaf = 128;      // leaf blocks live in shared memory
+constexpr int kMaxRank = 64;       // per-block rank cap (2r x 2r node matrices in smem)
+constexpr int kAcaTile = 1024;     // columns (rows) of one ACA work item
+
+// ---------------------------------------------------------------------------------------
+// Covariance functions (Table 1 with length scale ell and amplitude a; Matern nu = 3/2 and
+// 5/2 in closed form). r is the Euclidean distance between the two points.
+// ---------------------------------------------------------------------------------------
+struct Cov {
+  int kind;
+  double inv_ell;
+  double amp;
+};
+
+__device__ __forceinline__ double cov_r(const Cov& c, double r) {
+  switch (c.kind) {
+    case HODLR_K_EXP:
+      return c.amp * exp(-r * c.inv_ell);
+    case HODLR_K_SE: {
+      double t = r * c.inv_ell;
+      return c.amp * exp(-0.5 * t * t);
+    }
+    case HODLR_K_MATERN32: {
+      double s = 1.7320508075688772 * r * c.inv_ell;  // sqrt(3) r / ell
+      return c.amp * (1.0 + s) * exp(-s);
+    }
+    default: {
+      double s = 2.23606797749979 * r * c.inv_ell;  // sqrt(5) r / ell
+      return c.amp * (1.0 + s + s * s * (1.0 / 3.0)) * exp(-s);
+    }
+  }
+}
+
+// Sorted points in structure-of-arrays form: coordinate c of sorted point i is x[c * n + i].
+struct Pts {
+  const double* x;
+  int64_t n;
+  int d;
+};
+
+__device__ __forceinline__ double dist(const Pts& p, int i, int j) {
+  if (p.d == 1) return fabs(p.x[i] - p.x[j]);
+  double a = p.x[i] - p.x[j];
+  double b = p.x[p.n + i] - p.x[p.n + j];
+  return sqrt(a * a + b * b);
+}
+
+// Device error word bits (ctx->dflags).
+enum : int { kFlagNotSpd = 1, kFlagRankCap = 2, kFlagTimeout = 4 };
+
+// ---------------------------------------------------------------------------------------
+// Context: everything one problem owns on the device. Layouts (n rows, column stride n):
+//   xs       d x n sorted coordinates (SoA)
+//   perm     n int32: sorted row i is the caller's point perm[i]
+//   nodes    2^(kappa+1) int32: begin row of node id (level order, root = 0) and nodes[last]=n
+//   raw      per level j: n x rcap_j ACA columns (U rows in left children, V in right)
+//   phi      n x R   original U/V of every level, level j at columns [coff_j, coff_j + r_j)
+//   pan      n x R   working copy; after factor it holds Ut/Vt (finer inverses applied)
+//   Y        n x max_nrhs right-hand sides in sorted order (overwritten by C^-1 y)
+//   leafL    2^kappa x 128 x 128 Cholesky factors of the leaf blocks (row-major, lower)
+// ---------------------------------------------------------------------------------------
+struct Ctx {
+  // problem
+  int64_t n = 0;
+  int d = 1;
+  int kind = 0;
+  double ell = 1, amp = 1, sigma2 = 0, eps = 1e-12;
+  int leaf = 128, kappa = 0, max_rank = kMaxRank, max_nrhs = 16;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 152;
+
+  // tree (host mirror + device)
+  std::vector<int32_t> h_nodes;   // begin rows, 2^(kappa+1) entries (+1 sentinel)
+  int32_t* nodes = nullptr;
+  double* xs = nullptr;
+  int32_t* perm = nullptr;
+  int max_leaf_size = 0;
+
+  // ACA work decomposition (host-built, device copies)
+  int64_t n_items = 0;
+  int32_t* item_node = nullptr;   // internal node id of each work item
+  int32_t* item_start = nullptr;  // first row/column of the item's tile
+  int32_t* node_item0 = nullptr;  // first item of each internal node (nint + 1 entries)
+  std::vector<int64_t> h_raw_off; // offset (in doubles) of level j's raw panel
+  std::vector<int> h_rcap;        // raw columns of level j
+  double* raw = nullptr;
+  int64_t raw_elems = 0;
+
+  // ACA state, one entry per internal node
+  int32_t* st_rank = nullptr;
+  int32_t* st_row = nullptr;
+  int32_t* st_col = nullptr;
+  int32_t* st_done = nullptr;
+  int32_t* st_ok = nullptr;
+  int32_t* st_zero = nullptr;
+  int32_t* st_phase = nullptr;
+  int32_t* st_nused = nullptr;
+  int32_t* st_used = nullptr;     // nint x (2 max_rank + 2)
+  double* st_delta = nullptr;
+  double* st_s2 = nullptr;
+  double* aca_part = nullptr;     // n_items x (4 + 2 max_rank)
+  int32_t* active = nullptr;      // device counter
+  int32_t* h_active = nullptr;    // pinned host mirror
+
+  // compact factor panels
+  std::vector<int32_t> h_rank;    // per internal node
+  std::vector<int> h_rl;          // per-level padded rank r_j
+  std::vector<int> h_coff;        // column offset of level j (kappa + 1 entries)
+  int R = 0;
+  int64_t R_cap = 0;
+  double* phi = nullptr;
+  double* pan = nullptr;
+  int32_t* rank_dev = nullptr;
+
+  // factorization
+  double* Y = nullptr;            // n x max_nrhs
+  double* ysort = nullptr;        // copy of the first rhs (sorted) for the quadratic form
+  double* leafL = nullptr;
+  double* leaf_logdet = nullptr;  // 2^kappa
+  double* node_logdet = nullptr;  // 2^kappa - 1
+  double* Mlu = nullptr;          // level j at h_mlu_off[j]: (2 r_j)^2 per node
+  int32_t* Mpiv = nullptr;        // level j at h_piv_off[j]: 2 r_j per node
+  std::vector<int64_t> h_mlu_off, h_piv_off;
+  int64_t mlu_cap = 0, piv_cap = 0;
+  double* part = nullptr;         // leaf partial products, 2^kappa x part_stride
+  int64_t part_stride = 0;
+  double* part2 = nullptr;        // first-stage segment sums
+  double* half = nullptr;         // per half-node sums (2^(j+1) x part_stride)
+  double* Z = nullptr;            // scratch of the current level: 2 r_j x wz_j per node
+  int64_t z_elems = 0;
+  int64_t half_elems = 0;
+  double* scal = nullptr;         // [0] logdet, [1] quad, [2] loglik
+  int32_t* dflags = nullptr;
+  double* tmpvec = nullptr;       // n x max_nrhs staging for host/device copies
+
+  bool compressed = false;
+  bool factored = false;
+  int nrhs_fused = 0;
+  bool rank_capped = false;
+
+  cudaEvent_t ev[8] = {};
+  float phase_ms[6] = {0, 0, 0, 0, 0, 0};
+  int64_t launches = 0;   // kernels launched by this context
+  int64_t syncs = 0;      // host synchronisations
+  bool solve_timed = false;
+  std::string last_error;
+};
+
+// Launch wrappers (each .cu file defines its own); all are stream-ordered on ctx.stream.
+cudaError_t launch_sort_1d(Ctx& c, const double* x_dev_rowmajor);
+cudaError_t launch_sort_kd(Ctx& c, const double* x_dev_rowmajor);
+cudaError_t launch_aca(Ctx& c, int* steps_out);
+cudaError_t launch_pack(Ctx& c);
+cudaError_t launch_gather_rhs(Ctx& c, const double* y, int64_t ld, int nrhs);
+cudaError_t launch_scatter_rhs(Ctx& c, double* x, int64_t ld, int nrhs);
+cudaError_t launch_leaf_factor(Ctx& c, int nrhs);
+cudaError_t launch_leaf_solve(Ctx& c, int nrhs);
+cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode);
+cudaError_t launch_logdet_sum(Ctx& c);
+cudaError_t launch_quad_loglik(Ctx& c);
+cudaError_t launch_matvec(Ctx& c, const double* xin_sorted, double* yout_sorted);
+
+}  // namespace hodlr
+
+#define HODLR_CUDA_TRY(expr)                  \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return _e;         \
+  } while (0)

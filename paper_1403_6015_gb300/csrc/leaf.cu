@@ -1,0 +1,241 @@
+// Leaf stage of the factorization (Sec. 3.2: factoring K_kappa, the block diagonal of dense
+// leaf blocks, out of C applies each leaf inverse to the rows of every ancestor's U/V that
+// lie in the leaf; Sec. 4: the leaf determinants enter log det C).
+//
+// One CTA per leaf, 256 threads, the leaf block in shared memory (row-major, stride 129):
+//   factor mode: build C[I_leaf, I_leaf] from the sorted points (sigma^2 on the diagonal),
+//                Cholesky-factor it in place (right-looking), store L, log det = 2 sum log L_ii;
+//   solve mode:  load the stored L.
+// Then every panel column (the ancestors' U/V rows in factor mode, and the right-hand sides)
+// is solved with L L^T by one warp (lanes own rows lane + 32 m), and the warp also forms the
+// level-(kappa-1) partial products Phi_{kappa-1}^T x of the leaf's rows.
+#include <cuda_runtime.h>
+
+#include "hodlr_internal.cuh"
+
+namespace hodlr {
+namespace {
+
+constexpr int kLeafThreads = 256;
+constexpr int kLD = kMaxLeaf + 1;
+
+struct LeafArgs {
+  Pts pts;
+  Cov cov;
+  double sigma2;
+  const int32_t* nb;
+  const int32_t* ns;
+  int leaf0;          // node id of leaf 0
+  int kappa;
+  double* pan;        // n x R working panel (factor mode: cP = R columns processed)
+  int cP;             // panel columns to solve
+  double* Y;          // n x nrhs right-hand sides (sorted order)
+  int nrhs;
+  const double* phi;  // originals, for the partial of level kappa-1
+  int coff;           // column offset of level kappa-1 in phi
+  int rl;             // r_{kappa-1}
+  double* part;       // partial products, leaf-major
+  int64_t part_stride;
+  double* leafL;
+  double* leaf_logdet;
+  int32_t* flags;
+  int64_t n;
+};
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Solve L L^T x = b for one column held by a warp: element i in lane i % 32, slot i / 32.
+__device__ __forceinline__ void warp_chol_solve(const double* __restrict__ A, int p, int lane,
+                                                double (&x)[4]) {
+  // forward: L z = b
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    for (int kk = 0; kk < 32; ++kk) {
+      int k = s * 32 + kk;
+      if (k >= p) break;
+      double zk = __shfl_sync(0xffffffffu, x[s], kk) / A[k * kLD + k];
+      if (lane == kk) x[s] = zk;
+#pragma unroll
+      for (int m = s; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i > k && i < p) x[m] -= A[i * kLD + k] * zk;
+      }
+    }
+  }
+  // backward: L^T x = z
+#pragma unroll
+  for (int s = 3; s >= 0; --s) {
+    for (int kk = 31; kk >= 0; --kk) {
+      int k = s * 32 + kk;
+      if (k >= p) continue;
+      double xk = __shfl_sync(0xffffffffu, x[s], kk) / A[k * kLD + k];
+      if (lane == kk) x[s] = xk;
+#pragma unroll
+      for (int m = 0; m <= s; ++m) {
+        int i = m * 32 + lane;
+        if (i < k) x[m] -= A[k * kLD + i] * xk;
+      }
+    }
+  }
+}
+
+template <bool kFactor>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
+  extern __shared__ double A[];  // [kMaxLeaf][kLD]
+  __shared__ double xl[2 * kMaxLeaf];
+  __shared__ double red[kLeafThreads / 32];
+  __shared__ int bad;
+  int leaf = blockIdx.x;
+  int id = a.leaf0 + leaf;
+  int b = a.nb[id], p = a.ns[id];
+  int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  double* Lout = a.leafL + (int64_t)leaf * kMaxLeaf * kMaxLeaf;
+  if (kFactor) {
+    if (tid == 0) bad = 0;
+    for (int i = tid; i < p; i += kLeafThreads) {
+      xl[i] = a.pts.x[b + i];
+      if (a.pts.d == 2) xl[kMaxLeaf + i] = a.pts.x[a.pts.n + b + i];
+    }
+    __syncthreads();
+    for (int e = tid; e < p * p; e += kLeafThreads) {
+      int i = e / p, j = e - i * p;
+      if (j > i) continue;
+      double r;
+      if (a.pts.d == 1) {
+        r = fabs(xl[i] - xl[j]);
+      } else {
+        double u = xl[i] - xl[j], v = xl[kMaxLeaf + i] - xl[kMaxLeaf + j];
+        r = sqrt(u * u + v * v);
+      }
+      double c = cov_r(a.cov, r);
+      if (i == j) c += a.sigma2;
+      A[i * kLD + j] = c;
+    }
+    __syncthreads();
+    // right-looking Cholesky, column k per step
+    for (int k = 0; k < p; ++k) {
+      if (tid == 0) {
+        double dkk = A[k * kLD + k];
+        if (!(dkk > 0.0)) {
+          bad = 1;
+          dkk = 1.0;
+        }
+        A[k * kLD + k] = sqrt(dkk);
+      }
+      __syncthreads();
+      double inv = 1.0 / A[k * kLD + k];
+      for (int i = k + 1 + tid; i < p; i += kLeafThreads) A[i * kLD + k] *= inv;
+      __syncthreads();
+      for (int j = k + 1 + w; j < p; j += kLeafThreads / 32) {
+        double ljk = A[j * kLD + k];
+        for (int i = j + lane; i < p; i += 32) A[i * kLD + j] -= A[i * kLD + k] * ljk;
+      }
+      __syncthreads();
+    }
+    // store L (lower triangle, row-major, stride kMaxLeaf)
+    for (int e = tid; e < p * p; e += kLeafThreads) {
+      int i = e / p, j = e - i * p;
+      if (j <= i) Lout[i * kMaxLeaf + j] = A[i * kLD + j];
+    }
+    // log det = 2 sum log L_ii, fixed order
+    double s = 0.0;
+    for (int i = tid; i < p; i += kLeafThreads) s += log(A[i * kLD + i]);
+    s = wsum(s);
+    if (lane == 0) red[w] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int q = 0; q < kLeafThreads / 32; ++q) t += red[q];
+      a.leaf_logdet[leaf] = 2.0 * t;
+      if (bad) atomicOr(a.flags, kFlagNotSpd);
+    }
+  } else {
+    for (int e = tid; e < p * p; e += kLeafThreads) {
+      int i = e / p, j = e - i * p;
+      if (j <= i) A[i * kLD + j] = Lout[i * kMaxLeaf + j];
+    }
+    __syncthreads();
+  }
+  // columns: panel [0, cP) then right-hand sides [0, nrhs)
+  int ncol = a.cP + a.nrhs;
+  int wtot = ncol;  // partial row width
+  for (int c = w; c < ncol; c += kLeafThreads / 32) {
+    double* col = c < a.cP ? a.pan + (int64_t)c * a.n + b : a.Y + (int64_t)(c - a.cP) * a.n + b;
+    double x[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int i = m * 32 + lane;
+      x[m] = i < p ? col[i] : 0.0;
+    }
+    warp_chol_solve(A, p, lane, x);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int i = m * 32 + lane;
+      if (i < p) col[i] = x[m];
+    }
+    if (a.kappa > 0) {
+      double* out = a.part + (int64_t)leaf * a.part_stride;
+      for (int r = 0; r < a.rl; ++r) {
+        const double* ph = a.phi + (int64_t)(a.coff + r) * a.n + b;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          int i = m * 32 + lane;
+          if (i < p) s += ph[i] * x[m];
+        }
+        s = wsum(s);
+        if (lane == 0) out[r * wtot + c] = s;
+      }
+    }
+  }
+}
+
+LeafArgs make_args(Ctx& c, int nrhs, bool factor) {
+  LeafArgs a;
+  a.pts = Pts{c.xs, c.n, c.d};
+  a.cov = Cov{c.kind, 1.0 / c.ell, c.amp};
+  a.sigma2 = c.sigma2;
+  a.nb = c.nodes;
+  a.ns = c.nodes + ((int64_t)2 << c.kappa);
+  a.leaf0 = (1 << c.kappa) - 1;
+  a.kappa = c.kappa;
+  a.pan = c.pan;
+  a.cP = factor ? c.R : 0;
+  a.Y = c.Y;
+  a.nrhs = nrhs;
+  a.phi = c.phi;
+  a.coff = c.kappa > 0 ? c.h_coff[c.kappa - 1] : 0;
+  a.rl = c.kappa > 0 ? c.h_rl[c.kappa - 1] : 0;
+  a.part = c.part;
+  a.part_stride = c.part_stride;
+  a.leafL = c.leafL;
+  a.leaf_logdet = c.leaf_logdet;
+  a.flags = c.dflags;
+  a.n = c.n;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_factor(Ctx& c, int nrhs) {
+  LeafArgs a = make_args(c, nrhs, true);
+  size_t smem = sizeof(double) * kMaxLeaf * kLD;
+  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_leaf<true><<<1u << c.kappa, kLeafThreads, smem, c.stream>>>(a);
+  ++c.launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_solve(Ctx& c, int nrhs) {
+  LeafArgs a = make_args(c, nrhs, false);
+  size_t smem = sizeof(double) * kMaxLeaf * kLD;
+  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_leaf<false><<<1u << c.kappa, kLeafThreads, smem, c.stream>>>(a);
+  ++c.launches;
+  return cudaGetLastError();
+}
+
+}  // namespace hodlr

@@ -1,0 +1,527 @@
+// Level-by-level factorization and solve (Sec. 3.2): for j = kappa-1 down to 0, every node
+// of level j forms M = [I, V^T Vt; U^T Ut, I] (I + W L in the Sherman-Morrison-Woodbury
+// formula with L = blockdiag(Ut, Vt), W = [0 V^T; U^T 0]), LU-factors it (log det by
+// Sylvester's theorem, Sec. 4), and applies (I + L W)^-1 = I - L M^-1 W to every coarser
+// ancestor's U/V rows and to the right-hand sides on its rows:
+//   Z = M^-1 [V^T P_R; U^T P_L],  P_L -= Ut Z_top,  P_R -= Vt Z_bot.
+//
+// Work is expressed over leaf row tiles so all levels have the same parallelism:
+//   per-leaf partials  Phi_j[leaf]^T Q[leaf]       (written by the previous sweep step)
+//   k_segsum           fixed-order sums over each node half
+//   k_node             M, LU, log det, Z per node
+//   k_sweep            update of level u on each leaf fused with the partials of level u-1
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "hodlr_internal.cuh"
+
+namespace hodlr {
+namespace {
+
+constexpr int kSweepThreads = 256;
+constexpr int kSegChunk = 64;
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// out[g * stride + e] = sum_{t < h} in[(g h + t) * stride + e], e < E, fixed order.
+__global__ void k_segsum(const double* __restrict__ in, int64_t stride, int E, int h,
+                         double* __restrict__ out) {
+  int g = blockIdx.x;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    const double* p = in + (int64_t)g * h * stride + e;
+    double s = 0.0;
+    for (int t = 0; t < h; ++t) s += p[(int64_t)t * stride];
+    out[(int64_t)g * stride + e] = s;
+  }
+}
+
+cudaError_t segsum(const double* in, int64_t stride, int E, int64_t nleaf, int h, double* tmp,
+                   double* out, cudaStream_t s, int64_t* launches) {
+  int64_t groups = nleaf / h;
+  if (E == 0) return cudaSuccess;
+  int thr = E < 128 ? 64 : 128;
+  *launches += h <= kSegChunk ? 1 : 2;
+  if (h <= kSegChunk) {
+    k_segsum<<<(unsigned)groups, thr, 0, s>>>(in, stride, E, h, out);
+  } else {
+    k_segsum<<<(unsigned)(nleaf / kSegChunk), thr, 0, s>>>(in, stride, E, kSegChunk, tmp);
+    k_segsum<<<(unsigned)groups, thr, 0, s>>>(tmp, stride, E, h / kSegChunk, out);
+  }
+  return cudaGetLastError();
+}
+
+struct NodeArgs {
+  const double* half;   // per half-node sums, (2^(j+1)) x stride, each r x w row-major
+  int64_t stride;
+  int j, r, w;          // level, padded rank, partial width
+  int cj;               // own columns start (factor mode), -1 in solve mode
+  int wz;               // Z width
+  double* Mlu;          // level's LU factors, (2r)^2 per node
+  int32_t* Mpiv;        // level's pivots, 2r per node
+  double* node_logdet;  // per node (level order)
+  double* Z;            // level scratch, z_stride = 2 r wz per node
+  int64_t z_stride;
+  int32_t* flags;
+};
+
+// Partial column of Z column q: ancestors' panel columns keep their index, the right-hand
+// sides sit after the node's own r columns in factor mode.
+__device__ __forceinline__ int zcol(const NodeArgs& a, int q) {
+  return (a.cj >= 0 && q >= a.cj) ? q + a.r : q;
+}
+
+__global__ void __launch_bounds__(128) k_node(NodeArgs a, bool factor) {
+  extern __shared__ double M[];  // m2 x m2 row-major
+  __shared__ int piv[2 * kMaxRank];
+  __shared__ double lds;
+  __shared__ int sgn;
+  int k = blockIdx.x;
+  int node = (1 << a.j) - 1 + k;
+  int r = a.r, m2 = 2 * r, tid = threadIdx.x;
+  const double* L = a.half + (int64_t)(2 * k) * a.stride;      // U^T (.) over the left half
+  const double* Rt = a.half + (int64_t)(2 * k + 1) * a.stride; // V^T (.) over the right half
+  double* Mg = a.Mlu + (int64_t)k * m2 * m2;
+  int32_t* pg = a.Mpiv + (int64_t)k * m2;
+  if (factor) {
+    for (int e = tid; e < m2 * m2; e += blockDim.x) {
+      int row = e / m2, col = e - row * m2;
+      double v;
+      if (row < r && col < r) v = row == col ? 1.0 : 0.0;
+      else if (row >= r && col >= r) v = row == col ? 1.0 : 0.0;
+      else if (row < r) v = Rt[row * a.w + a.cj + (col - r)];   // V^T Vt
+      else v = L[(row - r) * a.w + a.cj + col];                 // U^T Ut
+      M[e] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      lds = 0.0;
+      sgn = 1;
+    }
+    for (int c = 0; c < m2; ++c) {
+      if (tid == 0) {
+        int p = c;
+        double best = fabs(M[c * m2 + c]);
+        for (int i = c + 1; i < m2; ++i)
+          if (fabs(M[i * m2 + c]) > best) {
+            best = fabs(M[i * m2 + c]);
+            p = i;
+          }
+        piv[c] = p;
+        if (p != c) sgn = -sgn;
+      }
+      __syncthreads();
+      int p = piv[c];
+      if (p != c)
+        for (int jj = tid; jj < m2; jj += blockDim.x) {
+          double t = M[c * m2 + jj];
+          M[c * m2 + jj] = M[p * m2 + jj];
+          M[p * m2 + jj] = t;
+        }
+      __syncthreads();
+      double d = M[c * m2 + c];
+      if (tid == 0) {
+        if (d == 0.0) sgn = 0;
+        else {
+          if (d < 0) sgn = -sgn;
+          lds += log(fabs(d));
+        }
+      }
+      for (int i = c + 1 + tid; i < m2; i += blockDim.x) {
+        double l = d != 0.0 ? M[i * m2 + c] / d : 0.0;
+        M[i * m2 + c] = l;
+        for (int jj = c + 1; jj < m2; ++jj) M[i * m2 + jj] -= l * M[c * m2 + jj];
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < m2 * m2; e += blockDim.x) Mg[e] = M[e];
+    for (int e = tid; e < m2; e += blockDim.x) pg[e] = piv[e];
+    if (tid == 0) {
+      a.node_logdet[node] = lds;
+      if (sgn <= 0) atomicOr(a.flags, kFlagNotSpd);
+    }
+  } else {
+    for (int e = tid; e < m2 * m2; e += blockDim.x) M[e] = Mg[e];
+    for (int e = tid; e < m2; e += blockDim.x) piv[e] = pg[e];
+  }
+  __syncthreads();
+  // Z = M^-1 [V^T P_R; U^T P_L], one thread per column
+  double* Zn = a.Z + (int64_t)k * a.z_stride;
+  for (int q = tid; q < a.wz; q += blockDim.x) {
+    int pc = zcol(a, q);
+    for (int row = 0; row < r; ++row) {
+      Zn[row * a.wz + q] = Rt[row * a.w + pc];
+      Zn[(r + row) * a.wz + q] = L[row * a.w + pc];
+    }
+    for (int c = 0; c < m2; ++c) {
+      int p = piv[c];
+      if (p != c) {
+        double t = Zn[c * a.wz + q];
+        Zn[c * a.wz + q] = Zn[p * a.wz + q];
+        Zn[p * a.wz + q] = t;
+      }
+    }
+    for (int i = 1; i < m2; ++i) {
+      double s = Zn[i * a.wz + q];
+      for (int c = 0; c < i; ++c) s -= M[i * m2 + c] * Zn[c * a.wz + q];
+      Zn[i * a.wz + q] = s;
+    }
+    for (int i = m2 - 1; i >= 0; --i) {
+      double s = Zn[i * a.wz + q];
+      for (int c = i + 1; c < m2; ++c) s -= M[i * m2 + c] * Zn[c * a.wz + q];
+      Zn[i * a.wz + q] = s / M[i * m2 + i];
+    }
+  }
+}
+
+struct SweepArgs {
+  const int32_t* nb;
+  const int32_t* ns;
+  int leaf0, kappa, u;
+  double* pan;
+  const double* phi;
+  double* Y;
+  int cP;        // panel columns updated (c_u in factor mode, 0 in solve mode)
+  int nrhs;
+  int cu, ru;    // level u: own columns in pan (Ut/Vt), rank
+  int cl, rl;    // level u-1: columns in phi, rank (rl = 0: no partial)
+  const double* Z;
+  int64_t z_stride;
+  double* part;
+  int64_t part_stride;
+  int64_t n;
+};
+
+// Level-u update of one leaf's rows, fused with the level-(u-1) partial products.
+__global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs a) {
+  extern __shared__ double sm[];
+  int leaf = blockIdx.x;
+  int id = a.leaf0 + leaf;
+  int b = a.nb[id], p = a.ns[id];
+  int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  double* tl = sm;                 // p x ru   (Ut/Vt of level u on these rows)
+  double* ph = sm + kMaxLeaf * a.ru;  // p x rl (Phi of level u-1)
+  for (int e = tid; e < p * a.ru; e += kSweepThreads) {
+    int i = e % p, c = e / p;
+    tl[i * a.ru + c] = a.pan[(int64_t)(a.cu + c) * a.n + b + i];
+  }
+  for (int e = tid; e < p * a.rl; e += kSweepThreads) {
+    int i = e % p, c = e / p;
+    ph[i * a.rl + c] = a.phi[(int64_t)(a.cl + c) * a.n + b + i];
+  }
+  __syncthreads();
+  int sh = a.kappa - a.u;
+  int side = (leaf >> (sh - 1)) & 1;
+  int wz = a.cP + a.nrhs;
+  const double* Zs = a.Z + (int64_t)(leaf >> sh) * a.z_stride + (int64_t)side * a.ru * wz;
+  double* out = a.part + (int64_t)leaf * a.part_stride;
+  for (int q = w; q < wz; q += kSweepThreads / 32) {
+    double* col = q < a.cP ? a.pan + (int64_t)q * a.n + b : a.Y + (int64_t)(q - a.cP) * a.n + b;
+    double x[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int i = m * 32 + lane;
+      x[m] = i < p ? col[i] : 0.0;
+    }
+    for (int c = 0; c < a.ru; ++c) {
+      double z = Zs[c * wz + q];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) x[m] -= tl[i * a.ru + c] * z;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int i = m * 32 + lane;
+      if (i < p) col[i] = x[m];
+    }
+    for (int c = 0; c < a.rl; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) s += ph[i * a.rl + c] * x[m];
+      }
+      s = wsum(s);
+      if (lane == 0) out[c * wz + q] = s;
+    }
+  }
+}
+
+// Deterministic sum of a (fixed-size grid of per-block partials, then one block).
+__global__ void k_sum_blocks(const double* __restrict__ v, const double* __restrict__ v2,
+                             int64_t m, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += v2 ? v[i] * v2[i] : v[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+constexpr int kRedBlocks = 256;
+
+__global__ void k_finish(const double* __restrict__ pl, const double* __restrict__ pn,
+                         const double* __restrict__ pq, double* scal, int64_t n, int mode) {
+  // mode 0: logdet only; mode 1: logdet and quadratic form -> log-likelihood
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < kRedBlocks; ++i) a += pl[i];
+  for (int i = 0; i < kRedBlocks; ++i) b += pn[i];
+  scal[0] = a + b;
+  if (mode == 1) {
+    double q = 0.0;
+    for (int i = 0; i < kRedBlocks; ++i) q += pq[i];
+    scal[1] = q;
+    scal[2] = -0.5 * q - 0.5 * scal[0] - 0.5 * (double)n * log(2.0 * 3.14159265358979323846);
+  }
+}
+
+__global__ void k_gather(const double* __restrict__ y, int64_t ld, int nrhs,
+                         const int32_t* __restrict__ perm, int64_t n, double* __restrict__ Y,
+                         double* __restrict__ ysort) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t p = perm[i];
+  for (int c = 0; c < nrhs; ++c) {
+    double v = y[c * ld + p];
+    Y[c * n + i] = v;
+    if (c == 0 && ysort) ysort[i] = v;
+  }
+}
+
+__global__ void k_scatter(const double* __restrict__ Y, int nrhs, const int32_t* __restrict__ perm,
+                          int64_t n, double* __restrict__ x, int64_t ld) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t p = perm[i];
+  for (int c = 0; c < nrhs; ++c) x[c * ld + p] = Y[c * n + i];
+}
+
+// ---- HODLR operator product (dense leaves + U V^T blocks) ------------------------------
+struct MvArgs {
+  Pts pts;
+  Cov cov;
+  double sigma2;
+  const int32_t* nb;
+  const int32_t* ns;
+  int leaf0, kappa, R;
+  const double* phi;
+  const int* coff;   // device copy not needed: passed by value below
+  const double* xin;
+  double* yout;
+  double* part;      // leaf x R partials (Phi^T x)
+  const double* half;  // per level half sums, level j at half + hoff[j]
+  int64_t n;
+};
+
+struct LevelTab {
+  int coff[33];
+  int rl[32];
+  int64_t hoff[32];
+};
+
+__global__ void k_mv_partials(MvArgs a, LevelTab t) {
+  int leaf = blockIdx.x;
+  int id = a.leaf0 + leaf;
+  int b = a.nb[id], p = a.ns[id];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = w; c < a.R; c += blockDim.x / 32) {
+    double s = 0.0;
+    for (int i = lane; i < p; i += 32) s += a.phi[(int64_t)c * a.n + b + i] * a.xin[b + i];
+    s = wsum(s);
+    if (lane == 0) a.part[(int64_t)leaf * a.R + c] = s;
+  }
+}
+
+__global__ void k_mv_apply(MvArgs a, LevelTab t) {
+  int leaf = blockIdx.x;
+  int id = a.leaf0 + leaf;
+  int b = a.nb[id], p = a.ns[id];
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    double s = 0.0;
+    for (int jj = 0; jj < p; ++jj) {
+      double r = dist(a.pts, b + i, b + jj);
+      double c = cov_r(a.cov, r);
+      if (jj == i) c += a.sigma2;
+      s += c * a.xin[b + jj];
+    }
+    for (int l = 0; l < a.kappa; ++l) {
+      int sh = a.kappa - l;
+      int k = leaf >> sh;
+      int side = (leaf >> (sh - 1)) & 1;
+      const double* hs = a.half + t.hoff[l] + (int64_t)(2 * k + (1 - side)) * t.rl[l];
+      for (int c = 0; c < t.rl[l]; ++c) s += a.phi[(int64_t)(t.coff[l] + c) * a.n + b + i] * hs[c];
+    }
+    a.yout[b + i] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gather_rhs(Ctx& c, const double* y, int64_t ld, int nrhs) {
+  unsigned g = (unsigned)((c.n + 255) / 256);
+  k_gather<<<g, 256, 0, c.stream>>>(y, ld, nrhs, c.perm, c.n, c.Y, c.ysort);
+  ++c.launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_rhs(Ctx& c, double* x, int64_t ld, int nrhs) {
+  unsigned g = (unsigned)((c.n + 255) / 256);
+  k_scatter<<<g, 256, 0, c.stream>>>(c.Y, nrhs, c.perm, c.n, x, ld);
+  ++c.launches;
+  return cudaGetLastError();
+}
+
+// Sweep of all internal levels after the leaf stage has written the level-(kappa-1)
+// partials. factor_mode: build and factor M per node (panel columns included); otherwise
+// reuse the stored LU factors and carry only the right-hand sides.
+cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
+  int K = c.kappa;
+  int64_t nleaf = (int64_t)1 << K;
+  for (int j = K - 1; j >= 0; --j) {
+    int r = c.h_rl[j];
+    int cj = c.h_coff[j];
+    int cP = factor_mode ? cj + r : 0;  // panel columns in the level-j partials
+    int w = cP + nrhs;
+    int h = 1 << (K - j - 1);
+    HODLR_CUDA_TRY(segsum(c.part, c.part_stride, r * w, nleaf, h, c.part2, c.half, c.stream, &c.launches));
+    NodeArgs na;
+    na.half = c.half;
+    na.stride = c.part_stride;
+    na.j = j;
+    na.r = r;
+    na.w = w;
+    na.cj = factor_mode ? cj : -1;
+    na.wz = (factor_mode ? cj : 0) + nrhs;
+    na.Mlu = c.Mlu + c.h_mlu_off[j];
+    na.Mpiv = c.Mpiv + c.h_piv_off[j];
+    na.node_logdet = c.node_logdet;
+    na.Z = c.Z;
+    na.z_stride = (int64_t)2 * r * na.wz;
+    na.flags = c.dflags;
+    if (r > 0) {
+      size_t smem = sizeof(double) * 4 * r * r;
+      if (smem > 48 * 1024)
+        HODLR_CUDA_TRY(cudaFuncSetAttribute(k_node, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_node<<<1u << j, 128, smem, c.stream>>>(na, factor_mode);
+      ++c.launches;
+      HODLR_CUDA_TRY(cudaGetLastError());
+    } else if (factor_mode) {
+      HODLR_CUDA_TRY(cudaMemsetAsync(c.node_logdet + ((1 << j) - 1), 0, sizeof(double) << j, c.stream));
+    }
+    if (r == 0) {
+      // nothing to apply at this level; the level-(j-1) partials must still be formed
+      // from unchanged rows: run the sweep with rank 0 (pure reduction).
+    }
+    SweepArgs sa;
+    sa.nb = c.nodes;
+    sa.ns = c.nodes + ((int64_t)2 << K);
+    sa.leaf0 = (int)(nleaf - 1);
+    sa.kappa = K;
+    sa.u = j;
+    sa.pan = c.pan;
+    sa.phi = c.phi;
+    sa.Y = c.Y;
+    sa.cP = factor_mode ? cj : 0;
+    sa.nrhs = nrhs;
+    sa.cu = cj;
+    sa.ru = r;
+    sa.cl = j > 0 ? c.h_coff[j - 1] : 0;
+    sa.rl = j > 0 ? c.h_rl[j - 1] : 0;
+    sa.Z = c.Z;
+    sa.z_stride = (int64_t)2 * r * (sa.cP + nrhs);
+    sa.part = c.part;
+    sa.part_stride = c.part_stride;
+    sa.n = c.n;
+    if (sa.cP + nrhs == 0) continue;  // nothing left to update (root level, no right-hand side)
+    size_t smem = sizeof(double) * kMaxLeaf * (sa.ru + sa.rl);
+    if (smem > 48 * 1024)
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_sweep<<<(unsigned)nleaf, kSweepThreads, smem, c.stream>>>(sa);
+    ++c.launches;
+    HODLR_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_logdet_sum(Ctx& c) {
+  int64_t nleaf = (int64_t)1 << c.kappa;
+  double* tmp = c.part2;  // scratch: 3 x kRedBlocks
+  k_sum_blocks<<<kRedBlocks, 256, 0, c.stream>>>(c.leaf_logdet, nullptr, nleaf, tmp);
+  k_sum_blocks<<<kRedBlocks, 256, 0, c.stream>>>(c.node_logdet, nullptr, nleaf - 1, tmp + kRedBlocks);
+  k_finish<<<1, 32, 0, c.stream>>>(tmp, tmp + kRedBlocks, nullptr, c.scal, c.n, 0);
+  c.launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quad_loglik(Ctx& c) {
+  int64_t nleaf = (int64_t)1 << c.kappa;
+  double* tmp = c.part2;
+  k_sum_blocks<<<kRedBlocks, 256, 0, c.stream>>>(c.leaf_logdet, nullptr, nleaf, tmp);
+  k_sum_blocks<<<kRedBlocks, 256, 0, c.stream>>>(c.node_logdet, nullptr, nleaf - 1, tmp + kRedBlocks);
+  k_sum_blocks<<<kRedBlocks, 256, 0, c.stream>>>(c.ysort, c.Y, c.n, tmp + 2 * kRedBlocks);
+  k_finish<<<1, 32, 0, c.stream>>>(tmp, tmp + kRedBlocks, tmp + 2 * kRedBlocks, c.scal, c.n, 1);
+  c.launches += 4;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec(Ctx& c, const double* xin, double* yout) {
+  int K = c.kappa;
+  int64_t nleaf = (int64_t)1 << K;
+  MvArgs a;
+  a.pts = Pts{c.xs, c.n, c.d};
+  a.cov = Cov{c.kind, 1.0 / c.ell, c.amp};
+  a.sigma2 = c.sigma2;
+  a.nb = c.nodes;
+  a.ns = c.nodes + ((int64_t)2 << K);
+  a.leaf0 = (int)(nleaf - 1);
+  a.kappa = K;
+  a.R = c.R;
+  a.phi = c.phi;
+  a.coff = nullptr;
+  a.xin = xin;
+  a.yout = yout;
+  a.part = c.part;
+  a.n = c.n;
+  LevelTab t;
+  int64_t off = 0;
+  for (int j = 0; j < 32; ++j) {
+    t.rl[j] = j < K ? c.h_rl[j] : 0;
+    t.hoff[j] = off;
+    if (j < K) off += ((int64_t)2 << j) * c.h_rl[j];
+  }
+  for (int j = 0; j < 33; ++j) t.coff[j] = j <= K ? c.h_coff[j] : 0;
+  double* half = c.half;
+  a.half = half;
+  if (K > 0 && c.R > 0) {
+    k_mv_partials<<<(unsigned)nleaf, 128, 0, c.stream>>>(a, t);
+    ++c.launches;
+    HODLR_CUDA_TRY(cudaGetLastError());
+    for (int j = 0; j < K; ++j) {
+      if (c.h_rl[j] == 0) continue;
+      // half sums of level j: groups of 2^(K-j-1) leaves; the level's columns start at coff_j
+      HODLR_CUDA_TRY(segsum(c.part + c.h_coff[j], c.R, c.h_rl[j], nleaf, 1 << (K - j - 1),
+                            c.part2, c.Z, c.stream, &c.launches));
+      // compact rows of width rl_j into half + hoff_j
+      HODLR_CUDA_TRY(cudaMemcpy2DAsync(half + t.hoff[j], sizeof(double) * c.h_rl[j], c.Z,
+                                       sizeof(double) * c.R, sizeof(double) * c.h_rl[j],
+                                       (size_t)2 << j, cudaMemcpyDeviceToDevice, c.stream));
+    }
+  }
+  k_mv_apply<<<(unsigned)nleaf, 128, 0, c.stream>>>(a, t);
+  ++c.launches;
+  return cudaGetLastError();
+}
+
+}  // namespace hodlr

@@ -1,0 +1,317 @@
+"""Python binding of the C ABI in include/hodlr.h (argument marshalling only).
+
+Every step of the computation runs in libhodlr_gb300.so's CUDA kernels. Arrays may be
+numpy arrays (host; the library copies them) or torch CUDA tensors (device; stream
+ordered). There is no CPU fallback: if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhodlr_gb300.so")
+
+KERNELS = {"exp": 0, "se": 1, "matern32": 2, "matern52": 3}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTSPD", 4: "ERANK", 5: "ETIMEOUT",
+          6: "ESTATE", 7: "ECUDA"}
+HODLR_OK, HODLR_EINVAL, HODLR_ENOMEM, HODLR_ENOTSPD, HODLR_ERANK = 0, 1, 2, 3, 4
+HODLR_ETIMEOUT, HODLR_ESTATE, HODLR_ECUDA = 5, 6, 7
+
+
+class hodlr_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("rank_mode", ctypes.c_int),
+                ("max_rank", ctypes.c_int), ("max_nrhs", ctypes.c_int),
+                ("refine_tol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.c_void_p  # host or device double*, passed as an address
+
+
+def load():
+    """Load the CUDA library (build it first with build_lib.build()). Raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "paper_1403_6015_gb300.build_lib.build() (no CPU fallback exists)")
+    L = ctypes.CDLL(LIB_PATH)
+    L.hodlr_default_opts.argtypes = [ctypes.POINTER(hodlr_opts)]
+    L.hodlr_build.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                              ctypes.c_int, ctypes.c_double, ctypes.POINTER(hodlr_opts),
+                              ctypes.POINTER(_vp)]
+    L.hodlr_rebuild.argtypes = [_vp, _dp, ctypes.c_double]
+    L.hodlr_factor.argtypes = [_vp]
+    L.hodlr_factor_solve.argtypes = [_vp, _dp, _dp, ctypes.c_int, ctypes.c_int64]
+    L.hodlr_solve.argtypes = [_vp, _dp, _dp, ctypes.c_int, ctypes.c_int64]
+    L.hodlr_logdet.argtypes = [_vp, _dp]
+    L.hodlr_loglik.argtypes = [_vp, _dp, _dp]
+    L.hodlr_ranks.argtypes = [_vp, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    L.hodlr_tree.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _dp]
+    L.hodlr_matvec.argtypes = [_vp, _dp, _dp]
+    L.hodlr_phase_ms.argtypes = [_vp, _dp]
+    L.hodlr_counters.argtypes = [_vp, _dp]
+    L.hodlr_last_error.argtypes = [_vp]
+    L.hodlr_last_error.restype = ctypes.c_char_p
+    L.hodlr_status_string.argtypes = [ctypes.c_int]
+    L.hodlr_status_string.restype = ctypes.c_char_p
+    L.hodlr_destroy.argtypes = [_vp]
+    for name in ("hodlr_build", "hodlr_rebuild", "hodlr_factor", "hodlr_factor_solve",
+                 "hodlr_solve", "hodlr_logdet", "hodlr_loglik", "hodlr_ranks", "hodlr_tree",
+                 "hodlr_matvec", "hodlr_phase_ms", "hodlr_counters"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class HodlrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _addr(a) -> int:
+    """Address of a numpy array or torch tensor's data."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _is_torch(a) -> bool:
+    return hasattr(a, "data_ptr") and hasattr(a, "is_cuda")
+
+
+def _f64_host(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---- the C ABI, name for name ------------------------------------------------------------
+
+def hodlr_default_opts() -> hodlr_opts:
+    o = hodlr_opts()
+    load().hodlr_default_opts(ctypes.byref(o))
+    return o
+
+
+def hodlr_build(x, n, d, kernel, theta, sigma2, leaf, eps, opts=None):
+    """Returns (status, ctx). x: host numpy (n, d) float64 or a CUDA tensor (row-major)."""
+    L = load()
+    th = _f64_host(theta)
+    out = _vp()
+    st = L.hodlr_build(_addr(x), n, d, kernel, th.ctypes.data, sigma2, leaf, eps,
+                       ctypes.byref(opts) if opts is not None else None, ctypes.byref(out))
+    return st, out.value
+
+
+def hodlr_rebuild(ctx, theta, sigma2):
+    th = _f64_host(theta)
+    return load().hodlr_rebuild(ctx, th.ctypes.data, sigma2)
+
+
+def hodlr_factor(ctx):
+    return load().hodlr_factor(ctx)
+
+
+def hodlr_factor_solve(ctx, y_addr, x_addr, nrhs, ld):
+    return load().hodlr_factor_solve(ctx, y_addr, x_addr, nrhs, ld)
+
+
+def hodlr_solve(ctx, y_addr, x_addr, nrhs, ld):
+    return load().hodlr_solve(ctx, y_addr, x_addr, nrhs, ld)
+
+
+def hodlr_logdet(ctx, out_addr):
+    return load().hodlr_logdet(ctx, out_addr)
+
+
+def hodlr_loglik(ctx, y_addr, out_addr):
+    return load().hodlr_loglik(ctx, y_addr, out_addr)
+
+
+def hodlr_ranks(ctx, buf, cap):
+    cnt = ctypes.c_int64()
+    st = load().hodlr_ranks(ctx, _addr(buf) if buf is not None else None, cap, ctypes.byref(cnt))
+    return st, cnt.value
+
+
+def hodlr_tree(ctx, perm=None):
+    k = ctypes.c_int()
+    st = load().hodlr_tree(ctx, ctypes.byref(k), _addr(perm) if perm is not None else None)
+    return st, k.value
+
+
+def hodlr_matvec(ctx, x_addr, y_addr):
+    return load().hodlr_matvec(ctx, x_addr, y_addr)
+
+
+def hodlr_phase_ms(ctx, buf):
+    return load().hodlr_phase_ms(ctx, _addr(buf))
+
+
+def hodlr_counters(ctx, buf):
+    return load().hodlr_counters(ctx, _addr(buf))
+
+
+def hodlr_last_error(ctx) -> str:
+    return load().hodlr_last_error(ctx).decode()
+
+
+def hodlr_status_string(st: int) -> str:
+    return load().hodlr_status_string(st).decode()
+
+
+def hodlr_destroy(ctx):
+    load().hodlr_destroy(ctx)
+
+
+# ---- convenience object ------------------------------------------------------------------
+
+class Hodlr:
+    """One HODLR problem: C = sigma2 I + K(x; theta) on one GPU.
+
+    x, y may be numpy arrays (host) or torch CUDA tensors (device). Outputs follow the
+    input's kind: numpy in, numpy out; CUDA tensor in, CUDA tensor out.
+    """
+
+    def __init__(self, x, kernel: str, theta, sigma2: float, leaf: int, eps: float,
+                 max_rank: int = 64, max_nrhs: int = 16, stream=None, allow_rank_cap=False):
+        if _is_torch(x):
+            if x.dtype.itemsize != 8 or not x.is_contiguous():
+                raise ValueError("x must be a contiguous float64 tensor")
+            self.n = x.shape[0]
+            self.d = 1 if x.dim() == 1 else x.shape[1]
+            xin = x
+        else:
+            xin = _f64_host(x)
+            self.n = xin.shape[0]
+            self.d = 1 if xin.ndim == 1 else xin.shape[1]
+        o = hodlr_default_opts()
+        o.max_rank = max_rank
+        o.max_nrhs = max_nrhs
+        if stream is not None:
+            o.stream = stream
+        self.kernel = kernel
+        st, ctx = hodlr_build(xin, self.n, self.d, KERNELS[kernel], theta, sigma2, leaf, eps, o)
+        self.status = st
+        if not ctx:
+            raise HodlrError(st, "hodlr_build failed")
+        self._ctx = ctx
+        if st not in (HODLR_OK,) and not (st == HODLR_ERANK and allow_rank_cap):
+            msg = hodlr_last_error(ctx)
+            self.close()
+            raise HodlrError(st, msg)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            hodlr_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != HODLR_OK:
+            raise HodlrError(st, f"{what}: {hodlr_last_error(self._ctx)}")
+
+    def rebuild(self, theta, sigma2):
+        self._check(hodlr_rebuild(self._ctx, theta, sigma2), "rebuild")
+
+    def factor(self):
+        self._check(hodlr_factor(self._ctx), "factor")
+
+    @staticmethod
+    def _cols(y):
+        if _is_torch(y):
+            one = y.dim() == 1
+            Y = y.reshape(-1, 1) if one else y
+            # column-major: a (nrhs, n) contiguous tensor viewed transposed
+            Yc = Y.t().contiguous() if not one else Y.contiguous()
+            return Yc, one, True
+        y = np.asarray(y, dtype=np.float64)
+        one = y.ndim == 1
+        Y = np.asfortranarray(y.reshape(-1, 1) if one else y)
+        return Y, one, False
+
+    def _out_like(self, Y, is_t):
+        if is_t:
+            import torch
+            return torch.empty_like(Y)
+        return np.zeros_like(Y, order="F")
+
+    @staticmethod
+    def _result(X, one, is_t):
+        if is_t:
+            return X.reshape(-1) if one else X.t()
+        return X[:, 0] if one else X
+
+    def factor_solve(self, y):
+        Y, one, is_t = self._cols(y)
+        X = self._out_like(Y, is_t)
+        nrhs = 1 if one else (Y.shape[0] if is_t else Y.shape[1])
+        self._check(hodlr_factor_solve(self._ctx, _addr(Y), _addr(X), nrhs, self.n), "factor_solve")
+        return self._result(X, one, is_t)
+
+    def solve(self, y):
+        Y, one, is_t = self._cols(y)
+        X = self._out_like(Y, is_t)
+        nrhs = 1 if one else (Y.shape[0] if is_t else Y.shape[1])
+        self._check(hodlr_solve(self._ctx, _addr(Y), _addr(X), nrhs, self.n), "solve")
+        return self._result(X, one, is_t)
+
+    def logdet(self, out=None) -> float:
+        buf = out if out is not None else np.zeros(1)
+        self._check(hodlr_logdet(self._ctx, _addr(buf)), "logdet")
+        return buf if out is not None else float(buf[0])
+
+    def loglik(self, y, out=None):
+        if _is_torch(y):
+            yy = y.contiguous()
+        else:
+            yy = _f64_host(y).reshape(-1)
+        buf = out if out is not None else np.zeros(1)
+        self._check(hodlr_loglik(self._ctx, _addr(yy), _addr(buf)), "loglik")
+        return buf if out is not None else float(buf[0])
+
+    def ranks(self) -> np.ndarray:
+        st, cnt = hodlr_ranks(self._ctx, None, 0)
+        buf = np.zeros(max(cnt, 1), dtype=np.int32)
+        self._check(hodlr_ranks(self._ctx, buf, cnt)[0], "ranks")
+        return buf[:cnt]
+
+    def tree(self):
+        perm = np.zeros(self.n, dtype=np.int64)
+        st, kappa = hodlr_tree(self._ctx, perm)
+        self._check(st, "tree")
+        return kappa, perm
+
+    def matvec(self, x):
+        if _is_torch(x):
+            xx = x.contiguous()
+            import torch
+            out = torch.empty_like(xx)
+        else:
+            xx = _f64_host(x).reshape(-1)
+            out = np.zeros_like(xx)
+        self._check(hodlr_matvec(self._ctx, _addr(xx), _addr(out)), "matvec")
+        return out
+
+    def phase_ms(self):
+        buf = np.zeros(6, dtype=np.float32)
+        self._check(hodlr_phase_ms(self._ctx, buf), "phase_ms")
+        return {"ordering": float(buf[0]), "compression": float(buf[1]),
+                "factor": float(buf[2]), "solve": float(buf[3]),
+                "leaf_kernel": float(buf[4]), "levels": float(buf[5])}
+
+    def counters(self):
+        buf = np.zeros(2, dtype=np.int64)
+        self._check(hodlr_counters(self._ctx, buf), "counters")
+        return {"launches": int(buf[0]), "syncs": int(buf[1])}
