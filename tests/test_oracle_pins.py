@@ -234,8 +234,10 @@ def test_kappa_reading():
 
 @pytest.mark.parametrize("name,rank", [("exp", 1), ("matern32", 2), ("matern52", 3)])
 def test_aca_exact_ranks(name, rank):
+    """Exact ranks 1 / 2 / 3 at eps = 1e-10 (at 1e-12 the rounding-noise term of a
+    Matern-5/2 block sits near the tolerance and is sometimes kept)."""
     x, _ = I.workload_1d(4096, 51)
-    H = O.Hodlr(x, name, [0.1, 1.0], 0.01, 64, 1e-12)
+    H = O.Hodlr(x, name, [0.1, 1.0], 0.01, 64, 1e-10)
     assert set(H.ranks().tolist()) == {rank}
 
 
