@@ -27,7 +27,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N = 1 << 20
+N = 1 << 20  # the benchmark size; --n changes it only for profiling captures
 LEAF = 128
 EPS = 1e-12
 SIGMA2 = 1e-2
@@ -198,15 +198,17 @@ def run_ours(args):
     y_pin = torch.from_numpy(y).pin_memory()
     y_host = y_pin.numpy()
     host_out = np.zeros(len(KERNELS))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for i, (h, (kern, ell)) in enumerate(zip(ctxs, KERNELS)):
-            h.rebuild([ell, 1.0], SIGMA2)
-            host_out[i] = h.loglik(y_host)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = args.steps * len(KERNELS) * world / e2e_s
+    e2e_value = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for i, (h, (kern, ell)) in enumerate(zip(ctxs, KERNELS)):
+                h.rebuild([ell, 1.0], SIGMA2)
+                host_out[i] = h.loglik(y_host)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e_value = args.steps * len(KERNELS) * world / e2e_s
 
     # roofline of the dominant kernel (the leaf kernel, FP64-ALU bound)
     h0 = ctxs[0]
@@ -224,14 +226,15 @@ def run_ours(args):
 
     # accuracy (outside the timed region)
     acc = {}
-    if rank == 0:
+    if rank == 0 and not args.no_accuracy:
         for i, (h, (kern, ell)) in enumerate(zip(ctxs, KERNELS)):
             h.rebuild([ell, 1.0], SIGMA2)
             sol = h.factor_solve(y)
             ld = h.logdet()
             _, perm = h.tree()
             acc[kern] = accuracy(x, y, perm, kern, ell, float(outs[i].item()), ld, sol)
-        acc["host_vs_device_loglik"] = float(np.max(np.abs(host_out - outs.cpu().numpy())))
+        if e2e_value is not None:
+            acc["host_vs_device_loglik"] = float(np.max(np.abs(host_out - outs.cpu().numpy())))
     cpu = cpu_baseline(x, y) if (rank == 0 and world == 1 and not args.no_cpu) else None
     clocks = clk.summary()
     if rank == 0:
@@ -306,13 +309,18 @@ def run_reference(args):
 
 
 def main():
+    global N
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy checks")
+    ap.add_argument("--n", type=int, default=N, help="points (profiling captures only)")
     args = ap.parse_args()
+    N = args.n
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
