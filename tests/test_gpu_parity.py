@@ -134,7 +134,12 @@ def test_2d_vs_dense(H):
     sol_d, ld_d = O.dense_solve(x, "se", th, s2, y)
     assert rel(h.logdet(), ld_d) <= 1e-10
     C = dense_C(x, "se", th, s2)
-    assert np.linalg.norm(C @ sol - y) / np.linalg.norm(y) <= 1e-9
+    # cond(C) ~ 2e5 here, so the residual of the method at eps=1e-12 is ~2e-9 (the oracle
+    # reaches 2.3e-9 itself): bound the GPU by the oracle's residual
+    ref = O.Hodlr(x, "se", th, s2, 32, 1e-12)
+    res_o = np.linalg.norm(C @ ref.factor_solve(y) - y) / np.linalg.norm(y)
+    res = np.linalg.norm(C @ sol - y) / np.linalg.norm(y)
+    assert res <= 2.0 * res_o + 1e-12
 
 
 @pytest.mark.parametrize("nrhs", [1, 3, 16, 21])
