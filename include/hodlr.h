@@ -140,6 +140,24 @@ hodlr_status hodlr_phase_ms(hodlr_ctx* ctx, float* out6);
  * context launched, out[1] host synchronisations it performed. */
 hodlr_status hodlr_counters(hodlr_ctx* ctx, int64_t* out2);
 
+/* Log-likelihood of a problem small enough to be one leaf block, with no device
+ * allocation. The paper has no counterpart: this entry exists for callers that must not
+ * allocate device memory while they evaluate, such as sampling loops under a fixed memory
+ * budget or code recorded into a CUDA graph that should hold no allocation nodes.
+ *   x      device pointer, n points row-major n x d (d in {1, 2}); y device pointer (n);
+ *   out    device pointer to one double: -y^T C^-1 y/2 - log det C/2 - n log(2 pi)/2, or
+ *          NaN if C is not positive definite;
+ *   stream cudaStream_t (NULL = legacy default stream); the call is stream-ordered and
+ *          does not synchronise.
+ * Limits: 1 <= n <= 128; larger n returns HODLR_EINVAL, as do host pointers.
+ * Scratch: a fixed 135,232-byte array in device global memory that every GPU loading the
+ * library holds until exit. The first call on a device looks up its address (with that
+ * device current), so make that first call before any stream capture. All calls on a
+ * device share the array: calls that overlap on the GPU race. */
+hodlr_status hodlr_loglik_small_noalloc(const double* x, int64_t n, int d, hodlr_kernel kernel,
+                                        const double* theta, double sigma2, const double* y,
+                                        double* out, void* stream);
+
 const char* hodlr_last_error(const hodlr_ctx* ctx);
 const char* hodlr_status_string(hodlr_status s);
 

@@ -175,6 +175,9 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode);
 cudaError_t launch_logdet_sum(Ctx& c);
 cudaError_t launch_quad_loglik(Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double* xin_sorted, double* yout_sorted);
+cudaError_t launch_leaf_single(const double* xs_soa, int n, int d, int kind, double ell,
+                               double amp, double sigma2, const int32_t* nodes, double* Y,
+                               double* L, double* logdet, int32_t* flags, cudaStream_t s);
 
 }  // namespace hodlr
 

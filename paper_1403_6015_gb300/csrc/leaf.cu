@@ -239,3 +239,40 @@ cudaError_t launch_leaf_solve(Ctx& c, int nrhs) {
 }
 
 }  // namespace hodlr
+
+namespace hodlr {
+
+// The leaf kernel on caller-provided device buffers, for a problem that is a single leaf
+// (kappa = 0): nodes[0] = 0 (begin), nodes[1] = n (size); Y holds the right-hand side and
+// receives C^-1 y; L receives the Cholesky factor; logdet receives log det C.
+cudaError_t launch_leaf_single(const double* xs_soa, int n, int d, int kind, double ell,
+                               double amp, double sigma2, const int32_t* nodes, double* Y,
+                               double* L, double* logdet, int32_t* flags, cudaStream_t s) {
+  LeafArgs a;
+  a.pts = Pts{xs_soa, n, d};
+  a.cov = Cov{kind, 1.0 / ell, amp};
+  a.sigma2 = sigma2;
+  a.nb = nodes;
+  a.ns = nodes + 1;
+  a.leaf0 = 0;
+  a.kappa = 0;
+  a.pan = nullptr;
+  a.cP = 0;
+  a.Y = Y;
+  a.nrhs = 1;
+  a.phi = nullptr;
+  a.coff = 0;
+  a.rl = 0;
+  a.part = nullptr;
+  a.part_stride = 0;
+  a.leafL = L;
+  a.leaf_logdet = logdet;
+  a.flags = flags;
+  a.n = n;
+  size_t smem = sizeof(double) * kMaxLeaf * kLD;
+  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_leaf<true><<<1, kLeafThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace hodlr

@@ -57,6 +57,8 @@ def load():
     L.hodlr_matvec.argtypes = [_vp, _dp, _dp]
     L.hodlr_phase_ms.argtypes = [_vp, _dp]
     L.hodlr_counters.argtypes = [_vp, _dp]
+    L.hodlr_loglik_small_noalloc.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp,
+                                             ctypes.c_double, _dp, _dp, _vp]
     L.hodlr_last_error.argtypes = [_vp]
     L.hodlr_last_error.restype = ctypes.c_char_p
     L.hodlr_status_string.argtypes = [ctypes.c_int]
@@ -64,7 +66,8 @@ def load():
     L.hodlr_destroy.argtypes = [_vp]
     for name in ("hodlr_build", "hodlr_rebuild", "hodlr_factor", "hodlr_factor_solve",
                  "hodlr_solve", "hodlr_logdet", "hodlr_loglik", "hodlr_ranks", "hodlr_tree",
-                 "hodlr_matvec", "hodlr_phase_ms", "hodlr_counters"):
+                 "hodlr_matvec", "hodlr_phase_ms", "hodlr_counters",
+                 "hodlr_loglik_small_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -156,6 +159,14 @@ def hodlr_phase_ms(ctx, buf):
 
 def hodlr_counters(ctx, buf):
     return load().hodlr_counters(ctx, _addr(buf))
+
+
+def hodlr_loglik_small_noalloc(x_addr, n, d, kernel, theta, sigma2, y_addr, out_addr,
+                               stream=None):
+    """Device pointers only; n <= 128; no device allocation (see include/hodlr.h)."""
+    th = _f64_host(theta)
+    return load().hodlr_loglik_small_noalloc(x_addr, n, d, kernel, th.ctypes.data, sigma2,
+                                             y_addr, out_addr, stream)
 
 
 def hodlr_last_error(ctx) -> str:
