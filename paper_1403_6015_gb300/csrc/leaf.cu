@@ -47,21 +47,33 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// Solve L L^T x = b for one column held by a warp: element i in lane i % 32, slot i / 32.
-__device__ __forceinline__ void warp_chol_solve(const double* __restrict__ A, int p, int lane,
-                                                double (&x)[4]) {
+// Solve L L^T x = b for NC columns held by a warp: element i of column c in lane i % 32,
+// slot i / 32 of x[c]. dinv holds 1 / L_ii, so no step divides.
+template <int NC>
+__device__ __forceinline__ void warp_chol_solve(const double* __restrict__ A,
+                                                const double* __restrict__ dinv, int p, int lane,
+                                                double (&x)[NC][4]) {
   // forward: L z = b
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     for (int kk = 0; kk < 32; ++kk) {
       int k = s * 32 + kk;
       if (k >= p) break;
-      double zk = __shfl_sync(0xffffffffu, x[s], kk) / A[k * kLD + k];
-      if (lane == kk) x[s] = zk;
+      double dk = dinv[k];
+      double zk[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        zk[c] = __shfl_sync(0xffffffffu, x[c][s], kk) * dk;
+        if (lane == kk) x[c][s] = zk[c];
+      }
 #pragma unroll
       for (int m = s; m < 4; ++m) {
         int i = m * 32 + lane;
-        if (i > k && i < p) x[m] -= A[i * kLD + k] * zk;
+        if (i > k && i < p) {
+          double lik = A[i * kLD + k];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) x[c][m] -= lik * zk[c];
+        }
       }
     }
   }
@@ -71,12 +83,21 @@ __device__ __forceinline__ void warp_chol_solve(const double* __restrict__ A, in
     for (int kk = 31; kk >= 0; --kk) {
       int k = s * 32 + kk;
       if (k >= p) continue;
-      double xk = __shfl_sync(0xffffffffu, x[s], kk) / A[k * kLD + k];
-      if (lane == kk) x[s] = xk;
+      double dk = dinv[k];
+      double xk[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        xk[c] = __shfl_sync(0xffffffffu, x[c][s], kk) * dk;
+        if (lane == kk) x[c][s] = xk[c];
+      }
 #pragma unroll
       for (int m = 0; m <= s; ++m) {
         int i = m * 32 + lane;
-        if (i < k) x[m] -= A[k * kLD + i] * xk;
+        if (i < k) {
+          double lki = A[k * kLD + i];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) x[c][m] -= lki * xk[c];
+        }
       }
     }
   }
@@ -86,7 +107,9 @@ template <bool kFactor>
 __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
   extern __shared__ double A[];  // [kMaxLeaf][kLD]
   __shared__ double xl[2 * kMaxLeaf];
+  __shared__ double dinv[kMaxLeaf];
   __shared__ double red[kLeafThreads / 32];
+  __shared__ double piv_inv;
   __shared__ int bad;
   int leaf = blockIdx.x;
   int id = a.leaf0 + leaf;
@@ -123,10 +146,12 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
           bad = 1;
           dkk = 1.0;
         }
-        A[k * kLD + k] = sqrt(dkk);
+        double lkk = sqrt(dkk);
+        A[k * kLD + k] = lkk;
+        piv_inv = 1.0 / lkk;
       }
       __syncthreads();
-      double inv = 1.0 / A[k * kLD + k];
+      double inv = piv_inv;
       for (int i = k + 1 + tid; i < p; i += kLeafThreads) A[i * kLD + k] *= inv;
       __syncthreads();
       for (int j = k + 1 + w; j < p; j += kLeafThreads / 32) {
@@ -159,35 +184,54 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
     }
     __syncthreads();
   }
-  // columns: panel [0, cP) then right-hand sides [0, nrhs)
+  for (int i = tid; i < p; i += kLeafThreads) dinv[i] = 1.0 / A[i * kLD + i];
+  __syncthreads();
+  // columns: panel [0, cP) then right-hand sides [0, nrhs), two per warp at a time
   int ncol = a.cP + a.nrhs;
   int wtot = ncol;  // partial row width
-  for (int c = w; c < ncol; c += kLeafThreads / 32) {
-    double* col = c < a.cP ? a.pan + (int64_t)c * a.n + b : a.Y + (int64_t)(c - a.cP) * a.n + b;
-    double x[4];
+  constexpr int NC = 2;
+  for (int c0 = w * NC; c0 < ncol; c0 += NC * (kLeafThreads / 32)) {
+    double* col[NC];
+    double x[NC][4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      int i = m * 32 + lane;
-      x[m] = i < p ? col[i] : 0.0;
+    for (int c = 0; c < NC; ++c) {
+      int cc = c0 + c < ncol ? c0 + c : c0;  // a missing second column repeats the first
+      col[c] = cc < a.cP ? a.pan + (int64_t)cc * a.n + b : a.Y + (int64_t)(cc - a.cP) * a.n + b;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        x[c][m] = i < p ? col[c][i] : 0.0;
+      }
     }
-    warp_chol_solve(A, p, lane, x);
+    warp_chol_solve<NC>(A, dinv, p, lane, x);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      int i = m * 32 + lane;
-      if (i < p) col[i] = x[m];
+    for (int c = 0; c < NC; ++c) {
+      if (c0 + c >= ncol) break;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) col[c][i] = x[c][m];
+      }
     }
     if (a.kappa > 0) {
       double* out = a.part + (int64_t)leaf * a.part_stride;
       for (int r = 0; r < a.rl; ++r) {
         const double* ph = a.phi + (int64_t)(a.coff + r) * a.n + b;
-        double s = 0.0;
+        double phv[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           int i = m * 32 + lane;
-          if (i < p) s += ph[i] * x[m];
+          phv[m] = i < p ? ph[i] : 0.0;
         }
-        s = wsum(s);
-        if (lane == 0) out[r * wtot + c] = s;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          if (c0 + c >= ncol) break;
+          double s = 0.0;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) s += phv[m] * x[c][m];
+          s = wsum(s);
+          if (lane == 0) out[r * wtot + c0 + c] = s;
+        }
       }
     }
   }
