@@ -4,10 +4,12 @@
 //
 // One CTA per leaf, 256 threads, the leaf block in shared memory (row-major, stride 129):
 //   factor mode: build C[I_leaf, I_leaf] from the sorted points (sigma^2 on the diagonal),
-//                Cholesky-factor it in place (right-looking), store L, log det = 2 sum log L_ii;
-//   solve mode:  load the stored L.
+//                factor it in place as L D L^T (the square-root-free Cholesky form, L unit
+//                lower, two pivots per step), store it, log det = sum log D_ii;
+//   solve mode:  load the stored factor.
 // Then every panel column (the ancestors' U/V rows in factor mode, and the right-hand sides)
-// is solved with L L^T by one warp (lanes own rows lane + 32 m), and the warp also forms the
+// is solved with L D L^T by one warp (lanes own rows lane + 32 m, two columns at a time; a
+// unit diagonal means every step is one shuffle and FMAs), and the warp also forms the
 // level-(kappa-1) partial products Phi_{kappa-1}^T x of the leaf's rows.
 #include <cuda_runtime.h>
 
@@ -47,49 +49,49 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// Solve L L^T x = b for NC columns held by a warp: element i of column c in lane i % 32,
-// slot i / 32 of x[c]. dinv holds 1 / L_ii, so no step divides.
+// Solve L D L^T x = b (L unit lower, stored below the diagonal of A) for NC columns held by
+// a warp: element i of column c in lane i % 32, slot i / 32 of x[c]. dinv holds 1 / D_ii.
 template <int NC>
-__device__ __forceinline__ void warp_chol_solve(const double* __restrict__ A,
-                                                const double* __restrict__ dinv, int p, int lane,
-                                                double (&x)[NC][4]) {
-  // forward: L z = b
+__device__ __forceinline__ void warp_ldl_solve(const double* __restrict__ A,
+                                               const double* __restrict__ dinv, int p, int lane,
+                                               double (&x)[NC][4]) {
+  // forward: L w = b
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     for (int kk = 0; kk < 32; ++kk) {
       int k = s * 32 + kk;
       if (k >= p) break;
-      double dk = dinv[k];
-      double zk[NC];
+      double wk[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        zk[c] = __shfl_sync(0xffffffffu, x[c][s], kk) * dk;
-        if (lane == kk) x[c][s] = zk[c];
-      }
+      for (int c = 0; c < NC; ++c) wk[c] = __shfl_sync(0xffffffffu, x[c][s], kk);
 #pragma unroll
       for (int m = s; m < 4; ++m) {
         int i = m * 32 + lane;
         if (i > k && i < p) {
           double lik = A[i * kLD + k];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) x[c][m] -= lik * zk[c];
+          for (int c = 0; c < NC; ++c) x[c][m] -= lik * wk[c];
         }
       }
     }
   }
-  // backward: L^T x = z
+  // v = D^-1 w
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    int i = m * 32 + lane;
+    double di = i < p ? dinv[i] : 0.0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) x[c][m] *= di;
+  }
+  // backward: L^T x = v
 #pragma unroll
   for (int s = 3; s >= 0; --s) {
     for (int kk = 31; kk >= 0; --kk) {
       int k = s * 32 + kk;
       if (k >= p) continue;
-      double dk = dinv[k];
       double xk[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        xk[c] = __shfl_sync(0xffffffffu, x[c][s], kk) * dk;
-        if (lane == kk) x[c][s] = xk[c];
-      }
+      for (int c = 0; c < NC; ++c) xk[c] = __shfl_sync(0xffffffffu, x[c][s], kk);
 #pragma unroll
       for (int m = 0; m <= s; ++m) {
         int i = m * 32 + lane;
@@ -108,8 +110,9 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
   extern __shared__ double A[];  // [kMaxLeaf][kLD]
   __shared__ double xl[2 * kMaxLeaf];
   __shared__ double dinv[kMaxLeaf];
+  __shared__ double T0[kMaxLeaf], T1[kMaxLeaf];
   __shared__ double red[kLeafThreads / 32];
-  __shared__ double piv_inv;
+  __shared__ double piv_inv[2], piv_t;
   __shared__ int bad;
   int leaf = blockIdx.x;
   int id = a.leaf0 + leaf;
@@ -138,34 +141,67 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
       A[i * kLD + j] = c;
     }
     __syncthreads();
-    // right-looking Cholesky, column k per step
-    for (int k = 0; k < p; ++k) {
+    // L D L^T, right-looking, pivots k and k+1 per step: on exit A[i][j] (j < i) = L_ij and
+    // A[k][k] = D_kk. The trailing update uses the unscaled columns kept in T0, T1:
+    // A_ij -= L_ik (L_jk D_kk) + L_i,k+1 (L_j,k+1 D_k+1,k+1).
+    for (int k = 0; k < p; k += 2) {
+      bool two = k + 1 < p;
       if (tid == 0) {
-        double dkk = A[k * kLD + k];
-        if (!(dkk > 0.0)) {
+        double dk = A[k * kLD + k];
+        if (!(dk > 0.0)) {
           bad = 1;
-          dkk = 1.0;
+          dk = 1.0;
         }
-        double lkk = sqrt(dkk);
-        A[k * kLD + k] = lkk;
-        piv_inv = 1.0 / lkk;
+        A[k * kLD + k] = dk;
+        double ik = 1.0 / dk;
+        piv_inv[0] = ik;
+        if (two) {
+          double t = A[(k + 1) * kLD + k];
+          double l = t * ik;
+          A[(k + 1) * kLD + k] = l;
+          double d1 = A[(k + 1) * kLD + k + 1] - l * t;
+          if (!(d1 > 0.0)) {
+            bad = 1;
+            d1 = 1.0;
+          }
+          A[(k + 1) * kLD + k + 1] = d1;
+          piv_inv[1] = 1.0 / d1;
+          piv_t = t;
+        }
       }
       __syncthreads();
-      double inv = piv_inv;
-      for (int i = k + 1 + tid; i < p; i += kLeafThreads) A[i * kLD + k] *= inv;
+      double i0v = piv_inv[0];
+      for (int i = k + 2 + tid; i < p; i += kLeafThreads) {
+        double t = A[i * kLD + k];
+        double l = t * i0v;
+        A[i * kLD + k] = l;
+        T0[i] = t;
+        if (two) {
+          double u = A[i * kLD + k + 1] - l * piv_t;
+          A[i * kLD + k + 1] = u * piv_inv[1];
+          T1[i] = u;
+        }
+      }
       __syncthreads();
-      for (int j = k + 1 + w; j < p; j += kLeafThreads / 32) {
-        double ljk = A[j * kLD + k];
-        for (int i = j + lane; i < p; i += 32) A[i * kLD + j] -= A[i * kLD + k] * ljk;
+      if (two) {
+        for (int j = k + 2 + w; j < p; j += kLeafThreads / 32) {
+          double t0 = T0[j], t1 = T1[j];
+          for (int i = j + lane; i < p; i += 32) {
+            double v = A[i * kLD + j];
+            v -= A[i * kLD + k] * t0;
+            v -= A[i * kLD + k + 1] * t1;
+            A[i * kLD + j] = v;
+          }
+        }
       }
       __syncthreads();
     }
-    // store L (lower triangle, row-major, stride kMaxLeaf)
+    // store the factor (L below the diagonal, D on it; row-major, stride kMaxLeaf)
     for (int e = tid; e < p * p; e += kLeafThreads) {
       int i = e / p, j = e - i * p;
       if (j <= i) Lout[i * kMaxLeaf + j] = A[i * kLD + j];
     }
-    // log det = 2 sum log L_ii, fixed order
+    // log det = sum log D_ii, fixed order
     double s = 0.0;
     for (int i = tid; i < p; i += kLeafThreads) s += log(A[i * kLD + i]);
     s = wsum(s);
@@ -174,7 +210,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
     if (tid == 0) {
       double t = 0.0;
       for (int q = 0; q < kLeafThreads / 32; ++q) t += red[q];
-      a.leaf_logdet[leaf] = 2.0 * t;
+      a.leaf_logdet[leaf] = t;
       if (bad) atomicOr(a.flags, kFlagNotSpd);
     }
   } else {
@@ -203,7 +239,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
         x[c][m] = i < p ? col[c][i] : 0.0;
       }
     }
-    warp_chol_solve<NC>(A, dinv, p, lane, x);
+    warp_ldl_solve<NC>(A, dinv, p, lane, x);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       if (c0 + c >= ncol) break;
