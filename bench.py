@@ -158,7 +158,7 @@ def run_ours(args):
     ctxs = []
     for kern, ell in KERNELS:
         ctxs.append(H.Hodlr(xd, kern, [ell, 1.0], SIGMA2, LEAF, EPS, max_rank=16, max_nrhs=1,
-                            stream=stream.cuda_stream))
+                            stream=stream.cuda_stream, precision=args.precision))
     outs = torch.zeros(len(KERNELS), dtype=torch.float64, device=dev)
 
     def step(leaf_ms=None):
@@ -319,6 +319,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy checks")
     ap.add_argument("--n", type=int, default=N, help="points (profiling captures only)")
+    ap.add_argument("--precision", type=int, default=0, help="0: FP64, 1: double-float leaf")
     args = ap.parse_args()
     N = args.n
     if args.warmup < 3 and args.impl == "ours":

@@ -56,7 +56,9 @@ typedef enum {
 } hodlr_kernel;
 
 typedef struct {
-  int precision;       /* 0: FP64 throughout (the only mode in this version)              */
+  int precision;       /* 0: FP64 throughout; 1: mixed: the leaf stage (block build,       */
+                       /*    L D L^T, panel solves) in double-float arithmetic on the FP32 */
+                       /*    pipe (~2^-48 unit roundoff), everything else FP64             */
   int rank_mode;       /* 0: adaptive ACA ranks                                            */
   int max_rank;        /* cap on the ACA rank of one off-diagonal block (1..64), default 64 */
   int max_nrhs;        /* right-hand sides carried through a fused factor, default 16     */

@@ -302,7 +302,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
       leaf > hodlr::kMaxLeaf || !(eps > 0) || !std::isfinite(eps) || !(sigma2 >= 0) ||
       !std::isfinite(sigma2) || bad_theta(theta) || (int)kernel < 0 || (int)kernel > 3 ||
       opts.max_rank < 1 || opts.max_rank > hodlr::kMaxRank || opts.max_nrhs < 1 ||
-      opts.precision != 0)
+      (opts.precision != 0 && opts.precision != 1))
     return HODLR_EINVAL;
   Ctx* c = new (std::nothrow) Ctx;
   if (!c) return HODLR_ENOMEM;
@@ -316,6 +316,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   c->leaf = leaf;
   c->max_rank = opts.max_rank;
   c->max_nrhs = opts.max_nrhs;
+  c->precision = opts.precision;
   c->stream = (cudaStream_t)opts.stream;
   c->kappa = kappa_for(n, leaf);
   auto bail = [&](hodlr_status s) {
@@ -456,7 +457,10 @@ static hodlr_status factor_impl(Ctx* c, int nrhs) {
   }
   TRY_CUDA(c, cudaMemsetAsync(c->dflags, 0, 4, c->stream), "flags");
   cudaEventRecord(c->ev[6], c->stream);
-  TRY_CUDA(c, hodlr::launch_leaf_factor(*c, nrhs), "leaf factor");
+  if (c->precision == 1)
+    TRY_CUDA(c, hodlr::launch_leaf_factor_ff(*c, nrhs, nullptr), "leaf factor (double-float)");
+  else
+    TRY_CUDA(c, hodlr::launch_leaf_factor(*c, nrhs), "leaf factor");
   cudaEventRecord(c->ev[7], c->stream);
   TRY_CUDA(c, hodlr::launch_levels(*c, nrhs, true), "levels");
   TRY_CUDA(c, hodlr::launch_logdet_sum(*c), "logdet");

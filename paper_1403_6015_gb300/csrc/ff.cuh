@@ -1,0 +1,145 @@
+// Double-float ("ff") arithmetic on the FP32 pipe: a value is the unevaluated sum hi + lo
+// of two floats with |lo| <= ulp(hi)/2, about 48 significant bits (unit roundoff ~2^-48).
+// On GB300 the FP32 pipe issues ~64x the operations of the FP64 pipe, so the dense leaf
+// work runs faster in ff than in native double while keeping ~1e-14 relative accuracy.
+//
+// Building blocks are the classic error-free transformations: Knuth's TwoSum, Dekker's
+// FastTwoSum, and the FMA-based exact product (TwoProd). The double-word operations follow
+// the algorithms analysed by Joldes, Muller and Popescu ("Tight and rigorous error bounds
+// for basic building blocks of double-word arithmetic", ACM TOMS 2017): products
+// (DWTimesDW with FMA) and the "sloppy" sum, whose error is bounded by a small multiple of
+// u^2 (|a| + |b|), the form that backward-stable factorizations rely on.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hodlr {
+
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+__device__ __forceinline__ ff ff_make(float h, float l) {
+  ff r;
+  fast_two_sum(h, l, r.hi, r.lo);
+  return r;
+}
+
+__device__ __forceinline__ ff ff_from_double(double d) {
+  ff r;
+  r.hi = __double2float_rn(d);
+  r.lo = __double2float_rn(d - (double)r.hi);
+  return r;
+}
+
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+
+// a + b, sloppy double-word sum
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  ff r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+
+// a * b, double-word product with FMA
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  ff r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+
+// c - a * b in one pass (exact leading product, sloppy sum)
+__device__ __forceinline__ ff ff_fms(ff c, ff a, ff b) {
+  float p = a.hi * b.hi;
+  float pe = fmaf(a.hi, b.hi, -p);
+  pe = fmaf(a.hi, b.lo, pe);
+  pe = fmaf(a.lo, b.hi, pe);
+  float s, e;
+  two_sum(c.hi, -p, s, e);
+  e += c.lo - pe;
+  ff r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+// c + a * b
+__device__ __forceinline__ ff ff_fma(ff c, ff a, ff b) { return ff_fms(c, ff_neg(a), b); }
+
+// a * f for a float f
+__device__ __forceinline__ ff ff_mulf(ff a, float f) {
+  float p = a.hi * f;
+  float e = fmaf(a.hi, f, -p);
+  e = fmaf(a.lo, f, e);
+  ff r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+
+// 1 / a: float reciprocal refined by one Newton step in double-word arithmetic
+__device__ __forceinline__ ff ff_rcp(ff a) {
+  float x = 1.0f / a.hi;
+  // residual 1 - a x, computed to double-word accuracy
+  ff ax = ff_mulf(a, x);
+  ff res = ff_sub(ff{1.0f, 0.0f}, ax);
+  // x + x * res
+  float corr = x * res.hi;
+  return ff_make(x, corr);
+}
+
+// exp(x) for a double-float x <= ~0 (covariances use exp of minus a distance). Reduction
+// x = n ln2/64 + r, |r| <= ln2/128 (Cody-Waite: ln2/64 = L1 + L2 with L1 holding 11
+// significant bits so n L1 is exact for |n| < 2^13, L2 a double-float), then
+// exp(x) = 2^(n div 64) 2^((n mod 64)/64) exp(r), exp(r) by its Taylor series to degree 6
+// in double-word arithmetic (remainder below 3e-20). tab64[j] = 2^(j/64) as double-floats.
+// Arguments below -87 return 0 (the covariances they model are below 2^-125).
+__device__ __forceinline__ ff ff_exp(ff x, const ff* __restrict__ tab64) {
+  if (x.hi < -87.0f) return ff{0.0f, 0.0f};
+  const float kInvL = 92.33248f;             // 64 / ln2
+  const float kL1 = 0.010833740234375f;      // 11-bit head of ln2/64
+  const ff kL2 = {-3.3155381515825866e-06f, 2.572804640231345e-14f};  // ln2/64 - kL1
+  float nf = rintf(x.hi * kInvL);
+  int n = (int)nf;
+  ff r = ff_add(x, ff{-nf * kL1, 0.0f});
+  r = ff_fms(r, ff{nf, 0.0f}, kL2);
+  // 1/k! as double-floats, k = 0..6
+  const ff c2 = {0.5f, 0.0f};
+  const ff c3 = {0.1666666716337204f, -4.967053879312289e-09f};
+  const ff c4 = {0.0416666679084301f, -1.2417634698280722e-09f};
+  const ff c5 = {0.008333333767950535f, -4.34617203337595e-10f};
+  const ff c6 = {0.0013888889225199819f, -3.3631094437103215e-11f};
+  ff q = ff_fma(c5, c6, r);
+  q = ff_fma(c4, q, r);
+  q = ff_fma(c3, q, r);
+  q = ff_fma(c2, q, r);
+  q = ff_fma(ff{1.0f, 0.0f}, q, r);
+  q = ff_fma(ff{1.0f, 0.0f}, q, r);
+  int j = n & 63;
+  int k = (n - j) / 64;
+  ff t = ff_mul(q, tab64[j]);
+  float sc = ldexpf(1.0f, k);
+  return ff{t.hi * sc, t.lo * sc};
+}
+
+}  // namespace hodlr

@@ -81,6 +81,7 @@ struct Ctx {
   int kind = 0;
   double ell = 1, amp = 1, sigma2 = 0, eps = 1e-12;
   int leaf = 128, kappa = 0, max_rank = kMaxRank, max_nrhs = 16;
+  int precision = 0;              // 0: FP64, 1: double-float leaf stage (mixed)
   cudaStream_t stream = nullptr;
   int device = 0;
   int sms = 152;
@@ -170,6 +171,7 @@ cudaError_t launch_pack(Ctx& c);
 cudaError_t launch_gather_rhs(Ctx& c, const double* y, int64_t ld, int nrhs);
 cudaError_t launch_scatter_rhs(Ctx& c, double* x, int64_t ld, int nrhs);
 cudaError_t launch_leaf_factor(Ctx& c, int nrhs);
+cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs, double* leafC);
 cudaError_t launch_leaf_solve(Ctx& c, int nrhs);
 cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode);
 cudaError_t launch_logdet_sum(Ctx& c);

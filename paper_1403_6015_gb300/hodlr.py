@@ -191,7 +191,8 @@ class Hodlr:
     """
 
     def __init__(self, x, kernel: str, theta, sigma2: float, leaf: int, eps: float,
-                 max_rank: int = 64, max_nrhs: int = 16, stream=None, allow_rank_cap=False):
+                 max_rank: int = 64, max_nrhs: int = 16, stream=None, allow_rank_cap=False,
+                 precision: int = 0):
         if _is_torch(x):
             if x.dtype.itemsize != 8 or not x.is_contiguous():
                 raise ValueError("x must be a contiguous float64 tensor")
@@ -205,6 +206,7 @@ class Hodlr:
         o = hodlr_default_opts()
         o.max_rank = max_rank
         o.max_nrhs = max_nrhs
+        o.precision = precision
         if stream is not None:
             o.stream = stream
         self.kernel = kernel
