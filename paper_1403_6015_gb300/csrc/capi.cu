@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -317,6 +318,8 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   c->max_rank = opts.max_rank;
   c->max_nrhs = opts.max_nrhs;
   c->precision = opts.precision;
+  if (const char* e = std::getenv("HODLR_LEAF_THREADS")) c->leaf_threads = std::atoi(e);
+  if (const char* e = std::getenv("HODLR_LEAF_THREADS64")) c->leaf_threads64 = std::atoi(e);
   c->stream = (cudaStream_t)opts.stream;
   c->kappa = kappa_for(n, leaf);
   auto bail = [&](hodlr_status s) {

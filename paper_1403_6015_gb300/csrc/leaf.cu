@@ -18,7 +18,6 @@
 namespace hodlr {
 namespace {
 
-constexpr int kLeafThreads = 256;
 constexpr int kLD = kMaxLeaf + 1;
 
 struct LeafArgs {
@@ -105,7 +104,7 @@ __device__ __forceinline__ void warp_ldl_solve(const double* __restrict__ A,
   }
 }
 
-template <bool kFactor>
+template <bool kFactor, int kLeafThreads>
 __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
   extern __shared__ double A[];  // [kMaxLeaf][kLD]
   __shared__ double xl[2 * kMaxLeaf];
@@ -300,22 +299,35 @@ LeafArgs make_args(Ctx& c, int nrhs, bool factor) {
 
 }  // namespace
 
+template <bool kFactor>
+cudaError_t launch_leaf(const LeafArgs& a, unsigned grid, int threads, cudaStream_t s) {
+  size_t smem = sizeof(double) * kMaxLeaf * kLD;
+  switch (threads) {
+    case 1024:
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf<kFactor, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_leaf<kFactor, 1024><<<grid, 1024, smem, s>>>(a);
+      break;
+    case 512:
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf<kFactor, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_leaf<kFactor, 512><<<grid, 512, smem, s>>>(a);
+      break;
+    default:
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf<kFactor, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_leaf<kFactor, 256><<<grid, 256, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_leaf_factor(Ctx& c, int nrhs) {
   LeafArgs a = make_args(c, nrhs, true);
-  size_t smem = sizeof(double) * kMaxLeaf * kLD;
-  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_leaf<true><<<1u << c.kappa, kLeafThreads, smem, c.stream>>>(a);
   ++c.launches;
-  return cudaGetLastError();
+  return launch_leaf<true>(a, 1u << c.kappa, c.leaf_threads64, c.stream);
 }
 
 cudaError_t launch_leaf_solve(Ctx& c, int nrhs) {
   LeafArgs a = make_args(c, nrhs, false);
-  size_t smem = sizeof(double) * kMaxLeaf * kLD;
-  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_leaf<false><<<1u << c.kappa, kLeafThreads, smem, c.stream>>>(a);
   ++c.launches;
-  return cudaGetLastError();
+  return launch_leaf<false>(a, 1u << c.kappa, c.leaf_threads64, c.stream);
 }
 
 }  // namespace hodlr
@@ -349,10 +361,7 @@ cudaError_t launch_leaf_single(const double* xs_soa, int n, int d, int kind, dou
   a.leaf_logdet = logdet;
   a.flags = flags;
   a.n = n;
-  size_t smem = sizeof(double) * kMaxLeaf * kLD;
-  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_leaf<true><<<1, kLeafThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_leaf<true>(a, 1, 256, s);
 }
 
 }  // namespace hodlr

@@ -16,7 +16,6 @@
 namespace hodlr {
 namespace {
 
-constexpr int kT = 256;
 constexpr int kLD = kMaxLeaf + 1;
 
 struct LeafFFArgs {
@@ -126,6 +125,7 @@ __device__ __forceinline__ void warp_ldl_solve_ff(const ff* __restrict__ A,
   }
 }
 
+template <int kT>
 __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
   extern __shared__ ff A[];  // [kMaxLeaf][kLD]
   __shared__ ff xl[2 * kMaxLeaf];
@@ -330,8 +330,20 @@ cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs, double* leafC) {
   a.leaf_logdet = c.leaf_logdet;
   a.flags = c.dflags;
   size_t smem = sizeof(ff) * kMaxLeaf * kLD;
-  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_leaf_ff<<<1u << c.kappa, kT, smem, c.stream>>>(a);
+  unsigned grid = 1u << c.kappa;
+  switch (c.leaf_threads) {
+    case 1024:
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_leaf_ff<1024><<<grid, 1024, smem, c.stream>>>(a);
+      break;
+    case 256:
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_leaf_ff<256><<<grid, 256, smem, c.stream>>>(a);
+      break;
+    default:
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_leaf_ff<512><<<grid, 512, smem, c.stream>>>(a);
+  }
   ++c.launches;
   return cudaGetLastError();
 }
