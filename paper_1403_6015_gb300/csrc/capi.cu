@@ -461,7 +461,7 @@ static hodlr_status factor_impl(Ctx* c, int nrhs) {
   TRY_CUDA(c, cudaMemsetAsync(c->dflags, 0, 4, c->stream), "flags");
   cudaEventRecord(c->ev[6], c->stream);
   if (c->precision == 1)
-    TRY_CUDA(c, hodlr::launch_leaf_factor_ff(*c, nrhs, nullptr), "leaf factor (double-float)");
+    TRY_CUDA(c, hodlr::launch_leaf_factor_ff(*c, nrhs), "leaf factor (double-float)");
   else
     TRY_CUDA(c, hodlr::launch_leaf_factor(*c, nrhs), "leaf factor");
   cudaEventRecord(c->ev[7], c->stream);
@@ -513,7 +513,10 @@ hodlr_status hodlr_solve(hodlr_ctx* ctx, const double* y, double* x, int nrhs, i
     if (s != HODLR_OK) return s;
     cudaEventRecord(c->ev[4], c->stream);
     TRY_CUDA(c, hodlr::launch_gather_rhs(*c, yd, ldd, nb), "gather");
-    TRY_CUDA(c, hodlr::launch_leaf_solve(*c, nb), "leaf solve");
+    if (c->precision == 1)
+      TRY_CUDA(c, hodlr::launch_leaf_solve_ff(*c, nb), "leaf solve (double-float)");
+    else
+      TRY_CUDA(c, hodlr::launch_leaf_solve(*c, nb), "leaf solve");
     TRY_CUDA(c, hodlr::launch_levels(*c, nb, false), "levels");
     cudaEventRecord(c->ev[5], c->stream);
     c->solve_timed = true;
@@ -553,7 +556,10 @@ hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out) {
     s = factor_impl(c, 1);
     if (s != HODLR_OK) return s;
   } else {
-    TRY_CUDA(c, hodlr::launch_leaf_solve(*c, 1), "leaf solve");
+    if (c->precision == 1)
+      TRY_CUDA(c, hodlr::launch_leaf_solve_ff(*c, 1), "leaf solve (double-float)");
+    else
+      TRY_CUDA(c, hodlr::launch_leaf_solve(*c, 1), "leaf solve");
     TRY_CUDA(c, hodlr::launch_levels(*c, 1, false), "levels");
   }
   TRY_CUDA(c, hodlr::launch_quad_loglik(*c), "loglik");

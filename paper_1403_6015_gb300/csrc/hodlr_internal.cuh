@@ -72,7 +72,8 @@ enum : int { kFlagNotSpd = 1, kFlagRankCap = 2, kFlagTimeout = 4 };
 //   phi      n x R   original U/V of every level, level j at columns [coff_j, coff_j + r_j)
 //   pan      n x R   working copy; after factor it holds Ut/Vt (finer inverses applied)
 //   Y        n x max_nrhs right-hand sides in sorted order (overwritten by C^-1 y)
-//   leafL    2^kappa x 128 x 128 Cholesky factors of the leaf blocks (row-major, lower)
+//   leafL    2^kappa x 128 x 128 L D L^T factors of the leaf blocks (row-major, lower;
+//            FP64, or double-float pairs in the mixed form)
 // ---------------------------------------------------------------------------------------
 struct Ctx {
   // problem
@@ -173,7 +174,8 @@ cudaError_t launch_pack(Ctx& c);
 cudaError_t launch_gather_rhs(Ctx& c, const double* y, int64_t ld, int nrhs);
 cudaError_t launch_scatter_rhs(Ctx& c, double* x, int64_t ld, int nrhs);
 cudaError_t launch_leaf_factor(Ctx& c, int nrhs);
-cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs, double* leafC);
+cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs);
+cudaError_t launch_leaf_solve_ff(Ctx& c, int nrhs);
 cudaError_t launch_leaf_solve(Ctx& c, int nrhs);
 cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode);
 cudaError_t launch_logdet_sum(Ctx& c);

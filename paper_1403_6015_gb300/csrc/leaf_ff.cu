@@ -2,12 +2,19 @@
 //
 // Same work as k_leaf (Sec. 3.2: factor K_kappa out of C, applying each leaf inverse to the
 // ancestors' U/V rows and to the right-hand sides; Sec. 4: leaf determinants), but every
-// operation on the leaf block runs in double-float (ff.cuh) on the FP32 pipe: the block is
-// built from the points with a double-float exp, factored as L D L^T, and applied to the
-// panel columns. Values enter and leave HBM as FP64; the log of each pivot is taken in
-// FP64. Unit roundoff ~2^-48 instead of 2^-53, at several times the FP64 throughput of
-// GB300. If leafC is given, the assembled block of C is also stored (FP64) for the
-// iterative-refinement residual.
+// operation on the leaf block runs in double-float (ff.cuh) on the FP32 pipe. Values enter
+// and leave HBM as FP64; the stored factor is kept as double-float pairs; the log of each
+// pivot is taken in FP64. Unit roundoff ~2^-48 instead of 2^-53.
+//
+// Blocked for the FP32 pipe (one CTA per leaf, all of it in shared memory):
+//   - the block is padded to P = 32 ceil(p / 32) with the identity, which changes neither
+//     the factor of the leading p x p block, the solutions, nor the log det;
+//   - L D L^T by 32-column panels: inside a panel, two columns per step (three barriers
+//     per pair; the next pair's first pivot is computed by the thread that updates it);
+//     below it, the trailing matrix is updated in 2 x 2 register tiles (32-term dots);
+//   - the panel columns and right-hand sides are solved in chunks of 32 columns held in
+//     shared memory: 32 x 32 diagonal blocks by one warp per column, the rest as dense
+//     updates with one thread per output element.
 #include <cuda_runtime.h>
 
 #include "ff.cuh"
@@ -16,7 +23,9 @@
 namespace hodlr {
 namespace {
 
-constexpr int kLD = kMaxLeaf + 1;
+constexpr int kLD = kMaxLeaf + 1;  // row stride of the block
+constexpr int kBS = 33;            // row stride of the 32-column buffers
+constexpr int kCW = 32;            // columns per solve chunk
 
 struct LeafFFArgs {
   const double* x;
@@ -36,8 +45,7 @@ struct LeafFFArgs {
   int coff, rl;
   double* part;
   int64_t part_stride;
-  double* leafL;
-  double* leafC;
+  ff* leafL;          // stored factor: L below the diagonal, D on it (double-float pairs)
   double* leaf_logdet;
   int32_t* flags;
 };
@@ -64,252 +72,296 @@ __device__ __forceinline__ ff shfl_ff(ff v, int src) {
   return ff{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
 }
 
-__device__ __forceinline__ ff wsum_ff(ff v) {
-  for (int o = 16; o > 0; o >>= 1) {
-    ff t = ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-    v = ff_add(v, t);
-  }
-  return v;
+__device__ __forceinline__ ff xor_ff(ff v, int m) {
+  return ff{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
 }
 
-// L D L^T x = b for NC columns held by a warp (element i of column c in lane i % 32,
-// slot i / 32); L unit lower below the diagonal of A, dinv = 1 / D.
-template <int NC>
-__device__ __forceinline__ void warp_ldl_solve_ff(const ff* __restrict__ A,
-                                                  const ff* __restrict__ dinv, int p, int lane,
-                                                  ff (&x)[NC][4]) {
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    for (int kk = 0; kk < 32; ++kk) {
-      int k = s * 32 + kk;
-      if (k >= p) break;
-      ff wk[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) wk[c] = shfl_ff(x[c][s], kk);
-#pragma unroll
-      for (int m = s; m < 4; ++m) {
-        int i = m * 32 + lane;
-        if (i > k && i < p) {
-          ff lik = A[i * kLD + k];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) x[c][m] = ff_fms(x[c][m], lik, wk[c]);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    int i = m * 32 + lane;
-    ff di = i < p ? dinv[i] : ff{0.0f, 0.0f};
-#pragma unroll
-    for (int c = 0; c < NC; ++c) x[c][m] = ff_mul(x[c][m], di);
-  }
-#pragma unroll
-  for (int s = 3; s >= 0; --s) {
-    for (int kk = 31; kk >= 0; --kk) {
-      int k = s * 32 + kk;
-      if (k >= p) continue;
-      ff xk[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) xk[c] = shfl_ff(x[c][s], kk);
-#pragma unroll
-      for (int m = 0; m <= s; ++m) {
-        int i = m * 32 + lane;
-        if (i < k) {
-          ff lki = A[k * kLD + i];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) x[c][m] = ff_fms(x[c][m], lki, xk[c]);
-        }
-      }
-    }
-  }
+// Row of the lower-triangle element with linear index e (row-major, diagonal included).
+__device__ __forceinline__ int tri_row(int e) {
+  int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (i * (i + 1) / 2 > e) --i;
+  while ((i + 1) * (i + 2) / 2 <= e) ++i;
+  return i;
 }
 
-template <int kT>
+template <int kT, bool kFactor>
 __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
-  extern __shared__ ff A[];  // [kMaxLeaf][kLD]
+  extern __shared__ ff sm[];
+  ff* A = sm;                          // [kMaxLeaf][kLD]
+  ff* Up = A + kMaxLeaf * kLD;         // [kMaxLeaf][kBS] unscaled panel columns
+  ff* B = Up + kMaxLeaf * kBS;         // [kMaxLeaf][kBS] solve chunk
   __shared__ ff xl[2 * kMaxLeaf];
   __shared__ ff dinv[kMaxLeaf];
-  __shared__ ff T0[kMaxLeaf], T1[kMaxLeaf];
   __shared__ ff tab[64];
+  __shared__ ff pinv[2];
   __shared__ double red[kT / 32];
-  __shared__ ff piv_inv[2], piv_t;
   __shared__ int bad;
+  constexpr int NW = kT / 32;
   int leaf = blockIdx.x;
   int id = a.leaf0 + leaf;
   int b = a.nb[id], p = a.ns[id];
+  int P = (p + 31) & ~31, NB = P / 32;
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (tid == 0) bad = 0;
-  if (tid < 64) tab[tid] = ff_from_double(exp2((double)tid / 64.0));
-  // coordinates relative to the leaf's first point: the FP64 subtraction keeps the small
-  // offsets (and so the distances) to full relative precision in double-float
-  for (int i = tid; i < p; i += kT) {
-    xl[i] = ff_from_double(a.x[b + i] - a.x[b]);
-    if (a.d == 2) xl[kMaxLeaf + i] = ff_from_double(a.x[a.n + b + i] - a.x[a.n + b]);
-  }
-  __syncthreads();
-  const ff cr = ff_from_double(a.cr), amp = ff_from_double(a.amp), s2 = ff_from_double(a.sigma2);
-  // lower triangle of the leaf block of C
-  for (int e = tid; e < p * p; e += kT) {
-    int i = e / p, j = e - i * p;
-    if (j > i) continue;
-    ff r;
-    if (a.d == 1) {
-      r = ff_sub(xl[i], xl[j]);
-      if (r.hi < 0.0f) r = ff_neg(r);
-    } else {
-      ff u = ff_sub(xl[i], xl[j]), v = ff_sub(xl[kMaxLeaf + i], xl[kMaxLeaf + j]);
-      ff q = ff_add(ff_mul(u, u), ff_mul(v, v));
-      // sqrt in double-float: float sqrt refined by one Newton step
-      float h = sqrtf(q.hi);
-      if (h > 0.0f) {
-        ff hh = ff_mul(ff{h, 0.0f}, ff{h, 0.0f});
-        ff res = ff_sub(q, hh);
-        r = ff_make(h, res.hi / (2.0f * h));
+  ff* Lst = a.leafL + (int64_t)leaf * kMaxLeaf * kMaxLeaf;
+  if (kFactor) {
+    if (tid == 0) bad = 0;
+    if (tid < 64) tab[tid] = ff_from_double(exp2((double)tid / 64.0));
+    // coordinates relative to the leaf's first point (keeps small offsets exact)
+    for (int i = tid; i < p; i += kT) {
+      xl[i] = ff_from_double(a.x[b + i] - a.x[b]);
+      if (a.d == 2) xl[kMaxLeaf + i] = ff_from_double(a.x[a.n + b + i] - a.x[a.n + b]);
+    }
+    __syncthreads();
+    const ff cr = ff_from_double(a.cr), amp = ff_from_double(a.amp);
+    const ff s2 = ff_from_double(a.sigma2);
+    // lower triangle of the padded block
+    for (int e = tid; e < P * (P + 1) / 2; e += kT) {
+      int i = tri_row(e), j = e - i * (i + 1) / 2;
+      ff c;
+      if (i < p) {
+        ff r;
+        if (a.d == 1) {
+          r = ff_sub(xl[i], xl[j]);
+          if (r.hi < 0.0f) r = ff_neg(r);
+        } else {
+          ff u = ff_sub(xl[i], xl[j]), v = ff_sub(xl[kMaxLeaf + i], xl[kMaxLeaf + j]);
+          ff q = ff_add(ff_mul(u, u), ff_mul(v, v));
+          float h = sqrtf(q.hi);
+          if (h > 0.0f) {
+            ff res = ff_sub(q, ff_mul(ff{h, 0.0f}, ff{h, 0.0f}));
+            r = ff_make(h, res.hi / (2.0f * h));
+          } else {
+            r = ff{0.0f, 0.0f};
+          }
+        }
+        c = cov_ff(a.kind, r, cr, amp, tab);
+        if (i == j) c = ff_add(c, s2);
       } else {
-        r = ff{0.0f, 0.0f};
+        c = ff{i == j ? 1.0f : 0.0f, 0.0f};
       }
+      A[i * kLD + j] = c;
     }
-    ff c = cov_ff(a.kind, r, cr, amp, tab);
-    if (i == j) c = ff_add(c, s2);
-    A[i * kLD + j] = c;
-  }
-  __syncthreads();
-  if (a.leafC) {
-    double* Cout = a.leafC + (int64_t)leaf * kMaxLeaf * kMaxLeaf;
-    for (int e = tid; e < p * p; e += kT) {
-      int i = e / p, j = e - i * p;
-      Cout[i * kMaxLeaf + j] = ff_to_double(j <= i ? A[i * kLD + j] : A[j * kLD + i]);
-    }
-  }
-  // L D L^T, two pivots per step (as in the FP64 leaf kernel)
-  for (int k = 0; k < p; k += 2) {
-    bool two = k + 1 < p;
-    if (tid == 0) {
-      ff dk = A[k * kLD + k];
-      if (!(dk.hi > 0.0f)) {
-        bad = 1;
-        dk = ff{1.0f, 0.0f};
-      }
-      A[k * kLD + k] = dk;
-      ff ik = ff_rcp(dk);
-      piv_inv[0] = ik;
-      if (two) {
-        ff t = A[(k + 1) * kLD + k];
-        ff l = ff_mul(t, ik);
-        A[(k + 1) * kLD + k] = l;
-        ff d1 = ff_fms(A[(k + 1) * kLD + k + 1], l, t);
-        if (!(d1.hi > 0.0f)) {
+    __syncthreads();
+    // blocked L D L^T
+    for (int J = 0; J < NB; ++J) {
+      int c0 = 32 * J;
+      if (tid == 0) {
+        ff dk = A[c0 * kLD + c0];
+        if (!(dk.hi > 0.0f)) {
           bad = 1;
-          d1 = ff{1.0f, 0.0f};
+          dk = ff{1.0f, 0.0f};
+          A[c0 * kLD + c0] = dk;
         }
-        A[(k + 1) * kLD + k + 1] = d1;
-        piv_inv[1] = ff_rcp(d1);
-        piv_t = t;
+        pinv[0] = ff_rcp(dk);
       }
-    }
-    __syncthreads();
-    ff i0v = piv_inv[0];
-    for (int i = k + 2 + tid; i < p; i += kT) {
-      ff t = A[i * kLD + k];
-      ff l = ff_mul(t, i0v);
-      A[i * kLD + k] = l;
-      T0[i] = t;
-      if (two) {
-        ff u = ff_fms(A[i * kLD + k + 1], l, piv_t);
-        A[i * kLD + k + 1] = ff_mul(u, piv_inv[1]);
-        T1[i] = u;
-      }
-    }
-    __syncthreads();
-    if (two) {
-      for (int j = k + 2 + w; j < p; j += kT / 32) {
-        ff t0 = T0[j], t1 = T1[j];
-        for (int i = j + lane; i < p; i += 32) {
-          ff v = A[i * kLD + j];
-          v = ff_fms(v, A[i * kLD + k], t0);
-          v = ff_fms(v, A[i * kLD + k + 1], t1);
-          A[i * kLD + j] = v;
+      __syncthreads();
+      // panel, two columns (col, col + 1) per step: pinv[0] holds 1 / D_col on entry
+      for (int c = 0; c < 32; c += 2) {
+        int col = c0 + c;
+        // the second pivot of the pair: D_{col+1} = A_{col+1,col+1} - L_{col+1,col} A_{col+1,col}
+        if (tid == 0) {
+          ff t = A[(col + 1) * kLD + col];
+          ff l = ff_mul(t, pinv[0]);
+          A[(col + 1) * kLD + col] = l;
+          Up[(col + 1) * kBS + c] = t;
+          ff d1 = ff_fms(A[(col + 1) * kLD + col + 1], l, t);
+          if (!(d1.hi > 0.0f)) {
+            bad = 1;
+            d1 = ff{1.0f, 0.0f};
+          }
+          A[(col + 1) * kLD + col + 1] = d1;
+          pinv[1] = ff_rcp(d1);
         }
+        __syncthreads();
+        // rows below the pair: scale both columns, keep the unscaled values
+        ff iv0 = pinv[0], iv1 = pinv[1], t10 = Up[(col + 1) * kBS + c];
+        for (int i = col + 2 + tid; i < P; i += kT) {
+          ff t = A[i * kLD + col];
+          ff l = ff_mul(t, iv0);
+          A[i * kLD + col] = l;
+          Up[i * kBS + c] = t;
+          ff u = ff_fms(A[i * kLD + col + 1], l, t10);
+          A[i * kLD + col + 1] = ff_mul(u, iv1);
+          Up[i * kBS + c + 1] = u;
+        }
+        __syncthreads();
+        // update the remaining panel columns cc in [c + 2, 32) on rows >= c0 + cc; warps
+        // take columns, lanes take rows; the next pair's first pivot by its updater
+        for (int cc = c + 2 + w; cc < 32; cc += NW) {
+          int jc = c0 + cc;
+          ff uj0 = Up[jc * kBS + c], uj1 = Up[jc * kBS + c + 1];
+          for (int i = jc + lane; i < P; i += 32) {
+            ff v = ff_fms(A[i * kLD + jc], A[i * kLD + col], uj0);
+            v = ff_fms(v, A[i * kLD + col + 1], uj1);
+            if (i == jc && cc == c + 2) {
+              if (!(v.hi > 0.0f)) {
+                bad = 1;
+                v = ff{1.0f, 0.0f};
+              }
+              pinv[0] = ff_rcp(v);
+            }
+            A[i * kLD + jc] = v;
+          }
+        }
+        __syncthreads();
       }
+      // trailing update of rows/columns [c0 + 32, P): A_ij -= sum_c L_ic U_jc, 2 x 2 tiles
+      int r0 = c0 + 32;
+      int M = (P - r0) / 2;
+      for (int e = tid; e < M * (M + 1) / 2; e += kT) {
+        int ti = tri_row(e), tj = e - ti * (ti + 1) / 2;
+        int i0 = r0 + 2 * ti, j0 = r0 + 2 * tj;
+        ff s00a = {0, 0}, s01a = {0, 0}, s10a = {0, 0}, s11a = {0, 0};
+        ff s00b = {0, 0}, s01b = {0, 0}, s10b = {0, 0}, s11b = {0, 0};
+#pragma unroll 4
+        for (int c = 0; c < 32; c += 2) {
+          ff l0 = A[i0 * kLD + c0 + c], l1 = A[(i0 + 1) * kLD + c0 + c];
+          ff u0 = Up[j0 * kBS + c], u1 = Up[(j0 + 1) * kBS + c];
+          s00a = ff_fma(s00a, l0, u0);
+          s01a = ff_fma(s01a, l0, u1);
+          s10a = ff_fma(s10a, l1, u0);
+          s11a = ff_fma(s11a, l1, u1);
+          ff m0 = A[i0 * kLD + c0 + c + 1], m1 = A[(i0 + 1) * kLD + c0 + c + 1];
+          ff v0 = Up[j0 * kBS + c + 1], v1 = Up[(j0 + 1) * kBS + c + 1];
+          s00b = ff_fma(s00b, m0, v0);
+          s01b = ff_fma(s01b, m0, v1);
+          s10b = ff_fma(s10b, m1, v0);
+          s11b = ff_fma(s11b, m1, v1);
+        }
+        A[i0 * kLD + j0] = ff_sub(A[i0 * kLD + j0], ff_add(s00a, s00b));
+        A[(i0 + 1) * kLD + j0] = ff_sub(A[(i0 + 1) * kLD + j0], ff_add(s10a, s10b));
+        A[(i0 + 1) * kLD + j0 + 1] = ff_sub(A[(i0 + 1) * kLD + j0 + 1], ff_add(s11a, s11b));
+        if (ti != tj) A[i0 * kLD + j0 + 1] = ff_sub(A[i0 * kLD + j0 + 1], ff_add(s01a, s01b));
+      }
+      __syncthreads();
+    }
+    // store the factor (leading p x p lower triangle)
+    for (int e = tid; e < p * (p + 1) / 2; e += kT) {
+      int i = tri_row(e), j = e - i * (i + 1) / 2;
+      Lst[i * kMaxLeaf + j] = A[i * kLD + j];
+    }
+  } else {
+    for (int e = tid; e < P * (P + 1) / 2; e += kT) {
+      int i = tri_row(e), j = e - i * (i + 1) / 2;
+      A[i * kLD + j] = i < p ? Lst[i * kMaxLeaf + j] : ff{i == j ? 1.0f : 0.0f, 0.0f};
     }
     __syncthreads();
   }
-  double* Lout = a.leafL + (int64_t)leaf * kMaxLeaf * kMaxLeaf;
-  for (int e = tid; e < p * p; e += kT) {
-    int i = e / p, j = e - i * p;
-    if (j <= i) Lout[i * kMaxLeaf + j] = ff_to_double(A[i * kLD + j]);
-  }
+  // log det = sum log D_ii (FP64), 1 / D
   double sl = 0.0;
-  for (int i = tid; i < p; i += kT) sl += log(ff_to_double(A[i * kLD + i]));
-  for (int o = 16; o > 0; o >>= 1) sl += __shfl_xor_sync(0xffffffffu, sl, o);
-  if (lane == 0) red[w] = sl;
-  for (int i = tid; i < p; i += kT) dinv[i] = ff_rcp(A[i * kLD + i]);
+  for (int i = tid; i < p; i += kT) {
+    ff di = A[i * kLD + i];
+    if (kFactor) sl += log(ff_to_double(di));
+    dinv[i] = ff_rcp(di);
+  }
+  for (int i = p + tid; i < P; i += kT) dinv[i] = ff{1.0f, 0.0f};
+  if (kFactor) {
+    for (int o = 16; o > 0; o >>= 1) sl += __shfl_xor_sync(0xffffffffu, sl, o);
+    if (lane == 0) red[w] = sl;
+  }
   __syncthreads();
-  if (tid == 0) {
+  if (kFactor && tid == 0) {
     double t = 0.0;
-    for (int q = 0; q < kT / 32; ++q) t += red[q];
+    for (int q = 0; q < NW; ++q) t += red[q];
     a.leaf_logdet[leaf] = t;
     if (bad) atomicOr(a.flags, kFlagNotSpd);
   }
+  // solves, 32 columns at a time: panel [0, cP) then right-hand sides [0, nrhs)
   int ncol = a.cP + a.nrhs;
-  constexpr int NC = 2;
-  for (int c0 = w * NC; c0 < ncol; c0 += NC * (kT / 32)) {
-    double* col[NC];
-    ff x[NC][4];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      int cc = c0 + c < ncol ? c0 + c : c0;
-      col[c] = cc < a.cP ? a.pan + (int64_t)cc * a.n + b : a.Y + (int64_t)(cc - a.cP) * a.n + b;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        int i = m * 32 + lane;
-        x[c][m] = i < p ? ff_from_double(col[c][i]) : ff{0.0f, 0.0f};
-      }
+  for (int q0 = 0; q0 < ncol; q0 += kCW) {
+    int cw = ncol - q0 < kCW ? ncol - q0 : kCW;
+    for (int e = tid; e < P * cw; e += kT) {
+      int c = e / P, i = e - c * P;
+      int q = q0 + c;
+      const double* col = q < a.cP ? a.pan + (int64_t)q * a.n + b : a.Y + (int64_t)(q - a.cP) * a.n + b;
+      B[i * kBS + c] = i < p ? ff_from_double(col[i]) : ff{0.0f, 0.0f};
     }
-    warp_ldl_solve_ff<NC>(A, dinv, p, lane, x);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if (c0 + c >= ncol) break;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        int i = m * 32 + lane;
-        if (i < p) col[c][i] = ff_to_double(x[c][m]);
+    __syncthreads();
+    // forward: L w = b
+    for (int J = 0; J < NB; ++J) {
+      int c0 = 32 * J;
+      for (int c = w; c < cw; c += NW) {
+        ff xv = B[(c0 + lane) * kBS + c];
+        for (int k = 0; k < 32; ++k) {
+          ff xk = shfl_ff(xv, k);
+          if (lane > k) xv = ff_fms(xv, A[(c0 + lane) * kLD + c0 + k], xk);
+        }
+        B[(c0 + lane) * kBS + c] = xv;
       }
+      __syncthreads();
+      int r0 = c0 + 32;
+      for (int e = tid; e < (P - r0) * cw; e += kT) {
+        int i = r0 + e / cw, c = e - (e / cw) * cw;
+        ff sa = {0, 0}, sb = {0, 0};
+#pragma unroll 4
+        for (int k = 0; k < 32; k += 2) {
+          sa = ff_fma(sa, A[i * kLD + c0 + k], B[(c0 + k) * kBS + c]);
+          sb = ff_fma(sb, A[i * kLD + c0 + k + 1], B[(c0 + k + 1) * kBS + c]);
+        }
+        B[i * kBS + c] = ff_sub(B[i * kBS + c], ff_add(sa, sb));
+      }
+      __syncthreads();
+    }
+    // v = D^-1 w
+    for (int e = tid; e < P * cw; e += kT) {
+      int i = e / cw, c = e - i * cw;
+      B[i * kBS + c] = ff_mul(B[i * kBS + c], dinv[i]);
+    }
+    __syncthreads();
+    // backward: L^T x = v
+    for (int J = NB - 1; J >= 0; --J) {
+      int c0 = 32 * J;
+      for (int c = w; c < cw; c += NW) {
+        ff xv = B[(c0 + lane) * kBS + c];
+        for (int k = 31; k >= 0; --k) {
+          ff xk = shfl_ff(xv, k);
+          if (lane < k) xv = ff_fms(xv, A[(c0 + k) * kLD + c0 + lane], xk);
+        }
+        B[(c0 + lane) * kBS + c] = xv;
+      }
+      __syncthreads();
+      for (int e = tid; e < c0 * cw; e += kT) {
+        int i = e / cw, c = e - i * cw;
+        ff sa = {0, 0}, sb = {0, 0};
+#pragma unroll 4
+        for (int k = 0; k < 32; k += 2) {
+          sa = ff_fma(sa, A[(c0 + k) * kLD + i], B[(c0 + k) * kBS + c]);
+          sb = ff_fma(sb, A[(c0 + k + 1) * kLD + i], B[(c0 + k + 1) * kBS + c]);
+        }
+        B[i * kBS + c] = ff_sub(B[i * kBS + c], ff_add(sa, sb));
+      }
+      __syncthreads();
+    }
+    // write back (FP64) and the level-(kappa-1) partial products, one warp per (r, column)
+    for (int e = tid; e < p * cw; e += kT) {
+      int c = e / p, i = e - c * p;
+      int q = q0 + c;
+      double* col = q < a.cP ? a.pan + (int64_t)q * a.n + b : a.Y + (int64_t)(q - a.cP) * a.n + b;
+      col[i] = ff_to_double(B[i * kBS + c]);
     }
     if (a.kappa > 0) {
       double* out = a.part + (int64_t)leaf * a.part_stride;
-      for (int r = 0; r < a.rl; ++r) {
+      for (int t = w; t < a.rl * cw; t += NW) {
+        int r = t / cw, c = t - r * cw;
         const double* ph = a.phi + (int64_t)(a.coff + r) * a.n + b;
-        ff phv[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          int i = m * 32 + lane;
-          phv[m] = i < p ? ff_from_double(ph[i]) : ff{0.0f, 0.0f};
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          if (c0 + c >= ncol) break;
-          ff s = {0.0f, 0.0f};
-#pragma unroll
-          for (int m = 0; m < 4; ++m) s = ff_fma(s, phv[m], x[c][m]);
-          s = wsum_ff(s);
-          if (lane == 0) out[r * ncol + c0 + c] = ff_to_double(s);
-        }
+        ff s = {0.0f, 0.0f};
+        for (int i = lane; i < p; i += 32) s = ff_fma(s, ff_from_double(ph[i]), B[i * kBS + c]);
+        for (int o = 16; o > 0; o >>= 1) s = ff_add(s, xor_ff(s, o));
+        if (lane == 0) out[r * ncol + q0 + c] = ff_to_double(s);
       }
     }
+    __syncthreads();
   }
 }
 
-}  // namespace
-
-cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs, double* leafC) {
+LeafFFArgs make_ff_args(Ctx& c, int nrhs, bool factor) {
   LeafFFArgs a;
   a.x = c.xs;
   a.n = c.n;
   a.d = c.d;
   a.kind = c.kind;
-  a.cr = (c.kind == HODLR_K_MATERN32 ? 1.7320508075688772 : c.kind == HODLR_K_MATERN52 ? 2.23606797749979 : 1.0) / c.ell;
+  a.cr = (c.kind == HODLR_K_MATERN32 ? 1.7320508075688772
+          : c.kind == HODLR_K_MATERN52 ? 2.23606797749979 : 1.0) / c.ell;
   a.amp = c.amp;
   a.sigma2 = c.sigma2;
   a.nb = c.nodes;
@@ -317,7 +369,7 @@ cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs, double* leafC) {
   a.leaf0 = (1 << c.kappa) - 1;
   a.kappa = c.kappa;
   a.pan = c.pan;
-  a.cP = c.R;
+  a.cP = factor ? c.R : 0;
   a.Y = c.Y;
   a.nrhs = nrhs;
   a.phi = c.phi;
@@ -325,27 +377,37 @@ cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs, double* leafC) {
   a.rl = c.kappa > 0 ? c.h_rl[c.kappa - 1] : 0;
   a.part = c.part;
   a.part_stride = c.part_stride;
-  a.leafL = c.leafL;
-  a.leafC = leafC;
+  a.leafL = reinterpret_cast<ff*>(c.leafL);
   a.leaf_logdet = c.leaf_logdet;
   a.flags = c.dflags;
-  size_t smem = sizeof(ff) * kMaxLeaf * kLD;
-  unsigned grid = 1u << c.kappa;
-  switch (c.leaf_threads) {
-    case 1024:
-      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_leaf_ff<1024><<<grid, 1024, smem, c.stream>>>(a);
-      break;
-    case 256:
-      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_leaf_ff<256><<<grid, 256, smem, c.stream>>>(a);
+  return a;
+}
+
+template <bool kFactor>
+cudaError_t launch_ff(const LeafFFArgs& a, unsigned grid, int threads, cudaStream_t s) {
+  size_t smem = sizeof(ff) * kMaxLeaf * (kLD + 2 * kBS);
+  switch (threads) {
+    case 512:
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff<512, kFactor>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_leaf_ff<512, kFactor><<<grid, 512, smem, s>>>(a);
       break;
     default:
-      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_leaf_ff<512><<<grid, 512, smem, c.stream>>>(a);
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff<1024, kFactor>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_leaf_ff<1024, kFactor><<<grid, 1024, smem, s>>>(a);
   }
-  ++c.launches;
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs) {
+  ++c.launches;
+  return launch_ff<true>(make_ff_args(c, nrhs, true), 1u << c.kappa, c.leaf_threads, c.stream);
+}
+
+cudaError_t launch_leaf_solve_ff(Ctx& c, int nrhs) {
+  ++c.launches;
+  return launch_ff<false>(make_ff_args(c, nrhs, false), 1u << c.kappa, c.leaf_threads, c.stream);
 }
 
 }  // namespace hodlr
