@@ -9,9 +9,11 @@
 //                      term) when |u||v| <= eps |S_k|; next row = argmax over unused rows
 // The block B = K[I_left, I_right] of node id lives in one column of the level's raw panel:
 // rows of the left child hold u, rows of the right child hold v. All reductions use fixed
-// orders, so results are deterministic.
+// orders, so results are deterministic. In the mixed form the block entries are evaluated
+// in double-float (ff.cuh) from the FP64 distances; everything else stays FP64.
 #include <cuda_runtime.h>
 
+#include "ff.cuh"
 #include "hodlr_internal.cuh"
 
 namespace hodlr {
@@ -23,6 +25,7 @@ constexpr int kPer = kAcaTile / kAcaThreads;  // elements per thread
 struct AcaArgs {
   Pts pts;
   Cov cov;
+  double cr;           // covariance scale for the double-float evaluation
   double eps;
   const int32_t* nb;   // node begin
   const int32_t* ns;   // node size
@@ -41,6 +44,16 @@ struct AcaArgs {
 };
 
 __device__ __forceinline__ int level_of(int id) { return 31 - __clz(id + 1); }
+
+// Entry k(x_i, x_j) of an off-diagonal block: FP64, or (mixed form) double-float
+// evaluation of the covariance from the FP64 distance.
+template <bool kFF>
+__device__ __forceinline__ double block_entry(const AcaArgs& a, int i, int j, const ff* tab,
+                                              ff cr, ff amp) {
+  double r = dist(a.pts, i, j);
+  if (!kFF) return cov_r(a.cov, r);
+  return ff_to_double(cov_ff(a.cov.kind, ff_from_double(r), cr, amp, tab));
+}
 
 __device__ __forceinline__ int rmax_of(const AcaArgs& a, int id) {
   int ml = a.ns[2 * id + 1], mr = a.ns[2 * id + 2];
@@ -87,11 +100,19 @@ __global__ void k_aca_init(AcaArgs a) {
 }
 
 // A: residual row of the current pivot row, stored unnormalised in column k of the V rows.
+template <bool kFF>
 __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   int item = blockIdx.x;
   int id = a.item_node[item];
   if (a.done[id]) return;
   __shared__ double uik[kMaxRank];
+  __shared__ ff tab[64];
+  ff cr = {0, 0}, amp = {0, 0};
+  if (kFF) {
+    ff_exp_table(tab, threadIdx.x, kAcaThreads);
+    cr = ff_from_double(a.cr);
+    amp = ff_from_double(a.cov.amp);
+  }
   __shared__ double wv[kAcaThreads / 32];
   __shared__ int wi[kAcaThreads / 32];
   int k = a.rank[id], i = a.row[id];
@@ -107,7 +128,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   for (int q = 0; q < kPer; ++q) {
     int b = start + q * kAcaThreads + threadIdx.x;
     if (b < mr) {
-      double v = cov_r(a.cov, dist(a.pts, bl + i, br + b));
+      double v = block_entry<kFF>(a, bl + i, br + b, tab, cr, amp);
       for (int l = 0; l < k; ++l) v -= uik[l] * raw[l * n + br + b];
       raw[(int64_t)k * n + br + b] = v;
       amax_merge(bv, bi, v, b);
@@ -178,11 +199,19 @@ __global__ void k_aca_pivot_row(AcaArgs a) {
 
 // C: residual column u (stored in column k of the U rows), normalised row v, and this tile's
 // contributions to |u|^2, |v|^2, u_l.u, v_l.v and argmax over unused rows of |u|.
+template <bool kFF>
 __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   int item = blockIdx.x;
   int id = a.item_node[item];
   if (a.done[id] || !a.phase[id]) return;
   __shared__ double vjk[kMaxRank];
+  __shared__ ff tab[64];
+  ff cr = {0, 0}, amp = {0, 0};
+  if (kFF) {
+    ff_exp_table(tab, threadIdx.x, kAcaThreads);
+    cr = ff_from_double(a.cr);
+    amp = ff_from_double(a.cov.amp);
+  }
   __shared__ int used[2 * kMaxRank + 2];
   __shared__ double red[2 * kMaxRank + 2][kAcaThreads / 32];
   __shared__ double wv[kAcaThreads / 32];
@@ -207,7 +236,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
     uu[q] = 0.0;
     vv[q] = 0.0;
     if (t < ml) {
-      double u = cov_r(a.cov, dist(a.pts, bl + t, br + j));
+      double u = block_entry<kFF>(a, bl + t, br + j, tab, cr, amp);
       for (int l = 0; l < k; ++l) u -= raw[l * n + bl + t] * vjk[l];
       raw[(int64_t)k * n + bl + t] = u;
       uu[q] = u;
@@ -371,6 +400,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   AcaArgs a;
   a.pts = Pts{c.xs, c.n, c.d};
   a.cov = Cov{c.kind, 1.0 / c.ell, c.amp};
+  a.cr = cov_scale(c.kind, c.ell);
   a.eps = c.eps;
   a.nb = c.nodes;
   a.ns = c.nodes + ((int64_t)2 << c.kappa);
@@ -393,9 +423,15 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   int max_steps = 2 * c.max_rank + 4;
   for (int s = 0; s < max_steps; ++s) {
     HODLR_CUDA_TRY(cudaMemsetAsync(c.active, 0, sizeof(int32_t), c.stream));
-    k_aca_row<<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
+    if (c.precision == 1)
+      k_aca_row<true><<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
+    else
+      k_aca_row<false><<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
     k_aca_pivot_row<<<wblocks, 256, 0, c.stream>>>(a);
-    k_aca_col<<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
+    if (c.precision == 1)
+      k_aca_col<true><<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
+    else
+      k_aca_col<false><<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
     k_aca_pivot_col<<<wblocks, 256, 0, c.stream>>>(a);
     c.launches += 4;
     HODLR_CUDA_TRY(cudaGetLastError());

@@ -142,4 +142,34 @@ __device__ __forceinline__ ff ff_exp(ff x, const ff* __restrict__ tab64) {
   return ff{t.hi * sc, t.lo * sc};
 }
 
+// Covariance k(r) = a f(cr r) in double-float (Table 1 with a length scale: exponential,
+// squared-exponential, Matern-3/2, Matern-5/2; cr = 1/ell, 1/ell, sqrt3/ell, sqrt5/ell).
+__device__ __forceinline__ ff cov_ff(int kind, ff r, ff cr, ff amp, const ff* tab) {
+  ff s = ff_mul(r, cr);
+  const ff one = {1.0f, 0.0f};
+  switch (kind) {
+    case 0:  // exponential
+      return ff_mul(amp, ff_exp(ff_neg(s), tab));
+    case 1:  // squared-exponential
+      return ff_mul(amp, ff_exp(ff_mulf(ff_mul(s, s), -0.5f), tab));
+    case 2:  // Matern-3/2
+      return ff_mul(amp, ff_mul(ff_add(one, s), ff_exp(ff_neg(s), tab)));
+    default: {  // Matern-5/2
+      const ff third = {0.3333333432674408f, -9.934107481068821e-09f};
+      ff poly = ff_add(ff_add(one, s), ff_mul(ff_mul(s, s), third));
+      return ff_mul(amp, ff_mul(poly, ff_exp(ff_neg(s), tab)));
+    }
+  }
+}
+
+// 2^(j/64), j = 0..63, as double-floats (from the FP64 exp2), for ff_exp.
+__device__ __forceinline__ void ff_exp_table(ff* tab, int tid, int nthreads) {
+  for (int j = tid; j < 64; j += nthreads) tab[j] = ff_from_double(exp2((double)j / 64.0));
+}
+
+// Factor applied to r for each covariance: 1/ell, 1/ell, sqrt3/ell, sqrt5/ell.
+__host__ __device__ inline double cov_scale(int kind, double ell) {
+  return (kind == 2 ? 1.7320508075688772 : kind == 3 ? 2.23606797749979 : 1.0) / ell;
+}
+
 }  // namespace hodlr

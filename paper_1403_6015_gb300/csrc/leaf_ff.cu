@@ -50,24 +50,6 @@ struct LeafFFArgs {
   int32_t* flags;
 };
 
-__device__ __forceinline__ ff cov_ff(int kind, ff r, ff cr, ff amp, const ff* tab) {
-  ff s = ff_mul(r, cr);
-  const ff one = {1.0f, 0.0f};
-  switch (kind) {
-    case HODLR_K_EXP:
-      return ff_mul(amp, ff_exp(ff_neg(s), tab));
-    case HODLR_K_SE:
-      return ff_mul(amp, ff_exp(ff_mulf(ff_mul(s, s), -0.5f), tab));
-    case HODLR_K_MATERN32:
-      return ff_mul(amp, ff_mul(ff_add(one, s), ff_exp(ff_neg(s), tab)));
-    default: {
-      const ff third = {0.3333333432674408f, -9.934107481068821e-09f};
-      ff poly = ff_add(ff_add(one, s), ff_mul(ff_mul(s, s), third));
-      return ff_mul(amp, ff_mul(poly, ff_exp(ff_neg(s), tab)));
-    }
-  }
-}
-
 __device__ __forceinline__ ff shfl_ff(ff v, int src) {
   return ff{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
 }
@@ -105,7 +87,7 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
   ff* Lst = a.leafL + (int64_t)leaf * kMaxLeaf * kMaxLeaf;
   if (kFactor) {
     if (tid == 0) bad = 0;
-    if (tid < 64) tab[tid] = ff_from_double(exp2((double)tid / 64.0));
+    ff_exp_table(tab, tid, kT);
     // coordinates relative to the leaf's first point (keeps small offsets exact)
     for (int i = tid; i < p; i += kT) {
       xl[i] = ff_from_double(a.x[b + i] - a.x[b]);
@@ -360,8 +342,7 @@ LeafFFArgs make_ff_args(Ctx& c, int nrhs, bool factor) {
   a.n = c.n;
   a.d = c.d;
   a.kind = c.kind;
-  a.cr = (c.kind == HODLR_K_MATERN32 ? 1.7320508075688772
-          : c.kind == HODLR_K_MATERN52 ? 2.23606797749979 : 1.0) / c.ell;
+  a.cr = cov_scale(c.kind, c.ell);
   a.amp = c.amp;
   a.sigma2 = c.sigma2;
   a.nb = c.nodes;
