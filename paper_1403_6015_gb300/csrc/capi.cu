@@ -68,6 +68,7 @@ __global__ void k_check_finite(const double* x, int64_t m, int32_t* flag) {
 
 void free_factor_buffers(Ctx* c) {
   dfree(c->phi); dfree(c->pan); dfree(c->part); dfree(c->part2); dfree(c->half); dfree(c->Z);
+  dfree(c->cnt);
   dfree(c->rank_dev);
   c->R_cap = 0;
 }
@@ -210,6 +211,11 @@ hodlr_status compress(Ctx* c) {
     hel += ((int64_t)2 << j) * r;
   }
   hel = std::max<int64_t>(hel, (nleaf + 1) * pstride);
+  // the fused sweep's last block of a level-j half sums 2^(K-j-1) partials of r_j w_j values
+  c->fused_work = 0;
+  for (int j = 0; j < K; ++j)
+    c->fused_work = std::max<int64_t>(c->fused_work, ((int64_t)1 << (K - j - 1)) *
+                                      c->h_rl[j] * (c->h_coff[j] + c->h_rl[j] + c->max_nrhs));
   bool realloc = c->R_cap < c->R || !c->part || c->part_stride < pstride || c->z_elems < zel ||
                  c->half_elems < hel;
   if (realloc) {
@@ -220,7 +226,8 @@ hodlr_status compress(Ctx* c) {
     TRY_CUDA(c, dalloc(&c->part, nleaf * pstride), "alloc partials");
     TRY_CUDA(c, dalloc(&c->part2, std::max<int64_t>(nleaf / 64 + 1, 8) * pstride + 4096), "alloc partials");
     TRY_CUDA(c, dalloc(&c->half, hel), "alloc partials");
-    TRY_CUDA(c, dalloc(&c->Z, zel), "alloc Z");
+    TRY_CUDA(c, dalloc(&c->Z, 2 * zel), "alloc Z");
+    TRY_CUDA(c, dalloc(&c->cnt, nleaf + nleaf / 2 + 2), "alloc counters");
     TRY_CUDA(c, dalloc(&c->rank_dev, std::max(nint, 1)), "alloc ranks");
     c->R_cap = Rc;
     c->part_stride = pstride;
@@ -320,6 +327,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   c->precision = opts.precision;
   if (const char* e = std::getenv("HODLR_LEAF_THREADS")) c->leaf_threads = std::atoi(e);
   if (const char* e = std::getenv("HODLR_LEAF_THREADS64")) c->leaf_threads64 = std::atoi(e);
+  if (const char* e = std::getenv("HODLR_NO_FUSED")) c->no_fused = std::atoi(e) != 0;
   c->stream = (cudaStream_t)opts.stream;
   c->kappa = kappa_for(n, leaf);
   auto bail = [&](hodlr_status s) {
@@ -448,6 +456,14 @@ static hodlr_status check_flags(Ctx* c) {
   return HODLR_OK;
 }
 
+// Level sweep: one launch per level when each level's reductions are small enough for
+// one block per half-node, else the segmented three-launch path.
+static cudaError_t sweep(Ctx* c, int nrhs, bool factor_mode) {
+  if (c->fused_work <= ((int64_t)1 << 22) && !c->no_fused)
+    return hodlr::launch_levels_fused(*c, nrhs, factor_mode);
+  return hodlr::launch_levels(*c, nrhs, factor_mode);
+}
+
 // Factor with nrhs right-hand sides already gathered into c->Y (nrhs may be 0).
 static hodlr_status factor_impl(Ctx* c, int nrhs) {
   if (!c->compressed) return fail(c, HODLR_ESTATE, "not compressed");
@@ -465,7 +481,7 @@ static hodlr_status factor_impl(Ctx* c, int nrhs) {
   else
     TRY_CUDA(c, hodlr::launch_leaf_factor(*c, nrhs), "leaf factor");
   cudaEventRecord(c->ev[7], c->stream);
-  TRY_CUDA(c, hodlr::launch_levels(*c, nrhs, true), "levels");
+  TRY_CUDA(c, sweep(c, nrhs, true), "levels");
   TRY_CUDA(c, hodlr::launch_logdet_sum(*c), "logdet");
   cudaEventRecord(c->ev[5], c->stream);
   c->factored = true;
@@ -517,7 +533,7 @@ hodlr_status hodlr_solve(hodlr_ctx* ctx, const double* y, double* x, int nrhs, i
       TRY_CUDA(c, hodlr::launch_leaf_solve_ff(*c, nb), "leaf solve (double-float)");
     else
       TRY_CUDA(c, hodlr::launch_leaf_solve(*c, nb), "leaf solve");
-    TRY_CUDA(c, hodlr::launch_levels(*c, nb, false), "levels");
+    TRY_CUDA(c, sweep(c, nb, false), "levels");
     cudaEventRecord(c->ev[5], c->stream);
     c->solve_timed = true;
     s = write_out(c, x + (int64_t)c0 * ld, nb, ld);
@@ -560,7 +576,7 @@ hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out) {
       TRY_CUDA(c, hodlr::launch_leaf_solve_ff(*c, 1), "leaf solve (double-float)");
     else
       TRY_CUDA(c, hodlr::launch_leaf_solve(*c, 1), "leaf solve");
-    TRY_CUDA(c, hodlr::launch_levels(*c, 1, false), "levels");
+    TRY_CUDA(c, sweep(c, 1, false), "levels");
   }
   TRY_CUDA(c, hodlr::launch_quad_loglik(*c), "loglik");
   return write_scalar(c, c->scal + 2, out);

@@ -85,6 +85,7 @@ struct Ctx {
   int precision = 0;              // 0: FP64, 1: double-float leaf stage (mixed)
   int leaf_threads = 1024;        // CTA size of the double-float leaf kernel (measured best)
   int leaf_threads64 = 512;       // CTA size of the FP64 leaf kernel (measured best)
+  bool no_fused = false;          // force the segmented level sweep
   cudaStream_t stream = nullptr;
   int device = 0;
   int sms = 152;
@@ -146,8 +147,10 @@ struct Ctx {
   int64_t part_stride = 0;
   double* part2 = nullptr;        // first-stage segment sums
   double* half = nullptr;         // per half-node sums (2^(j+1) x part_stride)
-  double* Z = nullptr;            // scratch of the current level: 2 r_j x wz_j per node
+  double* Z = nullptr;            // two buffers of z_elems: Z of levels with even / odd index
   int64_t z_elems = 0;
+  int32_t* cnt = nullptr;         // arrival counters of the fused level sweep
+  int64_t fused_work = 0;         // largest per-block reduction of the fused sweep (values)
   int64_t half_elems = 0;
   double* scal = nullptr;         // [0] logdet, [1] quad, [2] loglik
   int32_t* dflags = nullptr;
@@ -178,6 +181,8 @@ cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs);
 cudaError_t launch_leaf_solve_ff(Ctx& c, int nrhs);
 cudaError_t launch_leaf_solve(Ctx& c, int nrhs);
 cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode);
+cudaError_t launch_level_first(Ctx& c, int nrhs, bool factor_mode);
+cudaError_t launch_levels_fused(Ctx& c, int nrhs, bool factor_mode);
 cudaError_t launch_logdet_sum(Ctx& c);
 cudaError_t launch_quad_loglik(Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double* xin_sorted, double* yout_sorted);

@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "hodlr_internal.cuh"
+#include "node_solve.cuh"
 
 namespace hodlr {
 namespace {
@@ -54,127 +55,12 @@ cudaError_t segsum(const double* in, int64_t stride, int E, int64_t nleaf, int h
   return cudaGetLastError();
 }
 
-struct NodeArgs {
-  const double* half;   // per half-node sums, (2^(j+1)) x stride, each r x w row-major
-  int64_t stride;
-  int j, r, w;          // level, padded rank, partial width
-  int cj;               // own columns start (factor mode), -1 in solve mode
-  int wz;               // Z width
-  double* Mlu;          // level's LU factors, (2r)^2 per node
-  int32_t* Mpiv;        // level's pivots, 2r per node
-  double* node_logdet;  // per node (level order)
-  double* Z;            // level scratch, z_stride = 2 r wz per node
-  int64_t z_stride;
-  int32_t* flags;
-};
-
-// Partial column of Z column q: ancestors' panel columns keep their index, the right-hand
-// sides sit after the node's own r columns in factor mode.
-__device__ __forceinline__ int zcol(const NodeArgs& a, int q) {
-  return (a.cj >= 0 && q >= a.cj) ? q + a.r : q;
-}
-
 __global__ void __launch_bounds__(128) k_node(NodeArgs a, bool factor) {
   extern __shared__ double M[];  // m2 x m2 row-major
   __shared__ int piv[2 * kMaxRank];
   __shared__ double lds;
   __shared__ int sgn;
-  int k = blockIdx.x;
-  int node = (1 << a.j) - 1 + k;
-  int r = a.r, m2 = 2 * r, tid = threadIdx.x;
-  const double* L = a.half + (int64_t)(2 * k) * a.stride;      // U^T (.) over the left half
-  const double* Rt = a.half + (int64_t)(2 * k + 1) * a.stride; // V^T (.) over the right half
-  double* Mg = a.Mlu + (int64_t)k * m2 * m2;
-  int32_t* pg = a.Mpiv + (int64_t)k * m2;
-  if (factor) {
-    for (int e = tid; e < m2 * m2; e += blockDim.x) {
-      int row = e / m2, col = e - row * m2;
-      double v;
-      if (row < r && col < r) v = row == col ? 1.0 : 0.0;
-      else if (row >= r && col >= r) v = row == col ? 1.0 : 0.0;
-      else if (row < r) v = Rt[row * a.w + a.cj + (col - r)];   // V^T Vt
-      else v = L[(row - r) * a.w + a.cj + col];                 // U^T Ut
-      M[e] = v;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      lds = 0.0;
-      sgn = 1;
-    }
-    for (int c = 0; c < m2; ++c) {
-      if (tid == 0) {
-        int p = c;
-        double best = fabs(M[c * m2 + c]);
-        for (int i = c + 1; i < m2; ++i)
-          if (fabs(M[i * m2 + c]) > best) {
-            best = fabs(M[i * m2 + c]);
-            p = i;
-          }
-        piv[c] = p;
-        if (p != c) sgn = -sgn;
-      }
-      __syncthreads();
-      int p = piv[c];
-      if (p != c)
-        for (int jj = tid; jj < m2; jj += blockDim.x) {
-          double t = M[c * m2 + jj];
-          M[c * m2 + jj] = M[p * m2 + jj];
-          M[p * m2 + jj] = t;
-        }
-      __syncthreads();
-      double d = M[c * m2 + c];
-      if (tid == 0) {
-        if (d == 0.0) sgn = 0;
-        else {
-          if (d < 0) sgn = -sgn;
-          lds += log(fabs(d));
-        }
-      }
-      for (int i = c + 1 + tid; i < m2; i += blockDim.x) {
-        double l = d != 0.0 ? M[i * m2 + c] / d : 0.0;
-        M[i * m2 + c] = l;
-        for (int jj = c + 1; jj < m2; ++jj) M[i * m2 + jj] -= l * M[c * m2 + jj];
-      }
-      __syncthreads();
-    }
-    for (int e = tid; e < m2 * m2; e += blockDim.x) Mg[e] = M[e];
-    for (int e = tid; e < m2; e += blockDim.x) pg[e] = piv[e];
-    if (tid == 0) {
-      a.node_logdet[node] = lds;
-      if (sgn <= 0) atomicOr(a.flags, kFlagNotSpd);
-    }
-  } else {
-    for (int e = tid; e < m2 * m2; e += blockDim.x) M[e] = Mg[e];
-    for (int e = tid; e < m2; e += blockDim.x) piv[e] = pg[e];
-  }
-  __syncthreads();
-  // Z = M^-1 [V^T P_R; U^T P_L], one thread per column
-  double* Zn = a.Z + (int64_t)k * a.z_stride;
-  for (int q = tid; q < a.wz; q += blockDim.x) {
-    int pc = zcol(a, q);
-    for (int row = 0; row < r; ++row) {
-      Zn[row * a.wz + q] = Rt[row * a.w + pc];
-      Zn[(r + row) * a.wz + q] = L[row * a.w + pc];
-    }
-    for (int c = 0; c < m2; ++c) {
-      int p = piv[c];
-      if (p != c) {
-        double t = Zn[c * a.wz + q];
-        Zn[c * a.wz + q] = Zn[p * a.wz + q];
-        Zn[p * a.wz + q] = t;
-      }
-    }
-    for (int i = 1; i < m2; ++i) {
-      double s = Zn[i * a.wz + q];
-      for (int c = 0; c < i; ++c) s -= M[i * m2 + c] * Zn[c * a.wz + q];
-      Zn[i * a.wz + q] = s;
-    }
-    for (int i = m2 - 1; i >= 0; --i) {
-      double s = Zn[i * a.wz + q];
-      for (int c = i + 1; c < m2; ++c) s -= M[i * m2 + c] * Zn[c * a.wz + q];
-      Zn[i * a.wz + q] = s / M[i * m2 + i];
-    }
-  }
+  node_solve(a, blockIdx.x, factor, M, piv, &lds, &sgn);
 }
 
 struct SweepArgs {
@@ -453,6 +339,39 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
     HODLR_CUDA_TRY(cudaGetLastError());
   }
   return cudaSuccess;
+}
+
+// Node step of the finest internal level for the fused sweep: its half-nodes are single
+// leaves, so the leaf stage's partials are the half sums. Z goes to buffer (kappa-1) & 1.
+cudaError_t launch_level_first(Ctx& c, int nrhs, bool factor_mode) {
+  int j = c.kappa - 1;
+  int r = c.h_rl[j], cj = c.h_coff[j];
+  int w = (factor_mode ? cj + r : 0) + nrhs;
+  NodeArgs na;
+  na.half = c.part;
+  na.stride = c.part_stride;
+  na.j = j;
+  na.r = r;
+  na.w = w;
+  na.cj = factor_mode ? cj : -1;
+  na.wz = (factor_mode ? cj : 0) + nrhs;
+  na.Mlu = c.Mlu + c.h_mlu_off[j];
+  na.Mpiv = c.Mpiv + c.h_piv_off[j];
+  na.node_logdet = c.node_logdet;
+  na.Z = c.Z + (j & 1) * c.z_elems;
+  na.z_stride = (int64_t)2 * r * na.wz;
+  na.flags = c.dflags;
+  if (r == 0) {
+    if (factor_mode)
+      HODLR_CUDA_TRY(cudaMemsetAsync(c.node_logdet + ((1 << j) - 1), 0, sizeof(double) << j, c.stream));
+    return cudaSuccess;
+  }
+  size_t smem = sizeof(double) * 4 * r * r;
+  if (smem > 48 * 1024)
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_node, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_node<<<1u << j, 128, smem, c.stream>>>(na, factor_mode);
+  ++c.launches;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_logdet_sum(Ctx& c) {

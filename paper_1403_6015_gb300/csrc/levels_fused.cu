@@ -1,0 +1,222 @@
+// Level sweep with one launch per level (Sec. 3.2, the level-by-level factorization and the
+// SMW solve), for the usual case of small partial products.
+//
+// k_level(u) updates every leaf's rows with the level-u SMW correction,
+//   P_L -= Ut Z_top, P_R -= Vt Z_bot     (Z of level u, computed by the previous launch),
+// forms the level-(u-1) partial products Phi_{u-1}^T P of its leaves, and then, in the
+// same launch, finishes level u-1: the last block to finish a half-node sums that half's
+// partials in leaf order (fixed order: results are deterministic), and the last half of a
+// node runs the node step (M, LU, log det, Z of level u-1; node_solve.cuh). Blocks only
+// count arrivals with atomics; no block ever waits for another.
+#include <cuda_runtime.h>
+
+#include "hodlr_internal.cuh"
+#include "node_solve.cuh"
+
+namespace hodlr {
+namespace {
+
+constexpr int kLT = 256;  // threads per block
+constexpr int kG = 4;     // leaves per block
+
+struct FusedArgs {
+  const int32_t* nb;
+  const int32_t* ns;
+  int leaf0, kappa, u;
+  double* pan;
+  const double* phi;
+  double* Y;
+  int cP, nrhs;       // updated columns: panel [0, cP), right-hand sides [0, nrhs)
+  int cu, ru;         // level u: Ut/Vt columns in pan, rank
+  const double* Zu;   // level-u Z, 2 ru wz per node
+  int cl, rl;         // level u-1: Phi columns, rank (no reduction if rl == 0 or u == 0)
+  double* part;
+  int64_t part_stride;
+  int32_t* cnt;       // arrival counters: half-nodes [0, 2^u), then nodes [2^u, 2^u + 2^(u-1))
+  NodeArgs na;        // node step of level u-1
+  int factor;
+  int64_t n;
+};
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
+  extern __shared__ double M[];  // node step, (2 rl)^2
+  __shared__ int piv[2 * kMaxRank];
+  __shared__ double lds;
+  __shared__ int sgn;
+  __shared__ int flag;
+  int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int nleaf = 1 << a.kappa;
+  int leaf_base = blockIdx.x * kG;
+  int nl = nleaf - leaf_base < kG ? nleaf - leaf_base : kG;
+  int wz = a.cP + a.nrhs;
+  int sh = a.kappa - a.u;  // leaves per level-u half-node = 2^(sh - 1); per node = 2^sh
+  int zs = 2 * a.ru * wz;
+  for (int t = w; t < nl * wz; t += kLT / 32) {
+    int g = t / wz, q = t - g * wz;
+    int leaf = leaf_base + g;
+    int id = a.leaf0 + leaf;
+    int b = a.nb[id], p = a.ns[id];
+    double* col = q < a.cP ? a.pan + (int64_t)q * a.n + b : a.Y + (int64_t)(q - a.cP) * a.n + b;
+    double x[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int i = m * 32 + lane;
+      x[m] = i < p ? col[i] : 0.0;
+    }
+    if (a.ru > 0) {
+      int side = (leaf >> (sh - 1)) & 1;
+      const double* Zs = a.Zu + (int64_t)(leaf >> sh) * zs + (int64_t)side * a.ru * wz;
+      for (int c = 0; c < a.ru; ++c) {
+        double z = Zs[c * wz + q];
+        const double* tl = a.pan + (int64_t)(a.cu + c) * a.n + b;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          int i = m * 32 + lane;
+          if (i < p) x[m] -= tl[i] * z;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) col[i] = x[m];
+      }
+    }
+    if (a.u > 0 && a.rl > 0) {
+      double* out = a.part + (int64_t)leaf * a.part_stride;
+      for (int c = 0; c < a.rl; ++c) {
+        const double* ph = a.phi + (int64_t)(a.cl + c) * a.n + b;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          int i = m * 32 + lane;
+          if (i < p) s += ph[i] * x[m];
+        }
+        s = wsum(s);
+        if (lane == 0) out[c * wz + q] = s;
+      }
+    }
+  }
+  if (a.u == 0 || a.rl == 0) return;
+  // finish level l = u - 1: half-nodes of 2^sh' leaves with sh' = kappa - l - 1 = sh
+  int hl = 1 << sh;            // leaves per level-l half-node
+  int E = a.rl * wz;
+  __threadfence();
+  __syncthreads();
+  int h0 = leaf_base >> sh, h1 = (leaf_base + nl - 1) >> sh;
+  for (int h = h0; h <= h1; ++h) {
+    int lo = h * hl > leaf_base ? h * hl : leaf_base;
+    int hi = (h + 1) * hl < leaf_base + nl ? (h + 1) * hl : leaf_base + nl;
+    __syncthreads();  // every thread has read the previous flag
+    if (tid == 0) {
+      int old = atomicAdd(&a.cnt[h], hi - lo);
+      flag = old + (hi - lo) == hl;
+    }
+    __syncthreads();
+    if (!flag) continue;  // uniform across the block
+    __threadfence();
+    double* hs = const_cast<double*>(a.na.half) + (int64_t)h * a.na.stride;
+    const double* pbase = a.part + (int64_t)h * hl * a.part_stride;
+    if (hl >= 32) {
+      // one warp per entry: lanes stride over the half's leaves, then a fixed xor tree
+      for (int e = w; e < E; e += kLT / 32) {
+        double s = 0.0;
+        for (int t = lane; t < hl; t += 32) s += __ldcg(pbase + (int64_t)t * a.part_stride + e);
+        s = wsum(s);
+        if (lane == 0) hs[e] = s;
+      }
+    } else {
+      for (int e = tid; e < E; e += kLT) {
+        double s = 0.0;
+        for (int t = 0; t < hl; ++t) s += __ldcg(pbase + (int64_t)t * a.part_stride + e);
+        hs[e] = s;
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    int node = h >> 1;
+    if (tid == 0) {
+      a.cnt[h] = 0;
+      int old = atomicAdd(&a.cnt[(1 << a.u) + node], 1);
+      flag = old == 1;
+    }
+    __syncthreads();
+    if (!flag) continue;
+    __threadfence();
+    node_solve(a.na, node, a.factor != 0, M, piv, &lds, &sgn);
+    if (tid == 0) a.cnt[(1 << a.u) + node] = 0;
+  }
+}
+
+}  // namespace
+
+// Sweep of levels kappa-1 .. 0 when the leaf stage has written the level-(kappa-1)
+// partials: the level-(kappa-1) node step by the segmented path, then one k_level launch
+// per level. Z alternates between two buffers so a launch never overwrites the Z it reads.
+cudaError_t launch_levels_fused(Ctx& c, int nrhs, bool factor_mode) {
+  int K = c.kappa;
+  if (K == 0) return cudaSuccess;
+  int64_t nleaf = (int64_t)1 << K;
+  HODLR_CUDA_TRY(cudaMemsetAsync(c.cnt, 0, sizeof(int32_t) * (size_t)(nleaf + nleaf / 2 + 2), c.stream));
+  HODLR_CUDA_TRY(launch_level_first(c, nrhs, factor_mode));  // node step of level kappa-1
+  for (int u = K - 1; u >= 0; --u) {
+    int ru = c.h_rl[u], cu = c.h_coff[u];
+    int cP = factor_mode ? cu : 0;
+    int wz = cP + nrhs;
+    int l = u - 1;
+    FusedArgs fa;
+    fa.nb = c.nodes;
+    fa.ns = c.nodes + ((int64_t)2 << K);
+    fa.leaf0 = (int)(nleaf - 1);
+    fa.kappa = K;
+    fa.u = u;
+    fa.pan = c.pan;
+    fa.phi = c.phi;
+    fa.Y = c.Y;
+    fa.cP = cP;
+    fa.nrhs = nrhs;
+    fa.cu = cu;
+    fa.ru = ru;
+    fa.Zu = c.Z + (u & 1) * c.z_elems;
+    fa.cl = l >= 0 ? c.h_coff[l] : 0;
+    fa.rl = l >= 0 ? c.h_rl[l] : 0;
+    fa.part = c.part;
+    fa.part_stride = c.part_stride;
+    fa.cnt = c.cnt;
+    fa.factor = factor_mode;
+    fa.n = c.n;
+    if (l >= 0) {
+      NodeArgs& na = fa.na;
+      na.half = c.half;
+      na.stride = c.part_stride;
+      na.j = l;
+      na.r = fa.rl;
+      na.w = wz;
+      na.cj = factor_mode ? fa.cl : -1;
+      na.wz = (factor_mode ? fa.cl : 0) + nrhs;
+      na.Mlu = c.Mlu + c.h_mlu_off[l];
+      na.Mpiv = c.Mpiv + c.h_piv_off[l];
+      na.node_logdet = c.node_logdet;
+      na.Z = c.Z + (l & 1) * c.z_elems;
+      na.z_stride = (int64_t)2 * fa.rl * na.wz;
+      na.flags = c.dflags;
+      if (factor_mode && fa.rl == 0)
+        HODLR_CUDA_TRY(cudaMemsetAsync(c.node_logdet + ((1 << l) - 1), 0, sizeof(double) << l, c.stream));
+    }
+    if (wz == 0 && (l < 0 || fa.rl == 0)) continue;
+    size_t smem = sizeof(double) * 4 * fa.rl * fa.rl;
+    if (smem > 48 * 1024)
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    unsigned grid = (unsigned)((nleaf + kG - 1) / kG);
+    k_level<<<grid, kLT, smem, c.stream>>>(fa);
+    ++c.launches;
+    HODLR_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+}  // namespace hodlr
