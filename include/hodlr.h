@@ -121,8 +121,37 @@ hodlr_status hodlr_logdet(hodlr_ctx* ctx, double* logdet);
  * Errors: ENOTSPD, ECUDA. */
 hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out);
 
+/* Presized compression (no host synchronisation): fix the padded rank of every level,
+ * level_ranks[j] for j = 0 .. kappa-1 (host array, 0 <= rank < opts.max_rank), e.g. from
+ * a learned predictor or an earlier adaptive build (hodlr_ranks). Buffers are sized here;
+ * later rebuilds run rank + 2 cross steps per level without reading anything back, and
+ * factorizations skip their pivot check. A block whose ACA needs more than its level's
+ * rank, or does not converge, sets bit 2 of the device flags (its result is then not
+ * trustworthy: re-run that setting in adaptive mode); a non-positive pivot sets bit 1.
+ * level_ranks = NULL returns to adaptive mode. Errors: EINVAL, ENOMEM, ECUDA. */
+hodlr_status hodlr_presize(hodlr_ctx* ctx, const int32_t* level_ranks, int nlevels);
+
+/* Device flags accumulated since the last read (bit 1: a leaf pivot or node determinant
+ * was not positive; bit 2: a presized rank was exceeded or a block did not converge), into
+ * *flags (host); clears them. Synchronises opts.stream. */
+hodlr_status hodlr_status_flags(hodlr_ctx* ctx, int32_t* flags);
+
+/* Log-likelihoods of nset hyperparameter settings on the same points and right-hand side
+ * (a hyperparameter sweep, Sec. 2.5): for each setting b, recompression with
+ * theta[2b], theta[2b+1] (ell, a) and sigma2[b], fused factorization and solve, log det
+ * and log-likelihood -> out[b], and the device flags of that evaluation -> status[b]
+ * (0 = valid; status may be NULL). All arrays are device pointers; y has n entries.
+ * Requires presized mode and a non-default opts.stream. The first call captures one
+ * evaluation as a CUDA graph (after one direct evaluation) and replays it for every other
+ * setting; later calls with the same pointers replay it directly. Stream-ordered: the call
+ * returns before the results are ready. Errors: ESTATE (not presized), EINVAL, ECUDA. */
+hodlr_status hodlr_loglik_sweep(hodlr_ctx* ctx, int64_t nset, const double* theta,
+                                const double* sigma2, const double* y, double* out,
+                                int32_t* status);
+
 /* Ranks of the 2^kappa - 1 off-diagonal blocks in level order (root first), into a host
- * array of capacity cap. Returns the number of blocks via *count. Errors: EINVAL. */
+ * array of capacity cap, as found by the last adaptive compression. Returns the number of
+ * blocks via *count. Errors: EINVAL. */
 hodlr_status hodlr_ranks(hodlr_ctx* ctx, int32_t* ranks, int64_t cap, int64_t* count);
 
 /* Number of tree levels kappa, and the point permutation (sorted row i holds point
@@ -152,7 +181,7 @@ hodlr_status hodlr_counters(hodlr_ctx* ctx, int64_t* out2);
  *   stream cudaStream_t (NULL = legacy default stream); the call is stream-ordered and
  *          does not synchronise.
  * Limits: 1 <= n <= 128; larger n returns HODLR_EINVAL, as do host pointers.
- * Scratch: a fixed 135,232-byte array in device global memory that every GPU loading the
+ * Scratch: a fixed 135,296-byte array in device global memory that every GPU loading the
  * library holds until exit. The first call on a device looks up its address (with that
  * device current), so make that first call before any stream capture. All calls on a
  * device share the array: calls that overlap on the GPU race. */

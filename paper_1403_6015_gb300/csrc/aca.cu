@@ -13,6 +13,8 @@
 // in double-float (ff.cuh) from the FP64 distances; everything else stays FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "ff.cuh"
 #include "hodlr_internal.cuh"
 
@@ -24,8 +26,8 @@ constexpr int kPer = kAcaTile / kAcaThreads;  // elements per thread
 
 struct AcaArgs {
   Pts pts;
-  Cov cov;
-  double cr;           // covariance scale for the double-float evaluation
+  int kind;
+  const double* hyp;   // device hyperparameter slot
   double eps;
   const int32_t* nb;   // node begin
   const int32_t* ns;   // node size
@@ -41,24 +43,30 @@ struct AcaArgs {
   int max_rank;
   int32_t* active;
   int nint;
+  int pre[32];         // presized rank of each level (0: adaptive)
 };
-
-__device__ __forceinline__ int level_of(int id) { return 31 - __clz(id + 1); }
 
 // Entry k(x_i, x_j) of an off-diagonal block: FP64, or (mixed form) double-float
 // evaluation of the covariance from the FP64 distance.
 template <bool kFF>
-__device__ __forceinline__ double block_entry(const AcaArgs& a, int i, int j, const ff* tab,
-                                              ff cr, ff amp) {
+__device__ __forceinline__ double block_entry(const AcaArgs& a, const Cov& cov, int i, int j,
+                                              const ff* tab, ff cr, ff amp) {
   double r = dist(a.pts, i, j);
-  if (!kFF) return cov_r(a.cov, r);
-  return ff_to_double(cov_ff(a.cov.kind, ff_from_double(r), cr, amp, tab));
+  if (!kFF) return cov_r(cov, r);
+  return ff_to_double(cov_ff(a.kind, ff_from_double(r), cr, amp, tab));
 }
 
+__device__ __forceinline__ int level_of(int id) { return 31 - __clz(id + 1); }
+
+// Rank cap of a block: min(m_left, m_right, max_rank), and in presized mode the level's
+// rank + 1 (one extra cross step shows whether the block converged within its rank).
 __device__ __forceinline__ int rmax_of(const AcaArgs& a, int id) {
   int ml = a.ns[2 * id + 1], mr = a.ns[2 * id + 2];
   int m = ml < mr ? ml : mr;
-  return m < a.max_rank ? m : a.max_rank;
+  m = m < a.max_rank ? m : a.max_rank;
+  int pre = a.pre[level_of(id)];
+  if (pre > 0 && pre + 1 < m) m = pre + 1;
+  return m;
 }
 
 // Argmax of |v| with the lowest index on ties (idx < 0 means empty).
@@ -108,10 +116,11 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   __shared__ double uik[kMaxRank];
   __shared__ ff tab[64];
   ff cr = {0, 0}, amp = {0, 0};
+  const Cov cov = cov_from(a.kind, a.hyp);
   if (kFF) {
     ff_exp_table(tab, threadIdx.x, kAcaThreads);
-    cr = ff_from_double(a.cr);
-    amp = ff_from_double(a.cov.amp);
+    cr = ff_from_double(a.hyp[kHypScale]);
+    amp = ff_from_double(cov.amp);
   }
   __shared__ double wv[kAcaThreads / 32];
   __shared__ int wi[kAcaThreads / 32];
@@ -128,7 +137,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   for (int q = 0; q < kPer; ++q) {
     int b = start + q * kAcaThreads + threadIdx.x;
     if (b < mr) {
-      double v = block_entry<kFF>(a, bl + i, br + b, tab, cr, amp);
+      double v = block_entry<kFF>(a, cov, bl + i, br + b, tab, cr, amp);
       for (int l = 0; l < k; ++l) v -= uik[l] * raw[l * n + br + b];
       raw[(int64_t)k * n + br + b] = v;
       amax_merge(bv, bi, v, b);
@@ -207,10 +216,11 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   __shared__ double vjk[kMaxRank];
   __shared__ ff tab[64];
   ff cr = {0, 0}, amp = {0, 0};
+  const Cov cov = cov_from(a.kind, a.hyp);
   if (kFF) {
     ff_exp_table(tab, threadIdx.x, kAcaThreads);
-    cr = ff_from_double(a.cr);
-    amp = ff_from_double(a.cov.amp);
+    cr = ff_from_double(a.hyp[kHypScale]);
+    amp = ff_from_double(cov.amp);
   }
   __shared__ int used[2 * kMaxRank + 2];
   __shared__ double red[2 * kMaxRank + 2][kAcaThreads / 32];
@@ -236,7 +246,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
     uu[q] = 0.0;
     vv[q] = 0.0;
     if (t < ml) {
-      double u = block_entry<kFF>(a, bl + t, br + j, tab, cr, amp);
+      double u = block_entry<kFF>(a, cov, bl + t, br + j, tab, cr, amp);
       for (int l = 0; l < k; ++l) u -= raw[l * n + bl + t] * vjk[l];
       raw[(int64_t)k * n + bl + t] = u;
       uu[q] = u;
@@ -360,6 +370,16 @@ __global__ void k_aca_pivot_col(AcaArgs a) {
   atomicAdd(a.active, 1);
 }
 
+// Presized mode: flag every block that did not converge within its level's rank.
+__global__ void k_aca_check(AcaArgs a, int32_t* flags) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= a.nint) return;
+  int pre = a.pre[level_of(id)];
+  int ml = a.ns[2 * id + 1], mr = a.ns[2 * id + 2];
+  bool full = a.rank[id] >= (ml < mr ? ml : mr);  // the whole block: exact
+  if (!a.done[id] || (!a.ok[id] && !full) || a.rank[id] > pre) atomicOr(flags, kFlagRankCap);
+}
+
 // Compact panels: level j's columns [coff_j, coff_j + r_j) of phi and pan take the node's
 // first rank columns of the raw panel and zeros beyond (zero columns leave every product
 // of the factorization unchanged).
@@ -398,9 +418,14 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   *steps_out = 0;
   if (nint == 0) return cudaSuccess;
   AcaArgs a;
+  int maxpre = 0;
+  for (int j = 0; j < 32; ++j) {
+    a.pre[j] = (c.presized && j < c.kappa) ? std::max(c.h_rl[j], 1) : 0;
+    maxpre = std::max(maxpre, a.pre[j]);
+  }
   a.pts = Pts{c.xs, c.n, c.d};
-  a.cov = Cov{c.kind, 1.0 / c.ell, c.amp};
-  a.cr = cov_scale(c.kind, c.ell);
+  a.kind = c.kind;
+  a.hyp = c.hyp;
   a.eps = c.eps;
   a.nb = c.nodes;
   a.ns = c.nodes + ((int64_t)2 << c.kappa);
@@ -420,9 +445,11 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   k_aca_init<<<(nint + 255) / 256, 256, 0, c.stream>>>(a);
   ++c.launches;
   int wblocks = (nint * 32 + 255) / 256;
-  int max_steps = 2 * c.max_rank + 4;
+  // adaptive: until no block is active (host check per step); presized: a fixed number of
+  // steps (rank + 1 per block, one spare for a zero pivot) and a device-side check
+  int max_steps = c.presized ? maxpre + 2 : 2 * c.max_rank + 4;
   for (int s = 0; s < max_steps; ++s) {
-    HODLR_CUDA_TRY(cudaMemsetAsync(c.active, 0, sizeof(int32_t), c.stream));
+    if (!c.presized) HODLR_CUDA_TRY(cudaMemsetAsync(c.active, 0, sizeof(int32_t), c.stream));
     if (c.precision == 1)
       k_aca_row<true><<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
     else
@@ -435,13 +462,18 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
     k_aca_pivot_col<<<wblocks, 256, 0, c.stream>>>(a);
     c.launches += 4;
     HODLR_CUDA_TRY(cudaGetLastError());
+    *steps_out = s + 1;
+    if (c.presized) continue;
     HODLR_CUDA_TRY(cudaMemcpyAsync(c.h_active, c.active, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
     HODLR_CUDA_TRY(cudaStreamSynchronize(c.stream));
     ++c.syncs;
-    *steps_out = s + 1;
     if (*c.h_active == 0) break;
   }
-  return cudaSuccess;
+  if (c.presized) {
+    k_aca_check<<<(nint + 255) / 256, 256, 0, c.stream>>>(a, c.dflags);
+    ++c.launches;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack(Ctx& c) {

@@ -82,6 +82,10 @@ void free_all(Ctx* c) {
   dfree(c->st_delta); dfree(c->st_s2); dfree(c->aca_part); dfree(c->active);
   dfree(c->Y); dfree(c->ysort); dfree(c->leafL); dfree(c->leaf_logdet); dfree(c->node_logdet);
   dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->Mlu); dfree(c->Mpiv);
+  dfree(c->hyp);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+  dfree(c->sweep_idx);
   if (c->h_active) cudaFreeHost(c->h_active);
   c->h_active = nullptr;
   for (auto& e : c->ev)
@@ -162,36 +166,13 @@ hodlr_status setup_aca(Ctx* c) {
   return HODLR_OK;
 }
 
-// Compression of all off-diagonal blocks, then the rank-padded compact panels.
-hodlr_status compress(Ctx* c) {
+// Buffers whose sizes depend on the per-level ranks h_rl (set before the call).
+hodlr_status size_buffers(Ctx* c) {
   int K = c->kappa;
   int nint = (1 << K) - 1;
-  c->compressed = false;
-  c->factored = false;
-  c->rank_capped = false;
-  cudaEventRecord(c->ev[2], c->stream);
-  int steps = 0;
-  TRY_CUDA(c, hodlr::launch_aca(*c, &steps), "aca");
-  c->h_rank.assign(nint, 0);
-  std::vector<int32_t> ok(nint, 1);
-  if (nint > 0) {
-    TRY_CUDA(c, cudaMemcpyAsync(c->h_rank.data(), c->st_rank, 4 * (size_t)nint, cudaMemcpyDeviceToHost, c->stream), "ranks");
-    TRY_CUDA(c, cudaMemcpyAsync(ok.data(), c->st_ok, 4 * (size_t)nint, cudaMemcpyDeviceToHost, c->stream), "ranks");
-    TRY_CUDA(c, cudaStreamSynchronize(c->stream), "ranks");
-  ++c->syncs;
-  }
-  for (int id = 0; id < nint; ++id)
-    if (!ok[id]) c->rank_capped = true;
-  c->h_rl.assign(K, 0);
   c->h_coff.assign(K + 1, 0);
-  for (int j = 0; j < K; ++j) {
-    int mx = 0;
-    for (int k = 0; k < (1 << j); ++k) mx = std::max(mx, c->h_rank[(1 << j) - 1 + k]);
-    c->h_rl[j] = mx;
-    c->h_coff[j + 1] = c->h_coff[j] + mx;
-  }
+  for (int j = 0; j < K; ++j) c->h_coff[j + 1] = c->h_coff[j] + c->h_rl[j];
   c->R = c->h_coff[K];
-  // sizes that depend on the ranks
   int64_t nleaf = (int64_t)1 << K;
   int rmax_level = 0;
   for (int j = 0; j < K; ++j) rmax_level = std::max(rmax_level, c->h_rl[j]);
@@ -242,11 +223,56 @@ hodlr_status compress(Ctx* c) {
     c->mlu_cap = std::max<int64_t>(mlu, 1);
     c->piv_cap = std::max<int64_t>(piv, 1);
   }
+  return HODLR_OK;
+}
+
+bool capturing(Ctx* c) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c->stream, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// Compression of all off-diagonal blocks, then the rank-padded compact panels. Adaptive
+// mode reads the ranks back (one synchronisation); presized mode uses the fixed level
+// ranks and leaves any violation in the device flags.
+hodlr_status compress(Ctx* c) {
+  int K = c->kappa;
+  int nint = (1 << K) - 1;
+  c->compressed = false;
+  c->factored = false;
+  c->rank_capped = false;
+  bool cap = capturing(c);
+  if (!cap) cudaEventRecord(c->ev[2], c->stream);
+  int steps = 0;
+  TRY_CUDA(c, hodlr::launch_aca(*c, &steps), "aca");
+  if (!c->presized) {
+    c->h_rank.assign(nint, 0);
+    std::vector<int32_t> ok(nint, 1);
+    if (nint > 0) {
+      TRY_CUDA(c, cudaMemcpyAsync(c->h_rank.data(), c->st_rank, 4 * (size_t)nint, cudaMemcpyDeviceToHost, c->stream), "ranks");
+      TRY_CUDA(c, cudaMemcpyAsync(ok.data(), c->st_ok, 4 * (size_t)nint, cudaMemcpyDeviceToHost, c->stream), "ranks");
+      TRY_CUDA(c, cudaStreamSynchronize(c->stream), "ranks");
+      ++c->syncs;
+    }
+    for (int id = 0; id < nint; ++id)
+      if (!ok[id]) c->rank_capped = true;
+    c->h_rl.assign(K, 0);
+    for (int j = 0; j < K; ++j) {
+      int mx = 0;
+      for (int k = 0; k < (1 << j); ++k) mx = std::max(mx, c->h_rank[(1 << j) - 1 + k]);
+      c->h_rl[j] = mx;
+    }
+    hodlr_status s = size_buffers(c);
+    if (s != HODLR_OK) return s;
+  }
   // the panels keep their own copy of the ranks
   if (nint > 0)
     TRY_CUDA(c, cudaMemcpyAsync(c->rank_dev, c->st_rank, 4 * (size_t)nint, cudaMemcpyDeviceToDevice, c->stream), "ranks");
   TRY_CUDA(c, hodlr::launch_pack(*c), "pack");
-  cudaEventRecord(c->ev[3], c->stream);
+  if (!cap) cudaEventRecord(c->ev[3], c->stream);
   c->compressed = true;
   return HODLR_OK;
 }
@@ -344,6 +370,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   int64_t nleaf = (int64_t)1 << c->kappa;
   if (dalloc(&c->nodes, 2 * tot) || dalloc(&c->xs, n * d) || dalloc(&c->perm, n) ||
       dalloc(&c->dflags, 4) || dalloc(&c->scal, 8) || dalloc(&c->active, 1) ||
+      dalloc(&c->hyp, hodlr::kHypLen) ||
       dalloc(&c->Y, n * c->max_nrhs) || dalloc(&c->ysort, n) || dalloc(&c->tmpvec, n * c->max_nrhs) ||
       dalloc(&c->leaf_logdet, nleaf) || dalloc(&c->node_logdet, std::max<int64_t>(nleaf - 1, 1)) ||
       dalloc(&c->leafL, nleaf * hodlr::kMaxLeaf * hodlr::kMaxLeaf) ||
@@ -384,6 +411,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   }
   hodlr_status s = setup_aca(c);
   if (s != HODLR_OK) return bail(s);
+  if (hodlr::launch_set_hyp(*c, c->ell, c->amp, c->sigma2) != cudaSuccess) return bail(HODLR_ECUDA);
   s = compress(c);
   if (s != HODLR_OK) return bail(s);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(HODLR_ECUDA);
@@ -405,8 +433,10 @@ hodlr_status hodlr_rebuild(hodlr_ctx* ctx, const double* theta, double sigma2) {
   c->ell = theta[0];
   c->amp = theta[1];
   c->sigma2 = sigma2;
+  TRY_CUDA(c, hodlr::launch_set_hyp(*c, c->ell, c->amp, c->sigma2), "hyperparameters");
   hodlr_status s = compress(c);
   if (s != HODLR_OK) return s;
+  if (c->presized) return HODLR_OK;  // stream-ordered; violations go to the device flags
   TRY_CUDA(c, cudaStreamSynchronize(c->stream), "rebuild");
   ++c->syncs;
   cudaEventElapsedTime(&c->phase_ms[1], c->ev[2], c->ev[3]);
@@ -469,23 +499,25 @@ static hodlr_status factor_impl(Ctx* c, int nrhs) {
   if (!c->compressed) return fail(c, HODLR_ESTATE, "not compressed");
   if (c->factored) return fail(c, HODLR_ESTATE, "already factored (rebuild first)");
   c->solve_timed = false;
-  cudaEventRecord(c->ev[4], c->stream);
+  bool cap = capturing(c);
+  if (!cap) cudaEventRecord(c->ev[4], c->stream);
   if (c->R > 0 && c->kappa > 0) {
     // the working panel starts from the original U/V (a previous factor modified it)
     TRY_CUDA(c, cudaMemcpyAsync(c->pan, c->phi, sizeof(double) * c->n * c->R, cudaMemcpyDeviceToDevice, c->stream), "panel");
   }
-  TRY_CUDA(c, cudaMemsetAsync(c->dflags, 0, 4, c->stream), "flags");
-  cudaEventRecord(c->ev[6], c->stream);
+  if (!c->presized) TRY_CUDA(c, cudaMemsetAsync(c->dflags, 0, 4, c->stream), "flags");
+  if (!cap) cudaEventRecord(c->ev[6], c->stream);
   if (c->precision == 1)
     TRY_CUDA(c, hodlr::launch_leaf_factor_ff(*c, nrhs), "leaf factor (double-float)");
   else
     TRY_CUDA(c, hodlr::launch_leaf_factor(*c, nrhs), "leaf factor");
-  cudaEventRecord(c->ev[7], c->stream);
+  if (!cap) cudaEventRecord(c->ev[7], c->stream);
   TRY_CUDA(c, sweep(c, nrhs, true), "levels");
   TRY_CUDA(c, hodlr::launch_logdet_sum(*c), "logdet");
-  cudaEventRecord(c->ev[5], c->stream);
+  if (!cap) cudaEventRecord(c->ev[5], c->stream);
   c->factored = true;
   c->nrhs_fused = nrhs;
+  if (c->presized) return HODLR_OK;  // no synchronisation: see hodlr_status_flags
   hodlr_status s = check_flags(c);
   cudaEventElapsedTime(&c->phase_ms[2], c->ev[4], c->ev[5]);
   cudaEventElapsedTime(&c->phase_ms[4], c->ev[6], c->ev[7]);
@@ -580,6 +612,117 @@ hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out) {
   }
   TRY_CUDA(c, hodlr::launch_quad_loglik(*c), "loglik");
   return write_scalar(c, c->scal + 2, out);
+}
+
+hodlr_status hodlr_presize(hodlr_ctx* ctx, const int32_t* level_ranks, int nlevels) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  if (!level_ranks) {
+    c->presized = false;
+    c->graph_valid = false;
+    return HODLR_OK;
+  }
+  if (nlevels != c->kappa) return fail(c, HODLR_EINVAL, "presize: nlevels must equal kappa");
+  for (int j = 0; j < nlevels; ++j)
+    if (level_ranks[j] < 0 || level_ranks[j] + 1 > c->max_rank)
+      return fail(c, HODLR_EINVAL, "presize: level rank outside [0, max_rank - 1]");
+  c->h_rl.assign(level_ranks, level_ranks + nlevels);
+  hodlr_status s = size_buffers(c);
+  if (s != HODLR_OK) return s;
+  c->presized = true;
+  c->graph_valid = false;
+  c->compressed = false;
+  c->factored = false;
+  TRY_CUDA(c, cudaMemsetAsync(c->dflags, 0, 4, c->stream), "flags");
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_status_flags(hodlr_ctx* ctx, int32_t* flags) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !flags) return HODLR_EINVAL;
+  int32_t f = 0;
+  TRY_CUDA(c, cudaMemcpyAsync(&f, c->dflags, 4, cudaMemcpyDeviceToHost, c->stream), "flags");
+  TRY_CUDA(c, cudaMemsetAsync(c->dflags, 0, 4, c->stream), "flags");
+  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "flags");
+  ++c->syncs;
+  *flags = f;
+  return HODLR_OK;
+}
+
+// One evaluation for the setting idx[0] of the sweep arrays, ending with out[idx] =
+// log-likelihood, status[idx] = device flags of this evaluation, idx += 1.
+__global__ void k_store_setting(const double* scal, int32_t* flags, int32_t* idx, double* out,
+                                int32_t* status) {
+  int b = idx[0];
+  out[b] = scal[2];
+  if (status) status[b] = flags[0];
+  flags[0] = 0;
+  idx[0] = b + 1;
+}
+
+static hodlr_status sweep_eval(Ctx* c, const double* theta, const double* sigma2, const double* y,
+                               double* out, int32_t* status) {
+  TRY_CUDA(c, hodlr::launch_load_setting(*c, theta, sigma2, c->sweep_idx), "setting");
+  hodlr_status s = compress(c);
+  if (s != HODLR_OK) return s;
+  TRY_CUDA(c, hodlr::launch_gather_rhs(*c, y, c->n, 1), "gather");
+  c->factored = false;
+  s = factor_impl(c, 1);
+  if (s != HODLR_OK) return s;
+  TRY_CUDA(c, hodlr::launch_quad_loglik(*c), "loglik");
+  k_store_setting<<<1, 1, 0, c->stream>>>(c->scal, c->dflags, c->sweep_idx, out, status);
+  ++c->launches;
+  TRY_CUDA(c, cudaGetLastError(), "store");
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_loglik_sweep(hodlr_ctx* ctx, int64_t nset, const double* theta,
+                                const double* sigma2, const double* y, double* out,
+                                int32_t* status) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  if (!c->presized) return fail(c, HODLR_ESTATE, "sweep: presize the context first");
+  if (nset < 1 || !theta || !sigma2 || !y || !out || !is_device_ptr(theta) ||
+      !is_device_ptr(sigma2) || !is_device_ptr(y) || !is_device_ptr(out) ||
+      (status && !is_device_ptr(status)))
+    return fail(c, HODLR_EINVAL, "sweep: device arrays required");
+  if (!c->stream) return fail(c, HODLR_EINVAL, "sweep: needs a non-default stream");
+  if (!c->sweep_idx) TRY_CUDA(c, dalloc(&c->sweep_idx, 1), "alloc");
+  TRY_CUDA(c, cudaMemsetAsync(c->sweep_idx, 0, sizeof(int32_t), c->stream), "sweep");
+  bool same = c->graph_valid && c->g_theta == theta && c->g_sigma2 == sigma2 && c->g_y == y &&
+              c->g_out == out && c->g_status == status;
+  if (!same) {
+    // one eager evaluation first (sets kernel attributes), then capture one evaluation
+    hodlr_status s = sweep_eval(c, theta, sigma2, y, out, status);
+    if (s != HODLR_OK) return s;
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+    cudaGraph_t g = nullptr;
+    TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "capture");
+    int64_t l0 = c->launches;
+    s = sweep_eval(c, theta, sigma2, y, out, status);
+    c->launches_captured = c->launches - l0;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (s != HODLR_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    TRY_CUDA(c, e, "capture");
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    TRY_CUDA(c, e, "instantiate");
+    c->graph_valid = true;
+    c->g_theta = theta;
+    c->g_sigma2 = sigma2;
+    c->g_y = y;
+    c->g_out = out;
+    c->g_status = status;
+    c->graph_launches = c->launches_captured;
+    nset -= 1;  // the eager evaluation did setting 0
+  }
+  for (int64_t b = 0; b < nset; ++b) TRY_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream), "replay");
+  c->launches += nset * c->graph_launches;
+  return HODLR_OK;
 }
 
 hodlr_status hodlr_ranks(hodlr_ctx* ctx, int32_t* ranks, int64_t cap, int64_t* count) {

@@ -46,6 +46,15 @@ __device__ __forceinline__ double cov_r(const Cov& c, double r) {
   }
 }
 
+// Hyperparameters in device memory, so that kernels (and captured graphs) read the current
+// setting: hyp[0] = 1/ell, hyp[1] = amplitude a, hyp[2] = sigma^2, hyp[3] = covariance
+// scale cr (1/ell, 1/ell, sqrt3/ell, sqrt5/ell for exp, SE, Matern-3/2, Matern-5/2).
+enum { kHypInvEll = 0, kHypAmp = 1, kHypSigma2 = 2, kHypScale = 3, kHypLen = 8 };
+
+__device__ __forceinline__ Cov cov_from(int kind, const double* __restrict__ hyp) {
+  return Cov{kind, hyp[kHypInvEll], hyp[kHypAmp]};
+}
+
 // Sorted points in structure-of-arrays form: coordinate c of sorted point i is x[c * n + i].
 struct Pts {
   const double* x;
@@ -61,7 +70,7 @@ __device__ __forceinline__ double dist(const Pts& p, int i, int j) {
 }
 
 // Device error word bits (ctx->dflags).
-enum : int { kFlagNotSpd = 1, kFlagRankCap = 2, kFlagTimeout = 4 };
+enum : int { kFlagNotSpd = 1, kFlagRankCap = 2, kFlagTimeout = 4 };  // rank cap: also presize
 
 // ---------------------------------------------------------------------------------------
 // Context: everything one problem owns on the device. Layouts (n rows, column stride n):
@@ -153,6 +162,7 @@ struct Ctx {
   int64_t fused_work = 0;         // largest per-block reduction of the fused sweep (values)
   int64_t half_elems = 0;
   double* scal = nullptr;         // [0] logdet, [1] quad, [2] loglik
+  double* hyp = nullptr;          // device hyperparameter slot (kHyp* layout)
   int32_t* dflags = nullptr;
   double* tmpvec = nullptr;       // n x max_nrhs staging for host/device copies
 
@@ -160,6 +170,14 @@ struct Ctx {
   bool factored = false;
   int nrhs_fused = 0;
   bool rank_capped = false;
+  bool presized = false;          // fixed per-level ranks, no host synchronisation
+  // hyperparameter sweep: one captured evaluation replayed per setting
+  int32_t* sweep_idx = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  bool graph_valid = false;
+  const void *g_theta = nullptr, *g_sigma2 = nullptr, *g_y = nullptr, *g_out = nullptr,
+             *g_status = nullptr;
+  int64_t graph_launches = 0, launches_captured = 0;
 
   cudaEvent_t ev[8] = {};
   float phase_ms[6] = {0, 0, 0, 0, 0, 0};
@@ -186,9 +204,12 @@ cudaError_t launch_levels_fused(Ctx& c, int nrhs, bool factor_mode);
 cudaError_t launch_logdet_sum(Ctx& c);
 cudaError_t launch_quad_loglik(Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double* xin_sorted, double* yout_sorted);
-cudaError_t launch_leaf_single(const double* xs_soa, int n, int d, int kind, double ell,
-                               double amp, double sigma2, const int32_t* nodes, double* Y,
-                               double* L, double* logdet, int32_t* flags, cudaStream_t s);
+cudaError_t launch_set_hyp(Ctx& c, double ell, double amp, double sigma2);
+cudaError_t launch_load_setting(Ctx& c, const double* theta, const double* sigma2,
+                                const int32_t* idx);
+cudaError_t launch_leaf_single(const double* xs_soa, int n, int d, int kind, const double* hyp,
+                               const int32_t* nodes, double* Y, double* L, double* logdet,
+                               int32_t* flags, cudaStream_t s);
 
 }  // namespace hodlr
 

@@ -22,8 +22,8 @@ constexpr int kLD = kMaxLeaf + 1;
 
 struct LeafArgs {
   Pts pts;
-  Cov cov;
-  double sigma2;
+  int kind;
+  const double* hyp;  // device hyperparameter slot
   const int32_t* nb;
   const int32_t* ns;
   int leaf0;          // node id of leaf 0
@@ -119,6 +119,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   double* Lout = a.leafL + (int64_t)leaf * kMaxLeaf * kMaxLeaf;
   if (kFactor) {
+    const Cov cov = cov_from(a.kind, a.hyp);
+    const double sigma2 = a.hyp[kHypSigma2];
     if (tid == 0) bad = 0;
     for (int i = tid; i < p; i += kLeafThreads) {
       xl[i] = a.pts.x[b + i];
@@ -135,8 +137,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
         double u = xl[i] - xl[j], v = xl[kMaxLeaf + i] - xl[kMaxLeaf + j];
         r = sqrt(u * u + v * v);
       }
-      double c = cov_r(a.cov, r);
-      if (i == j) c += a.sigma2;
+      double c = cov_r(cov, r);
+      if (i == j) c += sigma2;
       A[i * kLD + j] = c;
     }
     __syncthreads();
@@ -275,8 +277,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
 LeafArgs make_args(Ctx& c, int nrhs, bool factor) {
   LeafArgs a;
   a.pts = Pts{c.xs, c.n, c.d};
-  a.cov = Cov{c.kind, 1.0 / c.ell, c.amp};
-  a.sigma2 = c.sigma2;
+  a.kind = c.kind;
+  a.hyp = c.hyp;
   a.nb = c.nodes;
   a.ns = c.nodes + ((int64_t)2 << c.kappa);
   a.leaf0 = (1 << c.kappa) - 1;
@@ -337,13 +339,13 @@ namespace hodlr {
 // The leaf kernel on caller-provided device buffers, for a problem that is a single leaf
 // (kappa = 0): nodes[0] = 0 (begin), nodes[1] = n (size); Y holds the right-hand side and
 // receives C^-1 y; L receives the Cholesky factor; logdet receives log det C.
-cudaError_t launch_leaf_single(const double* xs_soa, int n, int d, int kind, double ell,
-                               double amp, double sigma2, const int32_t* nodes, double* Y,
-                               double* L, double* logdet, int32_t* flags, cudaStream_t s) {
+cudaError_t launch_leaf_single(const double* xs_soa, int n, int d, int kind, const double* hyp,
+                               const int32_t* nodes, double* Y, double* L, double* logdet,
+                               int32_t* flags, cudaStream_t s) {
   LeafArgs a;
   a.pts = Pts{xs_soa, n, d};
-  a.cov = Cov{kind, 1.0 / ell, amp};
-  a.sigma2 = sigma2;
+  a.kind = kind;
+  a.hyp = hyp;
   a.nb = nodes;
   a.ns = nodes + 1;
   a.leaf0 = 0;

@@ -32,8 +32,7 @@ struct LeafFFArgs {
   int64_t n;
   int d;
   int kind;
-  double cr;     // factor applied to r before f: 1/ell (exp, SE), sqrt3/ell, sqrt5/ell
-  double amp, sigma2;
+  const double* hyp;  // device hyperparameter slot (cr, amplitude, sigma^2)
   const int32_t* nb;
   const int32_t* ns;
   int leaf0, kappa;
@@ -94,8 +93,8 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
       if (a.d == 2) xl[kMaxLeaf + i] = ff_from_double(a.x[a.n + b + i] - a.x[a.n + b]);
     }
     __syncthreads();
-    const ff cr = ff_from_double(a.cr), amp = ff_from_double(a.amp);
-    const ff s2 = ff_from_double(a.sigma2);
+    const ff cr = ff_from_double(a.hyp[kHypScale]), amp = ff_from_double(a.hyp[kHypAmp]);
+    const ff s2 = ff_from_double(a.hyp[kHypSigma2]);
     // lower triangle of the padded block
     for (int e = tid; e < P * (P + 1) / 2; e += kT) {
       int i = tri_row(e), j = e - i * (i + 1) / 2;
@@ -342,9 +341,7 @@ LeafFFArgs make_ff_args(Ctx& c, int nrhs, bool factor) {
   a.n = c.n;
   a.d = c.d;
   a.kind = c.kind;
-  a.cr = cov_scale(c.kind, c.ell);
-  a.amp = c.amp;
-  a.sigma2 = c.sigma2;
+  a.hyp = c.hyp;
   a.nb = c.nodes;
   a.ns = c.nodes + ((int64_t)2 << c.kappa);
   a.leaf0 = (1 << c.kappa) - 1;

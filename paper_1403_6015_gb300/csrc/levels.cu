@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "hodlr_internal.cuh"
+#include "ff.cuh"
 #include "node_solve.cuh"
 
 namespace hodlr {
@@ -197,8 +198,8 @@ __global__ void k_scatter(const double* __restrict__ Y, int nrhs, const int32_t*
 // ---- HODLR operator product (dense leaves + U V^T blocks) ------------------------------
 struct MvArgs {
   Pts pts;
-  Cov cov;
-  double sigma2;
+  int kind;
+  const double* hyp;
   const int32_t* nb;
   const int32_t* ns;
   int leaf0, kappa, R;
@@ -231,6 +232,8 @@ __global__ void k_mv_partials(MvArgs a, LevelTab t) {
 }
 
 __global__ void k_mv_apply(MvArgs a, LevelTab t) {
+  const Cov cov = cov_from(a.kind, a.hyp);
+  const double sigma2 = a.hyp[kHypSigma2];
   int leaf = blockIdx.x;
   int id = a.leaf0 + leaf;
   int b = a.nb[id], p = a.ns[id];
@@ -238,8 +241,8 @@ __global__ void k_mv_apply(MvArgs a, LevelTab t) {
     double s = 0.0;
     for (int jj = 0; jj < p; ++jj) {
       double r = dist(a.pts, b + i, b + jj);
-      double c = cov_r(a.cov, r);
-      if (jj == i) c += a.sigma2;
+      double c = cov_r(cov, r);
+      if (jj == i) c += sigma2;
       s += c * a.xin[b + jj];
     }
     for (int l = 0; l < a.kappa; ++l) {
@@ -374,6 +377,38 @@ cudaError_t launch_level_first(Ctx& c, int nrhs, bool factor_mode) {
   return cudaGetLastError();
 }
 
+// Device hyperparameter slot from host values (stream-ordered, capturable).
+__global__ void k_set_hyp(double* hyp, int kind, double ell, double amp, double sigma2) {
+  hyp[kHypInvEll] = 1.0 / ell;
+  hyp[kHypAmp] = amp;
+  hyp[kHypSigma2] = sigma2;
+  hyp[kHypScale] = cov_scale(kind, ell);
+}
+
+// The same from setting idx[0] of device arrays theta (ell, a pairs) and sigma2.
+__global__ void k_load_setting(double* hyp, int kind, const double* theta, const double* sigma2,
+                               const int32_t* idx) {
+  int b = idx[0];
+  double ell = theta[2 * b], amp = theta[2 * b + 1];
+  hyp[kHypInvEll] = 1.0 / ell;
+  hyp[kHypAmp] = amp;
+  hyp[kHypSigma2] = sigma2[b];
+  hyp[kHypScale] = cov_scale(kind, ell);
+}
+
+cudaError_t launch_set_hyp(Ctx& c, double ell, double amp, double sigma2) {
+  k_set_hyp<<<1, 1, 0, c.stream>>>(c.hyp, c.kind, ell, amp, sigma2);
+  ++c.launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_setting(Ctx& c, const double* theta, const double* sigma2,
+                                const int32_t* idx) {
+  k_load_setting<<<1, 1, 0, c.stream>>>(c.hyp, c.kind, theta, sigma2, idx);
+  ++c.launches;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_logdet_sum(Ctx& c) {
   int64_t nleaf = (int64_t)1 << c.kappa;
   double* tmp = c.part2;  // scratch: 3 x kRedBlocks
@@ -400,8 +435,8 @@ cudaError_t launch_matvec(Ctx& c, const double* xin, double* yout) {
   int64_t nleaf = (int64_t)1 << K;
   MvArgs a;
   a.pts = Pts{c.xs, c.n, c.d};
-  a.cov = Cov{c.kind, 1.0 / c.ell, c.amp};
-  a.sigma2 = c.sigma2;
+  a.kind = c.kind;
+  a.hyp = c.hyp;
   a.nb = c.nodes;
   a.ns = c.nodes + ((int64_t)2 << K);
   a.leaf0 = (int)(nleaf - 1);

@@ -9,7 +9,7 @@
 // their buffers in hodlr_build; this one uses a fixed array in device global memory that
 // the library defines once per loaded module.
 //
-// The scratch: a file-scope __device__ array of kNoAllocBytes (135,232 bytes). Every GPU
+// The scratch: a file-scope __device__ array of kNoAllocBytes (135,296 bytes). Every GPU
 // that loads the library holds one copy until the process exits. Host code cannot use the
 // array's name as a device address; the first call on a device (with that device current)
 // asks the runtime for the address with cudaGetSymbolAddress and keeps it for later calls
@@ -22,6 +22,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "ff.cuh"
 #include "hodlr_internal.cuh"
 
 namespace {
@@ -35,7 +36,8 @@ constexpr int kOffSol = kOffY + kNoAllocMaxN;                  // y, overwritten
 constexpr int kOffL = kOffSol + kNoAllocMaxN;                  // Cholesky factor, 128 x 128
 constexpr int kOffLd = kOffL + kNoAllocMaxN * kNoAllocMaxN;    // log det
 constexpr int kOffInt = kOffLd + 8;                            // int32 words: nodes[2], flags
-constexpr int kNoAllocDoubles = kOffInt + 8;
+constexpr int kOffHyp = kOffInt + 8;                           // hyperparameter slot
+constexpr int kNoAllocDoubles = kOffHyp + 8;
 constexpr size_t kNoAllocBytes = sizeof(double) * kNoAllocDoubles;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
@@ -64,12 +66,17 @@ cudaError_t scratch_address(double** out) {
 // Clear the flag word, write the one-leaf tree, copy x (row-major n x d) to structure of
 // arrays and y to both vectors.
 __global__ void k_noalloc_prep(double* s, const double* __restrict__ x, const double* __restrict__ y,
-                               int n, int d) {
+                               int n, int d, int kind, double ell, double amp, double sigma2) {
   int32_t* iw = reinterpret_cast<int32_t*>(s + kOffInt);
   if (threadIdx.x == 0) {
     iw[0] = 0;  // node begin
     iw[1] = n;  // node size
     iw[2] = 0;  // flags
+    double* hyp = s + kOffHyp;
+    hyp[hodlr::kHypInvEll] = 1.0 / ell;
+    hyp[hodlr::kHypAmp] = amp;
+    hyp[hodlr::kHypSigma2] = sigma2;
+    hyp[hodlr::kHypScale] = hodlr::cov_scale(kind, ell);
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     for (int c = 0; c < d; ++c) s[kOffX + c * n + i] = x[i * d + c];
@@ -124,11 +131,11 @@ extern "C" hodlr_status hodlr_loglik_small_noalloc(const double* x, int64_t n, i
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int32_t* iw = reinterpret_cast<int32_t*>(s + kOffInt);
-  k_noalloc_prep<<<1, 128, 0, st>>>(s, x, y, (int)n, d);
+  k_noalloc_prep<<<1, 128, 0, st>>>(s, x, y, (int)n, d, (int)kernel, theta[0], theta[1], sigma2);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
-    e = hodlr::launch_leaf_single(s + kOffX, (int)n, d, (int)kernel, theta[0], theta[1], sigma2,
-                                  iw, s + kOffSol, s + kOffL, s + kOffLd, iw + 2, st);
+    e = hodlr::launch_leaf_single(s + kOffX, (int)n, d, (int)kernel, s + kOffHyp, iw,
+                                  s + kOffSol, s + kOffL, s + kOffLd, iw + 2, st);
   if (e == cudaSuccess) {
     k_noalloc_finish<<<1, 128, 0, st>>>(s, (int)n, out);
     e = cudaGetLastError();

@@ -57,6 +57,9 @@ def load():
     L.hodlr_matvec.argtypes = [_vp, _dp, _dp]
     L.hodlr_phase_ms.argtypes = [_vp, _dp]
     L.hodlr_counters.argtypes = [_vp, _dp]
+    L.hodlr_presize.argtypes = [_vp, _dp, ctypes.c_int]
+    L.hodlr_status_flags.argtypes = [_vp, _dp]
+    L.hodlr_loglik_sweep.argtypes = [_vp, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp]
     L.hodlr_loglik_small_noalloc.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp,
                                              ctypes.c_double, _dp, _dp, _vp]
     L.hodlr_last_error.argtypes = [_vp]
@@ -67,7 +70,8 @@ def load():
     for name in ("hodlr_build", "hodlr_rebuild", "hodlr_factor", "hodlr_factor_solve",
                  "hodlr_solve", "hodlr_logdet", "hodlr_loglik", "hodlr_ranks", "hodlr_tree",
                  "hodlr_matvec", "hodlr_phase_ms", "hodlr_counters",
-                 "hodlr_loglik_small_noalloc"):
+                 "hodlr_loglik_small_noalloc", "hodlr_presize", "hodlr_status_flags",
+                 "hodlr_loglik_sweep"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -167,6 +171,25 @@ def hodlr_loglik_small_noalloc(x_addr, n, d, kernel, theta, sigma2, y_addr, out_
     th = _f64_host(theta)
     return load().hodlr_loglik_small_noalloc(x_addr, n, d, kernel, th.ctypes.data, sigma2,
                                              y_addr, out_addr, stream)
+
+
+def hodlr_presize(ctx, level_ranks):
+    """level_ranks: host int32 array of kappa entries, or None for adaptive mode."""
+    if level_ranks is None:
+        return load().hodlr_presize(ctx, None, 0)
+    r = np.ascontiguousarray(level_ranks, dtype=np.int32)
+    return load().hodlr_presize(ctx, r.ctypes.data, r.size)
+
+
+def hodlr_status_flags(ctx):
+    f = np.zeros(1, dtype=np.int32)
+    st = load().hodlr_status_flags(ctx, f.ctypes.data)
+    return st, int(f[0])
+
+
+def hodlr_loglik_sweep(ctx, nset, theta_addr, sigma2_addr, y_addr, out_addr, status_addr=None):
+    return load().hodlr_loglik_sweep(ctx, nset, theta_addr, sigma2_addr, y_addr, out_addr,
+                                     status_addr)
 
 
 def hodlr_last_error(ctx) -> str:
@@ -323,6 +346,33 @@ class Hodlr:
         return {"ordering": float(buf[0]), "compression": float(buf[1]),
                 "factor": float(buf[2]), "solve": float(buf[3]),
                 "leaf_kernel": float(buf[4]), "levels": float(buf[5])}
+
+    def level_ranks(self) -> np.ndarray:
+        """Largest rank of each level from the last adaptive compression."""
+        r = self.ranks()
+        kappa = self.tree()[0]
+        return np.array([int(r[(1 << j) - 1:(1 << (j + 1)) - 1].max()) for j in range(kappa)],
+                        dtype=np.int32)
+
+    def presize(self, level_ranks):
+        self._check(hodlr_presize(self._ctx, level_ranks), "presize")
+
+    def status_flags(self) -> int:
+        st, f = hodlr_status_flags(self._ctx)
+        self._check(st, "status_flags")
+        return f
+
+    def loglik_sweep(self, theta, sigma2, y, out=None, status=None):
+        """theta: CUDA tensor (nset, 2); sigma2, y: CUDA tensors; returns out (nset,)."""
+        import torch
+        nset = theta.shape[0]
+        if out is None:
+            out = torch.empty(nset, dtype=torch.float64, device=theta.device)
+        self._check(hodlr_loglik_sweep(self._ctx, nset, theta.data_ptr(), sigma2.data_ptr(),
+                                       y.data_ptr(), out.data_ptr(),
+                                       status.data_ptr() if status is not None else None),
+                    "loglik_sweep")
+        return out
 
     def counters(self):
         buf = np.zeros(2, dtype=np.int64)

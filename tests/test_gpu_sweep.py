@@ -1,0 +1,117 @@
+"""Presized (synchronisation-free) compression and the graph-replayed hyperparameter sweep.
+
+The sweep evaluates many (ell, sigma^2) settings on one set of points, as in
+hyperparameter adaptation (Sec. 2.5); each setting's log-likelihood must equal the one the
+adaptive path computes for that setting alone, and the Kalman filter's exact value.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1403_6015_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_1403_6015_gb300 import build_lib, hodlr
+    build_lib.build()
+    hodlr.load()
+    return hodlr
+
+
+def settings(nset, seed):
+    """ell log-uniform in [0.05, 2], sigma^2 log-uniform in [1e-4, 1]."""
+    u = I.uniform01(seed, 2 * nset)
+    ell = np.exp(np.log(0.05) + u[:nset] * (np.log(2.0) - np.log(0.05)))
+    s2 = np.exp(np.log(1e-4) + u[nset:] * (np.log(1.0) - np.log(1e-4)))
+    return ell, s2
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_presized_matches_adaptive(H, precision):
+    import torch
+    n = 1 << 14
+    x, y = I.workload_1d(n, 1004)
+    ell, s2 = settings(6, 77)
+    stream = torch.cuda.Stream()
+    ref = [H.Hodlr(x, "matern52", [e, 1.0], s, 128, 1e-12, precision=precision).loglik(y)
+           for e, s in zip(ell, s2)]
+    h = H.Hodlr(x, "matern52", [ell[0], 1.0], s2[0], 128, 1e-12, precision=precision,
+                stream=stream.cuda_stream)
+    h.presize(np.full(h.tree()[0], 4, dtype=np.int32))
+    for e, s, r in zip(ell, s2, ref):
+        h.rebuild([e, 1.0], s)
+        got = h.loglik(y)
+        assert rel(got, r) <= 1e-12, (got, r)
+    assert h.status_flags() == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sweep_graph(H, precision):
+    import torch
+    n, nset = 1 << 16, 24
+    x, y = I.workload_1d(n, 1004)
+    ell, s2 = settings(nset, 78)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.from_numpy(y).cuda()
+        theta = torch.from_numpy(np.stack([ell, np.ones(nset)], 1).copy()).cuda()
+        sig = torch.from_numpy(s2.copy()).cuda()
+        status = torch.full((nset,), -1, dtype=torch.int32, device="cuda")
+    stream.synchronize()
+    h = H.Hodlr(xd, "matern52", [ell[0], 1.0], s2[0], 128, 1e-12, precision=precision,
+                stream=stream.cuda_stream)
+    h.presize(np.full(h.tree()[0], 4, dtype=np.int32))
+    out = h.loglik_sweep(theta, sig, yd, status=status)
+    stream.synchronize()
+    got = out.cpu().numpy()
+    assert (status.cpu().numpy() == 0).all()
+    # every setting against an adaptive evaluation on its own
+    for b in [0, 1, 7, nset - 1]:
+        r = H.Hodlr(x, "matern52", [ell[b], 1.0], s2[b], 128, 1e-12, precision=precision).loglik(y)
+        assert rel(got[b], r) <= 1e-12
+    # against the exact Kalman log-likelihood (loosest where cond(C) is largest)
+    _, perm = h.tree()
+    for b in range(nset):
+        ld, q = O.matern_kalman(x[perm, 0], 5, ell[b], 1.0, s2[b], y[perm])
+        ll = -0.5 * q - 0.5 * ld - 0.5 * n * np.log(2 * np.pi)
+        assert rel(got[b], ll) <= 1e-9, (b, ell[b], s2[b], got[b], ll)
+    # a second sweep replays the captured graph: identical results
+    out2 = h.loglik_sweep(theta, sig, yd, status=status)
+    stream.synchronize()
+    np.testing.assert_array_equal(out2.cpu().numpy(), got)
+
+
+def test_sweep_flags_undersized_presize(H):
+    import torch
+    n, nset = 1 << 14, 4
+    x, y = I.workload_1d(n, 1005)
+    ell, s2 = settings(nset, 79)
+    stream = torch.cuda.Stream()
+    h = H.Hodlr(x, "matern52", [ell[0], 1.0], s2[0], 128, 1e-12, stream=stream.cuda_stream)
+    h.presize(np.full(h.tree()[0], 1, dtype=np.int32))  # Matern-5/2 blocks need rank 3
+    theta = torch.from_numpy(np.stack([ell, np.ones(nset)], 1).copy()).cuda()
+    sig = torch.from_numpy(s2.copy()).cuda()
+    yd = torch.from_numpy(y).cuda()
+    status = torch.zeros(nset, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    h.loglik_sweep(theta, sig, yd, status=status)
+    stream.synchronize()
+    assert ((status.cpu().numpy() & 2) != 0).all()
+
+
+def test_presize_rejects_bad_input(H):
+    x, _ = I.workload_1d(4096, 1006)
+    h = H.Hodlr(x, "exp", [0.2, 1.0], 0.01, 64, 1e-12)
+    with pytest.raises(H.HodlrError):
+        h.presize(np.ones(3, dtype=np.int32))  # kappa is 6
+    with pytest.raises(H.HodlrError):
+        h.presize(np.full(6, 64, dtype=np.int32))  # rank + 1 must fit max_rank
+    h.presize(None)
