@@ -34,6 +34,7 @@ extern "C" {
 #endif
 
 typedef struct hodlr_ctx hodlr_ctx; /* opaque; owns all device memory of one problem */
+typedef struct hodlr_mlp hodlr_mlp; /* opaque; the learned rank predictor */
 
 typedef enum {
   HODLR_OK = 0,
@@ -148,6 +149,54 @@ hodlr_status hodlr_status_flags(hodlr_ctx* ctx, int32_t* flags);
 hodlr_status hodlr_loglik_sweep(hodlr_ctx* ctx, int64_t nset, const double* theta,
                                 const double* sigma2, const double* y, double* out,
                                 int32_t* status);
+
+/* ---- Learned rank predictor (not in the paper; sizes presized mode from features) ------
+ * A multilayer perceptron 12 -> 64 -> 64 -> 1 (tanh hidden units, FP32) maps the features
+ * of an off-diagonal block to log(1 + rank). Parameters: W1 (12 x 64, row-major by input),
+ * b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1). Trained on the GPU (Adam, mean squared
+ * error) on (features, rank) pairs that the FP64 compressor emits. */
+int hodlr_mlp_num_params(void);   /* 5057 */
+int hodlr_mlp_num_features(void); /* 12 */
+
+/* Create with Glorot-uniform weights drawn from splitmix64(seed), zero biases; stream is a
+ * cudaStream_t (NULL = default). */
+hodlr_status hodlr_mlp_create(uint64_t seed, void* stream, hodlr_mlp** out);
+void hodlr_mlp_destroy(hodlr_mlp* m);
+
+/* Copy the parameters out (set = 0) or in (set = 1; resets the Adam state); params is a
+ * host or device array of hodlr_mlp_num_params() floats. Synchronises. */
+hodlr_status hodlr_mlp_params(hodlr_mlp* m, float* params, int set);
+
+/* Y[i] = network(X[i, 0..12)), X device N x 12 row-major, Y device N. Stream-ordered. */
+hodlr_status hodlr_mlp_forward(hodlr_mlp* m, const float* X, int64_t N, float* Y);
+
+/* Gradient of the mean squared error (1/N) sum (Y - T)^2 with respect to the parameters
+ * (grad: host or device, num_params floats; may be NULL), and the loss (host or device
+ * float; may be NULL). X, T device. Synchronises. */
+hodlr_status hodlr_mlp_gradient(hodlr_mlp* m, const float* X, const float* T, int64_t N,
+                                float* grad, float* loss);
+
+/* steps full-batch Adam steps (lr, beta1 0.9, beta2 0.999, eps 1e-8) on (X, T); the final
+ * loss into *loss (host or device; may be NULL). Synchronises. */
+hodlr_status hodlr_mlp_train(hodlr_mlp* m, const float* X, const float* T, int64_t N,
+                             int steps, float lr, float* loss);
+
+/* Checkpoint file: "HODLRMLP", uint32 version 1, uint32 parameter count, FP32 parameters. */
+hodlr_status hodlr_mlp_save(hodlr_mlp* m, const char* path);
+hodlr_status hodlr_mlp_load(hodlr_mlp* m, const char* path);
+
+/* Features of the 2^kappa - 1 off-diagonal blocks (level order) for length scale ell, into
+ * the device array X (row stride ld >= 12): log(diam_L/ell), log(diam_R/ell),
+ * log(|c_L - c_R|/ell), log2(m_L + m_R)/20, -log10(eps)/12, one-hot covariance (4), d - 1,
+ * log(max diam / |c_L - c_R|), 0 (diam, c: bounding-box diagonal and centre of a child's
+ * points). */
+hodlr_status hodlr_block_features(hodlr_ctx* ctx, double ell, float* X, int64_t ld);
+
+/* Predicted padded rank of every level for length scale ell: the largest predicted block
+ * rank of the level plus margin, capped at max_rank - 1, into the host array level_ranks
+ * (kappa entries), ready for hodlr_presize. Synchronises. */
+hodlr_status hodlr_predict_ranks(hodlr_ctx* ctx, hodlr_mlp* mlp, double ell, int margin,
+                                 int32_t* level_ranks);
 
 /* Ranks of the 2^kappa - 1 off-diagonal blocks in level order (root first), into a host
  * array of capacity cap, as found by the last adaptive compression. Returns the number of

@@ -86,6 +86,8 @@ void free_all(Ctx* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
   dfree(c->sweep_idx);
+  dfree(c->boxes);
+  dfree(c->feat);
   if (c->h_active) cudaFreeHost(c->h_active);
   c->h_active = nullptr;
   for (auto& e : c->ev)
@@ -722,6 +724,40 @@ hodlr_status hodlr_loglik_sweep(hodlr_ctx* ctx, int64_t nset, const double* thet
   }
   for (int64_t b = 0; b < nset; ++b) TRY_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream), "replay");
   c->launches += nset * c->graph_launches;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_block_features(hodlr_ctx* ctx, double ell, float* X, int64_t ld) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !X || !(ell > 0) || ld < 12 || !is_device_ptr(X)) return HODLR_EINVAL;
+  TRY_CUDA(c, hodlr::launch_block_features(*c, ell, X, ld), "features");
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_predict_ranks(hodlr_ctx* ctx, hodlr_mlp* mlp, double ell, int margin,
+                                 int32_t* level_ranks) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !mlp || !level_ranks || !(ell > 0) || margin < 0) return HODLR_EINVAL;
+  int K = c->kappa;
+  int nint = (1 << K) - 1;
+  if (nint == 0) return HODLR_OK;
+  if (!c->feat) TRY_CUDA(c, dalloc(&c->feat, (int64_t)nint * 13), "alloc features");
+  float* X = c->feat;
+  float* Yp = c->feat + (int64_t)nint * 12;
+  TRY_CUDA(c, hodlr::launch_block_features(*c, ell, X, 12), "features");
+  TRY_CUDA(c, hodlr::launch_mlp_forward(*c, mlp, X, nint, Yp), "predict");
+  std::vector<float> y(nint);
+  TRY_CUDA(c, cudaMemcpyAsync(y.data(), Yp, sizeof(float) * nint, cudaMemcpyDeviceToHost, c->stream), "predict");
+  TRY_CUDA(c, cudaStreamSynchronize(c->stream), "predict");
+  ++c->syncs;
+  for (int j = 0; j < K; ++j) {
+    int mx = 0;
+    for (int k = 0; k < (1 << j); ++k) {
+      double r = std::expm1((double)y[(1 << j) - 1 + k]);
+      mx = std::max(mx, (int)std::lround(std::max(r, 0.0)));
+    }
+    level_ranks[j] = std::min(mx + margin, c->max_rank - 1);
+  }
   return HODLR_OK;
 }
 

@@ -178,6 +178,9 @@ struct Ctx {
   const void *g_theta = nullptr, *g_sigma2 = nullptr, *g_y = nullptr, *g_out = nullptr,
              *g_status = nullptr;
   int64_t graph_launches = 0, launches_captured = 0;
+  // learned rank predictor
+  double* boxes = nullptr;        // bounding box of every node's points
+  float* feat = nullptr;          // block features (nint x 12) and predictions (nint)
 
   cudaEvent_t ev[8] = {};
   float phase_ms[6] = {0, 0, 0, 0, 0, 0};
@@ -205,6 +208,8 @@ cudaError_t launch_logdet_sum(Ctx& c);
 cudaError_t launch_quad_loglik(Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double* xin_sorted, double* yout_sorted);
 cudaError_t launch_set_hyp(Ctx& c, double ell, double amp, double sigma2);
+cudaError_t launch_block_features(Ctx& c, double ell, float* X, int64_t ld);
+cudaError_t launch_mlp_forward(Ctx& c, hodlr_mlp* m, const float* X, int64_t N, float* Y);
 cudaError_t launch_load_setting(Ctx& c, const double* theta, const double* sigma2,
                                 const int32_t* idx);
 cudaError_t launch_leaf_single(const double* xs_soa, int n, int d, int kind, const double* hyp,

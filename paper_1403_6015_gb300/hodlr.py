@@ -60,6 +60,18 @@ def load():
     L.hodlr_presize.argtypes = [_vp, _dp, ctypes.c_int]
     L.hodlr_status_flags.argtypes = [_vp, _dp]
     L.hodlr_loglik_sweep.argtypes = [_vp, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp]
+    L.hodlr_mlp_num_params.restype = ctypes.c_int
+    L.hodlr_mlp_num_features.restype = ctypes.c_int
+    L.hodlr_mlp_create.argtypes = [ctypes.c_uint64, _vp, ctypes.POINTER(_vp)]
+    L.hodlr_mlp_destroy.argtypes = [_vp]
+    L.hodlr_mlp_params.argtypes = [_vp, _dp, ctypes.c_int]
+    L.hodlr_mlp_forward.argtypes = [_vp, _dp, ctypes.c_int64, _dp]
+    L.hodlr_mlp_gradient.argtypes = [_vp, _dp, _dp, ctypes.c_int64, _dp, _dp]
+    L.hodlr_mlp_train.argtypes = [_vp, _dp, _dp, ctypes.c_int64, ctypes.c_int, ctypes.c_float, _dp]
+    L.hodlr_mlp_save.argtypes = [_vp, ctypes.c_char_p]
+    L.hodlr_mlp_load.argtypes = [_vp, ctypes.c_char_p]
+    L.hodlr_block_features.argtypes = [_vp, ctypes.c_double, _dp, ctypes.c_int64]
+    L.hodlr_predict_ranks.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int, _dp]
     L.hodlr_loglik_small_noalloc.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp,
                                              ctypes.c_double, _dp, _dp, _vp]
     L.hodlr_last_error.argtypes = [_vp]
@@ -71,7 +83,9 @@ def load():
                  "hodlr_solve", "hodlr_logdet", "hodlr_loglik", "hodlr_ranks", "hodlr_tree",
                  "hodlr_matvec", "hodlr_phase_ms", "hodlr_counters",
                  "hodlr_loglik_small_noalloc", "hodlr_presize", "hodlr_status_flags",
-                 "hodlr_loglik_sweep"):
+                 "hodlr_loglik_sweep", "hodlr_mlp_create", "hodlr_mlp_params",
+                 "hodlr_mlp_forward", "hodlr_mlp_gradient", "hodlr_mlp_train", "hodlr_mlp_save",
+                 "hodlr_mlp_load", "hodlr_block_features", "hodlr_predict_ranks"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -190,6 +204,56 @@ def hodlr_status_flags(ctx):
 def hodlr_loglik_sweep(ctx, nset, theta_addr, sigma2_addr, y_addr, out_addr, status_addr=None):
     return load().hodlr_loglik_sweep(ctx, nset, theta_addr, sigma2_addr, y_addr, out_addr,
                                      status_addr)
+
+
+def hodlr_mlp_num_params() -> int:
+    return load().hodlr_mlp_num_params()
+
+
+def hodlr_mlp_num_features() -> int:
+    return load().hodlr_mlp_num_features()
+
+
+def hodlr_mlp_create(seed=0, stream=None):
+    out = _vp()
+    st = load().hodlr_mlp_create(seed, stream, ctypes.byref(out))
+    return st, out.value
+
+
+def hodlr_mlp_destroy(m):
+    load().hodlr_mlp_destroy(m)
+
+
+def hodlr_mlp_params(m, buf, set_):
+    return load().hodlr_mlp_params(m, _addr(buf), 1 if set_ else 0)
+
+
+def hodlr_mlp_forward(m, x_addr, n, y_addr):
+    return load().hodlr_mlp_forward(m, x_addr, n, y_addr)
+
+
+def hodlr_mlp_gradient(m, x_addr, t_addr, n, grad_addr, loss_addr):
+    return load().hodlr_mlp_gradient(m, x_addr, t_addr, n, grad_addr, loss_addr)
+
+
+def hodlr_mlp_train(m, x_addr, t_addr, n, steps, lr, loss_addr):
+    return load().hodlr_mlp_train(m, x_addr, t_addr, n, steps, lr, loss_addr)
+
+
+def hodlr_mlp_save(m, path):
+    return load().hodlr_mlp_save(m, path.encode())
+
+
+def hodlr_mlp_load(m, path):
+    return load().hodlr_mlp_load(m, path.encode())
+
+
+def hodlr_block_features(ctx, ell, x_addr, ld):
+    return load().hodlr_block_features(ctx, ell, x_addr, ld)
+
+
+def hodlr_predict_ranks(ctx, mlp, ell, margin, out):
+    return load().hodlr_predict_ranks(ctx, mlp, ell, margin, _addr(out))
 
 
 def hodlr_last_error(ctx) -> str:
@@ -373,6 +437,19 @@ class Hodlr:
                                        status.data_ptr() if status is not None else None),
                     "loglik_sweep")
         return out
+
+    def block_features(self, ell):
+        """Features of every off-diagonal block (torch CUDA tensor, (2^kappa - 1) x 12)."""
+        import torch
+        m = (1 << self.tree()[0]) - 1
+        X = torch.empty((max(m, 1), 12), dtype=torch.float32, device="cuda")
+        self._check(hodlr_block_features(self._ctx, ell, X.data_ptr(), 12), "block_features")
+        return X[:m]
+
+    def predict_level_ranks(self, mlp, ell, margin=1):
+        out = np.zeros(max(self.tree()[0], 1), dtype=np.int32)
+        self._check(hodlr_predict_ranks(self._ctx, mlp._m, ell, margin, out), "predict_ranks")
+        return out[:self.tree()[0]]
 
     def counters(self):
         buf = np.zeros(2, dtype=np.int64)

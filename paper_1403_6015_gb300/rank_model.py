@@ -1,0 +1,93 @@
+"""Learned rank predictor: the network object, pair collection and training.
+
+The network (12 -> 64 -> 64 -> 1, tanh) and its training run in libhodlr_gb300.so
+(hodlr_mlp_*); this module only gathers (block features, rank) pairs from the FP64
+compressor over a grid of problems and calls the library.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import hodlr as H
+
+
+class RankMLP:
+    def __init__(self, seed: int = 0, stream=None):
+        st, m = H.hodlr_mlp_create(seed, stream)
+        if st != H.HODLR_OK:
+            raise H.HodlrError(st, "hodlr_mlp_create")
+        self._m = m
+
+    def close(self):
+        if getattr(self, "_m", None):
+            H.hodlr_mlp_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(H.hodlr_mlp_num_params(), dtype=np.float32)
+        H.hodlr_mlp_params(self._m, p, False)
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        H.hodlr_mlp_params(self._m, p, True)
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        st = H.hodlr_mlp_forward(self._m, X.data_ptr(), X.shape[0], Y.data_ptr())
+        if st != H.HODLR_OK:
+            raise H.HodlrError(st, "hodlr_mlp_forward")
+        torch.cuda.synchronize()
+        return Y
+
+    def gradient(self, X, T):
+        g = np.zeros(H.hodlr_mlp_num_params(), dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        st = H.hodlr_mlp_gradient(self._m, X.data_ptr(), T.data_ptr(), X.shape[0], g.ctypes.data,
+                                  loss.ctypes.data)
+        if st != H.HODLR_OK:
+            raise H.HodlrError(st, "hodlr_mlp_gradient")
+        return g, float(loss[0])
+
+    def train(self, X, T, steps: int, lr: float = 1e-3) -> float:
+        loss = np.zeros(1, dtype=np.float32)
+        st = H.hodlr_mlp_train(self._m, X.data_ptr(), T.data_ptr(), X.shape[0], steps, lr,
+                               loss.ctypes.data)
+        if st != H.HODLR_OK:
+            raise H.HodlrError(st, "hodlr_mlp_train")
+        return float(loss[0])
+
+    def save(self, path: str):
+        if H.hodlr_mlp_save(self._m, path) != H.HODLR_OK:
+            raise IOError(path)
+
+    def load(self, path: str):
+        if H.hodlr_mlp_load(self._m, path) != H.HODLR_OK:
+            raise IOError(path)
+
+
+def collect_pairs(problems, max_rank: int = 64):
+    """(features, log(1 + rank)) of every block of every problem, from the FP64 compressor.
+
+    problems: iterable of (x, kernel, ell, sigma2, leaf, eps). Returns torch CUDA tensors
+    X (N x 12, float32) and T (N, float32), and the raw ranks (numpy).
+    """
+    import torch
+    Xs, Ts, R = [], [], []
+    for x, kern, ell, s2, leaf, eps in problems:
+        h = H.Hodlr(x, kern, [ell, 1.0], s2, leaf, eps, max_rank=max_rank, allow_rank_cap=True)
+        r = h.ranks()
+        if r.size == 0:
+            continue
+        Xs.append(h.block_features(ell).clone())
+        Ts.append(torch.from_numpy(np.log1p(r.astype(np.float32))).cuda())
+        R.append(r)
+        h.close()
+    return torch.cat(Xs), torch.cat(Ts), np.concatenate(R)

@@ -1,0 +1,128 @@
+"""The learned rank predictor: GPU network kernels against the FP64 oracle network, GPU
+training, checkpoints, and its use for presizing with the adaptive fallback."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+from paper_1403_6015_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_1403_6015_gb300 import build_lib, hodlr
+    build_lib.build()
+    hodlr.load()
+    return hodlr
+
+
+@pytest.fixture(scope="module")
+def RM(H):
+    from paper_1403_6015_gb300 import rank_model
+    return rank_model
+
+
+def test_forward_and_gradient_vs_oracle(H, RM):
+    import torch
+    rng = np.random.default_rng(5)
+    p = (rng.standard_normal(M.NPARAMS) * 0.2).astype(np.float32)
+    X = rng.standard_normal((300, 12)).astype(np.float32)
+    T = rng.standard_normal(300).astype(np.float32)
+    net = RM.RankMLP(seed=1)
+    net.set_params(p)
+    np.testing.assert_array_equal(net.params(), p)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    y = net.forward(Xd).cpu().numpy()
+    y_o, _, _ = M.forward(p.astype(np.float64), X.astype(np.float64))
+    np.testing.assert_allclose(y, y_o, rtol=0, atol=2e-5 * np.abs(y_o).max())
+    g, loss = net.gradient(Xd, Td)
+    g_o = M.gradient(p.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss - M.loss(p, X, T)) <= 1e-5 * M.loss(p, X, T)
+    np.testing.assert_allclose(g, g_o, rtol=0, atol=2e-5 * np.abs(g_o).max())
+
+
+def test_gradient_deterministic(H, RM):
+    import torch
+    rng = np.random.default_rng(6)
+    X = torch.from_numpy(rng.standard_normal((1000, 12)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.standard_normal(1000).astype(np.float32)).cuda()
+    net = RM.RankMLP(seed=2)
+    g1, _ = net.gradient(X, T)
+    g2, _ = net.gradient(X, T)
+    np.testing.assert_array_equal(g1, g2)
+
+
+def problems(kernels, ells, ns, epss, seed):
+    out = []
+    for i, n in enumerate(ns):
+        x, _ = I.workload_1d(n, seed + i)
+        for kern in kernels:
+            for ell in ells:
+                for eps in epss:
+                    out.append((x, kern, float(ell), 0.01, 64, eps))
+    return out
+
+
+@pytest.fixture(scope="module")
+def trained(H, RM, tmp_path_factory):
+    """A predictor trained on the GPU on blocks of the FP64 compressor."""
+    ells = np.exp(np.linspace(np.log(0.03), np.log(2.0), 9))
+    X, T, R = RM.collect_pairs(problems(["exp", "se", "matern32", "matern52"], ells,
+                                        [1 << 12, 1 << 13], [1e-8, 1e-12], 900))
+    net = RM.RankMLP(seed=7)
+    loss0 = net.gradient(X, T)[1]
+    loss = net.train(X, T, steps=1500, lr=3e-3)
+    path = str(tmp_path_factory.mktemp("mlp") / "rank_mlp.bin")
+    net.save(path)
+    return net, loss0, loss, X.shape[0], path
+
+
+def test_training_reduces_loss(trained):
+    net, loss0, loss, npairs, _ = trained
+    assert npairs > 5000
+    assert loss < 0.1 * loss0 and loss < 0.05
+
+
+def test_checkpoint_roundtrip(RM, trained):
+    net, _, _, _, path = trained
+    other = RM.RankMLP(seed=99)
+    other.load(path)
+    np.testing.assert_array_equal(other.params(), net.params())
+
+
+@pytest.mark.parametrize("kern,ell", [("se", 0.07), ("se", 0.5), ("matern52", 0.2), ("exp", 1.3)])
+def test_predicted_presize_gives_adaptive_result(H, trained, kern, ell):
+    """Held-out problems: presizing from the network reproduces the adaptive result, and
+    the predicted level ranks cover the true ones."""
+    import torch
+    net = trained[0]
+    n = 1 << 14
+    x, y = I.workload_1d(n, 951)
+    ref = H.Hodlr(x, kern, [ell, 1.0], 0.01, 64, 1e-10)
+    true = ref.level_ranks()
+    ll_ref = ref.loglik(y)
+    stream = torch.cuda.Stream()
+    h = H.Hodlr(x, kern, [ell, 1.0], 0.01, 64, 1e-10, stream=stream.cuda_stream)
+    pred = h.predict_level_ranks(net, ell, margin=2)
+    h.presize(pred)
+    h.rebuild([ell, 1.0], 0.01)
+    ll = h.loglik(y)
+    flags = h.status_flags()
+    if (pred >= true).all():
+        assert flags == 0
+        assert abs(ll - ll_ref) <= 1e-12 * abs(ll_ref)
+    else:
+        # under-prediction must be caught by the device check (the fallback signal)
+        assert flags & 2
+
+
+def test_undersized_prediction_is_flagged(H):
+    import torch
+    x, y = I.workload_1d(1 << 13, 952)
+    stream = torch.cuda.Stream()
+    h = H.Hodlr(x, "se", [0.05, 1.0], 0.01, 64, 1e-10, stream=stream.cuda_stream)
+    h.presize(np.ones(h.tree()[0], dtype=np.int32))
+    h.rebuild([0.05, 1.0], 0.01)
+    h.loglik(y)
+    assert h.status_flags() & 2
