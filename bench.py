@@ -267,6 +267,7 @@ def run_ours(args):
     head = max(ok, key=lambda p: results[p]["value"]) if ok else forms[-1]
     r = results[head]
     cpu = cpu_baseline(x, y) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    sweeps = run_sweeps(args) if (rank == 0 and not args.no_sweeps) else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": r["value"], "unit": "evals/s", "n_gpus": world,
@@ -285,6 +286,7 @@ def run_ours(args):
             "accuracy": r["accuracy"],
             "accepted": r["accepted"],
             "cpu_baseline": cpu,
+            "sweeps": sweeps,
         }
         for p in forms:
             if p != head:
@@ -296,6 +298,108 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def sweep_settings(nset, seed):
+    """ell log-uniform in [0.05, 2], sigma^2 log-uniform in [1e-4, 1] (the hyperparameter
+    sweep workload)."""
+    from paper_1403_6015_gb300 import inputs as I
+    u = I.uniform01(seed, 2 * nset)
+    ell = np.exp(np.log(0.05) + u[:nset] * (np.log(2.0) - np.log(0.05)))
+    s2 = np.exp(np.log(1e-4) + u[nset:] * (np.log(1.0) - np.log(1e-4)))
+    return ell, s2
+
+
+def run_sweeps(args):
+    """Batched hyperparameter sweeps on n = 65536 points (untimed by the headline):
+    graph-replayed presized evaluations against the adaptive per-setting loop, and the
+    learned rank predictor's gain on a squared-exponential sweep whose ranks vary with ell."""
+    import torch
+
+    from paper_1403_6015_gb300 import hodlr as H
+    from paper_1403_6015_gb300 import inputs as I
+    from paper_1403_6015_gb300 import rank_model as RM
+    n = 1 << 16
+    x, y = I.workload_1d(n, 1004)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        yd = torch.from_numpy(y).cuda()
+    stream.synchronize()
+    out = {}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    # (1) 256 Matern-5/2 settings: one captured evaluation replayed per setting
+    nset = 256
+    ell, s2 = sweep_settings(nset, 2004)
+    res = {"n": n, "settings": nset, "kernel": "matern52", "leaf": 128, "eps": 1e-12}
+    for prec, name in [(0, "fp64"), (1, "mixed")]:
+        h = H.Hodlr(x, "matern52", [ell[0], 1.0], s2[0], 128, 1e-12, precision=prec,
+                    stream=stream.cuda_stream)
+
+        def adaptive():
+            v = np.zeros(nset)
+            for b in range(nset):
+                h.rebuild([ell[b], 1.0], s2[b])
+                v[b] = h.loglik(yd)
+            return v
+        adaptive()  # warm-up
+        ref, ta = timed(adaptive)
+        h.presize(np.full(h.tree()[0], 4, dtype=np.int32))
+        theta = torch.from_numpy(np.stack([ell, np.ones(nset)], 1).copy()).cuda()
+        sig = torch.from_numpy(s2.copy()).cuda()
+        status = torch.zeros(nset, dtype=torch.int32, device="cuda")
+        h.loglik_sweep(theta, sig, yd, status=status)  # capture
+        got, tg = timed(lambda: h.loglik_sweep(theta, sig, yd, status=status).cpu().numpy())
+        res[name] = {"graph_evals_per_s": nset / tg, "adaptive_evals_per_s": nset / ta,
+                     "speedup": ta / tg, "max_rel_diff": float(np.max(np.abs(got - ref) / np.abs(ref))),
+                     "status_ok": bool((status.cpu().numpy() == 0).all())}
+        h.close()
+    out["batched_matern52"] = res
+
+    # (2) learned rank predictor: trained on the GPU on the FP64 compressor's blocks
+    t0 = time.perf_counter()
+    probs = []
+    ells_tr = np.exp(np.linspace(np.log(0.03), np.log(2.0), 9))
+    for i, nn in enumerate([1 << 12, 1 << 13]):
+        xt, _ = I.workload_1d(nn, 900 + i)
+        for kern in ["exp", "se", "matern32", "matern52"]:
+            for e in ells_tr:
+                for eps in [1e-8, 1e-12]:
+                    probs.append((xt, kern, float(e), 0.01, 64, eps))
+    X, T, R = RM.collect_pairs(probs)
+    net = RM.RankMLP(seed=7)
+    loss = net.train(X, T, steps=1500, lr=3e-3)
+    t_train = time.perf_counter() - t0
+    nset = 64
+    ell, s2 = sweep_settings(nset, 2005)
+    h = H.Hodlr(x, "se", [ell[0], 1.0], s2[0], 128, 1e-10, stream=stream.cuda_stream)
+
+    def adaptive_se():
+        v = np.zeros(nset)
+        for b in range(nset):
+            h.rebuild([ell[b], 1.0], s2[b])
+            v[b] = h.loglik(yd)
+        return v
+    adaptive_se()
+    ref, ta = timed(adaptive_se)
+    RM.sweep_with_predictor(h, net, ell, s2, yd, margin=1)  # captures the groups' graphs
+    (got, st), tp = timed(lambda: RM.sweep_with_predictor(h, net, ell, s2, yd, margin=1))
+    out["predictor_se"] = {
+        "n": n, "settings": nset, "kernel": "se", "eps": 1e-10,
+        "adaptive_evals_per_s": nset / ta, "predicted_evals_per_s": nset / tp, "gain": ta / tp,
+        "groups": st["groups"], "fallbacks": st["fallbacks"],
+        "max_rel_diff": float(np.max(np.abs(got - ref) / np.abs(ref))),
+        "train": {"pairs": int(X.shape[0]), "final_mse": loss, "seconds": t_train,
+                  "steps": 1500}}
+    h.close()
+    net.close()
+    return out
 
 
 def cpu_baseline(x, y):
@@ -353,6 +457,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy checks")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the hyperparameter sweeps")
     ap.add_argument("--n", type=int, default=N, help="points (profiling captures only)")
     ap.add_argument("--precision", type=int, default=-1,
                     help="-1: both forms (default), 0: FP64 only, 1: mixed only")

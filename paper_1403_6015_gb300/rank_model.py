@@ -91,3 +91,35 @@ def collect_pairs(problems, max_rank: int = 64):
         R.append(r)
         h.close()
     return torch.cat(Xs), torch.cat(Ts), np.concatenate(R)
+
+
+def sweep_with_predictor(h, net, ells, sigma2s, y, margin: int = 1):
+    """Log-likelihoods of the settings (ells[b], sigma2s[b]) on the context h (presized per
+    group of settings that share a predicted rank profile, one captured graph per group),
+    with the adaptive path as the fallback for every setting whose evaluation flagged a rank
+    above its prediction. y: CUDA tensor. Returns (loglik array, stats)."""
+    import torch
+    ells = np.asarray(ells, dtype=np.float64)
+    sigma2s = np.asarray(sigma2s, dtype=np.float64)
+    groups = {}
+    for b, ell in enumerate(ells):
+        prof = tuple(int(v) for v in h.predict_level_ranks(net, float(ell), margin))
+        groups.setdefault(prof, []).append(b)
+    out = np.zeros(len(ells))
+    fallback = []
+    for prof, idx in groups.items():
+        idx = np.asarray(idx)
+        h.presize(np.asarray(prof, dtype=np.int32))
+        theta = torch.from_numpy(np.stack([ells[idx], np.ones(len(idx))], 1).copy()).cuda()
+        sig = torch.from_numpy(sigma2s[idx].copy()).cuda()
+        status = torch.zeros(len(idx), dtype=torch.int32, device="cuda")
+        res = h.loglik_sweep(theta, sig, y, status=status)
+        torch.cuda.synchronize()
+        out[idx] = res.cpu().numpy()
+        bad = idx[status.cpu().numpy() != 0]
+        fallback.extend(bad.tolist())
+    h.presize(None)
+    for b in fallback:
+        h.rebuild([float(ells[b]), 1.0], float(sigma2s[b]))
+        out[b] = h.loglik(y)
+    return out, {"groups": len(groups), "fallbacks": len(fallback)}
