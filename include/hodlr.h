@@ -150,6 +150,28 @@ hodlr_status hodlr_loglik_sweep(hodlr_ctx* ctx, int64_t nset, const double* thet
                                 const double* sigma2, const double* y, double* out,
                                 int32_t* status);
 
+/* One lane of a batched run: a presized context with its own non-default stream, and the
+ * settings it evaluates: b = first, first + stride, ..., count of them, each reading
+ * theta[2b], theta[2b+1] (ell, a), sigma2[b], writing out[b] and status[b] (status may be
+ * NULL). y is the context's right-hand side (its n entries). All arrays device pointers. */
+typedef struct {
+  hodlr_ctx* ctx;
+  const double* theta;
+  const double* sigma2;
+  const double* y;
+  double* out;
+  int32_t* status;
+  int64_t first, stride, count;
+} hodlr_batch_lane;
+
+/* Batched evaluation (many settings of one problem, or many independent problems of uneven
+ * size): every lane evaluates its settings in rounds; one round of all lanes is captured as
+ * a single CUDA graph that forks from `stream` (cudaStream_t, not a lane's) into the lanes'
+ * streams, runs them concurrently and joins, and the graph is replayed for the remaining
+ * rounds. The first round runs directly (it sets kernel attributes). Lanes must use
+ * distinct contexts. Stream-ordered on `stream`. Errors: EINVAL, ENOMEM, ECUDA. */
+hodlr_status hodlr_loglik_batched(const hodlr_batch_lane* lanes, int nlanes, void* stream);
+
 /* ---- Learned rank predictor (not in the paper; sizes presized mode from features) ------
  * A multilayer perceptron 12 -> 64 -> 64 -> 1 (tanh hidden units, FP32) maps the features
  * of an off-diagonal block to log(1 + rank). Parameters: W1 (12 x 64, row-major by input),

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 
+#include "ff.cuh"
 #include "hodlr_internal.cuh"
 
 using hodlr::Ctx;
@@ -758,6 +759,131 @@ hodlr_status hodlr_predict_ranks(hodlr_ctx* ctx, hodlr_mlp* mlp, double ell, int
     }
     level_ranks[j] = std::min(mx + margin, c->max_rank - 1);
   }
+  return HODLR_OK;
+}
+
+// Lane step r of a batched run: setting b = first + min(r, count - 1) stride into the
+// device hyperparameter slot (rounds past count repeat the last setting and store nothing).
+__global__ void k_lane_load(double* hyp, int kind, const double* theta, const double* sigma2,
+                            const int32_t* round, int64_t first, int64_t stride, int64_t count) {
+  int64_t r = round[0];
+  int64_t b = first + (r < count ? r : count - 1) * stride;
+  double ell = theta[2 * b], amp = theta[2 * b + 1];
+  hyp[hodlr::kHypInvEll] = 1.0 / ell;
+  hyp[hodlr::kHypAmp] = amp;
+  hyp[hodlr::kHypSigma2] = sigma2[b];
+  hyp[hodlr::kHypScale] = hodlr::cov_scale(kind, ell);
+}
+
+__global__ void k_lane_store(const double* scal, int32_t* flags, int32_t* round, double* out,
+                             int32_t* status, int64_t first, int64_t stride, int64_t count) {
+  int64_t r = round[0];
+  if (r < count) {
+    int64_t b = first + r * stride;
+    out[b] = scal[2];
+    if (status) status[b] = flags[0];
+  }
+  flags[0] = 0;
+  round[0] = (int32_t)(r + 1);
+}
+
+static hodlr_status lane_eval(const hodlr_batch_lane& L) {
+  Ctx* c = reinterpret_cast<Ctx*>(L.ctx);
+  k_lane_load<<<1, 1, 0, c->stream>>>(c->hyp, c->kind, L.theta, L.sigma2, c->sweep_idx, L.first,
+                                      L.stride, L.count);
+  ++c->launches;
+  hodlr_status s = compress(c);
+  if (s != HODLR_OK) return s;
+  TRY_CUDA(c, hodlr::launch_gather_rhs(*c, L.y, c->n, 1), "gather");
+  c->factored = false;
+  s = factor_impl(c, 1);
+  if (s != HODLR_OK) return s;
+  TRY_CUDA(c, hodlr::launch_quad_loglik(*c), "loglik");
+  k_lane_store<<<1, 1, 0, c->stream>>>(c->scal, c->dflags, c->sweep_idx, L.out, L.status, L.first,
+                                       L.stride, L.count);
+  ++c->launches;
+  TRY_CUDA(c, cudaGetLastError(), "store");
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_loglik_batched(const hodlr_batch_lane* lanes, int nlanes, void* stream) {
+  if (!lanes || nlanes < 1 || !stream) return HODLR_EINVAL;
+  cudaStream_t origin = static_cast<cudaStream_t>(stream);
+  int64_t rounds = 0;
+  for (int i = 0; i < nlanes; ++i) {
+    const hodlr_batch_lane& L = lanes[i];
+    Ctx* c = reinterpret_cast<Ctx*>(L.ctx);
+    if (!c || !c->presized || !c->stream || c->stream == origin || L.count < 1 || L.first < 0 ||
+        L.stride < 1 || !is_device_ptr(L.theta) || !is_device_ptr(L.sigma2) ||
+        !is_device_ptr(L.y) || !is_device_ptr(L.out) || (L.status && !is_device_ptr(L.status)))
+      return HODLR_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (lanes[j].ctx == L.ctx) return HODLR_EINVAL;
+    if (!c->sweep_idx && dalloc(&c->sweep_idx, 1) != cudaSuccess) return HODLR_ENOMEM;
+    rounds = std::max(rounds, L.count);
+  }
+  std::vector<cudaEvent_t> ev(nlanes + 1, nullptr);
+  for (auto& e : ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto& f : ev)
+        if (f) cudaEventDestroy(f);
+      return HODLR_ECUDA;
+    }
+  auto cleanup = [&]() {
+    for (auto& f : ev)
+      if (f) cudaEventDestroy(f);
+  };
+  // round counters to zero, ordered before the graph on the origin stream
+  for (int i = 0; i < nlanes; ++i) {
+    Ctx* c = reinterpret_cast<Ctx*>(lanes[i].ctx);
+    cudaMemsetAsync(c->sweep_idx, 0, sizeof(int32_t), origin);
+  }
+  // one direct round first (sets kernel attributes outside the capture)
+  cudaEventRecord(ev[nlanes], origin);
+  for (int i = 0; i < nlanes; ++i) {
+    Ctx* c = reinterpret_cast<Ctx*>(lanes[i].ctx);
+    cudaStreamWaitEvent(c->stream, ev[nlanes], 0);
+    hodlr_status s = lane_eval(lanes[i]);
+    if (s != HODLR_OK) {
+      cleanup();
+      return s;
+    }
+    cudaEventRecord(ev[i], c->stream);
+    cudaStreamWaitEvent(origin, ev[i], 0);
+  }
+  if (rounds > 1) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed);
+    hodlr_status s = HODLR_OK;
+    if (e == cudaSuccess) {
+      cudaEventRecord(ev[nlanes], origin);
+      for (int i = 0; i < nlanes && s == HODLR_OK; ++i) {
+        Ctx* c = reinterpret_cast<Ctx*>(lanes[i].ctx);
+        cudaStreamWaitEvent(c->stream, ev[nlanes], 0);
+        s = lane_eval(lanes[i]);
+        cudaEventRecord(ev[i], c->stream);
+        cudaStreamWaitEvent(origin, ev[i], 0);
+      }
+      e = cudaStreamEndCapture(origin, &g);
+    }
+    if (s == HODLR_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    for (int64_t r = 1; r < rounds && s == HODLR_OK && e == cudaSuccess; ++r)
+      e = cudaGraphLaunch(ge, origin);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (s == HODLR_OK && e != cudaSuccess) {
+      cudaGetLastError();
+      s = HODLR_ECUDA;
+    }
+    if (s != HODLR_OK) {
+      cleanup();
+      return s;
+    }
+  }
+  // events may be destroyed once recorded work is enqueued
+  cleanup();
   return HODLR_OK;
 }
 

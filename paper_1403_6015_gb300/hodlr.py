@@ -21,6 +21,12 @@ HODLR_OK, HODLR_EINVAL, HODLR_ENOMEM, HODLR_ENOTSPD, HODLR_ERANK = 0, 1, 2, 3, 4
 HODLR_ETIMEOUT, HODLR_ESTATE, HODLR_ECUDA = 5, 6, 7
 
 
+class hodlr_batch_lane(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("theta", ctypes.c_void_p), ("sigma2", ctypes.c_void_p),
+                ("y", ctypes.c_void_p), ("out", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("first", ctypes.c_int64), ("stride", ctypes.c_int64), ("count", ctypes.c_int64)]
+
+
 class hodlr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rank_mode", ctypes.c_int),
                 ("max_rank", ctypes.c_int), ("max_nrhs", ctypes.c_int),
@@ -60,6 +66,7 @@ def load():
     L.hodlr_presize.argtypes = [_vp, _dp, ctypes.c_int]
     L.hodlr_status_flags.argtypes = [_vp, _dp]
     L.hodlr_loglik_sweep.argtypes = [_vp, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp]
+    L.hodlr_loglik_batched.argtypes = [ctypes.POINTER(hodlr_batch_lane), ctypes.c_int, _vp]
     L.hodlr_mlp_num_params.restype = ctypes.c_int
     L.hodlr_mlp_num_features.restype = ctypes.c_int
     L.hodlr_mlp_create.argtypes = [ctypes.c_uint64, _vp, ctypes.POINTER(_vp)]
@@ -85,7 +92,8 @@ def load():
                  "hodlr_loglik_small_noalloc", "hodlr_presize", "hodlr_status_flags",
                  "hodlr_loglik_sweep", "hodlr_mlp_create", "hodlr_mlp_params",
                  "hodlr_mlp_forward", "hodlr_mlp_gradient", "hodlr_mlp_train", "hodlr_mlp_save",
-                 "hodlr_mlp_load", "hodlr_block_features", "hodlr_predict_ranks"):
+                 "hodlr_mlp_load", "hodlr_block_features", "hodlr_predict_ranks",
+                 "hodlr_loglik_batched"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -204,6 +212,29 @@ def hodlr_status_flags(ctx):
 def hodlr_loglik_sweep(ctx, nset, theta_addr, sigma2_addr, y_addr, out_addr, status_addr=None):
     return load().hodlr_loglik_sweep(ctx, nset, theta_addr, sigma2_addr, y_addr, out_addr,
                                      status_addr)
+
+
+def hodlr_loglik_batched(lanes, stream):
+    """lanes: sequence of hodlr_batch_lane; stream: cudaStream_t handle (int)."""
+    arr = (hodlr_batch_lane * len(lanes))(*lanes)
+    return load().hodlr_loglik_batched(arr, len(lanes), stream)
+
+
+def loglik_batched(contexts, theta, sigma2, y, out, status=None, stream=None):
+    """Settings b of (theta (nset, 2), sigma2 (nset,)) on len(contexts) presized contexts of
+    the same points, lane i taking settings i, i + L, ...; CUDA tensors throughout."""
+    import torch
+    nset = theta.shape[0]
+    L = len(contexts)
+    lanes = [hodlr_batch_lane(h._ctx, theta.data_ptr(), sigma2.data_ptr(), y.data_ptr(),
+                              out.data_ptr(), status.data_ptr() if status is not None else None,
+                              i, L, (nset - i + L - 1) // L)
+             for i, h in enumerate(contexts) if i < nset]
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    st = hodlr_loglik_batched(lanes, s)
+    if st != HODLR_OK:
+        raise HodlrError(st, "hodlr_loglik_batched")
+    return out
 
 
 def hodlr_mlp_num_params() -> int:

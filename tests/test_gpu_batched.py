@@ -1,0 +1,105 @@
+"""Batched evaluation: one CUDA graph forks a round of evaluations into several presized
+contexts (lanes) on their own streams; every result must equal the adaptive single
+evaluation of the same setting."""
+import numpy as np
+import pytest
+
+from paper_1403_6015_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_1403_6015_gb300 import build_lib, hodlr
+    build_lib.build()
+    hodlr.load()
+    return hodlr
+
+
+def settings(nset, seed):
+    u = I.uniform01(seed, 2 * nset)
+    ell = np.exp(np.log(0.05) + u[:nset] * (np.log(2.0) - np.log(0.05)))
+    s2 = np.exp(np.log(1e-4) + u[nset:] * (np.log(1.0) - np.log(1e-4)))
+    return ell, s2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_sweep_lanes(H, precision):
+    import torch
+    n, nset, L = 1 << 14, 32, 8
+    x, y = I.workload_1d(n, 1010)
+    ell, s2 = settings(nset, 81)
+    streams = [torch.cuda.Stream() for _ in range(L)]
+    ctxs = []
+    for s in streams:
+        h = H.Hodlr(x, "matern52", [ell[0], 1.0], s2[0], 128, 1e-12, precision=precision,
+                    stream=s.cuda_stream)
+        h.presize(np.full(h.tree()[0], 4, dtype=np.int32))
+        ctxs.append(h)
+    theta = torch.from_numpy(np.stack([ell, np.ones(nset)], 1).copy()).cuda()
+    sig = torch.from_numpy(s2.copy()).cuda()
+    yd = torch.from_numpy(y).cuda()
+    out = torch.zeros(nset, dtype=torch.float64, device="cuda")
+    status = torch.full((nset,), -1, dtype=torch.int32, device="cuda")
+    origin = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    H.loglik_batched(ctxs, theta, sig, yd, out, status, stream=origin.cuda_stream)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert (status.cpu().numpy() == 0).all()
+    for b in range(nset):
+        r = H.Hodlr(x, "matern52", [ell[b], 1.0], s2[b], 128, 1e-12, precision=precision).loglik(y)
+        assert abs(got[b] - r) <= 1e-12 * abs(r), (b, got[b], r)
+
+
+def test_batched_uneven_instances(H):
+    """Independent problems of uneven size (n log-uniform in [2^12, 2^15]), one lane each,
+    three settings per problem."""
+    import torch
+    rng_n = I.uniform01(555, 6)
+    sizes = np.round(np.exp(np.log(4096) + rng_n * (np.log(32768) - np.log(4096)))).astype(int)
+    nset = 3
+    lanes, keep = [], []
+    origin = torch.cuda.Stream()
+    for i, n in enumerate(sizes):
+        x, y = I.workload_1d(int(n), 1100 + i)
+        ell, s2 = settings(nset, 200 + i)
+        s = torch.cuda.Stream()
+        h = H.Hodlr(x, "matern32", [ell[0], 1.0], s2[0], 64, 1e-12, stream=s.cuda_stream)
+        h.presize(np.full(h.tree()[0], 3, dtype=np.int32))
+        theta = torch.from_numpy(np.stack([ell, np.ones(nset)], 1).copy()).cuda()
+        sig = torch.from_numpy(s2.copy()).cuda()
+        yd = torch.from_numpy(y).cuda()
+        out = torch.zeros(nset, dtype=torch.float64, device="cuda")
+        st = torch.full((nset,), -1, dtype=torch.int32, device="cuda")
+        lanes.append(H.hodlr_batch_lane(h._ctx, theta.data_ptr(), sig.data_ptr(), yd.data_ptr(),
+                                        out.data_ptr(), st.data_ptr(), 0, 1, nset))
+        keep.append((h, s, x, y, ell, s2, theta, sig, yd, out, st))
+    torch.cuda.synchronize()
+    assert H.hodlr_loglik_batched(lanes, origin.cuda_stream) == H.HODLR_OK
+    torch.cuda.synchronize()
+    for h, s, x, y, ell, s2, theta, sig, yd, out, st in keep:
+        assert (st.cpu().numpy() == 0).all()
+        got = out.cpu().numpy()
+        for b in range(nset):
+            r = H.Hodlr(x, "matern32", [ell[b], 1.0], s2[b], 64, 1e-12).loglik(y)
+            assert abs(got[b] - r) <= 1e-12 * abs(r)
+
+
+def test_batched_rejects_bad_lanes(H):
+    import torch
+    x, y = I.workload_1d(4096, 1020)
+    s = torch.cuda.Stream()
+    h = H.Hodlr(x, "exp", [0.2, 1.0], 0.01, 64, 1e-12, stream=s.cuda_stream)  # not presized
+    theta = torch.ones((2, 2), dtype=torch.float64, device="cuda")
+    sig = torch.ones(2, dtype=torch.float64, device="cuda")
+    yd = torch.from_numpy(y).cuda()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    lane = H.hodlr_batch_lane(h._ctx, theta.data_ptr(), sig.data_ptr(), yd.data_ptr(),
+                              out.data_ptr(), None, 0, 1, 2)
+    origin = torch.cuda.Stream()
+    assert H.hodlr_loglik_batched([lane], origin.cuda_stream) == H.HODLR_EINVAL
+    h.presize(np.full(h.tree()[0], 2, dtype=np.int32))
+    assert H.hodlr_loglik_batched([lane], s.cuda_stream) == H.HODLR_EINVAL  # origin = lane stream
+    assert H.hodlr_loglik_batched([lane, lane], origin.cuda_stream) == H.HODLR_EINVAL
