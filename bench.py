@@ -311,9 +311,11 @@ def sweep_settings(nset, seed):
 
 
 def run_sweeps(args):
-    """Batched hyperparameter sweeps on n = 65536 points (untimed by the headline):
-    graph-replayed presized evaluations against the adaptive per-setting loop, and the
-    learned rank predictor's gain on a squared-exponential sweep whose ranks vary with ell."""
+    """Batched evaluation (outside the headline's timed region): 256 Matern-5/2 settings on
+    n = 65536 points, graph-replayed on one context and forked over 8 lanes, against the
+    adaptive per-setting loop; 64 independent problems of uneven size, one lane each; and
+    the learned rank predictor's gain on a squared-exponential sweep whose ranks vary with
+    ell."""
     import torch
 
     from paper_1403_6015_gb300 import hodlr as H
@@ -360,7 +362,88 @@ def run_sweeps(args):
                      "speedup": ta / tg, "max_rel_diff": float(np.max(np.abs(got - ref) / np.abs(ref))),
                      "status_ok": bool((status.cpu().numpy() == 0).all())}
         h.close()
+        # the same settings on L presized contexts (lanes), each on its own stream: one
+        # graph forks every round into all lanes, which run concurrently
+        L = 8
+        lane_streams = [torch.cuda.Stream() for _ in range(L)]
+        ctxs = []
+        for ls in lane_streams:
+            hl = H.Hodlr(x, "matern52", [ell[0], 1.0], s2[0], 128, 1e-12, precision=prec,
+                         stream=ls.cuda_stream)
+            hl.presize(np.full(hl.tree()[0], 4, dtype=np.int32))
+            ctxs.append(hl)
+        outl = torch.zeros(nset, dtype=torch.float64, device="cuda")
+        status.fill_(-1)
+        H.loglik_batched(ctxs, theta, sig, yd, outl, status, stream=stream.cuda_stream)
+        gotl, tl = timed(lambda: H.loglik_batched(ctxs, theta, sig, yd, outl, status,
+                                                  stream=stream.cuda_stream).cpu().numpy())
+        res[name].update({"lanes": L, "lanes_evals_per_s": nset / tl, "lanes_speedup": ta / tl,
+                          "lanes_max_rel_diff": float(np.max(np.abs(gotl - ref) / np.abs(ref))),
+                          "lanes_status_ok": bool((status.cpu().numpy() == 0).all())})
+        for hl in ctxs:
+            hl.close()
     out["batched_matern52"] = res
+
+    # (1b) 64 independent problems of uneven size (n log-uniform in [2^12, 2^18]), four
+    # settings each: one lane per problem against the per-problem adaptive loop
+    ninst, per = 64, 4
+    un = I.uniform01(3003, ninst)
+    sizes = np.round(np.exp(np.log(4096.0) + un * (np.log(262144.0) - np.log(4096.0)))).astype(int)
+    res = {"instances": ninst, "settings_per_instance": per, "n_min": int(sizes.min()),
+           "n_max": int(sizes.max()), "n_total": int(sizes.sum()), "kernel": "matern52",
+           "leaf": 128, "eps": 1e-12}
+    # torch hands out streams round-robin from a pool of 32: a fresh origin and 16 lane
+    # streams created back to back are distinct; instances share lane streams round-robin
+    origin = torch.cuda.Stream()
+    pool = [torch.cuda.Stream() for _ in range(16)]
+    for prec, name in [(0, "fp64"), (1, "mixed")]:
+        inst = []
+        for i, ni in enumerate(sizes):
+            xi, yi = I.workload_1d(int(ni), 3100 + i)
+            e_i, s_i = sweep_settings(per, 3300 + i)
+            si = pool[i % len(pool)]
+            hi = H.Hodlr(xi, "matern52", [e_i[0], 1.0], s_i[0], 128, 1e-12, precision=prec,
+                         stream=si.cuda_stream)
+            th = torch.from_numpy(np.stack([e_i, np.ones(per)], 1).copy()).cuda()
+            sg = torch.from_numpy(s_i.copy()).cuda()
+            yi_d = torch.from_numpy(yi).cuda()
+            inst.append((hi, si, e_i, s_i, th, sg, yi_d,
+                         torch.zeros(per, dtype=torch.float64, device="cuda"),
+                         torch.full((per,), -1, dtype=torch.int32, device="cuda")))
+        torch.cuda.synchronize()
+
+        def adaptive_inst():
+            v = np.zeros((ninst, per))
+            for i, (hi, si, e_i, s_i, th, sg, yi_d, _, _) in enumerate(inst):
+                for b in range(per):
+                    hi.rebuild([e_i[b], 1.0], s_i[b])
+                    v[i, b] = hi.loglik(yi_d)
+            return v
+        adaptive_inst()
+        ref, ta = timed(adaptive_inst)
+        for hi, *_ in inst:
+            hi.presize(np.full(hi.tree()[0], 4, dtype=np.int32))
+        lanes = [H.hodlr_batch_lane(hi._ctx, th.data_ptr(), sg.data_ptr(), yi_d.data_ptr(),
+                                    o.data_ptr(), st.data_ptr(), 0, 1, per)
+                 for hi, si, e_i, s_i, th, sg, yi_d, o, st in inst]
+
+        def lanes_inst():
+            st = H.hodlr_loglik_batched(lanes, origin.cuda_stream)
+            if st != H.HODLR_OK:
+                raise H.HodlrError(st, "; ".join(sorted({H.hodlr_last_error(t[0]._ctx)
+                                                         for t in inst})))
+            return np.stack([o.cpu().numpy() for *_, o, st in inst])
+        lanes_inst()
+        got, tl = timed(lanes_inst)
+        ok = all(bool((st.cpu().numpy() == 0).all()) for *_, st in inst)
+        res[name] = {"lane_streams": len(pool),
+                     "adaptive_evals_per_s": ninst * per / ta, "lanes_evals_per_s": ninst * per / tl,
+                     "speedup": ta / tl, "max_rel_diff": float(np.max(np.abs(got - ref) / np.abs(ref))),
+                     "status_ok": ok,
+                     "points_per_s": float(sizes.sum()) * per / tl}
+        for hi, *_ in inst:
+            hi.close()
+    out["uneven_instances"] = res
 
     # (2) learned rank predictor: trained on the GPU on the FP64 compressor's blocks
     t0 = time.perf_counter()

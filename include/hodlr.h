@@ -63,8 +63,15 @@ typedef struct {
   int rank_mode;       /* 0: adaptive ACA ranks                                            */
   int max_rank;        /* cap on the ACA rank of one off-diagonal block (1..64), default 64 */
   int max_nrhs;        /* right-hand sides carried through a fused factor, default 16     */
-  double refine_tol;   /* reserved (iterative refinement), default 1e-10                  */
-  int refine_maxit;    /* reserved, default 0                                             */
+  double refine_tol;   /* iterative refinement (not in the paper): stop when              */
+                       /*    ||y - C~ x||_2 <= refine_tol ||y||_2, C~ the FP64 HODLR       */
+                       /*    matrix (hodlr_matvec); default 1e-10, > 0 when refine_maxit>0 */
+  int refine_maxit;    /* most correction solves per right-hand side after every solve   */
+                       /*    (hodlr_factor_solve, hodlr_solve, hodlr_loglik and the sweep   */
+                       /*    and batched forms); each is one matvec + one solve with the   */
+                       /*    stored factor. 0 = off (default). The sweep and batched forms */
+                       /*    and solves under stream capture take exactly refine_maxit     */
+                       /*    corrections (no host check of the residual).                  */
   void* stream;        /* cudaStream_t for all device work; NULL = legacy default stream  */
 } hodlr_opts;
 
@@ -150,7 +157,7 @@ hodlr_status hodlr_loglik_sweep(hodlr_ctx* ctx, int64_t nset, const double* thet
                                 const double* sigma2, const double* y, double* out,
                                 int32_t* status);
 
-/* One lane of a batched run: a presized context with its own non-default stream, and the
+/* One lane of a batched run: a presized context on a non-default stream, and the
  * settings it evaluates: b = first, first + stride, ..., count of them, each reading
  * theta[2b], theta[2b+1] (ell, a), sigma2[b], writing out[b] and status[b] (status may be
  * NULL). y is the context's right-hand side (its n entries). All arrays device pointers. */
@@ -169,7 +176,9 @@ typedef struct {
  * a single CUDA graph that forks from `stream` (cudaStream_t, not a lane's) into the lanes'
  * streams, runs them concurrently and joins, and the graph is replayed for the remaining
  * rounds. The first round runs directly (it sets kernel attributes). Lanes must use
- * distinct contexts. Stream-ordered on `stream`. Errors: EINVAL, ENOMEM, ECUDA. */
+ * distinct contexts; lanes whose contexts share a stream run one after another on it. No
+ * lane's stream may be `stream` itself. Stream-ordered on `stream`. Errors (message in the
+ * offending lane's hodlr_last_error): EINVAL, ENOMEM, ECUDA. */
 hodlr_status hodlr_loglik_batched(const hodlr_batch_lane* lanes, int nlanes, void* stream);
 
 /* ---- Learned rank predictor (not in the paper; sizes presized mode from features) ------
@@ -241,6 +250,12 @@ hodlr_status hodlr_phase_ms(hodlr_ctx* ctx, float* out6);
 /* Counters since hodlr_build, into a host array of 2 int64: out[0] CUDA kernels this
  * context launched, out[1] host synchronisations it performed. */
 hodlr_status hodlr_counters(hodlr_ctx* ctx, int64_t* out2);
+
+/* Iterative refinement of the last solve (opts.refine_maxit > 0; not in the paper): the
+ * corrections it took over all right-hand sides, and the largest final relative residual
+ * ||y - C~ x|| / ||y|| it measured (0 when refinement is off or ran without host checks).
+ * Either output may be NULL. Errors: EINVAL. */
+hodlr_status hodlr_refine_info(hodlr_ctx* ctx, int32_t* corrections, double* residual);
 
 /* Log-likelihood of a problem small enough to be one leaf block, with no device
  * allocation. The paper has no counterpart: this entry exists for callers that must not

@@ -82,7 +82,7 @@ void free_all(Ctx* c) {
   dfree(c->st_zero); dfree(c->st_phase); dfree(c->st_nused); dfree(c->st_used);
   dfree(c->st_delta); dfree(c->st_s2); dfree(c->aca_part); dfree(c->active);
   dfree(c->Y); dfree(c->ysort); dfree(c->leafL); dfree(c->leaf_logdet); dfree(c->node_logdet);
-  dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->Mlu); dfree(c->Mpiv);
+  dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->ry); dfree(c->rw); dfree(c->Mlu); dfree(c->Mpiv);
   dfree(c->hyp);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
@@ -339,7 +339,8 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
       leaf > hodlr::kMaxLeaf || !(eps > 0) || !std::isfinite(eps) || !(sigma2 >= 0) ||
       !std::isfinite(sigma2) || bad_theta(theta) || (int)kernel < 0 || (int)kernel > 3 ||
       opts.max_rank < 1 || opts.max_rank > hodlr::kMaxRank || opts.max_nrhs < 1 ||
-      (opts.precision != 0 && opts.precision != 1))
+      (opts.precision != 0 && opts.precision != 1) || opts.refine_maxit < 0 ||
+      (opts.refine_maxit > 0 && (!(opts.refine_tol > 0) || !std::isfinite(opts.refine_tol))))
     return HODLR_EINVAL;
   Ctx* c = new (std::nothrow) Ctx;
   if (!c) return HODLR_ENOMEM;
@@ -354,6 +355,8 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   c->max_rank = opts.max_rank;
   c->max_nrhs = opts.max_nrhs;
   c->precision = opts.precision;
+  c->refine_tol = opts.refine_tol;
+  c->refine_maxit = opts.refine_maxit;
   if (const char* e = std::getenv("HODLR_LEAF_THREADS")) c->leaf_threads = std::atoi(e);
   if (const char* e = std::getenv("HODLR_LEAF_THREADS64")) c->leaf_threads64 = std::atoi(e);
   if (const char* e = std::getenv("HODLR_NO_FUSED")) c->no_fused = std::atoi(e) != 0;
@@ -377,6 +380,8 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
       dalloc(&c->Y, n * c->max_nrhs) || dalloc(&c->ysort, n) || dalloc(&c->tmpvec, n * c->max_nrhs) ||
       dalloc(&c->leaf_logdet, nleaf) || dalloc(&c->node_logdet, std::max<int64_t>(nleaf - 1, 1)) ||
       dalloc(&c->leafL, nleaf * hodlr::kMaxLeaf * hodlr::kMaxLeaf) ||
+      (c->refine_maxit > 0 && (dalloc(&c->ry, n * c->max_nrhs) ||
+                               dalloc(&c->rw, hodlr::refine_work_elems(n)))) ||
       cudaMallocHost(&c->h_active, sizeof(int32_t)) != cudaSuccess) {
     cudaGetLastError();
     return bail(HODLR_ENOMEM);
@@ -497,6 +502,59 @@ static cudaError_t sweep(Ctx* c, int nrhs, bool factor_mode) {
   return hodlr::launch_levels(*c, nrhs, factor_mode);
 }
 
+// Right-hand sides into c->Y in tree order (and, with refinement on, their copy in c->ry).
+static cudaError_t gather_rhs(Ctx* c, const double* y, int64_t ld, int nrhs) {
+  cudaError_t e = hodlr::launch_gather_rhs(*c, y, ld, nrhs);
+  if (e == cudaSuccess && c->refine_maxit > 0)
+    e = cudaMemcpyAsync(c->ry, c->Y, sizeof(double) * c->n * nrhs, cudaMemcpyDeviceToDevice, c->stream);
+  return e;
+}
+
+// Iterative refinement of the nrhs solutions in c->Y (not in the paper): per column,
+// r = y - C~ x with the FP64 HODLR product, stop when ||r|| / ||y|| <= refine_tol, else
+// solve C d = r with the stored factor (in place in the work vector) and x += d, at most
+// refine_maxit times. Under stream capture, and in the sweep and batched forms (fixed =
+// true, so that their eager first evaluation matches the replays), there is no host check:
+// exactly refine_maxit corrections per column.
+static hodlr_status refine(Ctx* c, int nrhs, bool fixed = false) {
+  c->refine_corr = 0;
+  c->refine_res = 0.0;
+  if (c->refine_maxit <= 0) return HODLR_OK;
+  bool cap = fixed || capturing(c);
+  int64_t n = c->n;
+  double* r = c->rw;
+  double* part = c->rw + n;
+  double* ratio = c->rw + hodlr::refine_work_elems(n) - 8;
+  for (int col = 0; col < nrhs; ++col) {
+    double* x = c->Y + (int64_t)col * n;
+    const double* y = c->ry + (int64_t)col * n;
+    for (int it = 0; it <= c->refine_maxit; ++it) {
+      if (cap && it == c->refine_maxit) break;
+      TRY_CUDA(c, hodlr::launch_matvec(*c, x, r), "refine: matvec");
+      TRY_CUDA(c, hodlr::launch_residual(*c, y, r, part, ratio), "refine: residual");
+      if (!cap) {
+        double res = 0.0;
+        TRY_CUDA(c, cudaMemcpyAsync(&res, ratio, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "refine");
+        TRY_CUDA(c, cudaStreamSynchronize(c->stream), "refine");
+        ++c->syncs;
+        if (res <= c->refine_tol || it == c->refine_maxit) {
+          c->refine_res = std::max(c->refine_res, res);
+          break;
+        }
+      }
+      double* ysave = c->Y;
+      c->Y = r;
+      cudaError_t e = c->precision == 1 ? hodlr::launch_leaf_solve_ff(*c, 1) : hodlr::launch_leaf_solve(*c, 1);
+      if (e == cudaSuccess) e = sweep(c, 1, false);
+      c->Y = ysave;
+      TRY_CUDA(c, e, "refine: correction solve");
+      TRY_CUDA(c, hodlr::launch_axpy(*c, x, r), "refine: update");
+      ++c->refine_corr;
+    }
+  }
+  return HODLR_OK;
+}
+
 // Factor with nrhs right-hand sides already gathered into c->Y (nrhs may be 0).
 static hodlr_status factor_impl(Ctx* c, int nrhs) {
   if (!c->compressed) return fail(c, HODLR_ESTATE, "not compressed");
@@ -545,8 +603,10 @@ hodlr_status hodlr_factor_solve(hodlr_ctx* ctx, const double* y, double* x, int 
   int64_t ldd;
   hodlr_status s = stage_in(c, y, nrhs, ld, &yd, &ldd);
   if (s != HODLR_OK) return s;
-  TRY_CUDA(c, hodlr::launch_gather_rhs(*c, yd, ldd, nrhs), "gather");
+  TRY_CUDA(c, gather_rhs(c, yd, ldd, nrhs), "gather");
   s = factor_impl(c, nrhs);
+  if (s != HODLR_OK) return s;
+  s = refine(c, nrhs);
   if (s != HODLR_OK) return s;
   return write_out(c, x, nrhs, ld);
 }
@@ -563,12 +623,14 @@ hodlr_status hodlr_solve(hodlr_ctx* ctx, const double* y, double* x, int nrhs, i
     hodlr_status s = stage_in(c, y + (int64_t)c0 * ld, nb, ld, &yd, &ldd);
     if (s != HODLR_OK) return s;
     cudaEventRecord(c->ev[4], c->stream);
-    TRY_CUDA(c, hodlr::launch_gather_rhs(*c, yd, ldd, nb), "gather");
+    TRY_CUDA(c, gather_rhs(c, yd, ldd, nb), "gather");
     if (c->precision == 1)
       TRY_CUDA(c, hodlr::launch_leaf_solve_ff(*c, nb), "leaf solve (double-float)");
     else
       TRY_CUDA(c, hodlr::launch_leaf_solve(*c, nb), "leaf solve");
     TRY_CUDA(c, sweep(c, nb, false), "levels");
+    s = refine(c, nb);
+    if (s != HODLR_OK) return s;
     cudaEventRecord(c->ev[5], c->stream);
     c->solve_timed = true;
     s = write_out(c, x + (int64_t)c0 * ld, nb, ld);
@@ -602,7 +664,7 @@ hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out) {
   int64_t ldd;
   hodlr_status s = stage_in(c, y, 1, c->n, &yd, &ldd);
   if (s != HODLR_OK) return s;
-  TRY_CUDA(c, hodlr::launch_gather_rhs(*c, yd, ldd, 1), "gather");
+  TRY_CUDA(c, gather_rhs(c, yd, ldd, 1), "gather");
   if (!c->factored) {
     s = factor_impl(c, 1);
     if (s != HODLR_OK) return s;
@@ -613,6 +675,8 @@ hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out) {
       TRY_CUDA(c, hodlr::launch_leaf_solve(*c, 1), "leaf solve");
     TRY_CUDA(c, sweep(c, 1, false), "levels");
   }
+  s = refine(c, 1);
+  if (s != HODLR_OK) return s;
   TRY_CUDA(c, hodlr::launch_quad_loglik(*c), "loglik");
   return write_scalar(c, c->scal + 2, out);
 }
@@ -668,9 +732,11 @@ static hodlr_status sweep_eval(Ctx* c, const double* theta, const double* sigma2
   TRY_CUDA(c, hodlr::launch_load_setting(*c, theta, sigma2, c->sweep_idx), "setting");
   hodlr_status s = compress(c);
   if (s != HODLR_OK) return s;
-  TRY_CUDA(c, hodlr::launch_gather_rhs(*c, y, c->n, 1), "gather");
+  TRY_CUDA(c, gather_rhs(c, y, c->n, 1), "gather");
   c->factored = false;
   s = factor_impl(c, 1);
+  if (s != HODLR_OK) return s;
+  s = refine(c, 1, true);
   if (s != HODLR_OK) return s;
   TRY_CUDA(c, hodlr::launch_quad_loglik(*c), "loglik");
   k_store_setting<<<1, 1, 0, c->stream>>>(c->scal, c->dflags, c->sweep_idx, out, status);
@@ -794,9 +860,11 @@ static hodlr_status lane_eval(const hodlr_batch_lane& L) {
   ++c->launches;
   hodlr_status s = compress(c);
   if (s != HODLR_OK) return s;
-  TRY_CUDA(c, hodlr::launch_gather_rhs(*c, L.y, c->n, 1), "gather");
+  TRY_CUDA(c, gather_rhs(c, L.y, c->n, 1), "gather");
   c->factored = false;
   s = factor_impl(c, 1);
+  if (s != HODLR_OK) return s;
+  s = refine(c, 1, true);
   if (s != HODLR_OK) return s;
   TRY_CUDA(c, hodlr::launch_quad_loglik(*c), "loglik");
   k_lane_store<<<1, 1, 0, c->stream>>>(c->scal, c->dflags, c->sweep_idx, L.out, L.status, L.first,
@@ -813,13 +881,19 @@ hodlr_status hodlr_loglik_batched(const hodlr_batch_lane* lanes, int nlanes, voi
   for (int i = 0; i < nlanes; ++i) {
     const hodlr_batch_lane& L = lanes[i];
     Ctx* c = reinterpret_cast<Ctx*>(L.ctx);
-    if (!c || !c->presized || !c->stream || c->stream == origin || L.count < 1 || L.first < 0 ||
-        L.stride < 1 || !is_device_ptr(L.theta) || !is_device_ptr(L.sigma2) ||
-        !is_device_ptr(L.y) || !is_device_ptr(L.out) || (L.status && !is_device_ptr(L.status)))
-      return HODLR_EINVAL;
+    if (!c) return HODLR_EINVAL;
+    if (!c->presized) return fail(c, HODLR_EINVAL, "batched: lane context is not presized");
+    if (!c->stream || c->stream == origin)
+      return fail(c, HODLR_EINVAL, "batched: a lane stream must be non-default and differ from the caller's stream");
+    if (L.count < 1 || L.first < 0 || L.stride < 1)
+      return fail(c, HODLR_EINVAL, "batched: bad first/stride/count");
+    if (!is_device_ptr(L.theta) || !is_device_ptr(L.sigma2) || !is_device_ptr(L.y) ||
+        !is_device_ptr(L.out) || (L.status && !is_device_ptr(L.status)))
+      return fail(c, HODLR_EINVAL, "batched: theta, sigma2, y, out, status must be device pointers");
     for (int j = 0; j < i; ++j)
-      if (lanes[j].ctx == L.ctx) return HODLR_EINVAL;
-    if (!c->sweep_idx && dalloc(&c->sweep_idx, 1) != cudaSuccess) return HODLR_ENOMEM;
+      if (lanes[j].ctx == L.ctx) return fail(c, HODLR_EINVAL, "batched: context used by two lanes");
+    if (!c->sweep_idx && dalloc(&c->sweep_idx, 1) != cudaSuccess)
+      return fail(c, HODLR_ENOMEM, "batched: counter");
     rounds = std::max(rounds, L.count);
   }
   std::vector<cudaEvent_t> ev(nlanes + 1, nullptr);
@@ -875,7 +949,8 @@ hodlr_status hodlr_loglik_batched(const hodlr_batch_lane* lanes, int nlanes, voi
     if (ge) cudaGraphExecDestroy(ge);
     if (s == HODLR_OK && e != cudaSuccess) {
       cudaGetLastError();
-      s = HODLR_ECUDA;
+      s = fail(reinterpret_cast<Ctx*>(lanes[0].ctx), HODLR_ECUDA,
+               std::string("batched: graph capture or replay: ") + cudaGetErrorString(e));
     }
     if (s != HODLR_OK) {
       cleanup();
@@ -924,6 +999,14 @@ hodlr_status hodlr_matvec(hodlr_ctx* ctx, const double* x, double* y) {
   TRY_CUDA(c, cudaMemcpyAsync(c->ysort, c->Y, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream), "copy");
   TRY_CUDA(c, hodlr::launch_matvec(*c, c->ysort, c->Y), "matvec");
   return write_out(c, y, 1, c->n);
+}
+
+hodlr_status hodlr_refine_info(hodlr_ctx* ctx, int32_t* corrections, double* residual) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  if (corrections) *corrections = c->refine_corr;
+  if (residual) *residual = c->refine_res;
+  return HODLR_OK;
 }
 
 hodlr_status hodlr_phase_ms(hodlr_ctx* ctx, float* out6) {

@@ -165,6 +165,13 @@ struct Ctx {
   double* hyp = nullptr;          // device hyperparameter slot (kHyp* layout)
   int32_t* dflags = nullptr;
   double* tmpvec = nullptr;       // n x max_nrhs staging for host/device copies
+  // iterative refinement (refine.cu): sorted right-hand sides and work vectors
+  double refine_tol = 1e-10;
+  int refine_maxit = 0;
+  double* ry = nullptr;           // n x max_nrhs sorted right-hand sides (refine_maxit > 0)
+  double* rw = nullptr;           // C~ x, then r and its correction (n), partials, ratio
+  int refine_corr = 0;            // corrections taken by the last solve (all columns)
+  double refine_res = 0.0;        // largest final ||y - C~ x|| / ||y|| of the last solve
 
   bool compressed = false;
   bool factored = false;
@@ -207,6 +214,9 @@ cudaError_t launch_levels_fused(Ctx& c, int nrhs, bool factor_mode);
 cudaError_t launch_logdet_sum(Ctx& c);
 cudaError_t launch_quad_loglik(Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double* xin_sorted, double* yout_sorted);
+int64_t refine_work_elems(int64_t n);
+cudaError_t launch_residual(Ctx& c, const double* y_sorted, double* ax, double* part, double* ratio);
+cudaError_t launch_axpy(Ctx& c, double* x, const double* d);
 cudaError_t launch_set_hyp(Ctx& c, double ell, double amp, double sigma2);
 cudaError_t launch_block_features(Ctx& c, double ell, float* X, int64_t ld);
 cudaError_t launch_mlp_forward(Ctx& c, hodlr_mlp* m, const float* X, int64_t N, float* Y);

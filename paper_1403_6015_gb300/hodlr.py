@@ -63,6 +63,7 @@ def load():
     L.hodlr_matvec.argtypes = [_vp, _dp, _dp]
     L.hodlr_phase_ms.argtypes = [_vp, _dp]
     L.hodlr_counters.argtypes = [_vp, _dp]
+    L.hodlr_refine_info.argtypes = [_vp, _dp, _dp]
     L.hodlr_presize.argtypes = [_vp, _dp, ctypes.c_int]
     L.hodlr_status_flags.argtypes = [_vp, _dp]
     L.hodlr_loglik_sweep.argtypes = [_vp, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp]
@@ -93,7 +94,7 @@ def load():
                  "hodlr_loglik_sweep", "hodlr_mlp_create", "hodlr_mlp_params",
                  "hodlr_mlp_forward", "hodlr_mlp_gradient", "hodlr_mlp_train", "hodlr_mlp_save",
                  "hodlr_mlp_load", "hodlr_block_features", "hodlr_predict_ranks",
-                 "hodlr_loglik_batched"):
+                 "hodlr_loglik_batched", "hodlr_refine_info"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -187,6 +188,11 @@ def hodlr_counters(ctx, buf):
     return load().hodlr_counters(ctx, _addr(buf))
 
 
+def hodlr_refine_info(ctx, corrections, residual):
+    """corrections: int32 numpy array (1); residual: float64 numpy array (1)."""
+    return load().hodlr_refine_info(ctx, _addr(corrections), _addr(residual))
+
+
 def hodlr_loglik_small_noalloc(x_addr, n, d, kernel, theta, sigma2, y_addr, out_addr,
                                stream=None):
     """Device pointers only; n <= 128; no device allocation (see include/hodlr.h)."""
@@ -233,7 +239,8 @@ def loglik_batched(contexts, theta, sigma2, y, out, status=None, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     st = hodlr_loglik_batched(lanes, s)
     if st != HODLR_OK:
-        raise HodlrError(st, "hodlr_loglik_batched")
+        msgs = {hodlr_last_error(h._ctx) for h in contexts} - {""}
+        raise HodlrError(st, "hodlr_loglik_batched: " + "; ".join(sorted(msgs)))
     return out
 
 
@@ -310,7 +317,7 @@ class Hodlr:
 
     def __init__(self, x, kernel: str, theta, sigma2: float, leaf: int, eps: float,
                  max_rank: int = 64, max_nrhs: int = 16, stream=None, allow_rank_cap=False,
-                 precision: int = 0):
+                 precision: int = 0, refine_maxit: int = 0, refine_tol: float = 1e-10):
         if _is_torch(x):
             if x.dtype.itemsize != 8 or not x.is_contiguous():
                 raise ValueError("x must be a contiguous float64 tensor")
@@ -325,6 +332,8 @@ class Hodlr:
         o.max_rank = max_rank
         o.max_nrhs = max_nrhs
         o.precision = precision
+        o.refine_maxit = refine_maxit
+        o.refine_tol = refine_tol
         if stream is not None:
             o.stream = stream
         self.kernel = kernel
@@ -486,3 +495,10 @@ class Hodlr:
         buf = np.zeros(2, dtype=np.int64)
         self._check(hodlr_counters(self._ctx, buf), "counters")
         return {"launches": int(buf[0]), "syncs": int(buf[1])}
+
+    def refine_info(self):
+        """(corrections, final relative residual) of the last solve's refinement."""
+        k = np.zeros(1, dtype=np.int32)
+        r = np.zeros(1, dtype=np.float64)
+        self._check(hodlr_refine_info(self._ctx, k, r), "refine_info")
+        return int(k[0]), float(r[0])

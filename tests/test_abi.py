@@ -63,3 +63,17 @@ def test_product_path_does_not_touch_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not pat.search(src), os.path.join(dirpath, f)
+
+
+def test_build_rejects_bad_refinement_options():
+    """Argument checks happen before any device work (no GPU needed)."""
+    import numpy as np
+
+    from paper_1403_6015_gb300 import hodlr
+    x = np.linspace(0, 1, 64)
+    for maxit, tol in [(-1, 1e-10), (2, 0.0), (2, float("nan"))]:
+        o = hodlr.hodlr_default_opts()
+        o.refine_maxit = maxit
+        o.refine_tol = tol
+        st, ctx = hodlr.hodlr_build(x, 64, 1, 0, [0.2, 1.0], 0.01, 16, 1e-12, o)
+        assert st == hodlr.HODLR_EINVAL and not ctx

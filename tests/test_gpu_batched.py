@@ -87,6 +87,39 @@ def test_batched_uneven_instances(H):
             assert abs(got[b] - r) <= 1e-12 * abs(r)
 
 
+def test_batched_lanes_sharing_streams(H):
+    """Ten problems on three lane streams (lanes on one stream run one after another)."""
+    import torch
+    origin = torch.cuda.Stream()
+    pool = [torch.cuda.Stream() for _ in range(3)]
+    nset = 2
+    lanes, keep = [], []
+    for i in range(10):
+        n = 3000 + 1700 * i
+        x, y = I.workload_1d(n, 1200 + i)
+        ell, s2 = settings(nset, 400 + i)
+        h = H.Hodlr(x, "exp", [ell[0], 1.0], s2[0], 128, 1e-12,
+                    stream=pool[i % 3].cuda_stream)
+        h.presize(np.full(h.tree()[0], 2, dtype=np.int32))
+        theta = torch.from_numpy(np.stack([ell, np.ones(nset)], 1).copy()).cuda()
+        sig = torch.from_numpy(s2.copy()).cuda()
+        yd = torch.from_numpy(y).cuda()
+        out = torch.zeros(nset, dtype=torch.float64, device="cuda")
+        st = torch.full((nset,), -1, dtype=torch.int32, device="cuda")
+        lanes.append(H.hodlr_batch_lane(h._ctx, theta.data_ptr(), sig.data_ptr(), yd.data_ptr(),
+                                        out.data_ptr(), st.data_ptr(), 0, 1, nset))
+        keep.append((h, x, y, ell, s2, theta, sig, yd, out, st))
+    torch.cuda.synchronize()
+    assert H.hodlr_loglik_batched(lanes, origin.cuda_stream) == H.HODLR_OK
+    torch.cuda.synchronize()
+    for h, x, y, ell, s2, theta, sig, yd, out, st in keep:
+        assert (st.cpu().numpy() == 0).all()
+        got = out.cpu().numpy()
+        for b in range(nset):
+            r = H.Hodlr(x, "exp", [ell[b], 1.0], s2[b], 128, 1e-12).loglik(y)
+            assert abs(got[b] - r) <= 1e-12 * abs(r)
+
+
 def test_batched_rejects_bad_lanes(H):
     import torch
     x, y = I.workload_1d(4096, 1020)
@@ -102,4 +135,6 @@ def test_batched_rejects_bad_lanes(H):
     assert H.hodlr_loglik_batched([lane], origin.cuda_stream) == H.HODLR_EINVAL
     h.presize(np.full(h.tree()[0], 2, dtype=np.int32))
     assert H.hodlr_loglik_batched([lane], s.cuda_stream) == H.HODLR_EINVAL  # origin = lane stream
+    assert "differ from the caller" in H.hodlr_last_error(h._ctx)
     assert H.hodlr_loglik_batched([lane, lane], origin.cuda_stream) == H.HODLR_EINVAL
+    assert "two lanes" in H.hodlr_last_error(h._ctx)

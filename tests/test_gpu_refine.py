@@ -1,0 +1,120 @@
+"""Iterative refinement of the solve: x += C^-1 r with the FP64 residual r = y - C~ x of the
+HODLR matrix itself, until ||r|| / ||y|| <= refine_tol or refine_maxit corrections."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1403_6015_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+N = 1 << 15
+ELL, S2 = 0.1, 1e-2
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_1403_6015_gb300 import build_lib, hodlr
+    build_lib.build()
+    hodlr.load()
+    return hodlr
+
+
+@pytest.fixture(scope="module")
+def problem():
+    x, y = I.workload_1d(N, 1030, nrhs=3)
+    return x, y
+
+
+def rel_res(h, y, x):
+    return np.linalg.norm(y - h.matvec(x)) / np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_refinement_reduces_residual(H, problem, precision):
+    x, y = problem
+    y0 = np.ascontiguousarray(y[:, 0])
+    plain = H.Hodlr(x, "matern32", [ELL, 1.0], S2, 128, 1e-12, precision=precision)
+    x0 = plain.factor_solve(y0)
+    r0 = rel_res(plain, y0, x0)
+    h = H.Hodlr(x, "matern32", [ELL, 1.0], S2, 128, 1e-12, precision=precision,
+                refine_maxit=3, refine_tol=1e-15)  # unreachable: all three corrections run
+    x1 = h.factor_solve(y0)
+    corr, res = h.refine_info()
+    assert corr == 3
+    r1 = rel_res(h, y0, x1)
+    print(f"precision {precision}: residual {r0:.3e} -> {r1:.3e} (reported {res:.3e})")
+    # the reported residual is measured after the last correction
+    assert res == pytest.approx(r1, rel=0.05, abs=1e-15)
+    # at the FP64 rounding floor of the product (~1e-12 here) it may only wander
+    assert r1 <= max(1.5 * r0, 5e-12)
+    # the refined solution is the HODLR solution to FP64 accuracy: close to the plain one
+    assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) <= 1e-9
+
+
+def test_converged_solve_takes_no_correction(H, problem):
+    x, y = problem
+    y0 = np.ascontiguousarray(y[:, 0])
+    plain = H.Hodlr(x, "matern32", [ELL, 1.0], S2, 128, 1e-12)
+    x0 = plain.factor_solve(y0)
+    h = H.Hodlr(x, "matern32", [ELL, 1.0], S2, 128, 1e-12, refine_maxit=2, refine_tol=1e-8)
+    x1 = h.factor_solve(y0)
+    corr, res = h.refine_info()
+    assert corr == 0 and 0 < res <= 1e-8
+    np.testing.assert_array_equal(x1, x0)
+
+
+def test_refined_multiple_rhs_and_loglik(H, problem):
+    x, y = problem
+    Y = np.asfortranarray(y)
+    h = H.Hodlr(x, "matern32", [ELL, 1.0], S2, 128, 1e-12, precision=1,
+                refine_maxit=4, refine_tol=1e-11)
+    X = h.factor_solve(Y)
+    corr, res = h.refine_info()
+    assert res <= 1e-11 and corr <= 12
+    for c in range(3):
+        assert rel_res(h, Y[:, c], np.ascontiguousarray(X[:, c])) <= 1e-11
+    # log-likelihood with refinement against the Kalman filter's exact value
+    h.rebuild([ELL, 1.0], S2)
+    ll = h.loglik(np.ascontiguousarray(Y[:, 0]))
+    _, perm = h.tree()
+    ld, q = O.matern_kalman(x[perm, 0], 3, ELL, 1.0, S2, Y[perm, 0])
+    ref = -0.5 * q - 0.5 * ld - 0.5 * N * np.log(2 * np.pi)
+    assert abs(ll - ref) <= 1e-10 * abs(ref)
+    # the standalone solve with the stored factor is refined too
+    X2 = h.solve(Y)
+    assert h.refine_info()[1] <= 1e-11
+    np.testing.assert_allclose(X2, X, rtol=0, atol=1e-9 * np.abs(X).max())
+
+
+def test_sweep_runs_fixed_corrections(H):
+    import torch
+    n, nset = 1 << 14, 6
+    x, y = I.workload_1d(n, 1031)
+    u = I.uniform01(91, 2 * nset)
+    ell = np.exp(np.log(0.05) + u[:nset] * (np.log(2.0) - np.log(0.05)))
+    s2 = np.exp(np.log(1e-4) + u[nset:] * (np.log(1.0) - np.log(1e-4)))
+    stream = torch.cuda.Stream()
+    h = H.Hodlr(x, "matern52", [ell[0], 1.0], s2[0], 128, 1e-12, precision=1,
+                stream=stream.cuda_stream, refine_maxit=1)
+    h.presize(np.full(h.tree()[0], 4, dtype=np.int32))
+    theta = torch.from_numpy(np.stack([ell, np.ones(nset)], 1).copy()).cuda()
+    sig = torch.from_numpy(s2.copy()).cuda()
+    yd = torch.from_numpy(y).cuda()
+    status = torch.full((nset,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    out = h.loglik_sweep(theta, sig, yd, status=status)
+    stream.synchronize()
+    got = out.cpu().numpy()
+    assert (status.cpu().numpy() == 0).all()
+    _, perm = h.tree()
+    for b in range(nset):
+        # the direct path with one correction forced (a tolerance it cannot meet)
+        d = H.Hodlr(x, "matern52", [ell[b], 1.0], s2[b], 128, 1e-12, precision=1,
+                    refine_maxit=1, refine_tol=1e-300)
+        r = d.loglik(y)
+        assert d.refine_info()[0] == 1
+        assert abs(got[b] - r) <= 1e-12 * abs(r), (b, got[b], r)
+        ld, q = O.matern_kalman(x[perm, 0], 5, ell[b], 1.0, s2[b], y[perm])
+        exact = -0.5 * q - 0.5 * ld - 0.5 * n * np.log(2 * np.pi)
+        assert abs(got[b] - exact) <= 1e-9 * abs(exact), (b, got[b], exact)
