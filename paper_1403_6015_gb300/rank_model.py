@@ -93,23 +93,26 @@ def collect_pairs(problems, max_rank: int = 64):
     return torch.cat(Xs), torch.cat(Ts), np.concatenate(R)
 
 
-def sweep_with_predictor(h, net, ells, sigma2s, y, margin: int = 1):
-    """Log-likelihoods of the settings (ells[b], sigma2s[b]) on the context h (presized per
-    group of settings that share a predicted rank profile, one captured graph per group),
-    with the adaptive path as the fallback for every setting whose evaluation flagged a rank
-    above its prediction. y: CUDA tensor. Returns (loglik array, stats)."""
+def sweep_with_predictor(h, net, ells, sigma2s, y, margin: int = 1, max_groups: int = 4):
+    """Log-likelihoods of the settings (ells[b], sigma2s[b]) on the context h, presized by
+    the network's predicted per-level ranks (+ margin), with the adaptive path as the
+    fallback for every setting whose evaluation flagged a rank above its presize.
+
+    Settings are sorted by predicted total rank and cut into at most max_groups chunks of
+    equal count; a chunk is presized to the elementwise maximum of its members' profiles
+    and evaluated as one captured graph replayed per setting. y: CUDA tensor.
+    Returns (loglik array, stats)."""
     import torch
     ells = np.asarray(ells, dtype=np.float64)
     sigma2s = np.asarray(sigma2s, dtype=np.float64)
-    groups = {}
-    for b, ell in enumerate(ells):
-        prof = tuple(int(v) for v in h.predict_level_ranks(net, float(ell), margin))
-        groups.setdefault(prof, []).append(b)
+    profs = np.array([h.predict_level_ranks(net, float(e), margin) for e in ells], dtype=np.int32)
+    order = np.argsort(profs.sum(axis=1), kind="stable")
+    chunks = [c for c in np.array_split(order, min(max_groups, len(ells))) if len(c)]
     out = np.zeros(len(ells))
     fallback = []
-    for prof, idx in groups.items():
-        idx = np.asarray(idx)
-        h.presize(np.asarray(prof, dtype=np.int32))
+    for idx in chunks:
+        prof = profs[idx].max(axis=0)
+        h.presize(prof.astype(np.int32))
         theta = torch.from_numpy(np.stack([ells[idx], np.ones(len(idx))], 1).copy()).cuda()
         sig = torch.from_numpy(sigma2s[idx].copy()).cuda()
         status = torch.zeros(len(idx), dtype=torch.int32, device="cuda")
@@ -122,4 +125,5 @@ def sweep_with_predictor(h, net, ells, sigma2s, y, margin: int = 1):
     for b in fallback:
         h.rebuild([float(ells[b]), 1.0], float(sigma2s[b]))
         out[b] = h.loglik(y)
-    return out, {"groups": len(groups), "fallbacks": len(fallback)}
+    return out, {"groups": len(chunks), "fallbacks": len(fallback),
+                 "distinct_profiles": len({tuple(p) for p in profs})}
