@@ -61,7 +61,11 @@ typedef struct {
                        /*    L D L^T, panel solves) in double-float arithmetic on the FP32 */
                        /*    pipe (~2^-48 unit roundoff), everything else FP64             */
   int rank_mode;       /* 0: adaptive ACA ranks                                            */
-  int max_rank;        /* cap on the ACA rank of one off-diagonal block (1..64), default 64 */
+  int max_rank;        /* cap on the ACA rank of one off-diagonal block (1..512), default  */
+                       /*    64. Levels whose rank exceeds 64 factor their node matrices  */
+                       /*    in global memory and use the unfused level sweep; memory     */
+                       /*    grows with max_rank (ACA columns n x min(max_rank, m/2) per  */
+                       /*    level, leaf partials 2^kappa x r x (R + max_nrhs))           */
   int max_nrhs;        /* right-hand sides carried through a fused factor, default 16     */
   double refine_tol;   /* iterative refinement (not in the paper): stop when              */
                        /*    ||y - C~ x||_2 <= refine_tol ||y||_2, C~ the FP64 HODLR       */

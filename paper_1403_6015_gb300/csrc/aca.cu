@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   int item = blockIdx.x;
   int id = a.item_node[item];
   if (a.done[id]) return;
-  __shared__ double uik[kMaxRank];
+  extern __shared__ double dsm[];
+  double* uik = dsm;  // max_rank
   __shared__ ff tab[64];
   ff cr = {0, 0}, amp = {0, 0};
   const Cov cov = cov_from(a.kind, a.hyp);
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   int bl = a.nb[2 * id + 1], br = a.nb[2 * id + 2], mr = a.ns[2 * id + 2];
   int64_t n = a.pts.n;
   double* raw = a.raw + a.raw_off[level_of(id)];
-  if (threadIdx.x < k) uik[threadIdx.x] = raw[threadIdx.x * n + bl + i];
+  for (int l = threadIdx.x; l < k; l += kAcaThreads) uik[l] = raw[l * n + bl + i];
   __syncthreads();
   int start = a.item_start[item];
   double bv = 0.0;
@@ -213,7 +214,13 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   int item = blockIdx.x;
   int id = a.item_node[item];
   if (a.done[id] || !a.phase[id]) return;
-  __shared__ double vjk[kMaxRank];
+  // dynamic shared memory: vjk[max_rank], red[(2 max_rank + 2) x warps], used[2 max_rank + 2]
+  extern __shared__ double dsm[];
+  constexpr int kW = kAcaThreads / 32;
+  const int nval = 2 + 2 * a.max_rank;
+  double* vjk = dsm;
+  double* red = dsm + a.max_rank;
+  int* used = reinterpret_cast<int*>(red + (int64_t)nval * kW);
   __shared__ ff tab[64];
   ff cr = {0, 0}, amp = {0, 0};
   const Cov cov = cov_from(a.kind, a.hyp);
@@ -222,8 +229,6 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
     cr = ff_from_double(a.hyp[kHypScale]);
     amp = ff_from_double(cov.amp);
   }
-  __shared__ int used[2 * kMaxRank + 2];
-  __shared__ double red[2 * kMaxRank + 2][kAcaThreads / 32];
   __shared__ double wv[kAcaThreads / 32];
   __shared__ int wi[kAcaThreads / 32];
   int k = a.rank[id], j = a.col[id];
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   int nu = a.nused[id];
   int64_t n = a.pts.n;
   double* raw = a.raw + a.raw_off[level_of(id)];
-  if (threadIdx.x < k) vjk[threadIdx.x] = raw[threadIdx.x * n + br + j];
+  for (int l = threadIdx.x; l < k; l += kAcaThreads) vjk[l] = raw[l * n + br + j];
   for (int q = threadIdx.x; q < nu; q += kAcaThreads) used[q] = a.used[(int64_t)id * a.used_stride + q];
   __syncthreads();
   int start = a.item_start[item];
@@ -267,8 +272,8 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   nv2 = warp_sum(nv2);
   warp_amax(bv, bi);
   if (lane == 0) {
-    red[0][w] = nu2;
-    red[1][w] = nv2;
+    red[0 * kW + w] = nu2;
+    red[1 * kW + w] = nv2;
     wv[w] = bv;
     wi[w] = bi;
   }
@@ -283,23 +288,23 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
     du = warp_sum(du);
     dv = warp_sum(dv);
     if (lane == 0) {
-      red[2 + l][w] = du;
-      red[2 + kMaxRank + l][w] = dv;
+      red[(2 + l) * kW + w] = du;
+      red[(2 + a.max_rank + l) * kW + w] = dv;
     }
   }
   __syncthreads();
   double* out = a.part + (int64_t)item * a.part_stride;
-  int nval = 2 + 2 * kMaxRank;
+  const int mr2 = 2 + a.max_rank;
   for (int e = threadIdx.x; e < nval; e += kAcaThreads) {
-    bool live = e < 2 || (e - 2 < k) || (e >= 2 + kMaxRank && e - 2 - kMaxRank < k);
+    bool live = e < 2 || (e - 2 < k) || (e >= mr2 && e - mr2 < k);
     if (!live) continue;
     double s = 0.0;
-    for (int q = 0; q < kAcaThreads / 32; ++q) s += red[e][q];
+    for (int q = 0; q < kW; ++q) s += red[e * kW + q];
     // layout: [0] argmax value, [1] argmax index, [2] |u|^2, [3] |v|^2, [4..] u_l.u, v_l.v
     if (e == 0) out[2] = s;
     else if (e == 1) out[3] = s;
-    else if (e < 2 + kMaxRank) out[4 + (e - 2)] = s;
-    else out[4 + a.max_rank + (e - 2 - kMaxRank)] = s;
+    else if (e < mr2) out[4 + (e - 2)] = s;
+    else out[4 + a.max_rank + (e - mr2)] = s;
   }
   if (threadIdx.x == 0) {
     double fv = 0.0;
@@ -445,20 +450,27 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   k_aca_init<<<(nint + 255) / 256, 256, 0, c.stream>>>(a);
   ++c.launches;
   int wblocks = (nint * 32 + 255) / 256;
+  const size_t smem_row = sizeof(double) * c.max_rank;
+  const size_t smem_col = sizeof(double) * (c.max_rank + (size_t)(2 + 2 * c.max_rank) * (kAcaThreads / 32)) +
+                          sizeof(int) * (2 * c.max_rank + 2);
+  if (smem_col > 48 * 1024) {
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));
+  }
   // adaptive: until no block is active (host check per step); presized: a fixed number of
   // steps (rank + 1 per block, one spare for a zero pivot) and a device-side check
   int max_steps = c.presized ? maxpre + 2 : 2 * c.max_rank + 4;
   for (int s = 0; s < max_steps; ++s) {
     if (!c.presized) HODLR_CUDA_TRY(cudaMemsetAsync(c.active, 0, sizeof(int32_t), c.stream));
     if (c.precision == 1)
-      k_aca_row<true><<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
+      k_aca_row<true><<<(unsigned)c.n_items, kAcaThreads, smem_row, c.stream>>>(a);
     else
-      k_aca_row<false><<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
+      k_aca_row<false><<<(unsigned)c.n_items, kAcaThreads, smem_row, c.stream>>>(a);
     k_aca_pivot_row<<<wblocks, 256, 0, c.stream>>>(a);
     if (c.precision == 1)
-      k_aca_col<true><<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
+      k_aca_col<true><<<(unsigned)c.n_items, kAcaThreads, smem_col, c.stream>>>(a);
     else
-      k_aca_col<false><<<(unsigned)c.n_items, kAcaThreads, 0, c.stream>>>(a);
+      k_aca_col<false><<<(unsigned)c.n_items, kAcaThreads, smem_col, c.stream>>>(a);
     k_aca_pivot_col<<<wblocks, 256, 0, c.stream>>>(a);
     c.launches += 4;
     HODLR_CUDA_TRY(cudaGetLastError());

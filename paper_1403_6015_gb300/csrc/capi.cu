@@ -288,7 +288,7 @@ void hodlr_default_opts(hodlr_opts* o) {
   if (!o) return;
   o->precision = 0;
   o->rank_mode = 0;
-  o->max_rank = hodlr::kMaxRank;
+  o->max_rank = hodlr::kDefaultMaxRank;
   o->max_nrhs = 16;
   o->refine_tol = 1e-10;
   o->refine_maxit = 0;
@@ -497,7 +497,9 @@ static hodlr_status check_flags(Ctx* c) {
 // Level sweep: one launch per level when each level's reductions are small enough for
 // one block per half-node, else the segmented three-launch path.
 static cudaError_t sweep(Ctx* c, int nrhs, bool factor_mode) {
-  if (c->fused_work <= ((int64_t)1 << 22) && !c->no_fused)
+  int rmax = 0;
+  for (int r : c->h_rl) rmax = std::max(rmax, r);
+  if (c->fused_work <= ((int64_t)1 << 22) && !c->no_fused && rmax <= hodlr::kSmemRank)
     return hodlr::launch_levels_fused(*c, nrhs, factor_mode);
   return hodlr::launch_levels(*c, nrhs, factor_mode);
 }

@@ -14,7 +14,10 @@
 namespace hodlr {
 
 constexpr int kMaxLeaf = 128;      // leaf blocks live in shared memory
-constexpr int kMaxRank = 64;       // per-block rank cap (2r x 2r node matrices in smem)
+constexpr int kMaxRank = 512;      // hard cap on a block's rank (opts.max_rank)
+constexpr int kDefaultMaxRank = 64;  // default opts.max_rank
+constexpr int kSmemRank = 64;      // ranks up to this use the shared-memory node step
+                                   // (2r x 2r in smem) and the fused level sweep
 constexpr int kAcaTile = 1024;     // columns (rows) of one ACA work item
 
 // ---------------------------------------------------------------------------------------
@@ -90,7 +93,7 @@ struct Ctx {
   int d = 1;
   int kind = 0;
   double ell = 1, amp = 1, sigma2 = 0, eps = 1e-12;
-  int leaf = 128, kappa = 0, max_rank = kMaxRank, max_nrhs = 16;
+  int leaf = 128, kappa = 0, max_rank = kDefaultMaxRank, max_nrhs = 16;
   int precision = 0;              // 0: FP64, 1: double-float leaf stage (mixed)
   int leaf_threads = 1024;        // CTA size of the double-float leaf kernel (measured best)
   int leaf_threads64 = 512;       // CTA size of the FP64 leaf kernel (measured best)

@@ -8,7 +8,8 @@
 // Work is expressed over leaf row tiles so all levels have the same parallelism:
 //   per-leaf partials  Phi_j[leaf]^T Q[leaf]       (written by the previous sweep step)
 //   k_segsum           fixed-order sums over each node half
-//   k_node             M, LU, log det, Z per node
+//   k_node             M, LU, log det, Z per node (M in shared memory, ranks <= 64)
+//   k_node_big         the same with M in global memory (ranks above 64)
 //   k_sweep            update of level u on each leaf fused with the partials of level u-1
 #include <cuda_runtime.h>
 
@@ -58,10 +59,37 @@ cudaError_t segsum(const double* in, int64_t stride, int E, int64_t nleaf, int h
 
 __global__ void __launch_bounds__(128) k_node(NodeArgs a, bool factor) {
   extern __shared__ double M[];  // m2 x m2 row-major
-  __shared__ int piv[2 * kMaxRank];
+  __shared__ int piv[2 * kSmemRank];
   __shared__ double lds;
   __shared__ int sgn;
   node_solve(a, blockIdx.x, factor, M, piv, &lds, &sgn);
+}
+
+constexpr int kNodeBigThreads = 512;
+
+__global__ void __launch_bounds__(kNodeBigThreads) k_node_big(NodeArgs a, bool factor) {
+  __shared__ double wv[kNodeBigThreads / 32];
+  __shared__ int wi[kNodeBigThreads / 32];
+  __shared__ int pv;
+  __shared__ double lds;
+  __shared__ int sgn;
+  node_solve_global(a, blockIdx.x, factor, wv, wi, &pv, &lds, &sgn);
+}
+
+// Node step of every node of level na.j: M in shared memory up to rank kSmemRank, else in
+// global memory.
+cudaError_t launch_node(Ctx& c, const NodeArgs& na, bool factor_mode) {
+  int r = na.r;
+  if (r <= kSmemRank) {
+    size_t smem = sizeof(double) * 4 * r * r;
+    if (smem > 48 * 1024)
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_node, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_node<<<1u << na.j, 128, smem, c.stream>>>(na, factor_mode);
+  } else {
+    k_node_big<<<1u << na.j, kNodeBigThreads, 0, c.stream>>>(na, factor_mode);
+  }
+  ++c.launches;
+  return cudaGetLastError();
 }
 
 struct SweepArgs {
@@ -83,23 +111,31 @@ struct SweepArgs {
 };
 
 // Level-u update of one leaf's rows, fused with the level-(u-1) partial products.
+// kStage: the leaf's rows of Ut/Vt (level u) and Phi (level u-1) are staged in shared
+// memory (p x (ru + rl) doubles); otherwise (large ranks) they are read from the panels.
+template <bool kStage>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs a) {
   extern __shared__ double sm[];
   int leaf = blockIdx.x;
   int id = a.leaf0 + leaf;
   int b = a.nb[id], p = a.ns[id];
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  double* tl = sm;                 // p x ru   (Ut/Vt of level u on these rows)
-  double* ph = sm + kMaxLeaf * a.ru;  // p x rl (Phi of level u-1)
-  for (int e = tid; e < p * a.ru; e += kSweepThreads) {
-    int i = e % p, c = e / p;
-    tl[i * a.ru + c] = a.pan[(int64_t)(a.cu + c) * a.n + b + i];
+  // element (i, c): staged at [i * r + c], in the panels at column c, row b + i
+  const double* tl = kStage ? sm : a.pan + (int64_t)a.cu * a.n + b;
+  const double* ph = kStage ? sm + kMaxLeaf * a.ru : a.phi + (int64_t)a.cl * a.n + b;
+  const int64_t tl_i = kStage ? a.ru : 1, tl_c = kStage ? 1 : a.n;
+  const int64_t ph_i = kStage ? a.rl : 1, ph_c = kStage ? 1 : a.n;
+  if (kStage) {
+    for (int e = tid; e < p * a.ru; e += kSweepThreads) {
+      int i = e % p, c = e / p;
+      sm[i * a.ru + c] = a.pan[(int64_t)(a.cu + c) * a.n + b + i];
+    }
+    for (int e = tid; e < p * a.rl; e += kSweepThreads) {
+      int i = e % p, c = e / p;
+      sm[kMaxLeaf * a.ru + i * a.rl + c] = a.phi[(int64_t)(a.cl + c) * a.n + b + i];
+    }
+    __syncthreads();
   }
-  for (int e = tid; e < p * a.rl; e += kSweepThreads) {
-    int i = e % p, c = e / p;
-    ph[i * a.rl + c] = a.phi[(int64_t)(a.cl + c) * a.n + b + i];
-  }
-  __syncthreads();
   int sh = a.kappa - a.u;
   int side = (leaf >> (sh - 1)) & 1;
   int wz = a.cP + a.nrhs;
@@ -118,7 +154,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs a) {
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         int i = m * 32 + lane;
-        if (i < p) x[m] -= tl[i * a.ru + c] * z;
+        if (i < p) x[m] -= tl[i * tl_i + c * tl_c] * z;
       }
     }
 #pragma unroll
@@ -131,7 +167,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs a) {
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         int i = m * 32 + lane;
-        if (i < p) s += ph[i * a.rl + c] * x[m];
+        if (i < p) s += ph[i * ph_i + c * ph_c] * x[m];
       }
       s = wsum(s);
       if (lane == 0) out[c * wz + q] = s;
@@ -300,12 +336,7 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
     na.z_stride = (int64_t)2 * r * na.wz;
     na.flags = c.dflags;
     if (r > 0) {
-      size_t smem = sizeof(double) * 4 * r * r;
-      if (smem > 48 * 1024)
-        HODLR_CUDA_TRY(cudaFuncSetAttribute(k_node, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_node<<<1u << j, 128, smem, c.stream>>>(na, factor_mode);
-      ++c.launches;
-      HODLR_CUDA_TRY(cudaGetLastError());
+      HODLR_CUDA_TRY(launch_node(c, na, factor_mode));
     } else if (factor_mode) {
       HODLR_CUDA_TRY(cudaMemsetAsync(c.node_logdet + ((1 << j) - 1), 0, sizeof(double) << j, c.stream));
     }
@@ -335,9 +366,13 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
     sa.n = c.n;
     if (sa.cP + nrhs == 0) continue;  // nothing left to update (root level, no right-hand side)
     size_t smem = sizeof(double) * kMaxLeaf * (sa.ru + sa.rl);
-    if (smem > 48 * 1024)
-      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sweep<<<(unsigned)nleaf, kSweepThreads, smem, c.stream>>>(sa);
+    if (smem <= 200 * 1024) {
+      if (smem > 48 * 1024)
+        HODLR_CUDA_TRY(cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_sweep<true><<<(unsigned)nleaf, kSweepThreads, smem, c.stream>>>(sa);
+    } else {
+      k_sweep<false><<<(unsigned)nleaf, kSweepThreads, 0, c.stream>>>(sa);
+    }
     ++c.launches;
     HODLR_CUDA_TRY(cudaGetLastError());
   }
@@ -369,12 +404,7 @@ cudaError_t launch_level_first(Ctx& c, int nrhs, bool factor_mode) {
       HODLR_CUDA_TRY(cudaMemsetAsync(c.node_logdet + ((1 << j) - 1), 0, sizeof(double) << j, c.stream));
     return cudaSuccess;
   }
-  size_t smem = sizeof(double) * 4 * r * r;
-  if (smem > 48 * 1024)
-    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_node, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_node<<<1u << j, 128, smem, c.stream>>>(na, factor_mode);
-  ++c.launches;
-  return cudaGetLastError();
+  return launch_node(c, na, factor_mode);
 }
 
 // Device hyperparameter slot from host values (stream-ordered, capturable).

@@ -45,7 +45,7 @@ __device__ __forceinline__ double wsum(double v) {
 
 __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
   extern __shared__ double M[];  // node step, (2 rl)^2
-  __shared__ int piv[2 * kMaxRank];
+  __shared__ int piv[2 * kSmemRank];
   __shared__ double lds;
   __shared__ int sgn;
   __shared__ int flag;

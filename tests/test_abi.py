@@ -65,8 +65,8 @@ def test_product_path_does_not_touch_oracle():
                 assert not pat.search(src), os.path.join(dirpath, f)
 
 
-def test_build_rejects_bad_refinement_options():
-    """Argument checks happen before any device work (no GPU needed)."""
+def test_build_rejects_bad_options():
+    """Refinement and rank-cap checks happen before any device work (no GPU needed)."""
     import numpy as np
 
     from paper_1403_6015_gb300 import hodlr
@@ -77,3 +77,9 @@ def test_build_rejects_bad_refinement_options():
         o.refine_tol = tol
         st, ctx = hodlr.hodlr_build(x, 64, 1, 0, [0.2, 1.0], 0.01, 16, 1e-12, o)
         assert st == hodlr.HODLR_EINVAL and not ctx
+    for mr in [0, 513]:
+        o = hodlr.hodlr_default_opts()
+        o.max_rank = mr
+        st, ctx = hodlr.hodlr_build(x, 64, 1, 0, [0.2, 1.0], 0.01, 16, 1e-12, o)
+        assert st == hodlr.HODLR_EINVAL and not ctx
+    assert hodlr.hodlr_default_opts().max_rank == 64
