@@ -95,7 +95,7 @@ struct Ctx {
   double ell = 1, amp = 1, sigma2 = 0, eps = 1e-12;
   int leaf = 128, kappa = 0, max_rank = kDefaultMaxRank, max_nrhs = 16;
   int precision = 0;              // 0: FP64, 1: double-float leaf stage (mixed)
-  int leaf_threads = 1024;        // CTA size of the double-float leaf kernel (measured best)
+  int leaf_threads = 512;         // CTA size of the double-float leaf kernel (two CTAs per SM)
   int leaf_threads64 = 512;       // CTA size of the FP64 leaf kernel (measured best)
   bool no_fused = false;          // force the segmented level sweep
   cudaStream_t stream = nullptr;

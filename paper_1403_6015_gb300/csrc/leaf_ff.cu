@@ -6,7 +6,11 @@
 // and leave HBM as FP64; the stored factor is kept as double-float pairs; the log of each
 // pivot is taken in FP64. Unit roundoff ~2^-48 instead of 2^-53.
 //
-// Blocked for the FP32 pipe (one CTA per leaf, all of it in shared memory):
+// Blocked for the FP32 pipe (one CTA per leaf, all of it in shared memory, two CTAs per
+// SM so that one leaf's barriers overlap the other's work):
+//   - only the lower triangle is kept, packed by rows (element (i, j), j <= i, at
+//     i (i + 1) / 2 + j); the unscaled panel columns of the factorization and the solve
+//     chunk share one buffer, which also holds the coordinates while the block is built;
 //   - the block is padded to P = 32 ceil(p / 32) with the identity, which changes neither
 //     the factor of the leading p x p block, the solutions, nor the log det;
 //   - L D L^T by 32-column panels: inside a panel, two columns per step (three barriers
@@ -23,9 +27,12 @@
 namespace hodlr {
 namespace {
 
-constexpr int kLD = kMaxLeaf + 1;  // row stride of the block
-constexpr int kBS = 33;            // row stride of the 32-column buffers
+constexpr int kTri = kMaxLeaf * (kMaxLeaf + 1) / 2;  // packed lower triangle
+constexpr int kBS = 33;            // row stride of the 32-column buffer
 constexpr int kCW = 32;            // columns per solve chunk
+
+// Offset of row i in the packed lower triangle.
+__device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
 
 struct LeafFFArgs {
   const double* x;
@@ -66,12 +73,12 @@ __device__ __forceinline__ int tri_row(int e) {
 }
 
 template <int kT, bool kFactor>
-__global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
+__global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
   extern __shared__ ff sm[];
-  ff* A = sm;                          // [kMaxLeaf][kLD]
-  ff* Up = A + kMaxLeaf * kLD;         // [kMaxLeaf][kBS] unscaled panel columns
-  ff* B = Up + kMaxLeaf * kBS;         // [kMaxLeaf][kBS] solve chunk
-  __shared__ ff xl[2 * kMaxLeaf];
+  ff* A = sm;                          // packed lower triangle, kTri
+  ff* Up = A + kTri;                   // [kMaxLeaf][kBS] unscaled panel columns (factor)
+  ff* B = Up;                          // [kMaxLeaf][kBS] solve chunk (after the factor)
+  ff* xl = Up;                         // 2 x kMaxLeaf coordinates (block build only)
   __shared__ ff dinv[kMaxLeaf];
   __shared__ ff tab[64];
   __shared__ ff pinv[2];
@@ -120,18 +127,18 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
       } else {
         c = ff{i == j ? 1.0f : 0.0f, 0.0f};
       }
-      A[i * kLD + j] = c;
+      A[e] = c;  // e = tri(i) + j
     }
     __syncthreads();
     // blocked L D L^T
     for (int J = 0; J < NB; ++J) {
       int c0 = 32 * J;
       if (tid == 0) {
-        ff dk = A[c0 * kLD + c0];
+        ff dk = A[tri(c0) + c0];
         if (!(dk.hi > 0.0f)) {
           bad = 1;
           dk = ff{1.0f, 0.0f};
-          A[c0 * kLD + c0] = dk;
+          A[tri(c0) + c0] = dk;
         }
         pinv[0] = ff_rcp(dk);
       }
@@ -141,28 +148,28 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
         int col = c0 + c;
         // the second pivot of the pair: D_{col+1} = A_{col+1,col+1} - L_{col+1,col} A_{col+1,col}
         if (tid == 0) {
-          ff t = A[(col + 1) * kLD + col];
+          ff t = A[tri(col + 1) + col];
           ff l = ff_mul(t, pinv[0]);
-          A[(col + 1) * kLD + col] = l;
+          A[tri(col + 1) + col] = l;
           Up[(col + 1) * kBS + c] = t;
-          ff d1 = ff_fms(A[(col + 1) * kLD + col + 1], l, t);
+          ff d1 = ff_fms(A[tri(col + 1) + col + 1], l, t);
           if (!(d1.hi > 0.0f)) {
             bad = 1;
             d1 = ff{1.0f, 0.0f};
           }
-          A[(col + 1) * kLD + col + 1] = d1;
+          A[tri(col + 1) + col + 1] = d1;
           pinv[1] = ff_rcp(d1);
         }
         __syncthreads();
         // rows below the pair: scale both columns, keep the unscaled values
         ff iv0 = pinv[0], iv1 = pinv[1], t10 = Up[(col + 1) * kBS + c];
         for (int i = col + 2 + tid; i < P; i += kT) {
-          ff t = A[i * kLD + col];
+          ff t = A[tri(i) + col];
           ff l = ff_mul(t, iv0);
-          A[i * kLD + col] = l;
+          A[tri(i) + col] = l;
           Up[i * kBS + c] = t;
-          ff u = ff_fms(A[i * kLD + col + 1], l, t10);
-          A[i * kLD + col + 1] = ff_mul(u, iv1);
+          ff u = ff_fms(A[tri(i) + col + 1], l, t10);
+          A[tri(i) + col + 1] = ff_mul(u, iv1);
           Up[i * kBS + c + 1] = u;
         }
         __syncthreads();
@@ -172,8 +179,8 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
           int jc = c0 + cc;
           ff uj0 = Up[jc * kBS + c], uj1 = Up[jc * kBS + c + 1];
           for (int i = jc + lane; i < P; i += 32) {
-            ff v = ff_fms(A[i * kLD + jc], A[i * kLD + col], uj0);
-            v = ff_fms(v, A[i * kLD + col + 1], uj1);
+            ff v = ff_fms(A[tri(i) + jc], A[tri(i) + col], uj0);
+            v = ff_fms(v, A[tri(i) + col + 1], uj1);
             if (i == jc && cc == c + 2) {
               if (!(v.hi > 0.0f)) {
                 bad = 1;
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
               }
               pinv[0] = ff_rcp(v);
             }
-            A[i * kLD + jc] = v;
+            A[tri(i) + jc] = v;
           }
         }
         __syncthreads();
@@ -196,42 +203,42 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
         ff s00b = {0, 0}, s01b = {0, 0}, s10b = {0, 0}, s11b = {0, 0};
 #pragma unroll 4
         for (int c = 0; c < 32; c += 2) {
-          ff l0 = A[i0 * kLD + c0 + c], l1 = A[(i0 + 1) * kLD + c0 + c];
+          ff l0 = A[tri(i0) + c0 + c], l1 = A[tri(i0 + 1) + c0 + c];
           ff u0 = Up[j0 * kBS + c], u1 = Up[(j0 + 1) * kBS + c];
           s00a = ff_fma(s00a, l0, u0);
           s01a = ff_fma(s01a, l0, u1);
           s10a = ff_fma(s10a, l1, u0);
           s11a = ff_fma(s11a, l1, u1);
-          ff m0 = A[i0 * kLD + c0 + c + 1], m1 = A[(i0 + 1) * kLD + c0 + c + 1];
+          ff m0 = A[tri(i0) + c0 + c + 1], m1 = A[tri(i0 + 1) + c0 + c + 1];
           ff v0 = Up[j0 * kBS + c + 1], v1 = Up[(j0 + 1) * kBS + c + 1];
           s00b = ff_fma(s00b, m0, v0);
           s01b = ff_fma(s01b, m0, v1);
           s10b = ff_fma(s10b, m1, v0);
           s11b = ff_fma(s11b, m1, v1);
         }
-        A[i0 * kLD + j0] = ff_sub(A[i0 * kLD + j0], ff_add(s00a, s00b));
-        A[(i0 + 1) * kLD + j0] = ff_sub(A[(i0 + 1) * kLD + j0], ff_add(s10a, s10b));
-        A[(i0 + 1) * kLD + j0 + 1] = ff_sub(A[(i0 + 1) * kLD + j0 + 1], ff_add(s11a, s11b));
-        if (ti != tj) A[i0 * kLD + j0 + 1] = ff_sub(A[i0 * kLD + j0 + 1], ff_add(s01a, s01b));
+        A[tri(i0) + j0] = ff_sub(A[tri(i0) + j0], ff_add(s00a, s00b));
+        A[tri(i0 + 1) + j0] = ff_sub(A[tri(i0 + 1) + j0], ff_add(s10a, s10b));
+        A[tri(i0 + 1) + j0 + 1] = ff_sub(A[tri(i0 + 1) + j0 + 1], ff_add(s11a, s11b));
+        if (ti != tj) A[tri(i0) + j0 + 1] = ff_sub(A[tri(i0) + j0 + 1], ff_add(s01a, s01b));
       }
       __syncthreads();
     }
     // store the factor (leading p x p lower triangle)
     for (int e = tid; e < p * (p + 1) / 2; e += kT) {
       int i = tri_row(e), j = e - i * (i + 1) / 2;
-      Lst[i * kMaxLeaf + j] = A[i * kLD + j];
+      Lst[i * kMaxLeaf + j] = A[tri(i) + j];
     }
   } else {
     for (int e = tid; e < P * (P + 1) / 2; e += kT) {
       int i = tri_row(e), j = e - i * (i + 1) / 2;
-      A[i * kLD + j] = i < p ? Lst[i * kMaxLeaf + j] : ff{i == j ? 1.0f : 0.0f, 0.0f};
+      A[tri(i) + j] = i < p ? Lst[i * kMaxLeaf + j] : ff{i == j ? 1.0f : 0.0f, 0.0f};
     }
     __syncthreads();
   }
   // log det = sum log D_ii (FP64), 1 / D
   double sl = 0.0;
   for (int i = tid; i < p; i += kT) {
-    ff di = A[i * kLD + i];
+    ff di = A[tri(i) + i];
     if (kFactor) sl += log(ff_to_double(di));
     dinv[i] = ff_rcp(di);
   }
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
         ff xv = B[(c0 + lane) * kBS + c];
         for (int k = 0; k < 32; ++k) {
           ff xk = shfl_ff(xv, k);
-          if (lane > k) xv = ff_fms(xv, A[(c0 + lane) * kLD + c0 + k], xk);
+          if (lane > k) xv = ff_fms(xv, A[tri(c0 + lane) + c0 + k], xk);
         }
         B[(c0 + lane) * kBS + c] = xv;
       }
@@ -276,8 +283,8 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
         ff sa = {0, 0}, sb = {0, 0};
 #pragma unroll 4
         for (int k = 0; k < 32; k += 2) {
-          sa = ff_fma(sa, A[i * kLD + c0 + k], B[(c0 + k) * kBS + c]);
-          sb = ff_fma(sb, A[i * kLD + c0 + k + 1], B[(c0 + k + 1) * kBS + c]);
+          sa = ff_fma(sa, A[tri(i) + c0 + k], B[(c0 + k) * kBS + c]);
+          sb = ff_fma(sb, A[tri(i) + c0 + k + 1], B[(c0 + k + 1) * kBS + c]);
         }
         B[i * kBS + c] = ff_sub(B[i * kBS + c], ff_add(sa, sb));
       }
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
         ff xv = B[(c0 + lane) * kBS + c];
         for (int k = 31; k >= 0; --k) {
           ff xk = shfl_ff(xv, k);
-          if (lane < k) xv = ff_fms(xv, A[(c0 + k) * kLD + c0 + lane], xk);
+          if (lane < k) xv = ff_fms(xv, A[tri(c0 + k) + c0 + lane], xk);
         }
         B[(c0 + lane) * kBS + c] = xv;
       }
@@ -306,8 +313,8 @@ __global__ void __launch_bounds__(kT) k_leaf_ff(LeafFFArgs a) {
         ff sa = {0, 0}, sb = {0, 0};
 #pragma unroll 4
         for (int k = 0; k < 32; k += 2) {
-          sa = ff_fma(sa, A[(c0 + k) * kLD + i], B[(c0 + k) * kBS + c]);
-          sb = ff_fma(sb, A[(c0 + k + 1) * kLD + i], B[(c0 + k + 1) * kBS + c]);
+          sa = ff_fma(sa, A[tri(c0 + k) + i], B[(c0 + k) * kBS + c]);
+          sb = ff_fma(sb, A[tri(c0 + k + 1) + i], B[(c0 + k + 1) * kBS + c]);
         }
         B[i * kBS + c] = ff_sub(B[i * kBS + c], ff_add(sa, sb));
       }
@@ -363,7 +370,7 @@ LeafFFArgs make_ff_args(Ctx& c, int nrhs, bool factor) {
 
 template <bool kFactor>
 cudaError_t launch_ff(const LeafFFArgs& a, unsigned grid, int threads, cudaStream_t s) {
-  size_t smem = sizeof(ff) * kMaxLeaf * (kLD + 2 * kBS);
+  size_t smem = sizeof(ff) * (kTri + kMaxLeaf * kBS);
   switch (threads) {
     case 512:
       HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff<512, kFactor>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
