@@ -41,7 +41,7 @@ FP64_PEAK = 152 * 2 * 2 * 2.07e9  # SMs x FP64 FMA/clk/SM x 2 flop x max SM cloc
 # DRAM bytes (read + write) of one launch of each form's leaf kernel at n = 2^20, from the
 # ncu captures summarised in profiles/ (scaled from the n = 2^18 capture by the number of
 # leaves); None until a capture matches the current kernel.
-LEAF_TRAFFIC_BYTES = {0: None, 1: 4 * (58.967552 + 125.307392) * 1e6}
+LEAF_TRAFFIC_BYTES = {0: None, 1: None}
 
 
 def config():
@@ -142,7 +142,7 @@ def accuracy(x, y, perm, kern, ell, ll, logdet, sol):
 # Double-float (mixed form) leaf kernel: FP64-equivalent peak of the FP32 pipe. One
 # double-float multiply-add (TwoProd by FMA, TwoSum, FastTwoSum) is 14 FP32 instructions.
 FF_PEAK = 152 * 128 * 2.07e9 / 14 * 2
-FORMS = {1: ("mixed", "f64/f32x2", "k_leaf_ff<1024,true> (double-float leaf block build + "
+FORMS = {1: ("mixed", "f64/f32x2", "k_leaf_ff<512,true> (double-float leaf block build + "
                                    "L D L^T + panel solves)", FF_PEAK,
              "FP32 pipe in double-float multiply-adds: 152 SMs x 128 lanes x 2.07 GHz / 14 "
              "instructions x 2 flop"),

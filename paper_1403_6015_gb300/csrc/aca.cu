@@ -10,7 +10,10 @@
 // The block B = K[I_left, I_right] of node id lives in one column of the level's raw panel:
 // rows of the left child hold u, rows of the right child hold v. All reductions use fixed
 // orders, so results are deterministic. In the mixed form the block entries are evaluated
-// in double-float (ff.cuh) from the FP64 distances; everything else stays FP64.
+// in double-float (ff.cuh) from the FP64 distances and the columns are stored and updated
+// as double-float pairs (8 bytes, like a double), so the per-element work runs on the FP32
+// pipe; the norm and dot-product partial sums that drive the stopping test are taken in
+// FP32 per thread and combined in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,6 +44,7 @@ struct AcaArgs {
   double *delta, *s2, *part;
   int part_stride;
   int max_rank;
+  const ff* tab;       // 2^(j/64) as double-floats (mixed form)
   int32_t* active;
   int nint;
   int pre[32];         // presized rank of each level (0: adaptive)
@@ -54,6 +58,12 @@ __device__ __forceinline__ double block_entry(const AcaArgs& a, const Cov& cov, 
   double r = dist(a.pts, i, j);
   if (!kFF) return cov_r(cov, r);
   return ff_to_double(cov_ff(a.kind, ff_from_double(r), cr, amp, tab));
+}
+
+// The same entry as a double-float (mixed form).
+__device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int i, int j, const ff* tab, ff cr,
+                                            ff amp) {
+  return cov_ff(a.kind, ff_from_double(dist(a.pts, i, j)), cr, amp, tab);
 }
 
 __device__ __forceinline__ int level_of(int id) { return 31 - __clz(id + 1); }
@@ -92,6 +102,29 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Argmax on float magnitudes (mixed form: the high word of each double-float).
+__device__ __forceinline__ void amax_merge_f(float& bv, int& bi, float v, int i) {
+  if (i < 0) return;
+  float av = fabsf(v), ab = fabsf(bv);
+  if (bi < 0 || av > ab || (av == ab && i < bi)) {
+    bv = v;
+    bi = i;
+  }
+}
+
+__device__ __forceinline__ void warp_amax_f(float& bv, int& bi) {
+  for (int o = 16; o > 0; o >>= 1) {
+    float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    amax_merge_f(bv, bi, ov, oi);
+  }
+}
+
 __global__ void k_aca_init(AcaArgs a) {
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= a.nint) return;
@@ -113,48 +146,73 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   int item = blockIdx.x;
   int id = a.item_node[item];
   if (a.done[id]) return;
-  extern __shared__ double dsm[];
-  double* uik = dsm;  // max_rank
+  extern __shared__ double dsm[];  // u_l(i), l < k (max_rank slots)
   __shared__ ff tab[64];
-  ff cr = {0, 0}, amp = {0, 0};
+  __shared__ double wv[kAcaThreads / 32];
+  __shared__ int wi[kAcaThreads / 32];
   const Cov cov = cov_from(a.kind, a.hyp);
+  ff cr = {0, 0}, amp = {0, 0};
   if (kFF) {
-    ff_exp_table(tab, threadIdx.x, kAcaThreads);
+    for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
     cr = ff_from_double(a.hyp[kHypScale]);
     amp = ff_from_double(cov.amp);
   }
-  __shared__ double wv[kAcaThreads / 32];
-  __shared__ int wi[kAcaThreads / 32];
   int k = a.rank[id], i = a.row[id];
   int bl = a.nb[2 * id + 1], br = a.nb[2 * id + 2], mr = a.ns[2 * id + 2];
   int64_t n = a.pts.n;
   double* raw = a.raw + a.raw_off[level_of(id)];
-  for (int l = threadIdx.x; l < k; l += kAcaThreads) uik[l] = raw[l * n + bl + i];
-  __syncthreads();
   int start = a.item_start[item];
-  double bv = 0.0;
-  int bi = -1;
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    int b = start + q * kAcaThreads + threadIdx.x;
-    if (b < mr) {
-      double v = block_entry<kFF>(a, cov, bl + i, br + b, tab, cr, amp);
-      for (int l = 0; l < k; ++l) v -= uik[l] * raw[l * n + br + b];
-      raw[(int64_t)k * n + br + b] = v;
-      amax_merge(bv, bi, v, b);
-    }
-  }
-  warp_amax(bv, bi);
   int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    wv[w] = bv;
-    wi[w] = bi;
+  int bi = -1;
+  if (!kFF) {
+    double* uik = dsm;
+    for (int l = threadIdx.x; l < k; l += kAcaThreads) uik[l] = raw[l * n + bl + i];
+    __syncthreads();
+    double bv = 0.0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      int b = start + q * kAcaThreads + threadIdx.x;
+      if (b < mr) {
+        double v = block_entry<false>(a, cov, bl + i, br + b, tab, cr, amp);
+        for (int l = 0; l < k; ++l) v -= uik[l] * raw[l * n + br + b];
+        raw[(int64_t)k * n + br + b] = v;
+        amax_merge(bv, bi, v, b);
+      }
+    }
+    warp_amax(bv, bi);
+    if ((threadIdx.x & 31) == 0) {
+      wv[w] = bv;
+      wi[w] = bi;
+    }
+  } else {
+    ff* rawf = reinterpret_cast<ff*>(raw);
+    ff* uik = reinterpret_cast<ff*>(dsm);
+    for (int l = threadIdx.x; l < k; l += kAcaThreads) uik[l] = rawf[l * n + bl + i];
+    __syncthreads();
+    float bv = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      int b = start + q * kAcaThreads + threadIdx.x;
+      if (b < mr) {
+        ff v = block_entry_ff(a, bl + i, br + b, tab, cr, amp);
+        for (int l = 0; l < k; ++l) v = ff_fms(v, uik[l], rawf[l * n + br + b]);
+        rawf[(int64_t)k * n + br + b] = v;
+        amax_merge_f(bv, bi, v.hi, b);
+      }
+    }
+    warp_amax_f(bv, bi);
+    if ((threadIdx.x & 31) == 0) {
+      wv[w] = bv;
+      wi[w] = bi;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double fv = 0.0;
     int fi = -1;
     for (int q = 0; q < kAcaThreads / 32; ++q) amax_merge(fv, fi, wv[q], wi[q]);
+    // the mixed form chose by the high word; the pivot value is the full double-float
+    if (kFF && fi >= 0) fv = ff_to_double(reinterpret_cast<const ff*>(raw)[(int64_t)k * n + br + fi]);
     a.part[(int64_t)item * a.part_stride + 0] = fv;
     a.part[(int64_t)item * a.part_stride + 1] = (double)fi;
   }
@@ -218,14 +276,13 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   extern __shared__ double dsm[];
   constexpr int kW = kAcaThreads / 32;
   const int nval = 2 + 2 * a.max_rank;
-  double* vjk = dsm;
   double* red = dsm + a.max_rank;
   int* used = reinterpret_cast<int*>(red + (int64_t)nval * kW);
   __shared__ ff tab[64];
   ff cr = {0, 0}, amp = {0, 0};
   const Cov cov = cov_from(a.kind, a.hyp);
   if (kFF) {
-    ff_exp_table(tab, threadIdx.x, kAcaThreads);
+    for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
     cr = ff_from_double(a.hyp[kHypScale]);
     amp = ff_from_double(cov.amp);
   }
@@ -238,58 +295,115 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   int nu = a.nused[id];
   int64_t n = a.pts.n;
   double* raw = a.raw + a.raw_off[level_of(id)];
-  for (int l = threadIdx.x; l < k; l += kAcaThreads) vjk[l] = raw[l * n + br + j];
   for (int q = threadIdx.x; q < nu; q += kAcaThreads) used[q] = a.used[(int64_t)id * a.used_stride + q];
-  __syncthreads();
   int start = a.item_start[item];
-  double uu[kPer], vv[kPer];
-  double nu2 = 0.0, nv2 = 0.0, bv = 0.0;
-  int bi = -1;
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    int t = start + q * kAcaThreads + threadIdx.x;
-    uu[q] = 0.0;
-    vv[q] = 0.0;
-    if (t < ml) {
-      double u = block_entry<kFF>(a, cov, bl + t, br + j, tab, cr, amp);
-      for (int l = 0; l < k; ++l) u -= raw[l * n + bl + t] * vjk[l];
-      raw[(int64_t)k * n + bl + t] = u;
-      uu[q] = u;
-      nu2 += u * u;
-      bool isu = false;
-      for (int s = 0; s < nu; ++s) isu |= used[s] == t;
-      if (!isu) amax_merge(bv, bi, u, t);
-    }
-    if (t < mr) {
-      double v = raw[(int64_t)k * n + br + t] / delta;
-      raw[(int64_t)k * n + br + t] = v;
-      vv[q] = v;
-      nv2 += v * v;
-    }
-  }
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  nu2 = warp_sum(nu2);
-  nv2 = warp_sum(nv2);
-  warp_amax(bv, bi);
-  if (lane == 0) {
-    red[0 * kW + w] = nu2;
-    red[1 * kW + w] = nv2;
-    wv[w] = bv;
-    wi[w] = bi;
-  }
-  for (int l = 0; l < k; ++l) {
-    double du = 0.0, dv = 0.0;
+  int bi = -1;
+  if (!kFF) {
+    double* vjk = dsm;
+    for (int l = threadIdx.x; l < k; l += kAcaThreads) vjk[l] = raw[l * n + br + j];
+    __syncthreads();
+    const double inv = 1.0 / delta;
+    double uu[kPer], vv[kPer];
+    double nu2 = 0.0, nv2 = 0.0, bv = 0.0;
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
       int t = start + q * kAcaThreads + threadIdx.x;
-      if (t < ml) du += raw[l * n + bl + t] * uu[q];
-      if (t < mr) dv += raw[l * n + br + t] * vv[q];
+      uu[q] = 0.0;
+      vv[q] = 0.0;
+      if (t < ml) {
+        double u = block_entry<false>(a, cov, bl + t, br + j, tab, cr, amp);
+        for (int l = 0; l < k; ++l) u -= raw[l * n + bl + t] * vjk[l];
+        raw[(int64_t)k * n + bl + t] = u;
+        uu[q] = u;
+        nu2 += u * u;
+        bool isu = false;
+        for (int s = 0; s < nu; ++s) isu |= used[s] == t;
+        if (!isu) amax_merge(bv, bi, u, t);
+      }
+      if (t < mr) {
+        double v = raw[(int64_t)k * n + br + t] * inv;
+        raw[(int64_t)k * n + br + t] = v;
+        vv[q] = v;
+        nv2 += v * v;
+      }
     }
-    du = warp_sum(du);
-    dv = warp_sum(dv);
+    nu2 = warp_sum(nu2);
+    nv2 = warp_sum(nv2);
+    warp_amax(bv, bi);
     if (lane == 0) {
-      red[(2 + l) * kW + w] = du;
-      red[(2 + a.max_rank + l) * kW + w] = dv;
+      red[0 * kW + w] = nu2;
+      red[1 * kW + w] = nv2;
+      wv[w] = bv;
+      wi[w] = bi;
+    }
+    for (int l = 0; l < k; ++l) {
+      double du = 0.0, dv = 0.0;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        int t = start + q * kAcaThreads + threadIdx.x;
+        if (t < ml) du += raw[l * n + bl + t] * uu[q];
+        if (t < mr) dv += raw[l * n + br + t] * vv[q];
+      }
+      du = warp_sum(du);
+      dv = warp_sum(dv);
+      if (lane == 0) {
+        red[(2 + l) * kW + w] = du;
+        red[(2 + a.max_rank + l) * kW + w] = dv;
+      }
+    }
+  } else {
+    ff* rawf = reinterpret_cast<ff*>(raw);
+    ff* vjk = reinterpret_cast<ff*>(dsm);
+    for (int l = threadIdx.x; l < k; l += kAcaThreads) vjk[l] = rawf[l * n + br + j];
+    __syncthreads();
+    const ff inv = ff_rcp(ff_from_double(delta));
+    float uu[kPer], vv[kPer];  // high words, for the dot products of the stopping test
+    float nu2 = 0.0f, nv2 = 0.0f, bv = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      int t = start + q * kAcaThreads + threadIdx.x;
+      uu[q] = 0.0f;
+      vv[q] = 0.0f;
+      if (t < ml) {
+        ff u = block_entry_ff(a, bl + t, br + j, tab, cr, amp);
+        for (int l = 0; l < k; ++l) u = ff_fms(u, rawf[l * n + bl + t], vjk[l]);
+        rawf[(int64_t)k * n + bl + t] = u;
+        uu[q] = u.hi;
+        nu2 += u.hi * u.hi;
+        bool isu = false;
+        for (int s = 0; s < nu; ++s) isu |= used[s] == t;
+        if (!isu) amax_merge_f(bv, bi, u.hi, t);
+      }
+      if (t < mr) {
+        ff v = ff_mul(rawf[(int64_t)k * n + br + t], inv);
+        rawf[(int64_t)k * n + br + t] = v;
+        vv[q] = v.hi;
+        nv2 += v.hi * v.hi;
+      }
+    }
+    double nu2d = warp_sum((double)nu2), nv2d = warp_sum((double)nv2);
+    warp_amax_f(bv, bi);
+    if (lane == 0) {
+      red[0 * kW + w] = nu2d;
+      red[1 * kW + w] = nv2d;
+      wv[w] = bv;
+      wi[w] = bi;
+    }
+    for (int l = 0; l < k; ++l) {
+      float du = 0.0f, dv = 0.0f;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        int t = start + q * kAcaThreads + threadIdx.x;
+        if (t < ml) du += rawf[l * n + bl + t].hi * uu[q];
+        if (t < mr) dv += rawf[l * n + br + t].hi * vv[q];
+      }
+      du = warp_sum_f(du);
+      dv = warp_sum_f(dv);
+      if (lane == 0) {
+        red[(2 + l) * kW + w] = du;
+        red[(2 + a.max_rank + l) * kW + w] = dv;
+      }
     }
   }
   __syncthreads();
@@ -407,12 +521,16 @@ __global__ void k_pack(PackArgs p) {
   int id = 0;
   for (int l = 0; l < j; ++l) id = i < p.nb[2 * id + 2] ? 2 * id + 1 : 2 * id + 2;
   int r = p.rank[id];
-  const double* src = p.raw + p.raw_off[j];
+  // 64-bit moves: the same code serves FP64 values and double-float pairs (all-zero bits
+  // are 0 in both)
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p.raw + p.raw_off[j]);
+  unsigned long long* phi = reinterpret_cast<unsigned long long*>(p.phi);
+  unsigned long long* pan = reinterpret_cast<unsigned long long*>(p.pan);
   for (int c = 0; c < p.rl[j]; ++c) {
-    double v = c < r ? src[c * p.n + i] : 0.0;
+    unsigned long long v = c < r ? src[c * p.n + i] : 0ull;
     int64_t o = (int64_t)(p.coff[j] + c) * p.n + i;
-    p.phi[o] = v;
-    p.pan[o] = v;
+    phi[o] = v;
+    pan[o] = v;
   }
 }
 
@@ -445,6 +563,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   a.delta = c.st_delta; a.s2 = c.st_s2; a.part = c.aca_part;
   a.part_stride = 4 + 2 * c.max_rank;
   a.max_rank = c.max_rank;
+  a.tab = reinterpret_cast<const ff*>(c.exp_tab);
   a.active = c.active;
   a.nint = nint;
   k_aca_init<<<(nint + 255) / 256, 256, 0, c.stream>>>(a);
@@ -485,6 +604,17 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
     k_aca_check<<<(nint + 255) / 256, 256, 0, c.stream>>>(a, c.dflags);
     ++c.launches;
   }
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_exp_table(ff* tab) { ff_exp_table(tab, threadIdx.x, blockDim.x); }
+}  // namespace
+
+// 2^(j/64), j < 64, as double-floats for the double-float exp (once per context).
+cudaError_t launch_exp_table(Ctx& c) {
+  k_exp_table<<<1, 64, 0, c.stream>>>(reinterpret_cast<ff*>(c.exp_tab));
+  ++c.launches;
   return cudaGetLastError();
 }
 

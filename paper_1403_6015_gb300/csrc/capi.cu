@@ -82,7 +82,7 @@ void free_all(Ctx* c) {
   dfree(c->st_zero); dfree(c->st_phase); dfree(c->st_nused); dfree(c->st_used);
   dfree(c->st_delta); dfree(c->st_s2); dfree(c->aca_part); dfree(c->active);
   dfree(c->Y); dfree(c->ysort); dfree(c->leafL); dfree(c->leaf_logdet); dfree(c->node_logdet);
-  dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->ry); dfree(c->rw); dfree(c->Mlu); dfree(c->Mpiv);
+  dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->ry); dfree(c->rw); dfree(c->exp_tab); dfree(c->Mlu); dfree(c->Mpiv);
   dfree(c->hyp);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
@@ -376,7 +376,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   int64_t nleaf = (int64_t)1 << c->kappa;
   if (dalloc(&c->nodes, 2 * tot) || dalloc(&c->xs, n * d) || dalloc(&c->perm, n) ||
       dalloc(&c->dflags, 4) || dalloc(&c->scal, 8) || dalloc(&c->active, 1) ||
-      dalloc(&c->hyp, hodlr::kHypLen) ||
+      dalloc(&c->hyp, hodlr::kHypLen) || dalloc(&c->exp_tab, 64) ||
       dalloc(&c->Y, n * c->max_nrhs) || dalloc(&c->ysort, n) || dalloc(&c->tmpvec, n * c->max_nrhs) ||
       dalloc(&c->leaf_logdet, nleaf) || dalloc(&c->node_logdet, std::max<int64_t>(nleaf - 1, 1)) ||
       dalloc(&c->leafL, nleaf * hodlr::kMaxLeaf * hodlr::kMaxLeaf) ||
@@ -387,6 +387,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
     return bail(HODLR_ENOMEM);
   }
   cudaMemcpyAsync(c->nodes, c->h_nodes.data(), 4 * c->h_nodes.size(), cudaMemcpyHostToDevice, c->stream);
+  if (hodlr::launch_exp_table(*c) != cudaSuccess) return bail(HODLR_ECUDA);
   // points on the device (row-major n x d), finiteness check
   const double* xd = x;
   double* xtmp = nullptr;

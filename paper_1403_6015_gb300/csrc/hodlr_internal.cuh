@@ -168,6 +168,7 @@ struct Ctx {
   double* hyp = nullptr;          // device hyperparameter slot (kHyp* layout)
   int32_t* dflags = nullptr;
   double* tmpvec = nullptr;       // n x max_nrhs staging for host/device copies
+  double* exp_tab = nullptr;      // 64 double-float pairs, 2^(j/64) (mixed form)
   // iterative refinement (refine.cu): sorted right-hand sides and work vectors
   double refine_tol = 1e-10;
   int refine_maxit = 0;
@@ -205,6 +206,7 @@ cudaError_t launch_sort_1d(Ctx& c, const double* x_dev_rowmajor);
 cudaError_t launch_sort_kd(Ctx& c, const double* x_dev_rowmajor);
 cudaError_t launch_aca(Ctx& c, int* steps_out);
 cudaError_t launch_pack(Ctx& c);
+cudaError_t launch_exp_table(Ctx& c);
 cudaError_t launch_gather_rhs(Ctx& c, const double* y, int64_t ld, int nrhs);
 cudaError_t launch_scatter_rhs(Ctx& c, double* x, int64_t ld, int nrhs);
 cudaError_t launch_leaf_factor(Ctx& c, int nrhs);

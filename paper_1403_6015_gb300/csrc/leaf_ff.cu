@@ -2,9 +2,10 @@
 //
 // Same work as k_leaf (Sec. 3.2: factor K_kappa out of C, applying each leaf inverse to the
 // ancestors' U/V rows and to the right-hand sides; Sec. 4: leaf determinants), but every
-// operation on the leaf block runs in double-float (ff.cuh) on the FP32 pipe. Values enter
-// and leave HBM as FP64; the stored factor is kept as double-float pairs; the log of each
-// pivot is taken in FP64. Unit roundoff ~2^-48 instead of 2^-53.
+// operation on the leaf block runs in double-float (ff.cuh) on the FP32 pipe. The panels
+// (Phi and the U/V columns) enter and leave HBM as double-float pairs, the right-hand sides
+// as FP64; the stored factor is kept as double-float pairs; the log of each pivot is taken
+// in FP64. Unit roundoff ~2^-48 instead of 2^-53.
 //
 // Blocked for the FP32 pipe (one CTA per leaf, all of it in shared memory, two CTAs per
 // SM so that one leaf's barriers overlap the other's work):
@@ -52,6 +53,7 @@ struct LeafFFArgs {
   double* part;
   int64_t part_stride;
   ff* leafL;          // stored factor: L below the diagonal, D on it (double-float pairs)
+  const ff* tab;      // 2^(j/64) as double-floats
   double* leaf_logdet;
   int32_t* flags;
 };
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
   ff* Lst = a.leafL + (int64_t)leaf * kMaxLeaf * kMaxLeaf;
   if (kFactor) {
     if (tid == 0) bad = 0;
-    ff_exp_table(tab, tid, kT);
+    for (int q = tid; q < 64; q += kT) tab[q] = a.tab[q];
     // coordinates relative to the leaf's first point (keeps small offsets exact)
     for (int i = tid; i < p; i += kT) {
       xl[i] = ff_from_double(a.x[b + i] - a.x[b]);
@@ -258,11 +260,14 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
   int ncol = a.cP + a.nrhs;
   for (int q0 = 0; q0 < ncol; q0 += kCW) {
     int cw = ncol - q0 < kCW ? ncol - q0 : kCW;
+    const ff* panf = reinterpret_cast<const ff*>(a.pan);
     for (int e = tid; e < P * cw; e += kT) {
       int c = e / P, i = e - c * P;
       int q = q0 + c;
-      const double* col = q < a.cP ? a.pan + (int64_t)q * a.n + b : a.Y + (int64_t)(q - a.cP) * a.n + b;
-      B[i * kBS + c] = i < p ? ff_from_double(col[i]) : ff{0.0f, 0.0f};
+      ff v = {0.0f, 0.0f};
+      if (i < p)
+        v = q < a.cP ? panf[(int64_t)q * a.n + b + i] : ff_from_double(a.Y[(int64_t)(q - a.cP) * a.n + b + i]);
+      B[i * kBS + c] = v;
     }
     __syncthreads();
     // forward: L w = b
@@ -324,16 +329,18 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
     for (int e = tid; e < p * cw; e += kT) {
       int c = e / p, i = e - c * p;
       int q = q0 + c;
-      double* col = q < a.cP ? a.pan + (int64_t)q * a.n + b : a.Y + (int64_t)(q - a.cP) * a.n + b;
-      col[i] = ff_to_double(B[i * kBS + c]);
+      if (q < a.cP)
+        reinterpret_cast<ff*>(a.pan)[(int64_t)q * a.n + b + i] = B[i * kBS + c];
+      else
+        a.Y[(int64_t)(q - a.cP) * a.n + b + i] = ff_to_double(B[i * kBS + c]);
     }
     if (a.kappa > 0) {
       double* out = a.part + (int64_t)leaf * a.part_stride;
       for (int t = w; t < a.rl * cw; t += NW) {
         int r = t / cw, c = t - r * cw;
-        const double* ph = a.phi + (int64_t)(a.coff + r) * a.n + b;
+        const ff* ph = reinterpret_cast<const ff*>(a.phi) + (int64_t)(a.coff + r) * a.n + b;
         ff s = {0.0f, 0.0f};
-        for (int i = lane; i < p; i += 32) s = ff_fma(s, ff_from_double(ph[i]), B[i * kBS + c]);
+        for (int i = lane; i < p; i += 32) s = ff_fma(s, ph[i], B[i * kBS + c]);
         for (int o = 16; o > 0; o >>= 1) s = ff_add(s, xor_ff(s, o));
         if (lane == 0) out[r * ncol + q0 + c] = ff_to_double(s);
       }
@@ -363,6 +370,7 @@ LeafFFArgs make_ff_args(Ctx& c, int nrhs, bool factor) {
   a.part = c.part;
   a.part_stride = c.part_stride;
   a.leafL = reinterpret_cast<ff*>(c.leafL);
+  a.tab = reinterpret_cast<const ff*>(c.exp_tab);
   a.leaf_logdet = c.leaf_logdet;
   a.flags = c.dflags;
   return a;

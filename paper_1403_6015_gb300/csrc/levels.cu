@@ -112,65 +112,134 @@ struct SweepArgs {
 
 // Level-u update of one leaf's rows, fused with the level-(u-1) partial products.
 // kStage: the leaf's rows of Ut/Vt (level u) and Phi (level u-1) are staged in shared
-// memory (p x (ru + rl) doubles); otherwise (large ranks) they are read from the panels.
-template <bool kStage>
+// memory (p x (ru + rl) elements); otherwise (large ranks) they are read from the panels.
+// T = ff (mixed form): the panels and Z's panel columns are double-float pairs and their
+// arithmetic runs in double-float on the FP32 pipe; the right-hand-side columns (and Z's
+// right-hand-side columns) stay FP64, reading the panels through conversions.
+template <class T> struct Elem;
+template <> struct Elem<double> {
+  static __device__ __forceinline__ double to_double(double v) { return v; }
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double from_rhs(double v) { return v; }
+  static __device__ __forceinline__ double to_rhs(double v) { return v; }
+  static __device__ __forceinline__ double fms(double c, double a, double b) { return c - a * b; }
+  static __device__ __forceinline__ double fma(double c, double a, double b) { return c + a * b; }
+  static __device__ __forceinline__ double wsum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  }
+};
+template <> struct Elem<ff> {
+  static __device__ __forceinline__ double to_double(ff v) { return ff_to_double(v); }
+  static __device__ __forceinline__ ff zero() { return ff{0.0f, 0.0f}; }
+  static __device__ __forceinline__ ff from_rhs(double v) { return ff_from_double(v); }
+  static __device__ __forceinline__ double to_rhs(ff v) { return ff_to_double(v); }
+  static __device__ __forceinline__ ff fms(ff c, ff a, ff b) { return ff_fms(c, a, b); }
+  static __device__ __forceinline__ ff fma(ff c, ff a, ff b) { return ff_fma(c, a, b); }
+  static __device__ __forceinline__ ff wsum(ff v) {
+    for (int o = 16; o > 0; o >>= 1)
+      v = ff_add(v, ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+    return v;
+  }
+};
+
+template <bool kStage, class T>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs a) {
-  extern __shared__ double sm[];
+  using E = Elem<T>;
+  extern __shared__ double smd[];
+  T* sm = reinterpret_cast<T*>(smd);
+  T* pan = reinterpret_cast<T*>(a.pan);
+  const T* phi = reinterpret_cast<const T*>(a.phi);
   int leaf = blockIdx.x;
   int id = a.leaf0 + leaf;
   int b = a.nb[id], p = a.ns[id];
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   // element (i, c): staged at [i * r + c], in the panels at column c, row b + i
-  const double* tl = kStage ? sm : a.pan + (int64_t)a.cu * a.n + b;
-  const double* ph = kStage ? sm + kMaxLeaf * a.ru : a.phi + (int64_t)a.cl * a.n + b;
+  const T* tl = kStage ? sm : pan + (int64_t)a.cu * a.n + b;
+  const T* ph = kStage ? sm + kMaxLeaf * a.ru : phi + (int64_t)a.cl * a.n + b;
   const int64_t tl_i = kStage ? a.ru : 1, tl_c = kStage ? 1 : a.n;
   const int64_t ph_i = kStage ? a.rl : 1, ph_c = kStage ? 1 : a.n;
   if (kStage) {
     for (int e = tid; e < p * a.ru; e += kSweepThreads) {
       int i = e % p, c = e / p;
-      sm[i * a.ru + c] = a.pan[(int64_t)(a.cu + c) * a.n + b + i];
+      sm[i * a.ru + c] = pan[(int64_t)(a.cu + c) * a.n + b + i];
     }
     for (int e = tid; e < p * a.rl; e += kSweepThreads) {
       int i = e % p, c = e / p;
-      sm[kMaxLeaf * a.ru + i * a.rl + c] = a.phi[(int64_t)(a.cl + c) * a.n + b + i];
+      sm[kMaxLeaf * a.ru + i * a.rl + c] = phi[(int64_t)(a.cl + c) * a.n + b + i];
     }
     __syncthreads();
   }
   int sh = a.kappa - a.u;
   int side = (leaf >> (sh - 1)) & 1;
   int wz = a.cP + a.nrhs;
-  const double* Zs = a.Z + (int64_t)(leaf >> sh) * a.z_stride + (int64_t)side * a.ru * wz;
+  const T* Zs = reinterpret_cast<const T*>(a.Z) + (int64_t)(leaf >> sh) * a.z_stride + (int64_t)side * a.ru * wz;
   double* out = a.part + (int64_t)leaf * a.part_stride;
   for (int q = w; q < wz; q += kSweepThreads / 32) {
-    double* col = q < a.cP ? a.pan + (int64_t)q * a.n + b : a.Y + (int64_t)(q - a.cP) * a.n + b;
-    double x[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      int i = m * 32 + lane;
-      x[m] = i < p ? col[i] : 0.0;
-    }
-    for (int c = 0; c < a.ru; ++c) {
-      double z = Zs[c * wz + q];
+    if (q < a.cP) {
+      T* colp = pan + (int64_t)q * a.n + b;
+      T x[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         int i = m * 32 + lane;
-        if (i < p) x[m] -= tl[i * tl_i + c * tl_c] * z;
+        x[m] = i < p ? colp[i] : E::zero();
       }
-    }
+      for (int c = 0; c < a.ru; ++c) {
+        T z = Zs[c * wz + q];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      int i = m * 32 + lane;
-      if (i < p) col[i] = x[m];
-    }
-    for (int c = 0; c < a.rl; ++c) {
-      double s = 0.0;
+        for (int m = 0; m < 4; ++m) {
+          int i = m * 32 + lane;
+          if (i < p) x[m] = E::fms(x[m], tl[i * tl_i + c * tl_c], z);
+        }
+      }
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         int i = m * 32 + lane;
-        if (i < p) s += ph[i * ph_i + c * ph_c] * x[m];
+        if (i < p) colp[i] = x[m];
       }
-      s = wsum(s);
-      if (lane == 0) out[c * wz + q] = s;
+      for (int c = 0; c < a.rl; ++c) {
+        T s = E::zero();
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          int i = m * 32 + lane;
+          if (i < p) s = E::fma(s, ph[i * ph_i + c * ph_c], x[m]);
+        }
+        s = E::wsum(s);
+        if (lane == 0) out[c * wz + q] = E::to_rhs(s);
+      }
+    } else {
+      // a right-hand side: FP64 throughout
+      double* coly = a.Y + (int64_t)(q - a.cP) * a.n + b;
+      const double* Zd = reinterpret_cast<const double*>(Zs);
+      double x[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        x[m] = i < p ? coly[i] : 0.0;
+      }
+      for (int c = 0; c < a.ru; ++c) {
+        double z = Zd[c * wz + q];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          int i = m * 32 + lane;
+          if (i < p) x[m] -= E::to_double(tl[i * tl_i + c * tl_c]) * z;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) coly[i] = x[m];
+      }
+      for (int c = 0; c < a.rl; ++c) {
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          int i = m * 32 + lane;
+          if (i < p) s += E::to_double(ph[i * ph_i + c * ph_c]) * x[m];
+        }
+        s = Elem<double>::wsum(s);
+        if (lane == 0) out[c * wz + q] = s;
+      }
     }
   }
 }
@@ -246,7 +315,12 @@ struct MvArgs {
   double* part;      // leaf x R partials (Phi^T x)
   const double* half;  // per level half sums, level j at half + hoff[j]
   int64_t n;
+  int phiff;           // 1: Phi holds double-float pairs (mixed form)
 };
+
+__device__ __forceinline__ double phi_at(const MvArgs& a, int64_t k) {
+  return a.phiff ? ff_to_double(reinterpret_cast<const ff*>(a.phi)[k]) : a.phi[k];
+}
 
 struct LevelTab {
   int coff[33];
@@ -261,7 +335,7 @@ __global__ void k_mv_partials(MvArgs a, LevelTab t) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int c = w; c < a.R; c += blockDim.x / 32) {
     double s = 0.0;
-    for (int i = lane; i < p; i += 32) s += a.phi[(int64_t)c * a.n + b + i] * a.xin[b + i];
+    for (int i = lane; i < p; i += 32) s += phi_at(a, (int64_t)c * a.n + b + i) * a.xin[b + i];
     s = wsum(s);
     if (lane == 0) a.part[(int64_t)leaf * a.R + c] = s;
   }
@@ -286,7 +360,7 @@ __global__ void k_mv_apply(MvArgs a, LevelTab t) {
       int k = leaf >> sh;
       int side = (leaf >> (sh - 1)) & 1;
       const double* hs = a.half + t.hoff[l] + (int64_t)(2 * k + (1 - side)) * t.rl[l];
-      for (int c = 0; c < t.rl[l]; ++c) s += a.phi[(int64_t)(t.coff[l] + c) * a.n + b + i] * hs[c];
+      for (int c = 0; c < t.rl[l]; ++c) s += phi_at(a, (int64_t)(t.coff[l] + c) * a.n + b + i) * hs[c];
     }
     a.yout[b + i] = s;
   }
@@ -305,6 +379,18 @@ cudaError_t launch_scatter_rhs(Ctx& c, double* x, int64_t ld, int nrhs) {
   unsigned g = (unsigned)((c.n + 255) / 256);
   k_scatter<<<g, 256, 0, c.stream>>>(c.Y, nrhs, c.perm, c.n, x, ld);
   ++c.launches;
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_sweep(const SweepArgs& sa, unsigned grid, size_t smem, cudaStream_t st) {
+  if (smem <= 200 * 1024) {
+    if (smem > 48 * 1024)
+      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_sweep<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_sweep<true, T><<<grid, kSweepThreads, smem, st>>>(sa);
+  } else {
+    k_sweep<false, T><<<grid, kSweepThreads, 0, st>>>(sa);
+  }
   return cudaGetLastError();
 }
 
@@ -335,6 +421,7 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
     na.Z = c.Z;
     na.z_stride = (int64_t)2 * r * na.wz;
     na.flags = c.dflags;
+    na.zff = c.precision == 1;
     if (r > 0) {
       HODLR_CUDA_TRY(launch_node(c, na, factor_mode));
     } else if (factor_mode) {
@@ -366,13 +453,10 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
     sa.n = c.n;
     if (sa.cP + nrhs == 0) continue;  // nothing left to update (root level, no right-hand side)
     size_t smem = sizeof(double) * kMaxLeaf * (sa.ru + sa.rl);
-    if (smem <= 200 * 1024) {
-      if (smem > 48 * 1024)
-        HODLR_CUDA_TRY(cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_sweep<true><<<(unsigned)nleaf, kSweepThreads, smem, c.stream>>>(sa);
-    } else {
-      k_sweep<false><<<(unsigned)nleaf, kSweepThreads, 0, c.stream>>>(sa);
-    }
+    if (c.precision == 1)
+      HODLR_CUDA_TRY(launch_sweep<ff>(sa, (unsigned)nleaf, smem, c.stream));
+    else
+      HODLR_CUDA_TRY(launch_sweep<double>(sa, (unsigned)nleaf, smem, c.stream));
     ++c.launches;
     HODLR_CUDA_TRY(cudaGetLastError());
   }
@@ -399,6 +483,7 @@ cudaError_t launch_level_first(Ctx& c, int nrhs, bool factor_mode) {
   na.Z = c.Z + (j & 1) * c.z_elems;
   na.z_stride = (int64_t)2 * r * na.wz;
   na.flags = c.dflags;
+  na.zff = c.precision == 1;
   if (r == 0) {
     if (factor_mode)
       HODLR_CUDA_TRY(cudaMemsetAsync(c.node_logdet + ((1 << j) - 1), 0, sizeof(double) << j, c.stream));
@@ -478,6 +563,7 @@ cudaError_t launch_matvec(Ctx& c, const double* xin, double* yout) {
   a.yout = yout;
   a.part = c.part;
   a.n = c.n;
+  a.phiff = c.precision == 1;
   LevelTab t;
   int64_t off = 0;
   for (int j = 0; j < 32; ++j) {

@@ -10,6 +10,7 @@
 // count arrivals with atomics; no block ever waits for another.
 #include <cuda_runtime.h>
 
+#include "ff.cuh"
 #include "hodlr_internal.cuh"
 #include "node_solve.cuh"
 
@@ -43,6 +44,111 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
+__device__ __forceinline__ ff wsum_ff(ff v) {
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff_add(v, ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  return v;
+}
+
+// Mixed form, a right-hand-side column: FP64 arithmetic (the solution keeps FP64
+// accuracy), the double-float panel values converted as they are read; Z's right-hand-side
+// columns are FP64.
+__device__ __forceinline__ void leaf_column_rhs(const FusedArgs& a, int leaf, int b, int p, int q,
+                                                int wz, int sh, int zs, int lane) {
+  const ff* panf = reinterpret_cast<const ff*>(a.pan);
+  const ff* phif = reinterpret_cast<const ff*>(a.phi);
+  double* col = a.Y + (int64_t)(q - a.cP) * a.n + b;
+  double x[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    int i = m * 32 + lane;
+    x[m] = i < p ? col[i] : 0.0;
+  }
+  if (a.ru > 0) {
+    int side = (leaf >> (sh - 1)) & 1;
+    const double* Zs = a.Zu + (int64_t)(leaf >> sh) * zs + (int64_t)side * a.ru * wz;
+    for (int c = 0; c < a.ru; ++c) {
+      double z = Zs[c * wz + q];
+      const ff* tl = panf + (int64_t)(a.cu + c) * a.n + b;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) x[m] -= ff_to_double(tl[i]) * z;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int i = m * 32 + lane;
+      if (i < p) col[i] = x[m];
+    }
+  }
+  if (a.u > 0 && a.rl > 0) {
+    double* out = a.part + (int64_t)leaf * a.part_stride;
+    for (int c = 0; c < a.rl; ++c) {
+      const ff* ph = phif + (int64_t)(a.cl + c) * a.n + b;
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) s += ff_to_double(ph[i]) * x[m];
+      }
+      s = wsum(s);
+      if (lane == 0) out[c * wz + q] = s;
+    }
+  }
+}
+
+// Mixed form, a panel column: the panels and Z's panel columns are double-float pairs; the
+// update and the partial products run on the FP32 pipe.
+__device__ __forceinline__ void leaf_column_ff(const FusedArgs& a, int leaf, int b, int p, int q,
+                                               int wz, int sh, int zs, int lane) {
+  if (q >= a.cP) {
+    leaf_column_rhs(a, leaf, b, p, q, wz, sh, zs, lane);
+    return;
+  }
+  ff* panf = reinterpret_cast<ff*>(a.pan);
+  const ff* phif = reinterpret_cast<const ff*>(a.phi);
+  ff x[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    int i = m * 32 + lane;
+    x[m] = i < p ? panf[(int64_t)q * a.n + b + i] : ff{0.0f, 0.0f};
+  }
+  if (a.ru > 0) {
+    int side = (leaf >> (sh - 1)) & 1;
+    const ff* Zs = reinterpret_cast<const ff*>(a.Zu) + (int64_t)(leaf >> sh) * zs + (int64_t)side * a.ru * wz;
+    for (int c = 0; c < a.ru; ++c) {
+      ff z = Zs[c * wz + q];
+      const ff* tl = panf + (int64_t)(a.cu + c) * a.n + b;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) x[m] = ff_fms(x[m], tl[i], z);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int i = m * 32 + lane;
+      if (i < p) panf[(int64_t)q * a.n + b + i] = x[m];
+    }
+  }
+  if (a.u > 0 && a.rl > 0) {
+    double* out = a.part + (int64_t)leaf * a.part_stride;
+    for (int c = 0; c < a.rl; ++c) {
+      const ff* ph = phif + (int64_t)(a.cl + c) * a.n + b;
+      ff s = {0.0f, 0.0f};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) s = ff_fma(s, ph[i], x[m]);
+      }
+      s = wsum_ff(s);
+      if (lane == 0) out[c * wz + q] = ff_to_double(s);
+    }
+  }
+}
+
+template <bool kFF>
 __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
   extern __shared__ double M[];  // node step, (2 rl)^2
   __shared__ int piv[2 * kSmemRank];
@@ -57,6 +163,13 @@ __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
   int sh = a.kappa - a.u;  // leaves per level-u half-node = 2^(sh - 1); per node = 2^sh
   int zs = 2 * a.ru * wz;
   for (int t = w; t < nl * wz; t += kLT / 32) {
+    if (kFF) {
+      int g = t / wz, q = t - g * wz;
+      int leaf = leaf_base + g;
+      int id = a.leaf0 + leaf;
+      leaf_column_ff(a, leaf, a.nb[id], a.ns[id], q, wz, sh, zs, lane);
+      continue;
+    }
     int g = t / wz, q = t - g * wz;
     int leaf = leaf_base + g;
     int id = a.leaf0 + leaf;
@@ -204,15 +317,22 @@ cudaError_t launch_levels_fused(Ctx& c, int nrhs, bool factor_mode) {
       na.Z = c.Z + (l & 1) * c.z_elems;
       na.z_stride = (int64_t)2 * fa.rl * na.wz;
       na.flags = c.dflags;
+      na.zff = c.precision == 1;
       if (factor_mode && fa.rl == 0)
         HODLR_CUDA_TRY(cudaMemsetAsync(c.node_logdet + ((1 << l) - 1), 0, sizeof(double) << l, c.stream));
     }
     if (wz == 0 && (l < 0 || fa.rl == 0)) continue;
     size_t smem = sizeof(double) * 4 * fa.rl * fa.rl;
-    if (smem > 48 * 1024)
-      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned grid = (unsigned)((nleaf + kG - 1) / kG);
-    k_level<<<grid, kLT, smem, c.stream>>>(fa);
+    if (c.precision == 1) {
+      if (smem > 48 * 1024)
+        HODLR_CUDA_TRY(cudaFuncSetAttribute(k_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_level<true><<<grid, kLT, smem, c.stream>>>(fa);
+    } else {
+      if (smem > 48 * 1024)
+        HODLR_CUDA_TRY(cudaFuncSetAttribute(k_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_level<false><<<grid, kLT, smem, c.stream>>>(fa);
+    }
     ++c.launches;
     HODLR_CUDA_TRY(cudaGetLastError());
   }

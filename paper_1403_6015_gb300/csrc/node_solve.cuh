@@ -5,6 +5,7 @@
 // Z = M^-1 [V^T P_R; U^T P_L] for the update P_L -= Ut Z_top, P_R -= Vt Z_bot.
 #pragma once
 
+#include "ff.cuh"
 #include "hodlr_internal.cuh"
 
 namespace hodlr {
@@ -21,6 +22,8 @@ struct NodeArgs {
   double* Z;            // level scratch, z_stride = 2 r wz per node
   int64_t z_stride;
   int32_t* flags;
+  int zff;              // 1 (mixed form): Z's panel columns (q < cj) as double-float pairs,
+                        // its right-hand-side columns FP64; 0: all FP64
 };
 
 // Partial column of Z column q: ancestors' panel columns keep their index, the right-hand
@@ -132,6 +135,9 @@ static __device__ void node_solve(const NodeArgs& a, int k, bool factor, double*
       for (int c = i + 1; c < m2; ++c) s -= M[i * m2 + c] * Zn[c * a.wz + q];
       Zn[i * a.wz + q] = s / M[i * m2 + i];
     }
+    if (a.zff && q < a.cj)  // a panel column, in place: this thread owns column q
+      for (int i = 0; i < m2; ++i)
+        reinterpret_cast<ff*>(Zn)[i * a.wz + q] = ff_from_double(Zn[i * a.wz + q]);
   }
 }
 
@@ -268,6 +274,9 @@ static __device__ void node_solve_global(const NodeArgs& a, int k, bool factor, 
       for (int c = i + 1; c < m2; ++c) s -= mi[c] * Zn[(int64_t)c * a.wz + q];
       Zn[(int64_t)i * a.wz + q] = s / mi[i];
     }
+    if (a.zff && q < a.cj)  // a panel column, in place: this thread owns column q
+      for (int i = 0; i < m2; ++i)
+        reinterpret_cast<ff*>(Zn)[(int64_t)i * a.wz + q] = ff_from_double(Zn[(int64_t)i * a.wz + q]);
   }
 }
 
