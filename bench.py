@@ -159,6 +159,12 @@ def measure_form(args, precision, x, y, xd, yd, stream, world, rank, local, dev)
     ctxs = [H.Hodlr(xd, kern, [ell, 1.0], SIGMA2, LEAF, EPS, max_rank=16, max_nrhs=1,
                     stream=stream.cuda_stream, precision=precision) for kern, ell in KERNELS]
     outs = torch.zeros(len(KERNELS), dtype=torch.float64, device=dev)
+    # launch configuration per context, chosen by the library's autotuner (untimed)
+    tuning = {}
+    for h, (kern, ell) in zip(ctxs, KERNELS):
+        if not args.no_autotune:
+            h.autotune(yd, reps=3)
+        tuning[kern] = h.tuning()
 
     def step(leaf_ms=None):
         for i, (h, (kern, ell)) in enumerate(zip(ctxs, KERNELS)):
@@ -192,7 +198,7 @@ def measure_form(args, precision, x, y, xd, yd, stream, world, rank, local, dev)
     ms = float(t.item())
     value = args.steps * len(KERNELS) * world / (ms / 1e3)
     res = {"value": value, "ms_per_step": ms / args.steps, "gpu_launches": launches,
-           "clocks": clk.summary(), "phase_ms": ctxs[0].phase_ms()}
+           "clocks": clk.summary(), "phase_ms": ctxs[0].phase_ms(), "tuning": tuning}
 
     # end to end through the C ABI with host buffers: pinned y in, host scalar out
     y_host = torch.from_numpy(y).pin_memory().numpy()
@@ -281,6 +287,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": len(KERNELS) * 8},
             "roofline": r["roofline"],
             "phase_ms": r["phase_ms"],
+            "tuning": r["tuning"],
             "gpu_launches": r["gpu_launches"],
             "clocks": r["clocks"],
             "accuracy": r["accuracy"],
@@ -294,7 +301,7 @@ def run_ours(args):
                 line[FORMS[p][0] + "_form"] = {
                     "value": o["value"], "ms_per_step": o["ms_per_step"], "dtype": o["dtype"],
                     "e2e": o.get("e2e"), "roofline": o["roofline"], "phase_ms": o["phase_ms"],
-                    "accuracy": o["accuracy"], "accepted": o["accepted"]}
+                    "tuning": o["tuning"], "accuracy": o["accuracy"], "accepted": o["accepted"]}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -541,6 +548,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy checks")
     ap.add_argument("--no-sweeps", action="store_true", help="skip the hyperparameter sweeps")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch configuration")
     ap.add_argument("--n", type=int, default=N, help="points (profiling captures only)")
     ap.add_argument("--precision", type=int, default=-1,
                     help="-1: both forms (default), 0: FP64 only, 1: mixed only")

@@ -255,6 +255,31 @@ hodlr_status hodlr_phase_ms(hodlr_ctx* ctx, float* out6);
  * context launched, out[1] host synchronisations it performed. */
 hodlr_status hodlr_counters(hodlr_ctx* ctx, int64_t* out2);
 
+/* Launch configuration of a context (not in the paper; nothing here changes what is
+ * computed, only how the work maps onto the GPU).
+ *   leaf_threads  CTA size of this context's leaf kernel: FP64 form 256, 512 or 1024;
+ *                 mixed form 512 (two leaves per SM) or 1024 (one).
+ *   sweep_mode    0: one launch per level when every level's reductions fit a block and
+ *                 no rank exceeds 64, else the segmented sweep; 1: always segmented. */
+typedef struct {
+  int leaf_threads;
+  int sweep_mode;
+} hodlr_tuning;
+
+/* Read or set the launch configuration. Errors: EINVAL (a value outside the lists). */
+hodlr_status hodlr_get_tuning(hodlr_ctx* ctx, hodlr_tuning* out);
+hodlr_status hodlr_set_tuning(hodlr_ctx* ctx, const hodlr_tuning* t);
+
+/* Autotuner: time every candidate configuration (leaf CTA sizes x sweep modes) on this
+ * context's own problem (one fused factorization with the right-hand side y, n doubles,
+ * host or device), each reps times after one untimed run, with CUDA events on
+ * opts.stream; keep the fastest (lowest median) and write it to *best (may be NULL) and
+ * its median milliseconds to *best_ms (may be NULL). The context must be compressed; it
+ * is left compressed and unfactored. Results do not depend on the configuration beyond
+ * the order of a few fixed-order sums (last bits). Errors: EINVAL, ESTATE, ENOTSPD, ECUDA. */
+hodlr_status hodlr_autotune(hodlr_ctx* ctx, const double* y, int reps, hodlr_tuning* best,
+                            float* best_ms);
+
 /* Iterative refinement of the last solve (opts.refine_maxit > 0; not in the paper): the
  * corrections it took over all right-hand sides, and the largest final relative residual
  * ||y - C~ x|| / ||y|| it measured (0 when refinement is off or ran without host checks).

@@ -1004,6 +1004,95 @@ hodlr_status hodlr_matvec(hodlr_ctx* ctx, const double* x, double* y) {
   return write_out(c, y, 1, c->n);
 }
 
+static bool valid_tuning(const Ctx* c, const hodlr_tuning* t) {
+  if (!t || (t->sweep_mode != 0 && t->sweep_mode != 1)) return false;
+  if (c->precision == 1) return t->leaf_threads == 512 || t->leaf_threads == 1024;
+  return t->leaf_threads == 256 || t->leaf_threads == 512 || t->leaf_threads == 1024;
+}
+
+hodlr_status hodlr_get_tuning(hodlr_ctx* ctx, hodlr_tuning* out) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !out) return HODLR_EINVAL;
+  out->leaf_threads = c->precision == 1 ? c->leaf_threads : c->leaf_threads64;
+  out->sweep_mode = c->no_fused ? 1 : 0;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_set_tuning(hodlr_ctx* ctx, const hodlr_tuning* t) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  if (!valid_tuning(c, t)) return fail(c, HODLR_EINVAL, "set_tuning: leaf_threads or sweep_mode");
+  if (c->precision == 1) c->leaf_threads = t->leaf_threads;
+  else c->leaf_threads64 = t->leaf_threads;
+  c->no_fused = t->sweep_mode == 1;
+  c->graph_valid = false;  // captured graphs hold the old launch shapes
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_autotune(hodlr_ctx* ctx, const double* y, int reps, hodlr_tuning* best,
+                            float* best_ms) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !y || reps < 1 || reps > 100) return HODLR_EINVAL;
+  if (!c->compressed) return fail(c, HODLR_ESTATE, "autotune: compress (build or rebuild) first");
+  if (capturing(c)) return fail(c, HODLR_ESTATE, "autotune: not under stream capture");
+  const double* yd;
+  int64_t ldd;
+  hodlr_status s = stage_in(c, y, 1, c->n, &yd, &ldd);
+  if (s != HODLR_OK) return s;
+  std::vector<int> threads = c->precision == 1 ? std::vector<int>{512, 1024}
+                                               : std::vector<int>{256, 512, 1024};
+  hodlr_tuning saved;
+  hodlr_get_tuning(ctx, &saved);
+  hodlr_tuning win = saved;
+  float win_ms = -1.0f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return fail(c, HODLR_ECUDA, "autotune: events");
+  }
+  for (int mode = 0; mode < 2 && s == HODLR_OK; ++mode)
+    for (int th : threads) {
+      hodlr_tuning t{th, mode};
+      hodlr_set_tuning(ctx, &t);
+      std::vector<float> ms;
+      for (int r = 0; r <= reps && s == HODLR_OK; ++r) {
+        cudaError_t e = gather_rhs(c, yd, ldd, 1);
+        if (e != cudaSuccess) {
+          s = fail(c, HODLR_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+          break;
+        }
+        c->factored = false;
+        cudaEventRecord(e0, c->stream);
+        s = factor_impl(c, 1);
+        cudaEventRecord(e1, c->stream);
+        if (s == HODLR_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+          float v = 0.0f;
+          cudaEventElapsedTime(&v, e0, e1);
+          if (r > 0) ms.push_back(v);  // the first run is untimed (attributes, caches)
+        }
+      }
+      if (s != HODLR_OK) break;
+      std::sort(ms.begin(), ms.end());
+      float med = ms.empty() ? 0.0f : ms[ms.size() / 2];
+      if (win_ms < 0.0f || med < win_ms) {
+        win_ms = med;
+        win = t;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->factored = false;
+  if (s != HODLR_OK) {
+    hodlr_set_tuning(ctx, &saved);
+    return s;
+  }
+  hodlr_set_tuning(ctx, &win);
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
+  return HODLR_OK;
+}
+
 hodlr_status hodlr_refine_info(hodlr_ctx* ctx, int32_t* corrections, double* residual) {
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!c) return HODLR_EINVAL;

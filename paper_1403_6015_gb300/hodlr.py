@@ -27,6 +27,10 @@ class hodlr_batch_lane(ctypes.Structure):
                 ("first", ctypes.c_int64), ("stride", ctypes.c_int64), ("count", ctypes.c_int64)]
 
 
+class hodlr_tuning(ctypes.Structure):
+    _fields_ = [("leaf_threads", ctypes.c_int), ("sweep_mode", ctypes.c_int)]
+
+
 class hodlr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rank_mode", ctypes.c_int),
                 ("max_rank", ctypes.c_int), ("max_nrhs", ctypes.c_int),
@@ -64,6 +68,10 @@ def load():
     L.hodlr_phase_ms.argtypes = [_vp, _dp]
     L.hodlr_counters.argtypes = [_vp, _dp]
     L.hodlr_refine_info.argtypes = [_vp, _dp, _dp]
+    L.hodlr_get_tuning.argtypes = [_vp, ctypes.POINTER(hodlr_tuning)]
+    L.hodlr_set_tuning.argtypes = [_vp, ctypes.POINTER(hodlr_tuning)]
+    L.hodlr_autotune.argtypes = [_vp, _dp, ctypes.c_int, ctypes.POINTER(hodlr_tuning),
+                                 ctypes.POINTER(ctypes.c_float)]
     L.hodlr_presize.argtypes = [_vp, _dp, ctypes.c_int]
     L.hodlr_status_flags.argtypes = [_vp, _dp]
     L.hodlr_loglik_sweep.argtypes = [_vp, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp]
@@ -94,7 +102,8 @@ def load():
                  "hodlr_loglik_sweep", "hodlr_mlp_create", "hodlr_mlp_params",
                  "hodlr_mlp_forward", "hodlr_mlp_gradient", "hodlr_mlp_train", "hodlr_mlp_save",
                  "hodlr_mlp_load", "hodlr_block_features", "hodlr_predict_ranks",
-                 "hodlr_loglik_batched", "hodlr_refine_info"):
+                 "hodlr_loglik_batched", "hodlr_refine_info", "hodlr_get_tuning",
+                 "hodlr_set_tuning", "hodlr_autotune"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -186,6 +195,20 @@ def hodlr_phase_ms(ctx, buf):
 
 def hodlr_counters(ctx, buf):
     return load().hodlr_counters(ctx, _addr(buf))
+
+
+def hodlr_get_tuning(ctx, out: hodlr_tuning):
+    return load().hodlr_get_tuning(ctx, ctypes.byref(out))
+
+
+def hodlr_set_tuning(ctx, t: hodlr_tuning):
+    return load().hodlr_set_tuning(ctx, ctypes.byref(t))
+
+
+def hodlr_autotune(ctx, y_addr, reps, best: hodlr_tuning, best_ms):
+    """best_ms: a ctypes.c_float (or None)."""
+    return load().hodlr_autotune(ctx, y_addr, reps, ctypes.byref(best),
+                                 ctypes.byref(best_ms) if best_ms is not None else None)
 
 
 def hodlr_refine_info(ctx, corrections, residual):
@@ -337,6 +360,7 @@ class Hodlr:
         if stream is not None:
             o.stream = stream
         self.kernel = kernel
+        self.precision = precision
         st, ctx = hodlr_build(xin, self.n, self.d, KERNELS[kernel], theta, sigma2, leaf, eps, o)
         self.status = st
         if not ctx:
@@ -495,6 +519,47 @@ class Hodlr:
         buf = np.zeros(2, dtype=np.int64)
         self._check(hodlr_counters(self._ctx, buf), "counters")
         return {"launches": int(buf[0]), "syncs": int(buf[1])}
+
+    def tuning(self) -> dict:
+        t = hodlr_tuning()
+        self._check(hodlr_get_tuning(self._ctx, t), "get_tuning")
+        return {"leaf_threads": t.leaf_threads, "sweep_mode": t.sweep_mode}
+
+    def set_tuning(self, leaf_threads: int, sweep_mode: int = 0):
+        t = hodlr_tuning(leaf_threads, sweep_mode)
+        self._check(hodlr_set_tuning(self._ctx, t), "set_tuning")
+
+    def autotune(self, y, reps: int = 3, cache: str | None = None) -> dict:
+        """Time the launch configurations on this problem and keep the fastest. With a
+        cache file (JSON), a configuration stored for the same GPU and problem shape is
+        applied without timing, and new results are added to it."""
+        import json
+        key = None
+        if cache is not None:
+            import torch
+            kappa = self.tree()[0]
+            r = self.ranks()
+            lv = [int(r[(1 << j) - 1:(1 << (j + 1)) - 1].max()) for j in range(kappa)] if r.size else []
+            key = "|".join(str(v) for v in (torch.cuda.get_device_name(), self.n, self.d, self.kernel,
+                                            self.precision, kappa, tuple(lv)))
+            try:
+                with open(cache) as f:
+                    table = json.load(f)
+            except (OSError, ValueError):
+                table = {}
+            if key in table:
+                self.set_tuning(table[key]["leaf_threads"], table[key]["sweep_mode"])
+                return dict(table[key], cached=True)
+        yy = y.contiguous() if _is_torch(y) else _f64_host(y).reshape(-1)
+        best = hodlr_tuning()
+        ms = ctypes.c_float()
+        self._check(hodlr_autotune(self._ctx, _addr(yy), reps, best, ms), "autotune")
+        res = {"leaf_threads": best.leaf_threads, "sweep_mode": best.sweep_mode, "ms": ms.value}
+        if key is not None:
+            table[key] = res
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+        return dict(res, cached=False)
 
     def refine_info(self):
         """(corrections, final relative residual) of the last solve's refinement."""

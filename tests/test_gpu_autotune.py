@@ -1,0 +1,65 @@
+"""Autotuner and launch configurations: every configuration computes the same result (up to
+the last bits of fixed-order sums), the autotuner picks one of them and can cache it."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_1403_6015_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_1403_6015_gb300 import build_lib, hodlr
+    build_lib.build()
+    hodlr.load()
+    return hodlr
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_configurations_agree_and_autotune_picks_one(H, precision):
+    n = 1 << 16
+    x, y = I.workload_1d(n, 1040)
+    h = H.Hodlr(x, "matern32", [0.1, 1.0], 1e-2, 128, 1e-12, precision=precision)
+    ref = h.loglik(y)
+    threads = [512, 1024] if precision == 1 else [256, 512, 1024]
+    for th in threads:
+        for mode in (0, 1):
+            h.set_tuning(th, mode)
+            assert h.tuning() == {"leaf_threads": th, "sweep_mode": mode}
+            h.rebuild([0.1, 1.0], 1e-2)
+            v = h.loglik(y)
+            assert abs(v - ref) <= 1e-13 * abs(ref), (th, mode, v, ref)
+    h.rebuild([0.1, 1.0], 1e-2)
+    best = h.autotune(y, reps=2)
+    assert best["leaf_threads"] in threads and best["sweep_mode"] in (0, 1) and best["ms"] > 0
+    assert h.tuning() == {"leaf_threads": best["leaf_threads"], "sweep_mode": best["sweep_mode"]}
+    v = h.loglik(y)  # the context is compressed and unfactored after the autotuner
+    assert abs(v - ref) <= 1e-13 * abs(ref)
+
+
+def test_tuning_rejects_bad_values(H):
+    x, y = I.workload_1d(4096, 1041)
+    h = H.Hodlr(x, "exp", [0.2, 1.0], 1e-2, 64, 1e-12, precision=1)
+    for th, mode in [(256, 0), (768, 0), (512, 2)]:  # 256 is FP64-only
+        with pytest.raises(H.HodlrError):
+            h.set_tuning(th, mode)
+    with pytest.raises(H.HodlrError):
+        h.autotune(y, reps=0)
+
+
+def test_autotune_cache(H, tmp_path):
+    n = 1 << 15
+    x, y = I.workload_1d(n, 1042)
+    cache = str(tmp_path / "tuning.json")
+    h1 = H.Hodlr(x, "matern52", [0.2, 1.0], 1e-2, 128, 1e-12, precision=1)
+    r1 = h1.autotune(y, reps=1, cache=cache)
+    assert r1["cached"] is False
+    table = json.load(open(cache))
+    assert len(table) == 1
+    h2 = H.Hodlr(x, "matern52", [0.2, 1.0], 1e-2, 128, 1e-12, precision=1)
+    r2 = h2.autotune(y, reps=1, cache=cache)
+    assert r2["cached"] is True
+    assert h2.tuning() == {"leaf_threads": r1["leaf_threads"], "sweep_mode": r1["sweep_mode"]}
