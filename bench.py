@@ -320,9 +320,9 @@ def sweep_settings(nset, seed):
 def run_sweeps(args):
     """Batched evaluation (outside the headline's timed region): 256 Matern-5/2 settings on
     n = 65536 points, graph-replayed on one context and forked over 8 lanes, against the
-    adaptive per-setting loop; 64 independent problems of uneven size, one lane each; and
-    the learned rank predictor's gain on a squared-exponential sweep whose ranks vary with
-    ell."""
+    adaptive per-setting loop; 64 independent problems of uneven size, one lane each; the
+    learned rank predictor's gain on a squared-exponential sweep whose ranks vary with ell;
+    and the predictor at scale on 2-D n = 2^20 points."""
     import torch
 
     from paper_1403_6015_gb300 import hodlr as H
@@ -480,13 +480,78 @@ def run_sweeps(args):
     ref, ta = timed(adaptive_se)
     RM.sweep_with_predictor(h, net, ell, s2, yd, margin=1)  # captures the groups' graphs
     (got, st), tp = timed(lambda: RM.sweep_with_predictor(h, net, ell, s2, yd, margin=1))
+    # the same presizes on 8 lanes (batched rounds over the settings of each group)
+    origin = torch.cuda.Stream()
+    lane_streams = [torch.cuda.Stream() for _ in range(8)]
+    lanes = [H.Hodlr(x, "se", [ell[0], 1.0], s2[0], 128, 1e-10, stream=ls.cuda_stream)
+             for ls in lane_streams]
+    RM.sweep_with_predictor(h, net, ell, s2, yd, margin=1, lanes=lanes, stream=origin.cuda_stream)
+    (gotl, stl), tl = timed(lambda: RM.sweep_with_predictor(h, net, ell, s2, yd, margin=1, lanes=lanes,
+                                                            stream=origin.cuda_stream))
+    for c in lanes:
+        c.close()
     out["predictor_se"] = {
         "n": n, "settings": nset, "kernel": "se", "eps": 1e-10,
         "adaptive_evals_per_s": nset / ta, "predicted_evals_per_s": nset / tp, "gain": ta / tp,
+        "predicted_lanes": 8, "predicted_lanes_evals_per_s": nset / tl, "lanes_gain": ta / tl,
+        "lanes_fallbacks": stl["fallbacks"],
+        "lanes_max_rel_diff": float(np.max(np.abs(gotl - ref) / np.abs(ref))),
         "groups": st["groups"], "fallbacks": st["fallbacks"],
         "max_rel_diff": float(np.max(np.abs(got - ref) / np.abs(ref))),
         "train": {"pairs": int(X.shape[0]), "final_mse": loss, "seconds": t_train,
                   "steps": 1500}}
+    h.close()
+    net.close()
+
+    # (3) the predictor at scale: 2-D n = 2^20 U[0,1]^2, squared-exponential ell = 0.1,
+    # eps = 1e-10 (top-level ranks ~225), mixed form; adaptive against predictor-presized
+    # at equal accuracy. The network is retrained with 2-D problems up to n = 2^16.
+    t0 = time.perf_counter()
+    probs = []
+    for i, nn in enumerate([1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16]):
+        lo = 0.04 if nn <= (1 << 14) else 0.06
+        x2s, _ = I.workload_2d(nn, 950 + i)
+        x1s, _ = I.workload_1d(nn, 900 + i)
+        for e in np.exp(np.linspace(np.log(lo), np.log(1.0), 11)):
+            for eps in [1e-8, 1e-10]:
+                probs.append((x2s, "se", float(e), 0.01, 128, eps))
+                if nn <= (1 << 14):
+                    probs.append((x1s, "se", float(e), 0.01, 128, eps))
+    X, T, R = RM.collect_pairs(probs, max_rank=512)
+    net = RM.RankMLP(seed=7)
+    loss = net.train(X, T, steps=3000, lr=3e-3)
+    t_train = time.perf_counter() - t0
+    n2 = 1 << 20
+    x2, y2 = I.workload_2d(n2, 1400)
+    x2d = torch.from_numpy(x2).cuda()
+    y2d = torch.from_numpy(np.ascontiguousarray(y2).reshape(-1)).cuda()
+    h = H.Hodlr(x2d, "se", [0.1, 1.0], 1e-2, 128, 1e-10, max_rank=320, precision=1)
+    k2 = h.tree()[0]
+    r2 = h.ranks()
+    lv = [int(r2[(1 << j) - 1:(1 << (j + 1)) - 1].max()) for j in range(k2)]
+
+    def one_eval():
+        h.rebuild([0.1, 1.0], 1e-2)
+        return h.loglik(y2d)
+    one_eval()
+    ll_a, ta = timed(one_eval)
+    pre = RM.presize_profile(h, net, 0.1, margin=1, scale=1.08)
+    h.presize(pre)
+    one_eval()
+    ll_p, tp = timed(one_eval)
+    flags = h.status_flags()
+    if flags:  # the fallback: the adaptive path
+        h.presize(None)
+        ll_p, tf = timed(one_eval)
+        tp += tf
+    out["predictor_2d"] = {
+        "n": n2, "d": 2, "kernel": "se", "ell": 0.1, "sigma2": 1e-2, "eps": 1e-10, "form": "mixed",
+        "adaptive_level_ranks": lv, "presized_level_ranks": [int(v) for v in pre],
+        "adaptive_s_per_eval": ta, "predicted_s_per_eval": tp, "gain": ta / tp,
+        "fallback": bool(flags), "rel_diff": abs(ll_p - ll_a) / abs(ll_a),
+        "train": {"pairs": int(X.shape[0]), "final_mse": loss, "seconds": t_train, "steps": 3000},
+        "ell_0.02": "not run: top-level ranks above 850 at n = 65536 and growing with n, "
+                    "beyond the 512 cap"}
     h.close()
     net.close()
     return out

@@ -361,6 +361,7 @@ class Hodlr:
             o.stream = stream
         self.kernel = kernel
         self.precision = precision
+        self.max_rank = max_rank
         st, ctx = hodlr_build(xin, self.n, self.d, KERNELS[kernel], theta, sigma2, leaf, eps, o)
         self.status = st
         if not ctx:

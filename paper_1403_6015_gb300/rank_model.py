@@ -93,30 +93,49 @@ def collect_pairs(problems, max_rank: int = 64):
     return torch.cat(Xs), torch.cat(Ts), np.concatenate(R)
 
 
-def sweep_with_predictor(h, net, ells, sigma2s, y, margin: int = 1, max_groups: int = 4):
+def presize_profile(h, net, ell: float, margin: int = 1, scale: float = 1.0):
+    """Per-level presize from the network: ceil(scale x predicted rank) + margin, capped at
+    the context's max_rank - 1 (the regression is on log(1 + r), so its errors are
+    relative: scale > 1 covers them at high ranks, margin at low ones)."""
+    p0 = h.predict_level_ranks(net, float(ell), 0).astype(np.float64)
+    pre = np.ceil(p0 * scale).astype(np.int32) + margin
+    return np.minimum(pre, h.max_rank - 1).astype(np.int32)
+
+
+def sweep_with_predictor(h, net, ells, sigma2s, y, margin: int = 1, max_groups: int = 4,
+                         scale: float = 1.0, lanes=None, stream=None):
     """Log-likelihoods of the settings (ells[b], sigma2s[b]) on the context h, presized by
-    the network's predicted per-level ranks (+ margin), with the adaptive path as the
+    the network's predicted per-level ranks (presize_profile), with the adaptive path as the
     fallback for every setting whose evaluation flagged a rank above its presize.
 
     Settings are sorted by predicted total rank and cut into at most max_groups chunks of
-    equal count; a chunk is presized to the elementwise maximum of its members' profiles
-    and evaluated as one captured graph replayed per setting. y: CUDA tensor.
-    Returns (loglik array, stats)."""
+    equal count; a chunk is presized to the elementwise maximum of its members' profiles.
+    Without lanes, a chunk is one captured graph on h replayed per setting; with lanes (a
+    list of contexts of the same points, each on its own stream, not stream), every lane is
+    presized to the chunk's profile and the chunk runs as batched rounds
+    (hodlr_loglik_batched). y: CUDA tensor. Returns (loglik array, stats)."""
     import torch
     ells = np.asarray(ells, dtype=np.float64)
     sigma2s = np.asarray(sigma2s, dtype=np.float64)
-    profs = np.array([h.predict_level_ranks(net, float(e), margin) for e in ells], dtype=np.int32)
+    profs = np.array([presize_profile(h, net, e, margin, scale) for e in ells], dtype=np.int32)
     order = np.argsort(profs.sum(axis=1), kind="stable")
     chunks = [c for c in np.array_split(order, min(max_groups, len(ells))) if len(c)]
     out = np.zeros(len(ells))
     fallback = []
     for idx in chunks:
-        prof = profs[idx].max(axis=0)
-        h.presize(prof.astype(np.int32))
+        prof = profs[idx].max(axis=0).astype(np.int32)
         theta = torch.from_numpy(np.stack([ells[idx], np.ones(len(idx))], 1).copy()).cuda()
         sig = torch.from_numpy(sigma2s[idx].copy()).cuda()
         status = torch.zeros(len(idx), dtype=torch.int32, device="cuda")
-        res = h.loglik_sweep(theta, sig, y, status=status)
+        if lanes:
+            for c in lanes:
+                c.presize(prof)
+            res = torch.zeros(len(idx), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            H.loglik_batched(lanes, theta, sig, y, res, status, stream=stream)
+        else:
+            h.presize(prof)
+            res = h.loglik_sweep(theta, sig, y, status=status)
         torch.cuda.synchronize()
         out[idx] = res.cpu().numpy()
         bad = idx[status.cpu().numpy() != 0]

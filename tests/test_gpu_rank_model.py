@@ -126,3 +126,29 @@ def test_undersized_prediction_is_flagged(H):
     h.rebuild([0.05, 1.0], 0.01)
     h.loglik(y)
     assert h.status_flags() & 2
+
+
+def test_sweep_with_predictor_on_lanes(H, RM, trained):
+    """Predictor presizes, settings grouped, each group run as batched rounds over three
+    lanes: every setting equals its adaptive evaluation (fallbacks included)."""
+    import torch
+    net = trained[0]
+    n = 1 << 14
+    x, y = I.workload_1d(n, 953)
+    u = I.uniform01(97, 24)
+    ell = np.exp(np.log(0.05) + u[:12] * (np.log(1.0) - np.log(0.05)))
+    s2 = np.exp(np.log(1e-3) + u[12:] * (np.log(1.0) - np.log(1e-3)))
+    yd = torch.from_numpy(y).cuda()
+    stream = torch.cuda.Stream()
+    h = H.Hodlr(x, "se", [ell[0], 1.0], s2[0], 64, 1e-10, stream=stream.cuda_stream)
+    origin = torch.cuda.Stream()
+    lane_streams = [torch.cuda.Stream() for _ in range(3)]
+    lanes = [H.Hodlr(x, "se", [ell[0], 1.0], s2[0], 64, 1e-10, stream=s.cuda_stream)
+             for s in lane_streams]
+    torch.cuda.synchronize()
+    got, st = RM.sweep_with_predictor(h, net, ell, s2, yd, margin=1, lanes=lanes,
+                                      stream=origin.cuda_stream)
+    assert st["groups"] <= 4
+    for b in range(len(ell)):
+        r = H.Hodlr(x, "se", [ell[b], 1.0], s2[b], 64, 1e-10).loglik(y)
+        assert abs(got[b] - r) <= 1e-12 * abs(r), (b, got[b], r)
