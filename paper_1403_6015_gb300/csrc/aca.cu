@@ -45,6 +45,8 @@ struct AcaArgs {
   int part_stride;
   int max_rank;
   const ff* tab;       // 2^(j/64) as double-floats (mixed form)
+  const ff* xrel;      // mixed form: per level, coordinates relative to each node's split
+                       // point (kappa x d x n double-floats)
   int32_t* active;
   int nint;
   int pre[32];         // presized rank of each level (0: adaptive)
@@ -60,10 +62,24 @@ __device__ __forceinline__ double block_entry(const AcaArgs& a, const Cov& cov, 
   return ff_to_double(cov_ff(a.kind, ff_from_double(r), cr, amp, tab));
 }
 
-// The same entry as a double-float (mixed form).
-__device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int i, int j, const ff* tab, ff cr,
-                                            ff amp) {
-  return cov_ff(a.kind, ff_from_double(dist(a.pts, i, j)), cr, amp, tab);
+// The same entry as a double-float (mixed form), for i in the left and j in the right
+// child of a level-lev node. The distance comes from the coordinates relative to the
+// node's split point (the first point of its right child): in 1-D the left child's are
+// <= 0 and the right child's >= 0, so r = x_j - x_i is a same-sign double-float sum whose
+// error is relative to r itself, also for the closest pairs across the split; no FP64.
+__device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int lev, int i, int j,
+                                            const ff* tab, ff cr, ff amp) {
+  const int64_t n = a.pts.n;
+  const ff* xr = a.xrel + (int64_t)lev * a.pts.d * n;
+  ff r;
+  if (a.pts.d == 1) {
+    r = ff_sub(xr[j], xr[i]);
+    if (r.hi < 0.0f) r = ff_neg(r);
+  } else {
+    ff u = ff_sub(xr[j], xr[i]), v = ff_sub(xr[n + j], xr[n + i]);
+    r = ff_sqrt(ff_add(ff_mul(u, u), ff_mul(v, v)));
+  }
+  return cov_ff(a.kind, r, cr, amp, tab);
 }
 
 __device__ __forceinline__ int level_of(int id) { return 31 - __clz(id + 1); }
@@ -194,7 +210,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
     for (int q = 0; q < kPer; ++q) {
       int b = start + q * kAcaThreads + threadIdx.x;
       if (b < mr) {
-        ff v = block_entry_ff(a, bl + i, br + b, tab, cr, amp);
+        ff v = block_entry_ff(a, level_of(id), bl + i, br + b, tab, cr, amp);
         for (int l = 0; l < k; ++l) v = ff_fms(v, uik[l], rawf[l * n + br + b]);
         rawf[(int64_t)k * n + br + b] = v;
         amax_merge_f(bv, bi, v.hi, b);
@@ -366,7 +382,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
       uu[q] = 0.0f;
       vv[q] = 0.0f;
       if (t < ml) {
-        ff u = block_entry_ff(a, bl + t, br + j, tab, cr, amp);
+        ff u = block_entry_ff(a, level_of(id), bl + t, br + j, tab, cr, amp);
         for (int l = 0; l < k; ++l) u = ff_fms(u, rawf[l * n + bl + t], vjk[l]);
         rawf[(int64_t)k * n + bl + t] = u;
         uu[q] = u.hi;
@@ -564,6 +580,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   a.part_stride = 4 + 2 * c.max_rank;
   a.max_rank = c.max_rank;
   a.tab = reinterpret_cast<const ff*>(c.exp_tab);
+  a.xrel = reinterpret_cast<const ff*>(c.xrel);
   a.active = c.active;
   a.nint = nint;
   k_aca_init<<<(nint + 255) / 256, 256, 0, c.stream>>>(a);
@@ -609,7 +626,31 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
 
 namespace {
 __global__ void k_exp_table(ff* tab) { ff_exp_table(tab, threadIdx.x, blockDim.x); }
+
+// xrel[(j d + c) n + i] = x_c(i) - x_c(s), s the first point of the right child of i's
+// level-j node, as a double-float (the one FP64 subtraction per point and level).
+__global__ void k_xrel(const double* __restrict__ xs, int64_t n, int d, const int32_t* nb,
+                       ff* __restrict__ xrel) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int j = blockIdx.y;
+  if (i >= n) return;
+  int id = 0;
+  for (int l = 0; l < j; ++l) id = i < nb[2 * id + 2] ? 2 * id + 1 : 2 * id + 2;
+  int64_t s = nb[2 * id + 2];
+  for (int c = 0; c < d; ++c)
+    xrel[((int64_t)j * d + c) * n + i] = ff_from_double(xs[c * n + i] - xs[c * n + s]);
+}
 }  // namespace
+
+// Relative coordinates for the mixed form's ACA (once per context: they do not depend on
+// the hyperparameters).
+cudaError_t launch_xrel(Ctx& c) {
+  if (c.kappa == 0) return cudaSuccess;
+  dim3 g((unsigned)((c.n + 255) / 256), (unsigned)c.kappa);
+  k_xrel<<<g, 256, 0, c.stream>>>(c.xs, c.n, c.d, c.nodes, reinterpret_cast<ff*>(c.xrel));
+  ++c.launches;
+  return cudaGetLastError();
+}
 
 // 2^(j/64), j < 64, as double-floats for the double-float exp (once per context).
 cudaError_t launch_exp_table(Ctx& c) {

@@ -82,7 +82,7 @@ void free_all(Ctx* c) {
   dfree(c->st_zero); dfree(c->st_phase); dfree(c->st_nused); dfree(c->st_used);
   dfree(c->st_delta); dfree(c->st_s2); dfree(c->aca_part); dfree(c->active);
   dfree(c->Y); dfree(c->ysort); dfree(c->leafL); dfree(c->leaf_logdet); dfree(c->node_logdet);
-  dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->ry); dfree(c->rw); dfree(c->exp_tab); dfree(c->Mlu); dfree(c->Mpiv);
+  dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->ry); dfree(c->rw); dfree(c->exp_tab); dfree(c->xrel); dfree(c->Mlu); dfree(c->Mpiv);
   dfree(c->hyp);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
@@ -420,6 +420,10 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   }
   hodlr_status s = setup_aca(c);
   if (s != HODLR_OK) return bail(s);
+  if (c->precision == 1 && c->kappa > 0) {
+    if (dalloc(&c->xrel, (int64_t)c->kappa * d * n) != cudaSuccess) return bail(HODLR_ENOMEM);
+    if (hodlr::launch_xrel(*c) != cudaSuccess) return bail(HODLR_ECUDA);
+  }
   if (hodlr::launch_set_hyp(*c, c->ell, c->amp, c->sigma2) != cudaSuccess) return bail(HODLR_ECUDA);
   s = compress(c);
   if (s != HODLR_OK) return bail(s);

@@ -108,6 +108,14 @@ __device__ __forceinline__ ff ff_rcp(ff a) {
   return ff_make(x, corr);
 }
 
+// sqrt(q) for q >= 0: the float root h refined by one Newton step, h + (q - h^2) / (2h).
+__device__ __forceinline__ ff ff_sqrt(ff q) {
+  float h = sqrtf(q.hi);
+  if (!(h > 0.0f)) return ff{0.0f, 0.0f};
+  ff res = ff_sub(q, ff_mul(ff{h, 0.0f}, ff{h, 0.0f}));
+  return ff_make(h, res.hi / (2.0f * h));
+}
+
 // exp(x) for a double-float x <= ~0 (covariances use exp of minus a distance). Reduction
 // x = n ln2/64 + r, |r| <= ln2/128 (Cody-Waite: ln2/64 = L1 + L2 with L1 holding 11
 // significant bits so n L1 is exact for |n| < 2^13, L2 a double-float), then

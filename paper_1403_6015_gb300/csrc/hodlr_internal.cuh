@@ -169,6 +169,8 @@ struct Ctx {
   int32_t* dflags = nullptr;
   double* tmpvec = nullptr;       // n x max_nrhs staging for host/device copies
   double* exp_tab = nullptr;      // 64 double-float pairs, 2^(j/64) (mixed form)
+  double* xrel = nullptr;         // mixed form: kappa x d x n double-float pairs, each
+                                  // point's coordinates relative to its level-j split point
   // iterative refinement (refine.cu): sorted right-hand sides and work vectors
   double refine_tol = 1e-10;
   int refine_maxit = 0;
@@ -207,6 +209,7 @@ cudaError_t launch_sort_kd(Ctx& c, const double* x_dev_rowmajor);
 cudaError_t launch_aca(Ctx& c, int* steps_out);
 cudaError_t launch_pack(Ctx& c);
 cudaError_t launch_exp_table(Ctx& c);
+cudaError_t launch_xrel(Ctx& c);
 cudaError_t launch_gather_rhs(Ctx& c, const double* y, int64_t ld, int nrhs);
 cudaError_t launch_scatter_rhs(Ctx& c, double* x, int64_t ld, int nrhs);
 cudaError_t launch_leaf_factor(Ctx& c, int nrhs);

@@ -115,14 +115,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
           if (r.hi < 0.0f) r = ff_neg(r);
         } else {
           ff u = ff_sub(xl[i], xl[j]), v = ff_sub(xl[kMaxLeaf + i], xl[kMaxLeaf + j]);
-          ff q = ff_add(ff_mul(u, u), ff_mul(v, v));
-          float h = sqrtf(q.hi);
-          if (h > 0.0f) {
-            ff res = ff_sub(q, ff_mul(ff{h, 0.0f}, ff{h, 0.0f}));
-            r = ff_make(h, res.hi / (2.0f * h));
-          } else {
-            r = ff{0.0f, 0.0f};
-          }
+          r = ff_sqrt(ff_add(ff_mul(u, u), ff_mul(v, v)));
         }
         c = cov_ff(a.kind, r, cr, amp, tab);
         if (i == j) c = ff_add(c, s2);
