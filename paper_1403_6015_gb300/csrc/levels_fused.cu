@@ -218,6 +218,21 @@ __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
   // finish level l = u - 1: half-nodes of 2^sh' leaves with sh' = kappa - l - 1 = sh
   int hl = 1 << sh;            // leaves per level-l half-node
   int E = a.rl * wz;
+  // Where a half-node spans several blocks, each block first sums its own leaves'
+  // partials (fixed order) into its first leaf's slot, so the last block of the half sums
+  // one value per block instead of one per leaf.
+  const bool pre = hl >= 2 * kG;  // then this block's kG leaves lie inside one half-node
+  __syncthreads();
+  if (pre) {
+    double* p0 = a.part + (int64_t)leaf_base * a.part_stride;
+    for (int e = tid; e < E; e += kLT) {
+      double s = p0[e];
+      for (int t = 1; t < nl; ++t) s += p0[(int64_t)t * a.part_stride + e];
+      p0[e] = s;
+    }
+  }
+  const int step = pre ? kG : 1;   // leaf stride between the slots to sum
+  const int nsl = hl / step;       // slots per half-node
   __threadfence();
   __syncthreads();
   int h0 = leaf_base >> sh, h1 = (leaf_base + nl - 1) >> sh;
@@ -234,18 +249,19 @@ __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
     __threadfence();
     double* hs = const_cast<double*>(a.na.half) + (int64_t)h * a.na.stride;
     const double* pbase = a.part + (int64_t)h * hl * a.part_stride;
-    if (hl >= 32) {
-      // one warp per entry: lanes stride over the half's leaves, then a fixed xor tree
+    const int64_t sst = (int64_t)step * a.part_stride;
+    if (nsl >= 32) {
+      // one warp per entry: lanes stride over the half's slots, then a fixed xor tree
       for (int e = w; e < E; e += kLT / 32) {
         double s = 0.0;
-        for (int t = lane; t < hl; t += 32) s += __ldcg(pbase + (int64_t)t * a.part_stride + e);
+        for (int t = lane; t < nsl; t += 32) s += __ldcg(pbase + (int64_t)t * sst + e);
         s = wsum(s);
         if (lane == 0) hs[e] = s;
       }
     } else {
       for (int e = tid; e < E; e += kLT) {
         double s = 0.0;
-        for (int t = 0; t < hl; ++t) s += __ldcg(pbase + (int64_t)t * a.part_stride + e);
+        for (int t = 0; t < nsl; ++t) s += __ldcg(pbase + (int64_t)t * sst + e);
         hs[e] = s;
       }
     }
