@@ -37,6 +37,7 @@ struct AcaArgs {
   const int32_t* item_node;
   const int32_t* item_start;
   const int32_t* node_item0;
+  const int32_t* node_item1;
   double* raw;
   int64_t raw_off[32];
   int32_t *rank, *row, *col, *done, *ok, *zero, *phase, *nused, *used;
@@ -239,7 +240,7 @@ __global__ void k_aca_pivot_row(AcaArgs a) {
   int id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (id >= a.nint || a.done[id]) return;
-  int i0 = a.node_item0[id], i1 = a.node_item0[id + 1];
+  int i0 = a.node_item0[id], i1 = a.node_item1[id];
   double bv = 0.0;
   int bi = -1;
   for (int it = i0 + lane; it < i1; it += 32) {
@@ -445,6 +446,196 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   }
 }
 
+// A and C for small nodes (both children <= kSmallNode points, one work item each): one warp
+// per node, eight nodes per block, warp-level reductions only; the same per-item outputs
+// as the tiled kernels (argmax, |u|^2, |v|^2, u_l.u, v_l.v).
+constexpr int kSmallPer = kSmallNode / 32;  // elements per lane
+
+template <bool kFF>
+__global__ void __launch_bounds__(kAcaThreads) k_aca_row_small(AcaArgs a, int item0, int nitem) {
+  __shared__ ff tab[64];
+  if (kFF) {
+    for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
+    __syncthreads();
+  }
+  int lane = threadIdx.x & 31;
+  int item = item0 + blockIdx.x * (kAcaThreads / 32) + (threadIdx.x >> 5);
+  if (item >= item0 + nitem) return;
+  int id = a.item_node[item];
+  if (a.done[id]) return;
+  const Cov cov = cov_from(a.kind, a.hyp);
+  int k = a.rank[id], i = a.row[id];
+  int bl = a.nb[2 * id + 1], br = a.nb[2 * id + 2], mr = a.ns[2 * id + 2];
+  int64_t n = a.pts.n;
+  int lev = level_of(id);
+  double* raw = a.raw + a.raw_off[lev];
+  int bi = -1;
+  double fv = 0.0;
+  if (!kFF) {
+    double bv = 0.0;
+#pragma unroll
+    for (int q = 0; q < kSmallPer; ++q) {
+      int b = q * 32 + lane;
+      if (b < mr) {
+        double v = block_entry<false>(a, cov, bl + i, br + b, tab, ff{0, 0}, ff{0, 0});
+        for (int l = 0; l < k; ++l) v -= raw[l * n + bl + i] * raw[l * n + br + b];
+        raw[(int64_t)k * n + br + b] = v;
+        amax_merge(bv, bi, v, b);
+      }
+    }
+    warp_amax(bv, bi);
+    fv = bv;
+  } else {
+    const ff cr = ff_from_double(a.hyp[kHypScale]), amp = ff_from_double(cov.amp);
+    ff* rawf = reinterpret_cast<ff*>(raw);
+    float bv = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kSmallPer; ++q) {
+      int b = q * 32 + lane;
+      if (b < mr) {
+        ff v = block_entry_ff(a, lev, bl + i, br + b, tab, cr, amp);
+        for (int l = 0; l < k; ++l) v = ff_fms(v, rawf[l * n + bl + i], rawf[l * n + br + b]);
+        rawf[(int64_t)k * n + br + b] = v;
+        amax_merge_f(bv, bi, v.hi, b);
+      }
+    }
+    warp_amax_f(bv, bi);
+    if (bi >= 0) fv = ff_to_double(rawf[(int64_t)k * n + br + bi]);  // full pivot value
+  }
+  if (lane == 0) {
+    a.part[(int64_t)item * a.part_stride + 0] = fv;
+    a.part[(int64_t)item * a.part_stride + 1] = (double)bi;
+  }
+}
+
+template <bool kFF>
+__global__ void __launch_bounds__(kAcaThreads) k_aca_col_small(AcaArgs a, int item0, int nitem) {
+  __shared__ ff tab[64];
+  if (kFF) {
+    for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
+    __syncthreads();
+  }
+  int lane = threadIdx.x & 31;
+  int item = item0 + blockIdx.x * (kAcaThreads / 32) + (threadIdx.x >> 5);
+  if (item >= item0 + nitem) return;
+  int id = a.item_node[item];
+  if (a.done[id] || !a.phase[id]) return;
+  const Cov cov = cov_from(a.kind, a.hyp);
+  int k = a.rank[id], j = a.col[id];
+  double delta = a.delta[id];
+  int bl = a.nb[2 * id + 1], ml = a.ns[2 * id + 1];
+  int br = a.nb[2 * id + 2], mr = a.ns[2 * id + 2];
+  int nu = a.nused[id];
+  const int* used = a.used + (int64_t)id * a.used_stride;
+  int64_t n = a.pts.n;
+  int lev = level_of(id);
+  double* raw = a.raw + a.raw_off[lev];
+  double* out = a.part + (int64_t)item * a.part_stride;
+  int bi = -1;
+  if (!kFF) {
+    const double inv = 1.0 / delta;
+    double uu[kSmallPer], vv[kSmallPer];
+    double nu2 = 0.0, nv2 = 0.0, bv = 0.0;
+#pragma unroll
+    for (int q = 0; q < kSmallPer; ++q) {
+      int t = q * 32 + lane;
+      uu[q] = 0.0;
+      vv[q] = 0.0;
+      if (t < ml) {
+        double u = block_entry<false>(a, cov, bl + t, br + j, tab, ff{0, 0}, ff{0, 0});
+        for (int l = 0; l < k; ++l) u -= raw[l * n + bl + t] * raw[l * n + br + j];
+        raw[(int64_t)k * n + bl + t] = u;
+        uu[q] = u;
+        nu2 += u * u;
+        bool isu = false;
+        for (int s2 = 0; s2 < nu; ++s2) isu |= used[s2] == t;
+        if (!isu) amax_merge(bv, bi, u, t);
+      }
+      if (t < mr) {
+        double v = raw[(int64_t)k * n + br + t] * inv;
+        raw[(int64_t)k * n + br + t] = v;
+        vv[q] = v;
+        nv2 += v * v;
+      }
+    }
+    nu2 = warp_sum(nu2);
+    nv2 = warp_sum(nv2);
+    warp_amax(bv, bi);
+    for (int l = 0; l < k; ++l) {
+      double du = 0.0, dv = 0.0;
+#pragma unroll
+      for (int q = 0; q < kSmallPer; ++q) {
+        int t = q * 32 + lane;
+        if (t < ml) du += raw[l * n + bl + t] * uu[q];
+        if (t < mr) dv += raw[l * n + br + t] * vv[q];
+      }
+      du = warp_sum(du);
+      dv = warp_sum(dv);
+      if (lane == 0) {
+        out[4 + l] = du;
+        out[4 + a.max_rank + l] = dv;
+      }
+    }
+    if (lane == 0) {
+      out[0] = bv;
+      out[1] = (double)bi;
+      out[2] = nu2;
+      out[3] = nv2;
+    }
+  } else {
+    const ff cr = ff_from_double(a.hyp[kHypScale]), amp = ff_from_double(cov.amp);
+    ff* rawf = reinterpret_cast<ff*>(raw);
+    const ff inv = ff_rcp(ff_from_double(delta));
+    float uu[kSmallPer], vv[kSmallPer];
+    float nu2 = 0.0f, nv2 = 0.0f, bv = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kSmallPer; ++q) {
+      int t = q * 32 + lane;
+      uu[q] = 0.0f;
+      vv[q] = 0.0f;
+      if (t < ml) {
+        ff u = block_entry_ff(a, lev, bl + t, br + j, tab, cr, amp);
+        for (int l = 0; l < k; ++l) u = ff_fms(u, rawf[l * n + bl + t], rawf[l * n + br + j]);
+        rawf[(int64_t)k * n + bl + t] = u;
+        uu[q] = u.hi;
+        nu2 += u.hi * u.hi;
+        bool isu = false;
+        for (int s2 = 0; s2 < nu; ++s2) isu |= used[s2] == t;
+        if (!isu) amax_merge_f(bv, bi, u.hi, t);
+      }
+      if (t < mr) {
+        ff v = ff_mul(rawf[(int64_t)k * n + br + t], inv);
+        rawf[(int64_t)k * n + br + t] = v;
+        vv[q] = v.hi;
+        nv2 += v.hi * v.hi;
+      }
+    }
+    double nu2d = warp_sum((double)nu2), nv2d = warp_sum((double)nv2);
+    warp_amax_f(bv, bi);
+    for (int l = 0; l < k; ++l) {
+      float du = 0.0f, dv = 0.0f;
+#pragma unroll
+      for (int q = 0; q < kSmallPer; ++q) {
+        int t = q * 32 + lane;
+        if (t < ml) du += rawf[l * n + bl + t].hi * uu[q];
+        if (t < mr) dv += rawf[l * n + br + t].hi * vv[q];
+      }
+      du = warp_sum_f(du);
+      dv = warp_sum_f(dv);
+      if (lane == 0) {
+        out[4 + l] = du;
+        out[4 + a.max_rank + l] = dv;
+      }
+    }
+    if (lane == 0) {
+      out[0] = bv;
+      out[1] = (double)bi;
+      out[2] = nu2d;
+      out[3] = nv2d;
+    }
+  }
+}
+
 // D: one warp per node combines the tiles, updates the norm estimate and decides.
 __global__ void k_aca_pivot_col(AcaArgs a) {
   int id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -455,7 +646,7 @@ __global__ void k_aca_pivot_col(AcaArgs a) {
     return;
   }
   int k = a.rank[id];
-  int i0 = a.node_item0[id], i1 = a.node_item0[id + 1];
+  int i0 = a.node_item0[id], i1 = a.node_item1[id];
   double bv = 0.0, nu2 = 0.0, nv2 = 0.0;
   int bi = -1;
   for (int it = i0 + lane; it < i1; it += 32) {
@@ -571,6 +762,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   a.item_node = c.item_node;
   a.item_start = c.item_start;
   a.node_item0 = c.node_item0;
+  a.node_item1 = c.node_item1;
   a.raw = c.raw;
   for (int j = 0; j < 32; ++j) a.raw_off[j] = j < c.kappa ? c.h_raw_off[j] : 0;
   a.rank = c.st_rank; a.row = c.st_row; a.col = c.st_col; a.done = c.st_done; a.ok = c.st_ok;
@@ -586,6 +778,8 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   k_aca_init<<<(nint + 255) / 256, 256, 0, c.stream>>>(a);
   ++c.launches;
   int wblocks = (nint * 32 + 255) / 256;
+  const int64_t nbig = c.n_big_items, nsmall = c.n_items - c.n_big_items;
+  const unsigned sgrid = (unsigned)((nsmall + kAcaThreads / 32 - 1) / (kAcaThreads / 32));
   const size_t smem_row = sizeof(double) * c.max_rank;
   const size_t smem_col = sizeof(double) * (c.max_rank + (size_t)(2 + 2 * c.max_rank) * (kAcaThreads / 32)) +
                           sizeof(int) * (2 * c.max_rank + 2);
@@ -598,17 +792,37 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   int max_steps = c.presized ? maxpre + 2 : 2 * c.max_rank + 4;
   for (int s = 0; s < max_steps; ++s) {
     if (!c.presized) HODLR_CUDA_TRY(cudaMemsetAsync(c.active, 0, sizeof(int32_t), c.stream));
-    if (c.precision == 1)
-      k_aca_row<true><<<(unsigned)c.n_items, kAcaThreads, smem_row, c.stream>>>(a);
-    else
-      k_aca_row<false><<<(unsigned)c.n_items, kAcaThreads, smem_row, c.stream>>>(a);
+    if (nbig > 0) {
+      if (c.precision == 1)
+        k_aca_row<true><<<(unsigned)nbig, kAcaThreads, smem_row, c.stream>>>(a);
+      else
+        k_aca_row<false><<<(unsigned)nbig, kAcaThreads, smem_row, c.stream>>>(a);
+      ++c.launches;
+    }
+    if (nsmall > 0) {
+      if (c.precision == 1)
+        k_aca_row_small<true><<<sgrid, kAcaThreads, 0, c.stream>>>(a, (int)nbig, (int)nsmall);
+      else
+        k_aca_row_small<false><<<sgrid, kAcaThreads, 0, c.stream>>>(a, (int)nbig, (int)nsmall);
+      ++c.launches;
+    }
     k_aca_pivot_row<<<wblocks, 256, 0, c.stream>>>(a);
-    if (c.precision == 1)
-      k_aca_col<true><<<(unsigned)c.n_items, kAcaThreads, smem_col, c.stream>>>(a);
-    else
-      k_aca_col<false><<<(unsigned)c.n_items, kAcaThreads, smem_col, c.stream>>>(a);
+    if (nbig > 0) {
+      if (c.precision == 1)
+        k_aca_col<true><<<(unsigned)nbig, kAcaThreads, smem_col, c.stream>>>(a);
+      else
+        k_aca_col<false><<<(unsigned)nbig, kAcaThreads, smem_col, c.stream>>>(a);
+      ++c.launches;
+    }
+    if (nsmall > 0) {
+      if (c.precision == 1)
+        k_aca_col_small<true><<<sgrid, kAcaThreads, 0, c.stream>>>(a, (int)nbig, (int)nsmall);
+      else
+        k_aca_col_small<false><<<sgrid, kAcaThreads, 0, c.stream>>>(a, (int)nbig, (int)nsmall);
+      ++c.launches;
+    }
     k_aca_pivot_col<<<wblocks, 256, 0, c.stream>>>(a);
-    c.launches += 4;
+    c.launches += 2;
     HODLR_CUDA_TRY(cudaGetLastError());
     *steps_out = s + 1;
     if (c.presized) continue;

@@ -77,7 +77,7 @@ void free_factor_buffers(Ctx* c) {
 void free_all(Ctx* c) {
   free_factor_buffers(c);
   dfree(c->nodes); dfree(c->xs); dfree(c->perm);
-  dfree(c->item_node); dfree(c->item_start); dfree(c->node_item0); dfree(c->raw);
+  dfree(c->item_node); dfree(c->item_start); dfree(c->node_item0); dfree(c->node_item1); dfree(c->raw);
   dfree(c->st_rank); dfree(c->st_row); dfree(c->st_col); dfree(c->st_done); dfree(c->st_ok);
   dfree(c->st_zero); dfree(c->st_phase); dfree(c->st_nused); dfree(c->st_used);
   dfree(c->st_delta); dfree(c->st_s2); dfree(c->aca_part); dfree(c->active);
@@ -123,16 +123,26 @@ hodlr_status setup_aca(Ctx* c) {
   if (nint == 0) return HODLR_OK;
   const int32_t* nb = c->h_nodes.data();
   const int32_t* ns = nb + ((int64_t)2 << K);
-  std::vector<int32_t> inode, istart, i0(nint + 1);
-  for (int id = 0; id < nint; ++id) {
-    i0[id] = (int32_t)inode.size();
-    int32_t m = std::max(ns[2 * id + 1], ns[2 * id + 2]);
-    for (int32_t s = 0; s < m; s += hodlr::kAcaTile) {
-      inode.push_back(id);
-      istart.push_back(s);
+  // work items: first the 1024-column tiles of the nodes with a child above kSmallNode
+  // points (one block each), then one item per small node (one warp each); node id owns
+  // items [i0[id], i1[id])
+  std::vector<int32_t> inode, istart, i0(nint + 1), i1(nint + 1, 0);
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) c->n_big_items = (int64_t)inode.size();
+    for (int id = 0; id < nint; ++id) {
+      int32_t m = std::max(ns[2 * id + 1], ns[2 * id + 2]);
+      bool small = m <= hodlr::kSmallNode;
+      if (small != (pass == 1)) continue;
+      i0[id] = (int32_t)inode.size();
+      for (int32_t s = 0; s < m || s == 0; s += hodlr::kAcaTile) {
+        inode.push_back(id);
+        istart.push_back(s);
+        if (small) break;
+      }
+      i1[id] = (int32_t)inode.size();
     }
   }
-  i0[nint] = (int32_t)inode.size();
+  i0[nint] = i1[nint] = (int32_t)inode.size();
   c->n_items = (int64_t)inode.size();
   c->h_raw_off.assign(K, 0);
   c->h_rcap.assign(K, 0);
@@ -148,6 +158,7 @@ hodlr_status setup_aca(Ctx* c) {
   TRY_CUDA(c, dalloc(&c->item_node, c->n_items), "alloc items");
   TRY_CUDA(c, dalloc(&c->item_start, c->n_items), "alloc items");
   TRY_CUDA(c, dalloc(&c->node_item0, nint + 1), "alloc items");
+  TRY_CUDA(c, dalloc(&c->node_item1, nint + 1), "alloc items");
   TRY_CUDA(c, dalloc(&c->raw, c->raw_elems), "alloc raw panel");
   TRY_CUDA(c, dalloc(&c->st_rank, nint), "alloc aca state");
   TRY_CUDA(c, dalloc(&c->st_row, nint), "alloc aca state");
@@ -164,6 +175,7 @@ hodlr_status setup_aca(Ctx* c) {
   TRY_CUDA(c, cudaMemcpyAsync(c->item_node, inode.data(), 4 * inode.size(), cudaMemcpyHostToDevice, c->stream), "upload");
   TRY_CUDA(c, cudaMemcpyAsync(c->item_start, istart.data(), 4 * istart.size(), cudaMemcpyHostToDevice, c->stream), "upload");
   TRY_CUDA(c, cudaMemcpyAsync(c->node_item0, i0.data(), 4 * i0.size(), cudaMemcpyHostToDevice, c->stream), "upload");
+  TRY_CUDA(c, cudaMemcpyAsync(c->node_item1, i1.data(), 4 * i1.size(), cudaMemcpyHostToDevice, c->stream), "upload");
   TRY_CUDA(c, cudaStreamSynchronize(c->stream), "upload");
   ++c->syncs;
   return HODLR_OK;

@@ -19,6 +19,7 @@ constexpr int kDefaultMaxRank = 64;  // default opts.max_rank
 constexpr int kSmemRank = 64;      // ranks up to this use the shared-memory node step
                                    // (2r x 2r in smem) and the fused level sweep
 constexpr int kAcaTile = 1024;     // columns (rows) of one ACA work item
+constexpr int kSmallNode = 256;    // nodes whose children both fit: one warp per node
 
 // ---------------------------------------------------------------------------------------
 // Covariance functions (Table 1 with length scale ell and amplitude a; Matern nu = 3/2 and
@@ -114,6 +115,8 @@ struct Ctx {
   int32_t* item_node = nullptr;   // internal node id of each work item
   int32_t* item_start = nullptr;  // first row/column of the item's tile
   int32_t* node_item0 = nullptr;  // first item of each internal node (nint + 1 entries)
+  int32_t* node_item1 = nullptr;  // one past its last item
+  int64_t n_big_items = 0;        // items [0, n_big_items): tiles; the rest: small nodes
   std::vector<int64_t> h_raw_off; // offset (in doubles) of level j's raw panel
   std::vector<int> h_rcap;        // raw columns of level j
   double* raw = nullptr;
