@@ -5,9 +5,10 @@ points uniform on [-1, 1] (seed 1002), y ~ N(0, 1) (seed 1003), sigma^2 = 1e-2, 
 eps = 1e-12, nrhs = 1, two kernels: Matern-3/2 with ell = 0.1 and exponential with
 ell = 0.2. One step = one log-likelihood evaluation of each kernel for its hyperparameters
 on the fixed points: recompression (ACA) + factorization with the solve fused + log det +
-y^T C^-1 y. Two forms are timed: FP64 throughout, and mixed (the leaf stage in
-double-float arithmetic on the FP32 pipe, the rest FP64); the headline is the faster form
-among those whose results meet the 1e-10 accuracy bar. The ordering of the points depends on x only and is done once, outside the
+y^T C^-1 y. Two forms are timed: FP64 throughout, and mixed (the leaf stage, the ACA
+columns and the panels in double-float arithmetic on the FP32 pipe; right-hand sides, sums,
+node matrices and log dets FP64); the headline is the faster form among those whose
+results meet the 1e-10 accuracy bar. The ordering of the points depends on x only and is done once, outside the
 timed region (as in a hyperparameter sweep). Every result is checked after timing against
 the exact O(n) oracles (Kalman filter, Ornstein-Uhlenbeck closed form) and exact residual
 rows; the accuracy is reported in the JSON line.
@@ -58,6 +59,24 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def combine_ranks(ms: float, units_local: int, world: int, device=None):
+    """Whole-job throughput of N replicas (one independent problem per rank, no data-path
+    collective): the slowest rank's time (max over ranks) and the units all ranks processed.
+    Returns (ms_max, units per second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_local * world / (ms / 1e3)
+
+
+def reference_runs_here(rank: int) -> bool:
+    """The reference arm (the CPU oracle) runs and prints on rank 0 only."""
+    return rank == 0
 
 
 class ClockSampler:
@@ -192,11 +211,7 @@ def measure_form(args, precision, x, y, xd, yd, stream, world, rank, local, dev)
         dist.barrier()
     ms = e0.elapsed_time(e1)
     launches = sum(h.counters()["launches"] for h in ctxs) - launches0
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = args.steps * len(KERNELS) * world / (ms / 1e3)
+    ms, value = combine_ranks(ms, args.steps * len(KERNELS), world, dev)
     res = {"value": value, "ms_per_step": ms / args.steps, "gpu_launches": launches,
            "clocks": clk.summary(), "phase_ms": ctxs[0].phase_ms(), "tuning": tuning}
 
@@ -573,7 +588,7 @@ def cpu_baseline(x, y):
 def run_reference(args):
     """The oracle as the reference arm, on rank 0 only; each step is one full-size step."""
     rank, world, _ = dist_env()
-    if rank != 0:
+    if not reference_runs_here(rank):
         return
     import oracle as O
     from paper_1403_6015_gb300 import inputs as I
