@@ -497,9 +497,38 @@ void oracle_tree_order(const double* x, int64_t n, int d, int leaf, int64_t* per
  *   residual row R(i,:) = B(i,:) - sum_l u_l(i) v_l^T; pivot column j = argmax |R(i,:)|;
  *   v = R(i,:) / R(i,j); u = residual column R(:,j); next row = argmax over unused rows of
  *   |u|. Frobenius norm of S_k = sum u_l v_l^T kept incrementally; stop (without keeping
- *   the term) when |u_k| |v_k| <= eps |S_k|_F. A zero pivot marks the row used and moves
- *   to the lowest-index unused row. Returns the rank; *ok = 0 if the cap was reached
- *   before the tolerance. Ties in argmax take the lowest index. */
+ *   the term) when |u_k| |v_k| <= eps |S_k|_F. Returns the rank; *ok = 0 if the cap was
+ *   reached before the tolerance. Ties in argmax take the lowest index.
+ * Start row and zero pivots (reading; the paper does not fix them): the first row is the
+ *   left-child point nearest the right child's first point, and a zero pivot marks the row
+ *   used and moves to the unused row nearest that point (squared Euclidean distance,
+ *   lowest index on ties). Rows far from the interface of a smooth, fast-decaying kernel
+ *   can be exactly zero in floating point; starting from them would end the cross with
+ *   rank 0 on a block that has entries of order one near the interface. */
+static double orc_d2_split(const orc_hodlr* H, int64_t a, int64_t s) {
+  double d2 = 0.0;
+  for (int c = 0; c < H->d; ++c) {
+    double t = H->xs[a * H->d + c] - H->xs[s * H->d + c];
+    d2 += t * t;
+  }
+  return d2;
+}
+
+static int64_t orc_nearest_unused(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br,
+                                  const char* used) {
+  int64_t best = -1;
+  double bd = 0.0;
+  for (int64_t a = 0; a < ml; ++a) {
+    if (used && used[a]) continue;
+    double d2 = orc_d2_split(H, bl + a, br);
+    if (best < 0 || d2 < bd) {
+      best = a;
+      bd = d2;
+    }
+  }
+  return best;
+}
+
 static int orc_aca(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int64_t mr,
                    double** Uo, double** Vo, int* ok) {
   int64_t cap64 = ml < mr ? ml : mr;
@@ -510,7 +539,7 @@ static int orc_aca(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int64
   double* col = (double*)malloc(sizeof(double) * ml);
   char* used = (char*)calloc((size_t)ml, 1);
   int k = 0;
-  int64_t i = 0;
+  int64_t i = ml > 0 ? orc_nearest_unused(H, bl, ml, br, NULL) : 0;
   double s2 = 0.0;
   int zero_tries = 0;
   *ok = 0;
@@ -527,9 +556,7 @@ static int orc_aca(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int64
     used[i] = 1;
     if (delta == 0.0) {
       if (++zero_tries > rmax) { *ok = 1; break; }
-      int64_t nx = -1;
-      for (int64_t a = 0; a < ml; ++a)
-        if (!used[a]) { nx = a; break; }
+      int64_t nx = orc_nearest_unused(H, bl, ml, br, used);
       if (nx < 0) { *ok = 1; break; }
       i = nx;
       continue;
