@@ -289,6 +289,7 @@ def run_ours(args):
     r = results[head]
     cpu = cpu_baseline(x, y) if (rank == 0 and world == 1 and not args.no_cpu) else None
     sweeps = run_sweeps(args) if (rank == 0 and not args.no_sweeps) else None
+    supp = run_supplementary(args) if (rank == 0 and not args.no_sweeps) else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": r["value"], "unit": "evals/s", "n_gpus": world,
@@ -309,7 +310,12 @@ def run_ours(args):
             "accepted": r["accepted"],
             "cpu_baseline": cpu,
             "sweeps": sweeps,
+            "supplementary": supp,
         }
+        if r.get("phase_ms"):
+            # the headline including the point ordering in every evaluation
+            per_eval = r["ms_per_step"] / len(KERNELS) + r["phase_ms"]["ordering"]
+            line["evals_per_s_including_ordering"] = 1e3 / per_eval
         for p in forms:
             if p != head:
                 o = results[p]
@@ -569,6 +575,131 @@ def run_sweeps(args):
                     "beyond the 512 cap"}
     h.close()
     net.close()
+    return out
+
+
+def run_supplementary(args):
+    """Measurements beside the headline (untimed by it): the paper's phase split at n = 2^20
+    (solve-only with 1 and 16 right-hand sides and log det given a factor, ordering), the
+    mixed form with refinement on n = 2^22 (1-D squared-exponential ell = 0.05,
+    sigma^2 = 1e-3), and paper-shaped rows (n = 1e6 on [-3, 3], unit length scale) next to
+    the paper's single-core timings (context only)."""
+    import torch
+
+    from paper_1403_6015_gb300 import hodlr as H
+    from paper_1403_6015_gb300 import inputs as I
+    out = {}
+
+    def ms_of(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    # (1) phases at n = 2^20, mixed form, per covariance
+    x, y = I.workload_1d(N, SEED)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.from_numpy(y).cuda()
+    Y16 = torch.from_numpy(I.normal(N, SEED + 7, 16)).cuda().t().contiguous().t()  # column-major
+    ph = {}
+    for kern, ell in KERNELS:
+        h = H.Hodlr(xd, kern, [ell, 1.0], SIGMA2, LEAF, EPS, max_rank=16, max_nrhs=16, precision=1)
+        order_ms = h.phase_ms()["ordering"]
+        comp_ms = ms_of(lambda: h.rebuild([ell, 1.0], SIGMA2))
+        h.rebuild([ell, 1.0], SIGMA2)
+
+        def factor_once():
+            h.rebuild([ell, 1.0], SIGMA2)
+            h.factor()
+        fac_ms = ms_of(factor_once) - comp_ms
+        s1 = ms_of(lambda: h.solve(yd))
+        s16 = ms_of(lambda: h.solve(Y16))
+        det_ms = ms_of(lambda: h.logdet())
+        ph[kern] = {"ordering_ms": order_ms, "compression_ms": comp_ms, "factor_ms": fac_ms,
+                    "solve_nrhs1_ms": s1, "solve_nrhs16_ms": s16, "logdet_given_factor_ms": det_ms}
+        h.close()
+    out["phases_n2p20_mixed"] = ph
+
+    # (2) mixed precision + refinement at n = 2^22 (1-D squared-exponential)
+    n3 = 1 << 22
+    x3, y3 = I.workload_1d(n3, 1003)
+    x3d = torch.from_numpy(x3).cuda()
+    y3d = torch.from_numpy(y3).cuda()
+    res3 = {"n": n3, "kernel": "se", "ell": 0.05, "sigma2": 1e-3, "leaf": 128, "eps": 1e-12}
+    lls = {}
+    for prec, name, rmax in [(1, "mixed_refined", 2), (0, "fp64", 0)]:
+        h = H.Hodlr(x3d, "se", [0.05, 1.0], 1e-3, 128, 1e-12, max_rank=64, precision=prec,
+                    refine_maxit=rmax, refine_tol=1e-13)
+
+        def ev():
+            h.rebuild([0.05, 1.0], 1e-3)
+            return h.loglik(y3d)
+        ev()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            lls[name] = ev()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        k3 = h.tree()[0]
+        r3 = h.ranks()
+        entry = {"evals_per_s": 1.0 / dt, "s_per_eval": dt,
+                 "level_ranks": [int(r3[(1 << j) - 1:(1 << (j + 1)) - 1].max()) for j in range(k3)]}
+        if prec == 1:
+            entry["refine_corrections"], entry["refine_residual"] = h.refine_info()
+            h.rebuild([0.05, 1.0], 1e-3)
+            sol = h.factor_solve(y3)
+            import oracle as O
+            rows = np.unique(np.linspace(0, n3 - 1, 16).astype(np.int64))
+            Cx = O.dense_matvec_rows(x3, "se", [0.05, 1.0], 1e-3, sol, rows)
+            entry["residual_rows"] = float(np.abs(Cx - y3[rows]).max() / np.abs(y3).max())
+        res3[name] = entry
+        h.close()
+    res3["loglik_rel_diff_mixed_vs_fp64"] = abs(lls["mixed_refined"] - lls["fp64"]) / abs(lls["fp64"])
+    out["mixed_refined_n2p22"] = res3
+
+    # (3) paper-shaped rows: n = 1e6 on [-3, 3]; the paper's phases (Assembly = ordering +
+    # compression, Factor, Solve, Det.) and the relative error of the solution of C x = b
+    # with b made from a known x (b = C~ x through the library's own product)
+    paper = {"gaussian_2I+exp(-r^2)": ("se", 0.5 ** 0.5, 2.0, [14.1, 23.2, 0.834, 1.52]),
+             "exponential_I+exp(-r)": ("exp", 1.0, 1.0, [18.8, 8.05, 0.636, 1.35])}
+    n4 = 1000000
+    x4 = I.uniform_points(n4, 1, -3.0, 3.0, 1005)
+    xt = I.normal(n4, 1006)
+    rows4 = {}
+    for name, (kern, ell, s2, ptimes) in paper.items():
+        r = {"n": n4, "kernel": kern, "ell": ell, "sigma2": s2, "leaf": LEAF, "eps": EPS,
+             "paper_s (one 1.3 GHz core)": dict(zip(["assembly", "factor", "solve", "det"], ptimes))}
+        for prec, fname in [(0, "fp64"), (1, "mixed")]:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = H.Hodlr(x4, kern, [ell, 1.0], s2, LEAF, EPS, precision=prec)
+            torch.cuda.synchronize()
+            asm_s = time.perf_counter() - t0
+            b = h.matvec(xt)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.factor()
+            torch.cuda.synchronize()
+            fac_s = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            xs = h.solve(b)
+            torch.cuda.synchronize()
+            sol_s = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            h.logdet()
+            det_s = time.perf_counter() - t0
+            r[fname] = {"assembly_s": asm_s, "factor_s": fac_s, "solve_s": sol_s, "det_s": det_s,
+                        "note": "assembly includes the host-to-device copy of x; solve "
+                                "includes host copies of b and x",
+                        "error": float(np.linalg.norm(xs - xt) / np.linalg.norm(xt))}
+            h.close()
+        rows4[name] = r
+    out["paper_shaped_n1e6"] = rows4
     return out
 
 

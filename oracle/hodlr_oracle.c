@@ -499,12 +499,12 @@ void oracle_tree_order(const double* x, int64_t n, int d, int leaf, int64_t* per
  *   |u|. Frobenius norm of S_k = sum u_l v_l^T kept incrementally; stop (without keeping
  *   the term) when |u_k| |v_k| <= eps |S_k|_F. Returns the rank; *ok = 0 if the cap was
  *   reached before the tolerance. Ties in argmax take the lowest index.
- * Start row and zero pivots (reading; the paper does not fix them): the first row is the
- *   left-child point nearest the right child's first point, and a zero pivot marks the row
- *   used and moves to the unused row nearest that point (squared Euclidean distance,
- *   lowest index on ties). Rows far from the interface of a smooth, fast-decaying kernel
- *   can be exactly zero in floating point; starting from them would end the cross with
- *   rank 0 on a block that has entries of order one near the interface. */
+ * Start row and zero pivots (reading; the paper does not fix them): the cross starts at
+ *   the first row; a zero pivot marks the row used and moves to the unused row nearest the
+ *   right child's first point (squared Euclidean distance, lowest index on ties). Rows far
+ *   from the interface of a fast-decaying kernel can be exactly zero in floating point;
+ *   moving on to the next rows by index would reach only more of them and end the cross
+ *   with rank 0 on a block that has entries of order one near the interface. */
 static double orc_d2_split(const orc_hodlr* H, int64_t a, int64_t s) {
   double d2 = 0.0;
   for (int c = 0; c < H->d; ++c) {
@@ -539,7 +539,7 @@ static int orc_aca(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int64
   double* col = (double*)malloc(sizeof(double) * ml);
   char* used = (char*)calloc((size_t)ml, 1);
   int k = 0;
-  int64_t i = ml > 0 ? orc_nearest_unused(H, bl, ml, br, NULL) : 0;
+  int64_t i = 0;
   double s2 = 0.0;
   int zero_tries = 0;
   *ok = 0;

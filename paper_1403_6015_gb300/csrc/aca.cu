@@ -9,7 +9,10 @@
 //                      term) when |u||v| <= eps |S_k|; next row = argmax over unused rows
 // The block B = K[I_left, I_right] of node id lives in one column of the level's raw panel:
 // rows of the left child hold u, rows of the right child hold v. All reductions use fixed
-// orders, so results are deterministic. In the mixed form the block entries are evaluated
+// orders, so results are deterministic. The cross starts at the first row; a zero pivot
+// moves to the unused row nearest the right child's first point (rows far from the
+// interface of a fast-decaying kernel can be exactly zero).
+// In the mixed form the block entries are evaluated
 // in double-float (ff.cuh) from the FP64 distances and the columns are stored and updated
 // as double-float pairs (8 bytes, like a double), so the per-element work runs on the FP32
 // pipe; the norm and dot-product partial sums that drive the stopping test are taken in
@@ -84,6 +87,18 @@ __device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int lev, int i, i
 }
 
 __device__ __forceinline__ int level_of(int id) { return 31 - __clz(id + 1); }
+
+// Squared distance of point i to point s, accumulated coordinate by coordinate without
+// fused multiply-adds (the same operations, in the same order, as the oracle's restart
+// rule, so both pick the same rows).
+__device__ __forceinline__ double split_d2(const Pts& p, int64_t i, int64_t s) {
+  double d2 = 0.0;
+  for (int c = 0; c < p.d; ++c) {
+    double t = __dsub_rn(p.x[c * p.n + i], p.x[c * p.n + s]);
+    d2 = __dadd_rn(d2, __dmul_rn(t, t));
+  }
+  return d2;
+}
 
 // Rank cap of a block: min(m_left, m_right, max_rank), and in presized mode the level's
 // rank + 1 (one extra cross step shows whether the block converged within its rank).
@@ -248,38 +263,64 @@ __global__ void k_aca_pivot_row(AcaArgs a) {
     amax_merge(bv, bi, p[0], (int)p[1]);
   }
   warp_amax(bv, bi);
-  if (lane != 0) return;
   int i = a.row[id];
   int* used = a.used + (int64_t)id * a.used_stride;
   int nu = a.nused[id];
-  used[nu++] = i;
-  a.nused[id] = nu;
-  if (bi < 0 || bv == 0.0) {
-    a.phase[id] = 0;
-    int rmax = rmax_of(a, id);
-    if (++a.zero[id] > rmax) {
-      a.done[id] = 1;
-      a.ok[id] = 1;
-      return;
+  if (lane == 0) {
+    used[nu] = i;
+    a.nused[id] = nu + 1;
+  }
+  ++nu;
+  if (bi >= 0 && bv != 0.0) {
+    if (lane == 0) {
+      a.col[id] = bi;
+      a.delta[id] = bv;
+      a.phase[id] = 1;
     }
-    int ml = a.ns[2 * id + 1];
-    int nx = -1;
-    for (int r = 0; r < ml && nx < 0; ++r) {
-      bool u = false;
-      for (int q = 0; q < nu; ++q) u |= used[q] == r;
-      if (!u) nx = r;
-    }
-    if (nx < 0) {
-      a.done[id] = 1;
-      a.ok[id] = 1;
-      return;
-    }
-    a.row[id] = nx;
     return;
   }
-  a.col[id] = bi;
-  a.delta[id] = bv;
-  a.phase[id] = 1;
+  // zero pivot: move to the unused row nearest the split (whole warp; lowest index on ties)
+  int rmax = rmax_of(a, id);
+  if (a.zero[id] + 1 > rmax) {
+    if (lane == 0) {
+      a.phase[id] = 0;
+      a.zero[id] += 1;
+      a.done[id] = 1;
+      a.ok[id] = 1;
+    }
+    return;
+  }
+  __syncwarp();
+  int bl = a.nb[2 * id + 1], ml = a.ns[2 * id + 1], br = a.nb[2 * id + 2];
+  double bd = 0.0;
+  int nx = -1;
+  for (int r = lane; r < ml; r += 32) {
+    bool u = false;
+    for (int q = 0; q < nu; ++q) u |= used[q] == r;
+    if (u) continue;
+    double d2 = split_d2(a.pts, bl + r, br);
+    if (nx < 0 || d2 < bd) {
+      bd = d2;
+      nx = r;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double od = __shfl_xor_sync(0xffffffffu, bd, o);
+    int on = __shfl_xor_sync(0xffffffffu, nx, o);
+    if (on >= 0 && (nx < 0 || od < bd || (od == bd && on < nx))) {
+      bd = od;
+      nx = on;
+    }
+  }
+  if (lane != 0) return;
+  a.phase[id] = 0;
+  a.zero[id] += 1;
+  if (nx < 0) {
+    a.done[id] = 1;
+    a.ok[id] = 1;
+    return;
+  }
+  a.row[id] = nx;
 }
 
 // C: residual column u (stored in column k of the U rows), normalised row v, and this tile's
@@ -854,6 +895,7 @@ __global__ void k_xrel(const double* __restrict__ xs, int64_t n, int d, const in
   for (int c = 0; c < d; ++c)
     xrel[((int64_t)j * d + c) * n + i] = ff_from_double(xs[c * n + i] - xs[c * n + s]);
 }
+
 }  // namespace
 
 // Relative coordinates for the mixed form's ACA (once per context: they do not depend on
