@@ -133,6 +133,22 @@ def dense_solve(x, kernel, theta, sigma2, y):
     return (X[:, 0] if one else X), ld.value
 
 
+def dense_predict(x, kernel, theta, sigma2, y, xtest):
+    """GP prediction from the dense factorization (O1): the posterior mean k_*^T C^-1 y
+    and the latent posterior variance k(x*, x*) - k_*^T C^-1 k_* at each test point (the
+    conditional distribution behind the likelihood of Sec. 1; the standard GP regression
+    formulas). x: (n, d) or (n,), xtest: (m, d) or (m,). Returns (mean, var), each (m,)."""
+    x = _f64(x).reshape(len(x), -1)
+    xt = _f64(xtest).reshape(len(xtest), -1)
+    r = np.sqrt(((x[:, None, :] - xt[None, :, :]) ** 2).sum(-1))
+    Ks = kernel_values(kernel, r, theta[0], theta[1])  # n x m
+    alpha, _ = dense_solve(x, kernel, theta, sigma2, y)
+    V, _ = dense_solve(x, kernel, theta, sigma2, np.asfortranarray(Ks))
+    mean = Ks.T @ alpha
+    var = float(kernel_values(kernel, np.zeros(1), theta[0], theta[1])[0]) - (Ks * V).sum(0)
+    return mean, var
+
+
 def dense_matvec_rows(x, kernel, theta, sigma2, v, rows):
     """Exact (C v)[rows] in FP64 with compensated summation, O(n) per row."""
     x = _f64(x)

@@ -388,3 +388,49 @@ def test_matern32_large_vs_kalman():
     ldk, q = O.matern_kalman(x[p, 0], 3, th[0], th[1], s2, y[p])
     assert abs(H.logdet() - ldk) <= 1e-10 * abs(ldk)
     assert abs(y @ sol - q) <= 1e-9 * abs(q)
+
+
+
+def test_predict_one_training_point_closed_form():
+    """n = 1: mean = k(x*, x1) y1 / (k(0) + s2), var = k(0) - k(x*, x1)^2 / (k(0) + s2)."""
+    x = np.array([[0.3]])
+    y = np.array([1.7])
+    xt = np.array([[0.3], [0.5], [-0.4]])
+    th, s2 = [0.2, 1.5], 0.1
+    mean, var = O.dense_predict(x, "matern52", th, s2, y, xt)
+    k = O.kernel_values("matern52", np.abs(xt[:, 0] - 0.3), 0.2, 1.5)
+    np.testing.assert_allclose(mean, k * 1.7 / (1.5 + s2), rtol=1e-14)
+    np.testing.assert_allclose(var, 1.5 - k * k / (1.5 + s2), rtol=1e-13, atol=1e-15)
+
+
+def test_predict_at_training_points_identities():
+    """At training point i, C alpha = y gives mean_i = y_i - s2 alpha_i, and
+    k_i = C e_i - s2 e_i gives var_i = s2 - s2^2 (C^-1)_ii (both exact identities)."""
+    x, y = I.workload_1d(200, 1031)
+    s2 = 0.05
+    idx = np.arange(0, 200, 17)
+    mean, var = O.dense_predict(x, "exp", [0.3, 1.0], s2, y, x[idx])
+    alpha, _ = O.dense_solve(x, "exp", [0.3, 1.0], s2, y)
+    E = np.zeros((200, len(idx)), order="F")
+    E[idx, np.arange(len(idx))] = 1.0
+    Cinv_cols, _ = O.dense_solve(x, "exp", [0.3, 1.0], s2, E)
+    np.testing.assert_allclose(mean, y[idx] - s2 * alpha[idx], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(var, s2 - s2 * s2 * Cinv_cols[idx, np.arange(len(idx))],
+                               rtol=1e-9, atol=1e-13)
+
+
+def test_predict_matches_scikit_learn():
+    """The same posterior from scikit-learn's GP regressor (Matern-3/2, fixed
+    hyperparameters, the noise as its diagonal alpha)."""
+    gp = pytest.importorskip("sklearn.gaussian_process")
+    kern = pytest.importorskip("sklearn.gaussian_process.kernels")
+    x, y = I.workload_1d(300, 1032)
+    xt = I.uniform_points(25, 1, -1.2, 1.2, 1033)
+    th, s2 = [0.15, 1.0], 0.05
+    mean, var = O.dense_predict(x, "matern32", th, s2, y, xt)
+    k = kern.ConstantKernel(1.0, "fixed") * kern.Matern(length_scale=0.15, nu=1.5,
+                                                        length_scale_bounds="fixed")
+    reg = gp.GaussianProcessRegressor(kernel=k, alpha=s2, optimizer=None).fit(x, y)
+    m2, sd = reg.predict(xt, return_std=True)
+    np.testing.assert_allclose(mean, m2, rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(var, sd ** 2, rtol=1e-8, atol=1e-10)
