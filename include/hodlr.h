@@ -280,6 +280,20 @@ hodlr_status hodlr_set_tuning(hodlr_ctx* ctx, const hodlr_tuning* t);
 hodlr_status hodlr_autotune(hodlr_ctx* ctx, const double* y, int reps, hodlr_tuning* best,
                             float* best_ms);
 
+/* GP prediction with the factorization (the conditional distribution behind the
+ * likelihood of Sec. 1; the standard GP regression formulas): at each test point x*,
+ * mean = k_*^T C^-1 y and the latent variance var = k(x*, x*) - k_*^T C^-1 k_*, with
+ * k_* = (k(x_i, x*))_i over the training points. The solves use the stored factorization
+ * (without refinement); the cross-covariances are evaluated in FP64.
+ *   xtest  m test points, row-major m x d (host or device)
+ *   y      the n training targets in the order of hodlr_build's x (host or device)
+ *   mean   m doubles out (host or device); var m doubles out, or NULL for the mean only
+ * Requires a factored context (hodlr_factor, hodlr_factor_solve or hodlr_loglik); the
+ * factorization is not changed. Synchronises the stream before returning.
+ * Errors: EINVAL, ESTATE (not factored, or under stream capture), ENOMEM, ECUDA. */
+hodlr_status hodlr_predict(hodlr_ctx* ctx, const double* xtest, int64_t m, const double* y,
+                           double* mean, double* var);
+
 /* Iterative refinement of the last solve (opts.refine_maxit > 0; not in the paper): the
  * corrections it took over all right-hand sides, and the largest final relative residual
  * ||y - C~ x|| / ||y|| it measured (0 when refinement is off or ran without host checks).

@@ -1109,6 +1109,66 @@ hodlr_status hodlr_autotune(hodlr_ctx* ctx, const double* y, int reps, hodlr_tun
   return HODLR_OK;
 }
 
+hodlr_status hodlr_predict(hodlr_ctx* ctx, const double* xtest, int64_t m, const double* y,
+                           double* mean, double* var) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return HODLR_EINVAL;
+  if (!xtest || m < 1 || !y || !mean) return fail(c, HODLR_EINVAL, "predict: bad xtest/m/y/mean");
+  if (!c->factored) return fail(c, HODLR_ESTATE, "predict before factor");
+  if (capturing(c)) return fail(c, HODLR_ESTATE, "predict: not under stream capture");
+  double *xt = nullptr, *alpha = nullptr, *part = nullptr, *res = nullptr;
+  auto cleanup = [&]() {
+    dfree(xt);
+    dfree(alpha);
+    dfree(part);
+    dfree(res);
+  };
+  if (dalloc(&xt, m * c->d) || dalloc(&alpha, c->n) ||
+      dalloc(&part, hodlr::predict_partial_elems(std::max<int64_t>(m, c->max_nrhs))) ||
+      dalloc(&res, 2 * m)) {
+    cudaGetLastError();
+    cleanup();
+    return fail(c, HODLR_ENOMEM, "predict: buffers");
+  }
+  auto run = [&]() -> hodlr_status {
+    TRY_CUDA(c, cudaMemcpyAsync(xt, xtest, sizeof(double) * m * c->d, cudaMemcpyDefault, c->stream), "xtest");
+    // alpha = C^-1 y with the stored factor (tree order)
+    const double* yd;
+    int64_t ldd;
+    hodlr_status s = stage_in(c, y, 1, c->n, &yd, &ldd);
+    if (s != HODLR_OK) return s;
+    TRY_CUDA(c, hodlr::launch_gather_rhs(*c, yd, ldd, 1), "gather");
+    TRY_CUDA(c, c->precision == 1 ? hodlr::launch_leaf_solve_ff(*c, 1) : hodlr::launch_leaf_solve(*c, 1), "leaf solve");
+    TRY_CUDA(c, sweep(c, 1, false), "levels");
+    TRY_CUDA(c, cudaMemcpyAsync(alpha, c->Y, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream), "alpha");
+    // mean in chunks of test points
+    const int64_t chunk = 4096;
+    for (int64_t j0 = 0; j0 < m; j0 += chunk) {
+      int nc = (int)std::min<int64_t>(chunk, m - j0);
+      TRY_CUDA(c, hodlr::launch_cross_dot(*c, xt, j0, nc, alpha, 0, 0, part, 0, res), "mean");
+    }
+    // variance: k_* columns solved max_nrhs at a time
+    if (var) {
+      for (int64_t j0 = 0; j0 < m; j0 += c->max_nrhs) {
+        int nc = (int)std::min<int64_t>(c->max_nrhs, m - j0);
+        TRY_CUDA(c, hodlr::launch_cross_fill(*c, xt, j0, nc), "cross");
+        TRY_CUDA(c, c->precision == 1 ? hodlr::launch_leaf_solve_ff(*c, nc) : hodlr::launch_leaf_solve(*c, nc), "leaf solve");
+        TRY_CUDA(c, sweep(c, nc, false), "levels");
+        TRY_CUDA(c, hodlr::launch_cross_dot(*c, xt, j0, nc, c->Y, c->n, 1, part, 1, res + m), "variance");
+      }
+    }
+    TRY_CUDA(c, cudaMemcpyAsync(mean, res, sizeof(double) * m, cudaMemcpyDefault, c->stream), "mean out");
+    if (var)
+      TRY_CUDA(c, cudaMemcpyAsync(var, res + m, sizeof(double) * m, cudaMemcpyDefault, c->stream), "var out");
+    TRY_CUDA(c, cudaStreamSynchronize(c->stream), "predict");
+    ++c->syncs;
+    return HODLR_OK;
+  };
+  hodlr_status s = run();
+  cleanup();
+  return s;
+}
+
 hodlr_status hodlr_refine_info(hodlr_ctx* ctx, int32_t* corrections, double* residual) {
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!c) return HODLR_EINVAL;

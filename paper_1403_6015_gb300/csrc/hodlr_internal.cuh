@@ -226,6 +226,10 @@ cudaError_t launch_logdet_sum(Ctx& c);
 cudaError_t launch_quad_loglik(Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double* xin_sorted, double* yout_sorted);
 int64_t refine_work_elems(int64_t n);
+int64_t predict_partial_elems(int64_t m);
+cudaError_t launch_cross_dot(Ctx& c, const double* xt, int64_t j0, int nc, const double* W,
+                             int64_t ldw, int wstep, double* partial, int mode, double* out);
+cudaError_t launch_cross_fill(Ctx& c, const double* xt, int64_t j0, int nc);
 cudaError_t launch_residual(Ctx& c, const double* y_sorted, double* ax, double* part, double* ratio);
 cudaError_t launch_axpy(Ctx& c, double* x, const double* d);
 cudaError_t launch_set_hyp(Ctx& c, double ell, double amp, double sigma2);

@@ -68,6 +68,7 @@ def load():
     L.hodlr_phase_ms.argtypes = [_vp, _dp]
     L.hodlr_counters.argtypes = [_vp, _dp]
     L.hodlr_refine_info.argtypes = [_vp, _dp, _dp]
+    L.hodlr_predict.argtypes = [_vp, _dp, ctypes.c_int64, _dp, _dp, _dp]
     L.hodlr_get_tuning.argtypes = [_vp, ctypes.POINTER(hodlr_tuning)]
     L.hodlr_set_tuning.argtypes = [_vp, ctypes.POINTER(hodlr_tuning)]
     L.hodlr_autotune.argtypes = [_vp, _dp, ctypes.c_int, ctypes.POINTER(hodlr_tuning),
@@ -103,7 +104,7 @@ def load():
                  "hodlr_mlp_forward", "hodlr_mlp_gradient", "hodlr_mlp_train", "hodlr_mlp_save",
                  "hodlr_mlp_load", "hodlr_block_features", "hodlr_predict_ranks",
                  "hodlr_loglik_batched", "hodlr_refine_info", "hodlr_get_tuning",
-                 "hodlr_set_tuning", "hodlr_autotune"):
+                 "hodlr_set_tuning", "hodlr_autotune", "hodlr_predict"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -209,6 +210,10 @@ def hodlr_autotune(ctx, y_addr, reps, best: hodlr_tuning, best_ms):
     """best_ms: a ctypes.c_float (or None)."""
     return load().hodlr_autotune(ctx, y_addr, reps, ctypes.byref(best),
                                  ctypes.byref(best_ms) if best_ms is not None else None)
+
+
+def hodlr_predict(ctx, xtest_addr, m, y_addr, mean_addr, var_addr):
+    return load().hodlr_predict(ctx, xtest_addr, m, y_addr, mean_addr, var_addr)
 
 
 def hodlr_refine_info(ctx, corrections, residual):
@@ -561,6 +566,26 @@ class Hodlr:
             with open(cache, "w") as f:
                 json.dump(table, f, indent=1, sort_keys=True)
         return dict(res, cached=False)
+
+    def predict(self, xtest, y, var: bool = True):
+        """Posterior mean (and latent variance) at the test points with the current
+        factorization. numpy in, numpy out; CUDA tensors in, CUDA tensors out."""
+        if _is_torch(xtest):
+            import torch
+            xt = xtest.contiguous()
+            m = xt.shape[0]
+            yy = y.contiguous()
+            mean = torch.empty(m, dtype=torch.float64, device=xt.device)
+            vv = torch.empty(m, dtype=torch.float64, device=xt.device) if var else None
+        else:
+            xt = _f64_host(xtest).reshape(len(xtest), -1)
+            m = xt.shape[0]
+            yy = _f64_host(y).reshape(-1)
+            mean = np.zeros(m)
+            vv = np.zeros(m) if var else None
+        self._check(hodlr_predict(self._ctx, _addr(xt), m, _addr(yy), _addr(mean),
+                                  _addr(vv) if vv is not None else None), "predict")
+        return (mean, vv) if var else mean
 
     def refine_info(self):
         """(corrections, final relative residual) of the last solve's refinement."""
