@@ -618,8 +618,12 @@ def run_supplementary(args):
         s1 = ms_of(lambda: h.solve(yd))
         s16 = ms_of(lambda: h.solve(Y16))
         det_ms = ms_of(lambda: h.logdet())
+        xt = torch.from_numpy(I.uniform_points(256, 1, -1.0, 1.0, SEED + 9)).cuda()
+        pm = ms_of(lambda: h.predict(xt, yd, var=False))
+        pv = ms_of(lambda: h.predict(xt, yd, var=True))
         ph[kern] = {"ordering_ms": order_ms, "compression_ms": comp_ms, "factor_ms": fac_ms,
-                    "solve_nrhs1_ms": s1, "solve_nrhs16_ms": s16, "logdet_given_factor_ms": det_ms}
+                    "solve_nrhs1_ms": s1, "solve_nrhs16_ms": s16, "logdet_given_factor_ms": det_ms,
+                    "predict_256_mean_ms": pm, "predict_256_mean_var_ms": pv}
         h.close()
     out["phases_n2p20_mixed"] = ph
 
