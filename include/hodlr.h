@@ -22,7 +22,7 @@
  *   - The context owns every buffer it allocates; the caller owns every pointer it passes.
  *   - Errors are return codes; nothing is thrown across the ABI. hodlr_last_error() gives
  *     a one-line description of the last failure on that context.
- *   - Sizes: 1 <= n < 2^31, 1 <= leaf <= 128, d in {1, 2}.
+ *   - Sizes: 1 <= n < 2^31, 1 <= leaf <= 128, d in {1, 2, 3}.
  */
 #ifndef HODLR_GB300_H
 #define HODLR_GB300_H
@@ -304,7 +304,7 @@ hodlr_status hodlr_refine_info(hodlr_ctx* ctx, int32_t* corrections, double* res
  * allocation. The paper has no counterpart: this entry exists for callers that must not
  * allocate device memory while they evaluate, such as sampling loops under a fixed memory
  * budget or code recorded into a CUDA graph that should hold no allocation nodes.
- *   x      device pointer, n points row-major n x d (d in {1, 2}); y device pointer (n);
+ *   x      device pointer, n points row-major n x d (d in {1, 2, 3}); y device pointer (n);
  *   out    device pointer to one double: -y^T C^-1 y/2 - log det C/2 - n log(2 pi)/2, or
  *          NaN if C is not positive definite;
  *   stream cudaStream_t (NULL = legacy default stream); the call is stream-ordered and

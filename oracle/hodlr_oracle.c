@@ -598,7 +598,7 @@ static int64_t orc_nid(int j, int64_t k) { return ((int64_t)1 << j) - 1 + k; }
 
 void* oracle_hodlr_build(const double* x, int64_t n, int d, int kind, const double* theta,
                          double sigma2, int leaf, double eps, int max_rank, int* status) {
-  if (n < 1 || (d != 1 && d != 2) || leaf < 1 || !(eps > 0) || sigma2 < 0 || max_rank < 1) {
+  if (n < 1 || d < 1 || d > 3 || leaf < 1 || !(eps > 0) || sigma2 < 0 || max_rank < 1) {
     *status = ORC_EINVAL;
     return NULL;
   }

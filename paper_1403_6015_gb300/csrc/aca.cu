@@ -81,7 +81,12 @@ __device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int lev, int i, i
     if (r.hi < 0.0f) r = ff_neg(r);
   } else {
     ff u = ff_sub(xr[j], xr[i]), v = ff_sub(xr[n + j], xr[n + i]);
-    r = ff_sqrt(ff_add(ff_mul(u, u), ff_mul(v, v)));
+    ff s = ff_add(ff_mul(u, u), ff_mul(v, v));
+    if (a.pts.d == 3) {
+      ff w = ff_sub(xr[2 * n + j], xr[2 * n + i]);
+      s = ff_add(s, ff_mul(w, w));
+    }
+    r = ff_sqrt(s);
   }
   return cov_ff(a.kind, r, cr, amp, tab);
 }

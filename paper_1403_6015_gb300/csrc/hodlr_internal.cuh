@@ -70,7 +70,9 @@ __device__ __forceinline__ double dist(const Pts& p, int i, int j) {
   if (p.d == 1) return fabs(p.x[i] - p.x[j]);
   double a = p.x[i] - p.x[j];
   double b = p.x[p.n + i] - p.x[p.n + j];
-  return sqrt(a * a + b * b);
+  if (p.d == 2) return sqrt(a * a + b * b);
+  double e = p.x[2 * p.n + i] - p.x[2 * p.n + j];
+  return sqrt(a * a + b * b + e * e);
 }
 
 // Device error word bits (ctx->dflags).

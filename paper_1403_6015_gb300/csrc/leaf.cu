@@ -107,7 +107,7 @@ __device__ __forceinline__ void warp_ldl_solve(const double* __restrict__ A,
 template <bool kFactor, int kLeafThreads>
 __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
   extern __shared__ double A[];  // [kMaxLeaf][kLD]
-  __shared__ double xl[2 * kMaxLeaf];
+  __shared__ double xl[3 * kMaxLeaf];
   __shared__ double dinv[kMaxLeaf];
   __shared__ double T0[kMaxLeaf], T1[kMaxLeaf];
   __shared__ double red[kLeafThreads / 32];
@@ -123,8 +123,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
     const double sigma2 = a.hyp[kHypSigma2];
     if (tid == 0) bad = 0;
     for (int i = tid; i < p; i += kLeafThreads) {
-      xl[i] = a.pts.x[b + i];
-      if (a.pts.d == 2) xl[kMaxLeaf + i] = a.pts.x[a.pts.n + b + i];
+      for (int c = 0; c < a.pts.d; ++c) xl[c * kMaxLeaf + i] = a.pts.x[c * a.pts.n + b + i];
     }
     __syncthreads();
     for (int e = tid; e < p * p; e += kLeafThreads) {
@@ -135,7 +134,12 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
         r = fabs(xl[i] - xl[j]);
       } else {
         double u = xl[i] - xl[j], v = xl[kMaxLeaf + i] - xl[kMaxLeaf + j];
-        r = sqrt(u * u + v * v);
+        if (a.pts.d == 2) {
+          r = sqrt(u * u + v * v);
+        } else {
+          double w = xl[2 * kMaxLeaf + i] - xl[2 * kMaxLeaf + j];
+          r = sqrt(u * u + v * v + w * w);
+        }
       }
       double c = cov_r(cov, r);
       if (i == j) c += sigma2;

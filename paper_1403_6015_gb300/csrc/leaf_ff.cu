@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
   ff* A = sm;                          // packed lower triangle, kTri
   ff* Up = A + kTri;                   // [kMaxLeaf][kBS] unscaled panel columns (factor)
   ff* B = Up;                          // [kMaxLeaf][kBS] solve chunk (after the factor)
-  ff* xl = Up;                         // 2 x kMaxLeaf coordinates (block build only)
+  ff* xl = Up;                         // d x kMaxLeaf coordinates (block build only)
   __shared__ ff dinv[kMaxLeaf];
   __shared__ ff tab[64];
   __shared__ ff pinv[2];
@@ -98,8 +98,8 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
     for (int q = tid; q < 64; q += kT) tab[q] = a.tab[q];
     // coordinates relative to the leaf's first point (keeps small offsets exact)
     for (int i = tid; i < p; i += kT) {
-      xl[i] = ff_from_double(a.x[b + i] - a.x[b]);
-      if (a.d == 2) xl[kMaxLeaf + i] = ff_from_double(a.x[a.n + b + i] - a.x[a.n + b]);
+      for (int c = 0; c < a.d; ++c)
+        xl[c * kMaxLeaf + i] = ff_from_double(a.x[c * a.n + b + i] - a.x[c * a.n + b]);
     }
     __syncthreads();
     const ff cr = ff_from_double(a.hyp[kHypScale]), amp = ff_from_double(a.hyp[kHypAmp]);
@@ -115,7 +115,12 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
           if (r.hi < 0.0f) r = ff_neg(r);
         } else {
           ff u = ff_sub(xl[i], xl[j]), v = ff_sub(xl[kMaxLeaf + i], xl[kMaxLeaf + j]);
-          r = ff_sqrt(ff_add(ff_mul(u, u), ff_mul(v, v)));
+          ff s = ff_add(ff_mul(u, u), ff_mul(v, v));
+          if (a.d == 3) {
+            ff w = ff_sub(xl[2 * kMaxLeaf + i], xl[2 * kMaxLeaf + j]);
+            s = ff_add(s, ff_mul(w, w));
+          }
+          r = ff_sqrt(s);
         }
         c = cov_ff(a.kind, r, cr, amp, tab);
         if (i == j) c = ff_add(c, s2);

@@ -30,8 +30,8 @@ namespace {
 constexpr int kNoAllocMaxN = hodlr::kMaxLeaf;  // largest n accepted (one leaf block)
 
 // Scratch layout, in doubles.
-constexpr int kOffX = 0;                                       // sorted-free coordinates, 2 x 128 (SoA)
-constexpr int kOffY = kOffX + 2 * kNoAllocMaxN;                // y, kept for y^T C^-1 y
+constexpr int kOffX = 0;                                       // sorted-free coordinates, d x 128 (SoA)
+constexpr int kOffY = kOffX + 3 * kNoAllocMaxN;                // y, kept for y^T C^-1 y
 constexpr int kOffSol = kOffY + kNoAllocMaxN;                  // y, overwritten by C^-1 y
 constexpr int kOffL = kOffSol + kNoAllocMaxN;                  // Cholesky factor, 128 x 128
 constexpr int kOffLd = kOffL + kNoAllocMaxN * kNoAllocMaxN;    // log det
@@ -119,7 +119,7 @@ extern "C" hodlr_status hodlr_loglik_small_noalloc(const double* x, int64_t n, i
                                                    hodlr_kernel kernel, const double* theta,
                                                    double sigma2, const double* y, double* out,
                                                    void* stream) {
-  if (n < 1 || n > kNoAllocMaxN || (d != 1 && d != 2) || (int)kernel < 0 || (int)kernel > 3 ||
+  if (n < 1 || n > kNoAllocMaxN || d < 1 || d > 3 || (int)kernel < 0 || (int)kernel > 3 ||
       !theta || !(theta[0] > 0) || !(theta[1] > 0) || !std::isfinite(theta[0]) ||
       !std::isfinite(theta[1]) || !(sigma2 >= 0) || !std::isfinite(sigma2) || !x || !y || !out)
     return HODLR_EINVAL;

@@ -17,7 +17,9 @@ __device__ __forceinline__ double cross_r(const Pts& pts, int64_t i, const doubl
   double a = pts.x[i] - xt[j * pts.d];
   if (pts.d == 1) return fabs(a);
   double b = pts.x[pts.n + i] - xt[j * pts.d + 1];
-  return sqrt(a * a + b * b);
+  if (pts.d == 2) return sqrt(a * a + b * b);
+  double e = pts.x[2 * pts.n + i] - xt[j * pts.d + 2];
+  return sqrt(a * a + b * b + e * e);
 }
 
 // partial[b * kPSlices + s] = sum over the training points of slice s of k(x_i, x*_{j0+b})

@@ -80,3 +80,8 @@ def workload_1d(n: int, seed: int, nrhs: int = 1, lo: float = -1.0, hi: float = 
 def workload_2d(n: int, seed: int, nrhs: int = 1):
     """n points U[0,1)^2 and nrhs N(0,1) right-hand sides."""
     return uniform_points(n, 2, 0.0, 1.0, seed), normal(n, seed + 1, nrhs)
+
+
+def workload_3d(n: int, seed: int, nrhs: int = 1):
+    """n points U[0,1)^3 and nrhs N(0,1) right-hand sides."""
+    return uniform_points(n, 3, 0.0, 1.0, seed), normal(n, seed + 1, nrhs)

@@ -76,6 +76,25 @@ def test_predict_2d(H):
     np.testing.assert_allclose(var, v_o, rtol=0, atol=1e-7)
 
 
+def test_predict_3d(H):
+    n = 2048
+    x, y = I.workload_3d(n, 1055)
+    y = np.ascontiguousarray(y).reshape(-1)
+    xt = I.uniform_points(19, 3, -0.1, 1.1, 1056)
+    th, s2 = [0.7, 1.0], 1e-2
+    for precision in (0, 1):
+        h = H.Hodlr(x, "se", th, s2, 64, 1e-12, max_rank=512, precision=precision)
+        h.loglik(y)
+        mean, var = h.predict(xt, y)
+        m_2, v_2 = o2_predict(x, "se", th, s2, y, xt, 64, max_rank=512)
+        tol = 1e-10 if precision == 0 else 1e-7
+        np.testing.assert_allclose(mean, m_2, rtol=0, atol=tol * np.abs(m_2).max())
+        np.testing.assert_allclose(var, v_2, rtol=0, atol=tol)
+        m_o, v_o = O.dense_predict(x, "se", th, s2, y, xt)
+        np.testing.assert_allclose(mean, m_o, rtol=0, atol=1e-7 * np.abs(m_o).max())
+        np.testing.assert_allclose(var, v_o, rtol=0, atol=1e-7)
+
+
 def test_predict_needs_a_factor(H):
     x, y = I.workload_1d(1024, 1054)
     h = H.Hodlr(x, "exp", [0.2, 1.0], 1e-2, 64, 1e-12)

@@ -202,9 +202,11 @@ def test_tree_order_1d_is_stable_sort():
     np.testing.assert_array_equal(O.tree_order(x, 32), np.argsort(x[:, 0], kind="stable"))
 
 
-def test_tree_order_2d_kd_invariant():
+@pytest.mark.parametrize("d", [2, 3])
+def test_tree_order_kd_invariant(d):
+    """Sec. 3: each split halves its node by point count along dimension depth mod d."""
     n, leaf = 3000, 20
-    x = I.uniform_points(n, 2, 0, 1, 4)
+    x = I.uniform_points(n, d, 0, 1, 4)
     perm = O.tree_order(x, leaf)
     assert sorted(perm.tolist()) == list(range(n))
     xs = x[perm]
@@ -213,7 +215,7 @@ def test_tree_order_2d_kd_invariant():
     def check(b, m, depth):
         if depth >= kap:
             return
-        dim = depth % 2
+        dim = depth % d
         ml = m // 2
         assert xs[b:b + ml, dim].max() <= xs[b + ml:b + m, dim].min()
         check(b, ml, depth + 1)
@@ -326,6 +328,22 @@ def test_hodlr_2d_vs_dense():
     sol = H.factor_solve(y)
     assert abs(H.logdet() - ld_d) <= 1e-10 * abs(ld_d)
     assert rel_residual(x, "se", th, s2, sol, y) <= 1e-9
+
+
+@pytest.mark.parametrize("kern,ell,eps,tol", [("se", 1.0, 1e-12, 1e-10), ("matern52", 0.5, 1e-10, 1e-9)])
+def test_hodlr_3d_vs_dense(kern, ell, eps, tol):
+    """3-D points: the same factorization, with the kd ordering cycling through three
+    coordinates (block ranks here reach 130 for SE and several hundred for Matern-5/2)."""
+    n = 1500
+    x, y = I.workload_3d(n, 92)
+    th, s2 = [ell, 1.0], 0.01
+    sol_d, ld_d = O.dense_solve(x, kern, th, s2, y)
+    H = O.Hodlr(x, kern, th, s2, 32, eps, max_rank=1000)
+    sol = H.factor_solve(y)
+    assert abs(H.logdet() - ld_d) <= tol * abs(ld_d)
+    # each level's blocks are off by about eps times their norm (entries <= 1, so <= eps m
+    # for an m-point node) and |C^-1| <= 1/sigma^2: |r|/|y| <= eps n kappa / sigma^2
+    assert rel_residual(x, kern, th, s2, sol, y) <= eps * n * O.kappa(n, 32) / s2
 
 
 def test_hodlr_matvec_matches_dense():

@@ -25,10 +25,10 @@ def H():
 
 
 @pytest.mark.parametrize("n,d,kern", [(100, 1, "matern32"), (128, 2, "se"), (1, 1, "exp"),
-                                      (57, 1, "matern52")])
+                                      (57, 1, "matern52"), (128, 3, "matern52")])
 def test_noalloc_matches_regular_entry_twice(H, n, d, kern):
     import torch
-    x = I.uniform_points(n, d, -1.0, 1.0, 500 + n) if d == 1 else I.workload_2d(n, 500 + n)[0]
+    x = I.uniform_points(n, d, -1.0, 1.0, 500 + n) if d != 2 else I.workload_2d(n, 500 + n)[0]
     y = I.normal(n, 600 + n)
     th, s2 = [0.3, 1.1], 0.05
     ref = H.Hodlr(x, kern, th, s2, 128, 1e-12).loglik(y)  # regular path (one leaf)
