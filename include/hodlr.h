@@ -22,7 +22,7 @@
  *   - The context owns every buffer it allocates; the caller owns every pointer it passes.
  *   - Errors are return codes; nothing is thrown across the ABI. hodlr_last_error() gives
  *     a one-line description of the last failure on that context.
- *   - Sizes: 1 <= n < 2^31, 1 <= leaf <= 128, d in {1, 2, 3}.
+ *   - Sizes: 1 <= n < 2^31, 1 <= leaf <= 128, 1 <= d <= 64.
  */
 #ifndef HODLR_GB300_H
 #define HODLR_GB300_H
@@ -59,7 +59,8 @@ typedef enum {
 typedef struct {
   int precision;       /* 0: FP64 throughout; 1: mixed: the leaf stage (block build,       */
                        /*    L D L^T, panel solves) in double-float arithmetic on the FP32 */
-                       /*    pipe (~2^-48 unit roundoff), everything else FP64             */
+                       /*    pipe (~2^-48 unit roundoff), everything else FP64; it keeps  */
+                       /*    per-level relative coordinates, kappa x d x n x 8 bytes     */
   int rank_mode;       /* 0: adaptive ACA ranks                                            */
   int max_rank;        /* cap on the ACA rank of one off-diagonal block (1..512), default  */
                        /*    64. Levels whose rank exceeds 64 factor their node matrices  */

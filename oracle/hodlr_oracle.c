@@ -31,6 +31,8 @@
 
 enum { ORC_EXP = 0, ORC_SE = 1, ORC_M32 = 2, ORC_M52 = 3 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENOTSPD = 3, ORC_ERANK = 4, ORC_ESTATE = 6 };
+/* Largest point dimension accepted (the high-dimension experiments of Sec. 5 go to 64). */
+#define ORC_MAX_D 64
 
 int oracle_num_threads(void) {
 #ifdef _OPENMP
@@ -598,7 +600,7 @@ static int64_t orc_nid(int j, int64_t k) { return ((int64_t)1 << j) - 1 + k; }
 
 void* oracle_hodlr_build(const double* x, int64_t n, int d, int kind, const double* theta,
                          double sigma2, int leaf, double eps, int max_rank, int* status) {
-  if (n < 1 || d < 1 || d > 3 || leaf < 1 || !(eps > 0) || sigma2 < 0 || max_rank < 1) {
+  if (n < 1 || d < 1 || d > ORC_MAX_D || leaf < 1 || !(eps > 0) || sigma2 < 0 || max_rank < 1) {
     *status = ORC_EINVAL;
     return NULL;
   }

@@ -82,8 +82,8 @@ __device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int lev, int i, i
   } else {
     ff u = ff_sub(xr[j], xr[i]), v = ff_sub(xr[n + j], xr[n + i]);
     ff s = ff_add(ff_mul(u, u), ff_mul(v, v));
-    if (a.pts.d == 3) {
-      ff w = ff_sub(xr[2 * n + j], xr[2 * n + i]);
+    for (int c = 2; c < a.pts.d; ++c) {
+      ff w = ff_sub(xr[c * n + j], xr[c * n + i]);
       s = ff_add(s, ff_mul(w, w));
     }
     r = ff_sqrt(s);

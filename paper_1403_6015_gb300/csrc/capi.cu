@@ -347,7 +347,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   hodlr_opts opts;
   hodlr_default_opts(&opts);
   if (o) opts = *o;
-  if (!x || n < 1 || n >= ((int64_t)1 << 31) || d < 1 || d > 3 || leaf < 1 ||
+  if (!x || n < 1 || n >= ((int64_t)1 << 31) || d < 1 || d > hodlr::kMaxDim || leaf < 1 ||
       leaf > hodlr::kMaxLeaf || !(eps > 0) || !std::isfinite(eps) || !(sigma2 >= 0) ||
       !std::isfinite(sigma2) || bad_theta(theta) || (int)kernel < 0 || (int)kernel > 3 ||
       opts.max_rank < 1 || opts.max_rank > hodlr::kMaxRank || opts.max_nrhs < 1 ||

@@ -14,6 +14,7 @@
 namespace hodlr {
 
 constexpr int kMaxLeaf = 128;      // leaf blocks live in shared memory
+constexpr int kMaxDim = 64;        // largest point dimension d
 constexpr int kMaxRank = 512;      // hard cap on a block's rank (opts.max_rank)
 constexpr int kDefaultMaxRank = 64;  // default opts.max_rank
 constexpr int kSmemRank = 64;      // ranks up to this use the shared-memory node step
@@ -72,7 +73,12 @@ __device__ __forceinline__ double dist(const Pts& p, int i, int j) {
   double b = p.x[p.n + i] - p.x[p.n + j];
   if (p.d == 2) return sqrt(a * a + b * b);
   double e = p.x[2 * p.n + i] - p.x[2 * p.n + j];
-  return sqrt(a * a + b * b + e * e);
+  double s = a * a + b * b + e * e;
+  for (int c = 3; c < p.d; ++c) {
+    double t = p.x[c * p.n + i] - p.x[c * p.n + j];
+    s += t * t;
+  }
+  return sqrt(s);
 }
 
 // Device error word bits (ctx->dflags).

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
     const double sigma2 = a.hyp[kHypSigma2];
     if (tid == 0) bad = 0;
     for (int i = tid; i < p; i += kLeafThreads) {
-      for (int c = 0; c < a.pts.d; ++c) xl[c * kMaxLeaf + i] = a.pts.x[c * a.pts.n + b + i];
+      for (int c = 0; c < a.pts.d && c < 3; ++c) xl[c * kMaxLeaf + i] = a.pts.x[c * a.pts.n + b + i];
     }
     __syncthreads();
     for (int e = tid; e < p * p; e += kLeafThreads) {
@@ -136,9 +136,11 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
         double u = xl[i] - xl[j], v = xl[kMaxLeaf + i] - xl[kMaxLeaf + j];
         if (a.pts.d == 2) {
           r = sqrt(u * u + v * v);
-        } else {
+        } else if (a.pts.d == 3) {
           double w = xl[2 * kMaxLeaf + i] - xl[2 * kMaxLeaf + j];
           r = sqrt(u * u + v * v + w * w);
+        } else {
+          r = dist(a.pts, b + i, b + j);  // d > 3: coordinates from global memory
         }
       }
       double c = cov_r(cov, r);

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
     for (int q = tid; q < 64; q += kT) tab[q] = a.tab[q];
     // coordinates relative to the leaf's first point (keeps small offsets exact)
     for (int i = tid; i < p; i += kT) {
-      for (int c = 0; c < a.d; ++c)
+      for (int c = 0; c < a.d && c < 3; ++c)
         xl[c * kMaxLeaf + i] = ff_from_double(a.x[c * a.n + b + i] - a.x[c * a.n + b]);
     }
     __syncthreads();
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
         if (a.d == 1) {
           r = ff_sub(xl[i], xl[j]);
           if (r.hi < 0.0f) r = ff_neg(r);
-        } else {
+        } else if (a.d <= 3) {
           ff u = ff_sub(xl[i], xl[j]), v = ff_sub(xl[kMaxLeaf + i], xl[kMaxLeaf + j]);
           ff s = ff_add(ff_mul(u, u), ff_mul(v, v));
           if (a.d == 3) {
@@ -121,6 +121,8 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
             s = ff_add(s, ff_mul(w, w));
           }
           r = ff_sqrt(s);
+        } else {
+          r = ff_from_double(dist(Pts{a.x, a.n, a.d}, b + i, b + j));  // d > 3: FP64 distance
         }
         c = cov_ff(a.kind, r, cr, amp, tab);
         if (i == j) c = ff_add(c, s2);

@@ -18,8 +18,12 @@ __device__ __forceinline__ double cross_r(const Pts& pts, int64_t i, const doubl
   if (pts.d == 1) return fabs(a);
   double b = pts.x[pts.n + i] - xt[j * pts.d + 1];
   if (pts.d == 2) return sqrt(a * a + b * b);
-  double e = pts.x[2 * pts.n + i] - xt[j * pts.d + 2];
-  return sqrt(a * a + b * b + e * e);
+  double s = a * a + b * b;
+  for (int c = 2; c < pts.d; ++c) {
+    double e = pts.x[c * pts.n + i] - xt[j * pts.d + c];
+    s += e * e;
+  }
+  return sqrt(s);
 }
 
 // partial[b * kPSlices + s] = sum over the training points of slice s of k(x_i, x*_{j0+b})

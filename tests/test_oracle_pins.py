@@ -346,6 +346,21 @@ def test_hodlr_3d_vs_dense(kern, ell, eps, tol):
     assert rel_residual(x, kern, th, s2, sol, y) <= eps * n * O.kappa(n, 32) / s2
 
 
+@pytest.mark.parametrize("n,d,half", [(600, 8, 1.0), (2000, 32, 3.0)])
+def test_hodlr_high_dim_vs_dense(n, d, half):
+    """High dimension (Sec. 5, the d-dimensional Gaussian tables: C = 2I + exp(-r^2),
+    points in [-h, h]^d). d = 8 in a small cube keeps its blocks at full rank; d = 32 in
+    [-3, 3]^32 has nearly zero off-diagonal blocks and ranks of a few tens."""
+    x = I.uniform_points(n, d, -half, half, 1500 + d)
+    y = I.normal(n, 1501 + d)
+    th, s2 = [1.0 / np.sqrt(2.0), 1.0], 2.0
+    sol_d, ld_d = O.dense_solve(x, "se", th, s2, y)
+    H = O.Hodlr(x, "se", th, s2, 32, 1e-12, max_rank=n)
+    sol = H.factor_solve(y)
+    assert abs(H.logdet() - ld_d) <= 1e-12 * abs(ld_d)
+    np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-10 * np.abs(sol_d).max())
+
+
 def test_hodlr_matvec_matches_dense():
     n = 800
     x, y = I.workload_1d(n, 95)
