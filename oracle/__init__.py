@@ -16,7 +16,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hodlr_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-KERNELS = {"exp": 0, "se": 1, "matern32": 2, "matern52": 3}
+KERNELS = {"exp": 0, "se": 1, "matern32": 2, "matern52": 3, "rq": 4, "imq": 5, "mq": 6,
+           "biharmonic": 7}
+# Kernels whose matrices are indefinite: factor, solve and log |det| with its sign, no
+# log-likelihood.
+INDEFINITE = ("mq", "biharmonic")
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTSPD", 4: "ERANK", 6: "ESTATE"}
 
 _lib = None
@@ -42,8 +46,10 @@ def lib():
         build()
         L = ctypes.CDLL(_LIB)
         L.oracle_num_threads.restype = ctypes.c_int
-        L.oracle_kernel_values.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, ctypes.c_double,
-                                           ctypes.c_double, _dp]
+        L.oracle_kernel_values.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, _dp, _dp]
+        L.oracle_dense_lu_solve.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp,
+                                            ctypes.c_double, _dp, ctypes.c_int, ctypes.c_int64, _dp,
+                                            ctypes.c_int64, _dp, _ip]
         L.oracle_dense_solve.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp,
                                          ctypes.c_double, _dp, ctypes.c_int, ctypes.c_int64, _dp,
                                          ctypes.c_int64, _dp]
@@ -74,6 +80,7 @@ def lib():
         L.oracle_hodlr_factor_solve.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_int,
                                                 ctypes.c_int64]
         L.oracle_hodlr_logdet.argtypes = [ctypes.c_void_p, _dp]
+        L.oracle_hodlr_logdet_sign.argtypes = [ctypes.c_void_p, _ip]
         L.oracle_hodlr_level_logdets.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.oracle_hodlr_loglik.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.oracle_hodlr_matvec.argtypes = [ctypes.c_void_p, _dp, _dp]
@@ -106,10 +113,19 @@ def num_threads() -> int:
     return lib().oracle_num_threads()
 
 
-def kernel_values(kernel: str, r, ell: float, amp: float = 1.0) -> np.ndarray:
+def _theta(theta) -> np.ndarray:
+    """{ell, a} or {ell, a, alpha} (alpha: the rational quadratic's exponent, default 1)."""
+    th = np.ones(3)
+    t = np.asarray(theta, dtype=np.float64).reshape(-1)
+    th[: t.size] = t
+    return th
+
+
+def kernel_values(kernel: str, r, ell: float, amp: float = 1.0, alpha: float = 1.0) -> np.ndarray:
     r = _f64(r)
     out = np.empty_like(r)
-    lib().oracle_kernel_values(KERNELS[kernel], _d(r), r.size, ell, amp, _d(out))
+    th = _theta([ell, amp, alpha])
+    lib().oracle_kernel_values(KERNELS[kernel], _d(r), r.size, _d(th), _d(out))
     return out
 
 
@@ -127,7 +143,7 @@ def dense_solve(x, kernel, theta, sigma2, y):
     Y, one = _cols(y)
     X = np.zeros_like(Y, order="F")
     ld = ctypes.c_double()
-    th = _f64(theta)
+    th = _theta(theta)
     _check(lib().oracle_dense_solve(_d(x), n, d, KERNELS[kernel], _d(th), sigma2, _d(Y), Y.shape[1],
                                     n, _d(X), n, ctypes.byref(ld)), "dense_solve")
     return (X[:, 0] if one else X), ld.value
@@ -141,12 +157,28 @@ def dense_predict(x, kernel, theta, sigma2, y, xtest):
     x = _f64(x).reshape(len(x), -1)
     xt = _f64(xtest).reshape(len(xtest), -1)
     r = np.sqrt(((x[:, None, :] - xt[None, :, :]) ** 2).sum(-1))
-    Ks = kernel_values(kernel, r, theta[0], theta[1])  # n x m
-    alpha, _ = dense_solve(x, kernel, theta, sigma2, y)
-    V, _ = dense_solve(x, kernel, theta, sigma2, np.asfortranarray(Ks))
-    mean = Ks.T @ alpha
-    var = float(kernel_values(kernel, np.zeros(1), theta[0], theta[1])[0]) - (Ks * V).sum(0)
+    th = _theta(theta)
+    Ks = kernel_values(kernel, r, *th)  # n x m
+    w, _ = dense_solve(x, kernel, th, sigma2, y)
+    V, _ = dense_solve(x, kernel, th, sigma2, np.asfortranarray(Ks))
+    mean = Ks.T @ w
+    var = float(kernel_values(kernel, np.zeros(1), *th)[0]) - (Ks * V).sum(0)
     return mean, var
+
+
+def dense_lu_solve(x, kernel, theta, sigma2, y):
+    """O1 for any C (definite or not): (C^-1 y, log |det C|, sign det C) by dense LU with
+    partial pivoting; y (n,) or (n, nrhs)."""
+    x = _f64(x)
+    n, d = (x.shape[0], 1) if x.ndim == 1 else x.shape
+    Y, one = _cols(y)
+    X = np.zeros_like(Y, order="F")
+    ld, sg = ctypes.c_double(), ctypes.c_int()
+    th = _theta(theta)
+    _check(lib().oracle_dense_lu_solve(_d(x), n, d, KERNELS[kernel], _d(th), sigma2, _d(Y),
+                                       Y.shape[1], n, _d(X), n, ctypes.byref(ld),
+                                       ctypes.byref(sg)), "dense_lu_solve")
+    return (X[:, 0] if one else X), ld.value, sg.value
 
 
 def dense_matvec_rows(x, kernel, theta, sigma2, v, rows):
@@ -156,7 +188,7 @@ def dense_matvec_rows(x, kernel, theta, sigma2, v, rows):
     v = _f64(v)
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     out = np.empty(rows.size)
-    th = _f64(theta)
+    th = _theta(theta)
     lib().oracle_dense_matvec_rows(_d(x), n, d, KERNELS[kernel], _d(th), sigma2, _d(v),
                                    rows.ctypes.data_as(_lp), rows.size, _d(out))
     return out
@@ -219,7 +251,7 @@ class Hodlr:
         x = _f64(x)
         self.n, self.d = (x.shape[0], 1) if x.ndim == 1 else x.shape
         st = ctypes.c_int()
-        th = _f64(theta)
+        th = _theta(theta)
         self._h = lib().oracle_hodlr_build(_d(x), self.n, self.d, KERNELS[kernel], _d(th), sigma2,
                                            leaf, eps, max_rank, ctypes.byref(st))
         if not self._h:
@@ -266,6 +298,11 @@ class Hodlr:
     def logdet(self) -> float:
         v = ctypes.c_double()
         _check(lib().oracle_hodlr_logdet(self._h, ctypes.byref(v)), "logdet")
+        return v.value
+
+    def logdet_sign(self) -> int:
+        v = ctypes.c_int()
+        _check(lib().oracle_hodlr_logdet_sign(self._h, ctypes.byref(v)), "logdet_sign")
         return v.value
 
     def level_logdets(self):

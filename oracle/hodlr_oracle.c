@@ -29,7 +29,8 @@
 #include <omp.h>
 #endif
 
-enum { ORC_EXP = 0, ORC_SE = 1, ORC_M32 = 2, ORC_M52 = 3 };
+enum { ORC_EXP = 0, ORC_SE = 1, ORC_M32 = 2, ORC_M52 = 3, ORC_RQ = 4, ORC_IMQ = 5, ORC_MQ = 6,
+       ORC_BH = 7 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENOTSPD = 3, ORC_ERANK = 4, ORC_ESTATE = 6 };
 /* Largest point dimension accepted (the high-dimension experiments of Sec. 5 go to 64). */
 #define ORC_MAX_D 64
@@ -44,11 +45,33 @@ int oracle_num_threads(void) {
 
 /* ------------------------------------------------------------------------------------
  * Covariance functions. k(r) = a f(r / ell), r the Euclidean distance (Table 1 with a
- * length scale ell and amplitude a; Matern nu = 3/2 and 5/2 in their closed forms).
+ * length scale ell and amplitude a; Matern nu = 3/2 and 5/2 in their closed forms), and
+ * the radial functions of Sec. 5 with the distance in units of ell: rational quadratic
+ * (1 + r^2)^-alpha (Table 1), inverse multiquadric 1/sqrt(1 + r^2), multiquadric
+ * sqrt(1 + r^2) (the form of Sec. 5's text; its table caption prints sqrt(1 + r)), and
+ * biharmonic r^2 log r (0 at r = 0, its limit). The last two give indefinite matrices.
  * ---------------------------------------------------------------------------------- */
+typedef struct {
+  int kind;
+  double ell, amp, alpha; /* alpha: the rational quadratic's exponent */
+} orc_cov;
+
+/* theta = {ell, a} (and alpha third for the rational quadratic). */
+static orc_cov orc_cov_make(int kind, const double* theta) {
+  orc_cov k;
+  k.kind = kind;
+  k.ell = theta[0];
+  k.amp = theta[1];
+  k.alpha = kind == ORC_RQ ? theta[2] : 1.0;
+  return k;
+}
+
+static int orc_indefinite(int kind) { return kind == ORC_MQ || kind == ORC_BH; }
+
 /* r is the distance, r2 its square (both passed so neither is recomputed from the other). */
-static double orc_kernel(int kind, double r, double r2, double ell, double amp) {
-  switch (kind) {
+static double orc_kernel(const orc_cov* k, double r, double r2) {
+  double ell = k->ell, amp = k->amp;
+  switch (k->kind) {
     case ORC_EXP: return amp * exp(-r / ell);
     case ORC_SE: return amp * exp(-0.5 * r2 / (ell * ell));
     case ORC_M32: {
@@ -59,35 +82,42 @@ static double orc_kernel(int kind, double r, double r2, double ell, double amp) 
       double s = sqrt(5.0) * r / ell;
       return amp * (1.0 + s + s * s / 3.0) * exp(-s);
     }
+    case ORC_RQ: return amp * pow(1.0 + r2 / (ell * ell), -k->alpha);
+    case ORC_IMQ: return amp / sqrt(1.0 + r2 / (ell * ell));
+    case ORC_MQ: return amp * sqrt(1.0 + r2 / (ell * ell));
+    case ORC_BH: {
+      if (!(r > 0.0)) return 0.0;
+      double t = r / ell;
+      return amp * t * t * log(t);
+    }
   }
   return NAN;
 }
 
 /* k(x_i, x_j): in 1-D r = |x_i - x_j|, otherwise r = sqrt(sum of squared differences). */
-static double orc_kij(const double* x, int d, int kind, double ell, double amp, int64_t i,
-                      int64_t j) {
+static double orc_kij(const double* x, int d, const orc_cov* k, int64_t i, int64_t j) {
   if (d == 1) {
     double r = fabs(x[i] - x[j]);
-    return orc_kernel(kind, r, r * r, ell, amp);
+    return orc_kernel(k, r, r * r);
   }
   double s = 0.0;
   for (int c = 0; c < d; ++c) {
     double t = x[i * d + c] - x[j * d + c];
     s += t * t;
   }
-  return orc_kernel(kind, sqrt(s), s, ell, amp);
+  return orc_kernel(k, sqrt(s), s);
 }
 
 /* Entry of C = sigma^2 I + K (Sec. 5, C_ij = sigma^2 delta_ij + k(r_i, r_j)). */
-static double orc_entry(const double* x, int d, int kind, double ell, double amp, double sigma2,
-                        int64_t i, int64_t j) {
-  double v = orc_kij(x, d, kind, ell, amp, i, j);
+static double orc_entry(const double* x, int d, const orc_cov* k, double sigma2, int64_t i,
+                        int64_t j) {
+  double v = orc_kij(x, d, k, i, j);
   return i == j ? v + sigma2 : v;
 }
 
-void oracle_kernel_values(int kind, const double* r, int64_t m, double ell, double amp,
-                          double* out) {
-  for (int64_t i = 0; i < m; ++i) out[i] = orc_kernel(kind, r[i], r[i] * r[i], ell, amp);
+void oracle_kernel_values(int kind, const double* r, int64_t m, const double* theta, double* out) {
+  orc_cov k = orc_cov_make(kind, theta);
+  for (int64_t i = 0; i < m; ++i) out[i] = orc_kernel(&k, r[i], r[i] * r[i]);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -111,13 +141,13 @@ int oracle_dense_solve(const double* x, int64_t n, int d, int kind, const double
                        double sigma2, const double* y, int nrhs, int64_t ldy, double* xout,
                        int64_t ldx, double* logdet) {
   if (n < 1 || d < 1) return ORC_EINVAL;
-  double ell = theta[0], amp = theta[1];
+  orc_cov k = orc_cov_make(kind, theta);
   double* L = (double*)malloc(sizeof(double) * n * n);
   if (!L) return ORC_ENOMEM;
   /* lower triangle of C, row-major */
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t i = 0; i < n; ++i)
-    for (int64_t j = 0; j <= i; ++j) L[i * n + j] = orc_entry(x, d, kind, ell, amp, sigma2, i, j);
+    for (int64_t j = 0; j <= i; ++j) L[i * n + j] = orc_entry(x, d, &k, sigma2, i, j);
   int bad = 0;
   for (int64_t j = 0; j < n && !bad; ++j) {
     double djj = L[j * n + j] - dot4(L + j * n, L + j * n, j);
@@ -152,13 +182,13 @@ int oracle_dense_solve(const double* x, int64_t n, int d, int kind, const double
 void oracle_dense_matvec_rows(const double* x, int64_t n, int d, int kind, const double* theta,
                               double sigma2, const double* v, const int64_t* rows, int64_t nrows,
                               double* out) {
-  double ell = theta[0], amp = theta[1];
+  orc_cov k = orc_cov_make(kind, theta);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t t = 0; t < nrows; ++t) {
     int64_t i = rows[t];
     double s = 0.0, c = 0.0;
     for (int64_t j = 0; j < n; ++j) {
-      double term = orc_entry(x, d, kind, ell, amp, sigma2, i, j) * v[j];
+      double term = orc_entry(x, d, &k, sigma2, i, j) * v[j];
       double u = s + term;
       if (fabs(s) >= fabs(term)) c += (s - u) + term; else c += (term - u) + s;
       s = u;
@@ -421,13 +451,44 @@ void oracle_lu_solve_dense(const double* A, int m, const double* b, double* x) {
   free(piv);
 }
 
+/* O1 for any C, positive definite or not: the dense matrix, LU with partial pivoting,
+ * x = C^-1 y, log |det C| and its sign. Limited to n < 46341 (m^2 in int). */
+int oracle_dense_lu_solve(const double* x, int64_t n, int d, int kind, const double* theta,
+                          double sigma2, const double* y, int nrhs, int64_t ldy, double* xout,
+                          int64_t ldx, double* logabsdet, int* sign) {
+  if (n < 1 || d < 1 || n > 46340) return ORC_EINVAL;
+  orc_cov k = orc_cov_make(kind, theta);
+  int m = (int)n;
+  double* A = (double*)malloc(sizeof(double) * n * n);
+  int* piv = (int*)malloc(sizeof(int) * n);
+  if (!A || !piv) { free(A); free(piv); return ORC_ENOMEM; }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) A[i * n + j] = orc_entry(x, d, &k, sigma2, i, j);
+  int sg = 1;
+  double ld = orc_lu(A, m, piv, &sg);
+  *logabsdet = ld;
+  *sign = sg;
+  if (sg == 0) { free(A); free(piv); return ORC_ENOTSPD; }
+  for (int c = 0; c < nrhs; ++c) {
+    double* xo = xout + (int64_t)c * ldx;
+    memcpy(xo, y + (int64_t)c * ldy, sizeof(double) * n);
+    orc_lu_solve(A, m, piv, xo, 1);
+  }
+  free(A);
+  free(piv);
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------------------
  * O2: the HODLR method.
  * ---------------------------------------------------------------------------------- */
 typedef struct {
   int64_t n;
   int d, kind, leaf, max_rank, kappa;
-  double ell, amp, sigma2, eps;
+  orc_cov cov;
+  double sigma2, eps;
+  int logdet_sign; /* sign of det C (indefinite kernels; +1 otherwise) */
   double* xs;      /* sorted points, n x d row-major */
   int64_t* perm;   /* sorted row i is original point perm[i] */
   int64_t* nb;     /* node begin, node id (j, k) -> (1 << j) - 1 + k */
@@ -547,7 +608,7 @@ static int orc_aca(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int64
   *ok = 0;
   while (k < rmax) {
     for (int64_t b = 0; b < mr; ++b) {
-      double v = orc_kij(H->xs, H->d, H->kind, H->ell, H->amp, bl + i, br + b);
+      double v = orc_kij(H->xs, H->d, &H->cov, bl + i, br + b);
       for (int l = 0; l < k; ++l) v -= U[l * ml + i] * V[l * mr + b];
       row[b] = v;
     }
@@ -565,7 +626,7 @@ static int orc_aca(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int64
     }
     for (int64_t b = 0; b < mr; ++b) row[b] /= delta;
     for (int64_t a = 0; a < ml; ++a) {
-      double u = orc_kij(H->xs, H->d, H->kind, H->ell, H->amp, bl + a, br + j);
+      double u = orc_kij(H->xs, H->d, &H->cov, bl + a, br + j);
       for (int l = 0; l < k; ++l) u -= U[l * ml + a] * V[l * mr + j];
       col[a] = u;
     }
@@ -600,13 +661,14 @@ static int64_t orc_nid(int j, int64_t k) { return ((int64_t)1 << j) - 1 + k; }
 
 void* oracle_hodlr_build(const double* x, int64_t n, int d, int kind, const double* theta,
                          double sigma2, int leaf, double eps, int max_rank, int* status) {
-  if (n < 1 || d < 1 || d > ORC_MAX_D || leaf < 1 || !(eps > 0) || sigma2 < 0 || max_rank < 1) {
+  if (n < 1 || d < 1 || d > ORC_MAX_D || leaf < 1 || !(eps > 0) || sigma2 < 0 || max_rank < 1 ||
+      kind < 0 || kind > ORC_BH || (kind == ORC_RQ && !(theta[2] > 0))) {
     *status = ORC_EINVAL;
     return NULL;
   }
   orc_hodlr* H = (orc_hodlr*)calloc(1, sizeof(orc_hodlr));
   H->n = n; H->d = d; H->kind = kind; H->leaf = leaf; H->max_rank = max_rank;
-  H->ell = theta[0]; H->amp = theta[1]; H->sigma2 = sigma2; H->eps = eps;
+  H->cov = orc_cov_make(kind, theta); H->sigma2 = sigma2; H->eps = eps;
   H->kappa = oracle_kappa(n, leaf);
   int kap = H->kappa;
   H->perm = (int64_t*)malloc(sizeof(int64_t) * n);
@@ -718,7 +780,10 @@ static void orc_leaf_apply(orc_hodlr* H, int64_t k, double* P, int64_t ld, int n
  * and its SMW inverse is applied to every coarser ancestor's copy on the node's rows.
  * If y != NULL (sorted order, column-major, nrhs columns, stride n) the same inverses are
  * applied to it, so on return it holds C^-1 y. log det C = sum of leaf and node log dets
- * (Sec. 4: Sylvester's theorem gives det(I + L W) = det(I + W L) = det M). */
+ * (Sec. 4: Sylvester's theorem gives det(I + L W) = det(I + W L) = det M). For a positive
+ * definite C every factor has a positive determinant and a non-positive one is an error;
+ * for the indefinite kernels (multiquadric, biharmonic) the factors' signs multiply into
+ * the sign of det C and only a zero determinant is an error. */
 static int orc_factor_impl(orc_hodlr* H, double* y, int nrhs) {
   int kap = H->kappa;
   int64_t nint = ((int64_t)1 << kap) - 1, nleaf = (int64_t)1 << kap;
@@ -738,20 +803,22 @@ static int orc_factor_impl(orc_hodlr* H, double* y, int nrhs) {
   H->Mlu = (double**)calloc((size_t)(nint > 0 ? nint : 1), sizeof(double*));
   H->Mpiv = (int**)calloc((size_t)(nint > 0 ? nint : 1), sizeof(int*));
   H->nodelogdet = (double*)calloc((size_t)(nint > 0 ? nint : 1), sizeof(double));
-  int bad = 0;
+  int bad = 0, nneg = 0;
+  const int indef = orc_indefinite(H->kind);
   /* Leaves: LU of the dense diagonal blocks of C, then K_kappa^-1 on the ancestors' rows. */
-#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad) reduction(+ : nneg)
   for (int64_t k = 0; k < nleaf; ++k) {
     int64_t id = orc_nid(kap, k), b = H->nb[id];
     int s = (int)H->ns[id];
     double* A = (double*)malloc(sizeof(double) * (s > 0 ? s * s : 1));
     for (int a = 0; a < s; ++a)
       for (int c = 0; c < s; ++c)
-        A[a * s + c] = orc_entry(H->xs, H->d, H->kind, H->ell, H->amp, H->sigma2, b + a, b + c);
+        A[a * s + c] = orc_entry(H->xs, H->d, &H->cov, H->sigma2, b + a, b + c);
     int* piv = (int*)malloc(sizeof(int) * (s > 0 ? s : 1));
     int sg = 1;
     double ld = s > 0 ? orc_lu(A, s, piv, &sg) : 0.0;
-    if (sg <= 0) bad = 1;
+    if (sg == 0 || (sg < 0 && !indef)) bad = 1;
+    if (sg < 0) nneg += 1;
     H->leafLU[k] = A;
     H->leafpiv[k] = piv;
     H->leaflogdet[k] = ld;
@@ -765,7 +832,7 @@ static int orc_factor_impl(orc_hodlr* H, double* y, int nrhs) {
   }
   /* Levels, finest internal level first. */
   for (int j = kap - 1; j >= 0 && !bad; --j) {
-#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad) reduction(+ : nneg)
     for (int64_t k = 0; k < ((int64_t)1 << j); ++k) {
       int64_t id = orc_nid(j, k);
       int r = H->rank[id];
@@ -785,7 +852,8 @@ static int orc_factor_impl(orc_hodlr* H, double* y, int nrhs) {
         }
       int sg = 1;
       double ld = m2 > 0 ? orc_lu(M, m2, piv, &sg) : 0.0;
-      if (sg <= 0) bad = 1;
+      if (sg == 0 || (sg < 0 && !indef)) bad = 1;
+      if (sg < 0) nneg += 1;
       H->Mlu[id] = M;
       H->Mpiv[id] = piv;
       H->nodelogdet[id] = ld;
@@ -804,6 +872,7 @@ static int orc_factor_impl(orc_hodlr* H, double* y, int nrhs) {
   for (int64_t k = 0; k < nleaf; ++k) sl += H->leaflogdet[k];
   for (int64_t id = 0; id < nint; ++id) sn += H->nodelogdet[id];
   H->logdet = sl + sn;
+  H->logdet_sign = (nneg & 1) ? -1 : 1;
   H->factored = 1;
   return ORC_OK;
 }
@@ -860,10 +929,19 @@ int oracle_hodlr_factor_solve(void* h, const double* y, double* x, int nrhs, int
   return st;
 }
 
+/* log |det C| (log det C for a positive definite C). */
 int oracle_hodlr_logdet(void* h, double* out) {
   orc_hodlr* H = (orc_hodlr*)h;
   if (!H->factored) return ORC_ESTATE;
   *out = H->logdet;
+  return ORC_OK;
+}
+
+/* Sign of det C: the product of the leaf and node determinants' signs. */
+int oracle_hodlr_logdet_sign(void* h, int* out) {
+  orc_hodlr* H = (orc_hodlr*)h;
+  if (!H->factored) return ORC_ESTATE;
+  *out = H->logdet_sign;
   return ORC_OK;
 }
 
@@ -878,6 +956,7 @@ void oracle_hodlr_level_logdets(void* h, double* leaf_out, double* node_out) {
  * -1/2 y^T C^-1 y - 1/2 log det C - n/2 log(2 pi). */
 int oracle_hodlr_loglik(void* h, const double* y, double* out) {
   orc_hodlr* H = (orc_hodlr*)h;
+  if (orc_indefinite(H->kind)) return ORC_EINVAL; /* not a covariance: no Gaussian density */
   double* x = (double*)malloc(sizeof(double) * H->n);
   int st = H->factored ? oracle_hodlr_solve(h, y, x, 1, H->n)
                        : oracle_hodlr_factor_solve(h, y, x, 1, H->n);
@@ -903,7 +982,7 @@ void oracle_hodlr_matvec(void* h, const double* v, double* out) {
     for (int64_t a = 0; a < s; ++a) {
       double t = 0.0;
       for (int64_t c = 0; c < s; ++c)
-        t += orc_entry(H->xs, H->d, H->kind, H->ell, H->amp, H->sigma2, b + a, b + c) * w[b + c];
+        t += orc_entry(H->xs, H->d, &H->cov, H->sigma2, b + a, b + c) * w[b + c];
       o[b + a] += t;
     }
   }

@@ -31,7 +31,8 @@ def dense_C(x, kern, theta, s2):
     if x.ndim == 1:
         x = x[:, None]
     r = np.sqrt(((x[:, None, :] - x[None, :, :]) ** 2).sum(-1))
-    K = O.kernel_values(kern, r.ravel(), theta[0], theta[1]).reshape(r.shape)
+    th = list(theta) + [1.0] * (3 - len(theta))
+    K = O.kernel_values(kern, r.ravel(), *th).reshape(r.shape)
     return K + s2 * np.eye(len(x))
 
 
@@ -74,6 +75,69 @@ def test_se_special_values():
     # k(ell) = exp(-1/2), k(0) = a, k(2 ell) = exp(-2)
     v = O.kernel_values("se", np.array([0.0, 0.3, 0.6]), 0.3, 1.7)
     np.testing.assert_allclose(v, 1.7 * np.array([1.0, np.exp(-0.5), np.exp(-2.0)]), rtol=1e-15)
+
+
+def test_radial_kernels_special_values():
+    """Sec. 5's radial functions with the distance in units of ell (a = 1.3, ell = 0.4)."""
+    a, ell = 1.3, 0.4
+    e = np.e
+    # multiquadric sqrt(1 + t^2): 1 at 0, 2 at t = sqrt(3)
+    np.testing.assert_allclose(O.kernel_values("mq", np.array([0.0, ell * np.sqrt(3.0)]), ell, a),
+                               [a, 2 * a], rtol=1e-15)
+    # inverse multiquadric 1/sqrt(1 + t^2): 1/2 at t = sqrt(3)
+    np.testing.assert_allclose(O.kernel_values("imq", np.array([0.0, ell * np.sqrt(3.0)]), ell, a),
+                               [a, a / 2], rtol=1e-15)
+    # biharmonic t^2 log t: 0 at 0 and 1, e^2 at e, -1/e^2 at 1/e, 4 log 2 at 2
+    r = ell * np.array([0.0, 1.0, e, 1 / e, 2.0])
+    np.testing.assert_allclose(O.kernel_values("biharmonic", r, ell, a),
+                               a * np.array([0.0, 0.0, e * e, -1 / e ** 2, 4 * np.log(2.0)]),
+                               rtol=1e-14, atol=1e-16)
+    # rational quadratic (1 + t^2)^-alpha: 2^-alpha at t = 1, 4^-2.5 = 1/32 at t = sqrt(3)
+    np.testing.assert_allclose(O.kernel_values("rq", np.array([0.0, ell, ell * np.sqrt(3.0)]), ell,
+                                               a, 2.5),
+                               a * np.array([1.0, 2 ** -2.5, 1 / 32]), rtol=1e-15)
+
+
+def test_radial_kernel_identities():
+    r = np.linspace(0.0, 5.0, 301)
+    ell, a = 0.7, 1.1
+    mq = O.kernel_values("mq", r, ell, a)
+    imq = O.kernel_values("imq", r, ell, a)
+    np.testing.assert_allclose(mq * imq, a * a, rtol=1e-15)
+    # the inverse multiquadric is the rational quadratic with alpha = 1/2
+    np.testing.assert_allclose(O.kernel_values("rq", r, ell, a, 0.5), imq, rtol=1e-15)
+    # (1 + r^2 / (2 alpha l^2))^-alpha -> exp(-r^2 / (2 l^2)) as alpha grows (relative
+    # error about r^4 / (8 alpha l^4), below 2e-7 for r <= 3)
+    l0, big = 0.9, 1e8
+    r3 = r[r <= 3.0]
+    rq = O.kernel_values("rq", r3, l0 * np.sqrt(2 * big), a, big)
+    np.testing.assert_allclose(rq, O.kernel_values("se", r3, l0, a), rtol=3e-7)
+
+
+def test_radial_kernel_matrix_signatures():
+    """Eigenvalue structure fixed by the theory of radial functions: a multiquadric matrix
+    of distinct points has exactly one positive eigenvalue (Micchelli 1986); the biharmonic
+    r^2 log r is conditionally positive definite of order 2, so at most two of its
+    eigenvalues are non-positive; the inverse multiquadric matrix is positive definite.
+    Smooth kernels have eigenvalues that decay to the rounding level, so signs are counted
+    above 1e-10 of the largest magnitude (LAPACK's eigvalsh)."""
+    x = np.sort(I.uniform_points(300, 1, -3.0, 3.0, 41)[:, 0])
+    r = np.abs(x[:, None] - x[None, :])
+
+    def ev(kern, rr):
+        e = np.linalg.eigvalsh(O.kernel_values(kern, rr.ravel(), 1.0, 1.0).reshape(rr.shape))
+        return e / np.abs(e).max()
+
+    e_mq = ev("mq", r)
+    assert (e_mq > 1e-10).sum() == 1 and e_mq.max() == 1.0
+    assert (e_mq < -1e-10).sum() >= 5
+    e_bh = ev("biharmonic", r)
+    assert (e_bh < -1e-10).sum() <= 2 and (e_bh > 1e-10).sum() >= 5
+    assert np.linalg.eigvalsh(O.kernel_values("imq", r.ravel(), 1.0, 1.0).reshape(r.shape)).min() > -1e-12
+    x2 = I.uniform_points(200, 2, -3.0, 3.0, 42)
+    r2 = np.sqrt(((x2[:, None, :] - x2[None, :, :]) ** 2).sum(-1))
+    e2 = ev("mq", r2)
+    assert (e2 > 1e-10).sum() == 1 and (e2 < -1e-10).sum() >= 20
 
 
 # ---------------------------------------------------------------- O1 dense --------------
@@ -359,6 +423,55 @@ def test_hodlr_high_dim_vs_dense(n, d, half):
     sol = H.factor_solve(y)
     assert abs(H.logdet() - ld_d) <= 1e-12 * abs(ld_d)
     np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-10 * np.abs(sol_d).max())
+
+
+@pytest.mark.parametrize("kern,d,s2", [("mq", 1, 1.0), ("biharmonic", 1, 2.0), ("mq", 2, 1.0)])
+def test_dense_lu_matches_lapack(kern, d, s2):
+    """O1 for indefinite C (Sec. 5's multiquadric C = I + K and biharmonic C = 2I + K)
+    against LAPACK's LU (numpy slogdet and solve)."""
+    n = 700
+    x = I.uniform_points(n, d, -3.0, 3.0, 60 + d)
+    y = I.normal(n, 61)
+    sol, ld, sg = O.dense_lu_solve(x, kern, [1.0, 1.0], s2, y)
+    C = dense_C(x, kern, [1.0, 1.0], s2)
+    sg_np, ld_np = np.linalg.slogdet(C)
+    assert sg == int(sg_np) and abs(ld - ld_np) <= 1e-12 * abs(ld_np)
+    ref = np.linalg.solve(C, y)
+    np.testing.assert_allclose(sol, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+    assert np.linalg.eigvalsh(C).min() < 0  # the case is really indefinite
+
+
+@pytest.mark.parametrize("kern,d,s2,eps", [("mq", 1, 1.0, 1e-12), ("biharmonic", 1, 2.0, 1e-12),
+                                           ("mq", 2, 1.0, 1e-14), ("biharmonic", 2, 2.0, 1e-12)])
+def test_hodlr_indefinite_vs_dense(kern, d, s2, eps):
+    """The same factorization on an indefinite C: leaf and node LU determinants may be
+    negative, their signs multiply into sign det C (Sec. 4's product of determinants).
+    The 2-D multiquadric C has cond ~ 9e5 (smallest |eigenvalue| 0.008), which amplifies
+    the compression error (5.7e-10 relative in log |det| at eps = 1e-12, 5.7e-12 at 1e-14);
+    it runs at eps = 1e-14."""
+    n = 2000
+    x = I.uniform_points(n, d, -3.0, 3.0, 70 + d)
+    y = I.normal(n, 71)
+    sol_d, ld_d, sg_d = O.dense_lu_solve(x, kern, [1.0, 1.0], s2, y)
+    H = O.Hodlr(x, kern, [1.0, 1.0], s2, 32, eps, max_rank=1000)
+    sol = H.factor_solve(y)
+    assert H.logdet_sign() == sg_d
+    assert abs(H.logdet() - ld_d) <= 1e-10 * abs(ld_d)
+    np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-8 * np.abs(sol_d).max())
+    with pytest.raises(O.OracleError):
+        H.loglik(y)  # not a covariance: no log-likelihood
+
+
+@pytest.mark.parametrize("kern,theta", [("imq", [0.5, 1.0]), ("rq", [0.3, 1.2, 2.0])])
+def test_hodlr_positive_radial_vs_dense(kern, theta):
+    n = 2000
+    x, y = I.workload_1d(n, 75, lo=-3.0, hi=3.0)
+    sol_d, ld_d = O.dense_solve(x, kern, theta, 1.0, y)
+    H = O.Hodlr(x, kern, theta, 1.0, 32, 1e-12)
+    sol = H.factor_solve(y)
+    assert H.logdet_sign() == 1
+    assert abs(H.logdet() - ld_d) <= 1e-11 * abs(ld_d)
+    np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-9 * np.abs(sol_d).max())
 
 
 def test_hodlr_matvec_matches_dense():
