@@ -48,12 +48,19 @@ typedef enum {
 } hodlr_status;
 
 /* Covariance functions k(r) = a f(r / ell), theta = {ell, a} (Table 1 with a length scale
- * ell and amplitude a; Matern nu = 3/2 and 5/2 in closed form; nu = 1/2 is HODLR_K_EXP). */
+ * ell and amplitude a; Matern nu = 3/2 and 5/2 in closed form; nu = 1/2 is HODLR_K_EXP),
+ * and the radial functions of Sec. 5 with t = r / ell. The multiquadric and biharmonic
+ * give indefinite matrices: they factor with LU leaves and a signed log |det|
+ * (hodlr_logdet_signed), need precision 0, and have no log-likelihood (EINVAL). */
 typedef enum {
   HODLR_K_EXP = 0,      /* a exp(-r/ell)                              (Ornstein-Uhlenbeck) */
   HODLR_K_SE = 1,       /* a exp(-r^2/(2 ell^2))                      (Gaussian)           */
   HODLR_K_MATERN32 = 2, /* a (1 + sqrt3 r/ell) exp(-sqrt3 r/ell)                           */
-  HODLR_K_MATERN52 = 3  /* a (1 + sqrt5 r/ell + 5r^2/(3ell^2)) exp(-sqrt5 r/ell)           */
+  HODLR_K_MATERN52 = 3, /* a (1 + sqrt5 r/ell + 5r^2/(3ell^2)) exp(-sqrt5 r/ell)           */
+  HODLR_K_RQ = 4,       /* a (1 + t^2)^-alpha, alpha = opts.rq_alpha   (rational quadratic)*/
+  HODLR_K_IMQ = 5,      /* a / sqrt(1 + t^2)                     (inverse multiquadric)    */
+  HODLR_K_MQ = 6,       /* a sqrt(1 + t^2)             (multiquadric; indefinite C)        */
+  HODLR_K_BIHARMONIC = 7 /* a t^2 log t, 0 at t = 0    (thin-plate spline; indefinite C)   */
 } hodlr_kernel;
 
 typedef struct {
@@ -78,6 +85,7 @@ typedef struct {
                        /*    and solves under stream capture take exactly refine_maxit     */
                        /*    corrections (no host check of the residual).                  */
   void* stream;        /* cudaStream_t for all device work; NULL = legacy default stream  */
+  double rq_alpha;     /* exponent alpha > 0 of HODLR_K_RQ, default 1                      */
 } hodlr_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -125,13 +133,20 @@ hodlr_status hodlr_solve(hodlr_ctx* ctx, const double* y, double* x, int nrhs, i
 
 /* log det C = sum of the leaf log dets and of log det(I + W L) over all nodes (Sec. 4,
  * Sylvester's theorem and the product of block determinants), summed in a fixed order.
- * logdet is a host or device pointer to one double. Errors: ESTATE, ENOTSPD, ECUDA. */
+ * logdet is a host or device pointer to one double; for the indefinite kernels it receives
+ * log |det C|. Errors: ESTATE, ENOTSPD, ECUDA. */
 hodlr_status hodlr_logdet(hodlr_ctx* ctx, double* logdet);
+
+/* log |det C| and its sign (+1 or -1; the product of the signs of the leaf and node
+ * determinants, Sec. 4). For the positive definite kernels the sign is +1 and logabsdet
+ * equals hodlr_logdet. logabsdet: host or device pointer; sign: host pointer.
+ * Errors: ESTATE (not factored), EINVAL, ECUDA. */
+hodlr_status hodlr_logdet_signed(hodlr_ctx* ctx, double* logabsdet, int* sign);
 
 /* Gaussian log-likelihood of y (length n): -y^T C^-1 y / 2 - log det C / 2 - n log(2 pi) / 2
  * (Sec. 1, Eq. 1, with the normalising constant). If the context is not yet factored the
  * solve is fused into the factorization. out: host or device pointer to one double.
- * Errors: ENOTSPD, ECUDA. */
+ * Errors: ENOTSPD, EINVAL (an indefinite kernel: C is not a covariance), ECUDA. */
 hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out);
 
 /* Presized compression (no host synchronisation): fix the padded rank of every level,
@@ -141,11 +156,14 @@ hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out);
  * factorizations skip their pivot check. A block whose ACA needs more than its level's
  * rank, or does not converge, sets bit 2 of the device flags (its result is then not
  * trustworthy: re-run that setting in adaptive mode); a non-positive pivot sets bit 1.
- * level_ranks = NULL returns to adaptive mode. Errors: EINVAL, ENOMEM, ECUDA. */
+ * level_ranks = NULL returns to adaptive mode. Not for the indefinite kernels (EINVAL).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
 hodlr_status hodlr_presize(hodlr_ctx* ctx, const int32_t* level_ranks, int nlevels);
 
 /* Device flags accumulated since the last read (bit 1: a leaf pivot or node determinant
- * was not positive; bit 2: a presized rank was exceeded or a block did not converge), into
+ * was not positive, or for an indefinite kernel was zero; bit 2: a presized rank was
+ * exceeded or a block did not converge; bit 8: odd number of negative block determinants
+ * of an indefinite kernel, i.e. det C < 0), into
  * *flags (host); clears them. Synchronises opts.stream. */
 hodlr_status hodlr_status_flags(hodlr_ctx* ctx, int32_t* flags);
 

@@ -60,10 +60,10 @@ struct AcaArgs {
 // evaluation of the covariance from the FP64 distance.
 template <bool kFF>
 __device__ __forceinline__ double block_entry(const AcaArgs& a, const Cov& cov, int i, int j,
-                                              const ff* tab, ff cr, ff amp) {
+                                              const ff* tab, const CovFF& cf) {
   double r = dist(a.pts, i, j);
   if (!kFF) return cov_r(cov, r);
-  return ff_to_double(cov_ff(a.kind, ff_from_double(r), cr, amp, tab));
+  return ff_to_double(cov_ff(cf, ff_from_double(r), tab));
 }
 
 // The same entry as a double-float (mixed form), for i in the left and j in the right
@@ -72,7 +72,7 @@ __device__ __forceinline__ double block_entry(const AcaArgs& a, const Cov& cov, 
 // <= 0 and the right child's >= 0, so r = x_j - x_i is a same-sign double-float sum whose
 // error is relative to r itself, also for the closest pairs across the split; no FP64.
 __device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int lev, int i, int j,
-                                            const ff* tab, ff cr, ff amp) {
+                                            const ff* tab, const CovFF& cf) {
   const int64_t n = a.pts.n;
   const ff* xr = a.xrel + (int64_t)lev * a.pts.d * n;
   ff r;
@@ -88,7 +88,7 @@ __device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int lev, int i, i
     }
     r = ff_sqrt(s);
   }
-  return cov_ff(a.kind, r, cr, amp, tab);
+  return cov_ff(cf, r, tab);
 }
 
 __device__ __forceinline__ int level_of(int id) { return 31 - __clz(id + 1); }
@@ -188,11 +188,10 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   __shared__ double wv[kAcaThreads / 32];
   __shared__ int wi[kAcaThreads / 32];
   const Cov cov = cov_from(a.kind, a.hyp);
-  ff cr = {0, 0}, amp = {0, 0};
+  CovFF cf{};
   if (kFF) {
     for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
-    cr = ff_from_double(a.hyp[kHypScale]);
-    amp = ff_from_double(cov.amp);
+    cf = make_cov_ff(a.kind, a.hyp[kHypScale], cov.amp, cov.alpha);
   }
   int k = a.rank[id], i = a.row[id];
   int bl = a.nb[2 * id + 1], br = a.nb[2 * id + 2], mr = a.ns[2 * id + 2];
@@ -210,7 +209,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
     for (int q = 0; q < kPer; ++q) {
       int b = start + q * kAcaThreads + threadIdx.x;
       if (b < mr) {
-        double v = block_entry<false>(a, cov, bl + i, br + b, tab, cr, amp);
+        double v = block_entry<false>(a, cov, bl + i, br + b, tab, cf);
         for (int l = 0; l < k; ++l) v -= uik[l] * raw[l * n + br + b];
         raw[(int64_t)k * n + br + b] = v;
         amax_merge(bv, bi, v, b);
@@ -231,7 +230,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
     for (int q = 0; q < kPer; ++q) {
       int b = start + q * kAcaThreads + threadIdx.x;
       if (b < mr) {
-        ff v = block_entry_ff(a, level_of(id), bl + i, br + b, tab, cr, amp);
+        ff v = block_entry_ff(a, level_of(id), bl + i, br + b, tab, cf);
         for (int l = 0; l < k; ++l) v = ff_fms(v, uik[l], rawf[l * n + br + b]);
         rawf[(int64_t)k * n + br + b] = v;
         amax_merge_f(bv, bi, v.hi, b);
@@ -342,12 +341,11 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   double* red = dsm + a.max_rank;
   int* used = reinterpret_cast<int*>(red + (int64_t)nval * kW);
   __shared__ ff tab[64];
-  ff cr = {0, 0}, amp = {0, 0};
+  CovFF cf{};
   const Cov cov = cov_from(a.kind, a.hyp);
   if (kFF) {
     for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
-    cr = ff_from_double(a.hyp[kHypScale]);
-    amp = ff_from_double(cov.amp);
+    cf = make_cov_ff(a.kind, a.hyp[kHypScale], cov.amp, cov.alpha);
   }
   __shared__ double wv[kAcaThreads / 32];
   __shared__ int wi[kAcaThreads / 32];
@@ -375,7 +373,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
       uu[q] = 0.0;
       vv[q] = 0.0;
       if (t < ml) {
-        double u = block_entry<false>(a, cov, bl + t, br + j, tab, cr, amp);
+        double u = block_entry<false>(a, cov, bl + t, br + j, tab, cf);
         for (int l = 0; l < k; ++l) u -= raw[l * n + bl + t] * vjk[l];
         raw[(int64_t)k * n + bl + t] = u;
         uu[q] = u;
@@ -429,7 +427,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
       uu[q] = 0.0f;
       vv[q] = 0.0f;
       if (t < ml) {
-        ff u = block_entry_ff(a, level_of(id), bl + t, br + j, tab, cr, amp);
+        ff u = block_entry_ff(a, level_of(id), bl + t, br + j, tab, cf);
         for (int l = 0; l < k; ++l) u = ff_fms(u, rawf[l * n + bl + t], vjk[l]);
         rawf[(int64_t)k * n + bl + t] = u;
         uu[q] = u.hi;
@@ -523,7 +521,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row_small(AcaArgs a, int it
     for (int q = 0; q < kSmallPer; ++q) {
       int b = q * 32 + lane;
       if (b < mr) {
-        double v = block_entry<false>(a, cov, bl + i, br + b, tab, ff{0, 0}, ff{0, 0});
+        double v = block_entry<false>(a, cov, bl + i, br + b, tab, CovFF{});
         for (int l = 0; l < k; ++l) v -= raw[l * n + bl + i] * raw[l * n + br + b];
         raw[(int64_t)k * n + br + b] = v;
         amax_merge(bv, bi, v, b);
@@ -532,14 +530,14 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row_small(AcaArgs a, int it
     warp_amax(bv, bi);
     fv = bv;
   } else {
-    const ff cr = ff_from_double(a.hyp[kHypScale]), amp = ff_from_double(cov.amp);
+    const CovFF cf = make_cov_ff(a.kind, a.hyp[kHypScale], cov.amp, cov.alpha);
     ff* rawf = reinterpret_cast<ff*>(raw);
     float bv = 0.0f;
 #pragma unroll
     for (int q = 0; q < kSmallPer; ++q) {
       int b = q * 32 + lane;
       if (b < mr) {
-        ff v = block_entry_ff(a, lev, bl + i, br + b, tab, cr, amp);
+        ff v = block_entry_ff(a, lev, bl + i, br + b, tab, cf);
         for (int l = 0; l < k; ++l) v = ff_fms(v, rawf[l * n + bl + i], rawf[l * n + br + b]);
         rawf[(int64_t)k * n + br + b] = v;
         amax_merge_f(bv, bi, v.hi, b);
@@ -588,7 +586,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_small(AcaArgs a, int it
       uu[q] = 0.0;
       vv[q] = 0.0;
       if (t < ml) {
-        double u = block_entry<false>(a, cov, bl + t, br + j, tab, ff{0, 0}, ff{0, 0});
+        double u = block_entry<false>(a, cov, bl + t, br + j, tab, CovFF{});
         for (int l = 0; l < k; ++l) u -= raw[l * n + bl + t] * raw[l * n + br + j];
         raw[(int64_t)k * n + bl + t] = u;
         uu[q] = u;
@@ -629,7 +627,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_small(AcaArgs a, int it
       out[3] = nv2;
     }
   } else {
-    const ff cr = ff_from_double(a.hyp[kHypScale]), amp = ff_from_double(cov.amp);
+    const CovFF cf = make_cov_ff(a.kind, a.hyp[kHypScale], cov.amp, cov.alpha);
     ff* rawf = reinterpret_cast<ff*>(raw);
     const ff inv = ff_rcp(ff_from_double(delta));
     float uu[kSmallPer], vv[kSmallPer];
@@ -640,7 +638,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_small(AcaArgs a, int it
       uu[q] = 0.0f;
       vv[q] = 0.0f;
       if (t < ml) {
-        ff u = block_entry_ff(a, lev, bl + t, br + j, tab, cr, amp);
+        ff u = block_entry_ff(a, lev, bl + t, br + j, tab, cf);
         for (int l = 0; l < k; ++l) u = ff_fms(u, rawf[l * n + bl + t], rawf[l * n + br + j]);
         rawf[(int64_t)k * n + bl + t] = u;
         uu[q] = u.hi;

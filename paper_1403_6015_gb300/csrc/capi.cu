@@ -81,7 +81,7 @@ void free_all(Ctx* c) {
   dfree(c->st_rank); dfree(c->st_row); dfree(c->st_col); dfree(c->st_done); dfree(c->st_ok);
   dfree(c->st_zero); dfree(c->st_phase); dfree(c->st_nused); dfree(c->st_used);
   dfree(c->st_delta); dfree(c->st_s2); dfree(c->aca_part); dfree(c->active);
-  dfree(c->Y); dfree(c->ysort); dfree(c->leafL); dfree(c->leaf_logdet); dfree(c->node_logdet);
+  dfree(c->Y); dfree(c->ysort); dfree(c->leafL); dfree(c->leaf_logdet); dfree(c->node_logdet); dfree(c->leaf_perm);
   dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->ry); dfree(c->rw); dfree(c->exp_tab); dfree(c->xrel); dfree(c->Mlu); dfree(c->Mpiv);
   dfree(c->hyp);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -305,6 +305,7 @@ void hodlr_default_opts(hodlr_opts* o) {
   o->refine_tol = 1e-10;
   o->refine_maxit = 0;
   o->stream = nullptr;
+  o->rq_alpha = 1.0;
 }
 
 const char* hodlr_status_string(hodlr_status s) {
@@ -349,7 +350,10 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   if (o) opts = *o;
   if (!x || n < 1 || n >= ((int64_t)1 << 31) || d < 1 || d > hodlr::kMaxDim || leaf < 1 ||
       leaf > hodlr::kMaxLeaf || !(eps > 0) || !std::isfinite(eps) || !(sigma2 >= 0) ||
-      !std::isfinite(sigma2) || bad_theta(theta) || (int)kernel < 0 || (int)kernel > 3 ||
+      !std::isfinite(sigma2) || bad_theta(theta) || (int)kernel < 0 ||
+      (int)kernel > HODLR_K_BIHARMONIC ||
+      (kernel == HODLR_K_RQ && (!(opts.rq_alpha > 0) || !std::isfinite(opts.rq_alpha))) ||
+      (hodlr::kind_indefinite(kernel) && opts.precision != 0) ||
       opts.max_rank < 1 || opts.max_rank > hodlr::kMaxRank || opts.max_nrhs < 1 ||
       (opts.precision != 0 && opts.precision != 1) || opts.refine_maxit < 0 ||
       (opts.refine_maxit > 0 && (!(opts.refine_tol > 0) || !std::isfinite(opts.refine_tol))))
@@ -359,6 +363,8 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   c->n = n;
   c->d = d;
   c->kind = (int)kernel;
+  c->alpha = opts.rq_alpha;
+  c->indefinite = hodlr::kind_indefinite(kernel);
   c->ell = theta[0];
   c->amp = theta[1];
   c->sigma2 = sigma2;
@@ -392,6 +398,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
       dalloc(&c->Y, n * c->max_nrhs) || dalloc(&c->ysort, n) || dalloc(&c->tmpvec, n * c->max_nrhs) ||
       dalloc(&c->leaf_logdet, nleaf) || dalloc(&c->node_logdet, std::max<int64_t>(nleaf - 1, 1)) ||
       dalloc(&c->leafL, nleaf * hodlr::kMaxLeaf * hodlr::kMaxLeaf) ||
+      (c->indefinite && dalloc(&c->leaf_perm, nleaf * hodlr::kMaxLeaf)) ||
       (c->refine_maxit > 0 && (dalloc(&c->ry, n * c->max_nrhs) ||
                                dalloc(&c->rw, hodlr::refine_work_elems(n)))) ||
       cudaMallocHost(&c->h_active, sizeof(int32_t)) != cudaSuccess) {
@@ -506,8 +513,10 @@ static hodlr_status check_flags(Ctx* c) {
   ++c->syncs;
   if (fl & hodlr::kFlagNotSpd) {
     c->factored = false;
-    return fail(c, HODLR_ENOTSPD, "a leaf pivot or node determinant was not positive");
+    return fail(c, HODLR_ENOTSPD, c->indefinite ? "a leaf pivot or node determinant was zero"
+                                                : "a leaf pivot or node determinant was not positive");
   }
+  c->det_sign = (fl & hodlr::kFlagNegDet) ? -1 : 1;
   return HODLR_OK;
 }
 
@@ -676,9 +685,18 @@ hodlr_status hodlr_logdet(hodlr_ctx* ctx, double* logdet) {
   return write_scalar(c, c->scal, logdet);
 }
 
+hodlr_status hodlr_logdet_signed(hodlr_ctx* ctx, double* logabsdet, int* sign) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !logabsdet || !sign) return HODLR_EINVAL;
+  if (!c->factored) return fail(c, HODLR_ESTATE, "logdet before factor");
+  *sign = c->det_sign;
+  return write_scalar(c, c->scal, logabsdet);
+}
+
 hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out) {
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!c || !y || !out) return HODLR_EINVAL;
+  if (c->indefinite) return fail(c, HODLR_EINVAL, "loglik: the kernel's C is indefinite (not a covariance)");
   const double* yd;
   int64_t ldd;
   hodlr_status s = stage_in(c, y, 1, c->n, &yd, &ldd);
@@ -703,6 +721,8 @@ hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out) {
 hodlr_status hodlr_presize(hodlr_ctx* ctx, const int32_t* level_ranks, int nlevels) {
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!c) return HODLR_EINVAL;
+  if (c->indefinite && level_ranks)
+    return fail(c, HODLR_EINVAL, "presize: not for an indefinite kernel (its sign needs a read-back)");
   if (!level_ranks) {
     c->presized = false;
     c->graph_valid = false;

@@ -150,23 +150,61 @@ __device__ __forceinline__ ff ff_exp(ff x, const ff* __restrict__ tab64) {
   return ff{t.hi * sc, t.lo * sc};
 }
 
+// log(x) for a double-float x >= 1 (the argument 1 + t^2 of the rational quadratic): the
+// float logarithm y0 of x.hi, refined by one Newton step on exp: e = x exp(-y0) - 1 and
+// log x = y0 + log1p(e) = y0 + e - e^2/2 + O(e^3), |e| below ~1e-6 (the float log's error),
+// so the truncation is below 1e-18 and the result is good to about 2^-48 absolute.
+__device__ __forceinline__ ff ff_log(ff x, const ff* __restrict__ tab64) {
+  float y0 = logf(x.hi);
+  ff e = ff_sub(ff_mul(x, ff_exp(ff{-y0, 0.0f}, tab64)), ff{1.0f, 0.0f});
+  ff corr = ff_sub(e, ff_mulf(ff_mul(e, e), 0.5f));
+  return ff_add(ff{y0, 0.0f}, corr);
+}
+
+// A covariance's parameters as double-floats: kind, cr (the factor applied to r), the
+// amplitude a and the rational quadratic's exponent alpha.
+struct CovFF {
+  int kind;
+  ff cr, amp, alpha;
+};
+
+__device__ __forceinline__ CovFF make_cov_ff(int kind, double cr, double amp, double alpha) {
+  return CovFF{kind, ff_from_double(cr), ff_from_double(amp), ff_from_double(alpha)};
+}
+
 // Covariance k(r) = a f(cr r) in double-float (Table 1 with a length scale: exponential,
-// squared-exponential, Matern-3/2, Matern-5/2; cr = 1/ell, 1/ell, sqrt3/ell, sqrt5/ell).
-__device__ __forceinline__ ff cov_ff(int kind, ff r, ff cr, ff amp, const ff* tab) {
-  ff s = ff_mul(r, cr);
+// squared-exponential, Matern-3/2, Matern-5/2; cr = 1/ell, 1/ell, sqrt3/ell, sqrt5/ell; and
+// the positive definite radial functions of Sec. 5, rational quadratic (1 + t^2)^-alpha and
+// inverse multiquadric 1/sqrt(1 + t^2), t = r/ell). The indefinite multiquadric and
+// biharmonic have no double-float form (the mixed form's L D L^T leaves need a positive
+// definite C): NaN.
+// Rational quadratic (kind 4) and inverse multiquadric (kind 5) of s = t, out of line (see
+// cov_ff).
+static __device__ __noinline__ ff cov_ff_radial(const CovFF& k, ff s, const ff* tab) {
   const ff one = {1.0f, 0.0f};
-  switch (kind) {
+  ff q = ff_add(one, ff_mul(s, s));
+  if (k.kind == 4) return ff_mul(k.amp, ff_exp(ff_neg(ff_mul(k.alpha, ff_log(q, tab))), tab));
+  if (k.kind == 5) return ff_mul(k.amp, ff_rcp(ff_sqrt(q)));
+  return ff{nanf(""), 0.0f};
+}
+
+__device__ __forceinline__ ff cov_ff(const CovFF& k, ff r, const ff* tab) {
+  ff s = ff_mul(r, k.cr);
+  const ff one = {1.0f, 0.0f};
+  switch (k.kind) {
     case 0:  // exponential
-      return ff_mul(amp, ff_exp(ff_neg(s), tab));
+      return ff_mul(k.amp, ff_exp(ff_neg(s), tab));
     case 1:  // squared-exponential
-      return ff_mul(amp, ff_exp(ff_mulf(ff_mul(s, s), -0.5f), tab));
+      return ff_mul(k.amp, ff_exp(ff_mulf(ff_mul(s, s), -0.5f), tab));
     case 2:  // Matern-3/2
-      return ff_mul(amp, ff_mul(ff_add(one, s), ff_exp(ff_neg(s), tab)));
-    default: {  // Matern-5/2
+      return ff_mul(k.amp, ff_mul(ff_add(one, s), ff_exp(ff_neg(s), tab)));
+    case 3: {  // Matern-5/2
       const ff third = {0.3333333432674408f, -9.934107481068821e-09f};
       ff poly = ff_add(ff_add(one, s), ff_mul(ff_mul(s, s), third));
-      return ff_mul(amp, ff_mul(poly, ff_exp(ff_neg(s), tab)));
+      return ff_mul(k.amp, ff_mul(poly, ff_exp(ff_neg(s), tab)));
     }
+    default:  // rational quadratic exp(-alpha log(1 + t^2)), inverse multiquadric
+      return cov_ff_radial(k, s, tab);
   }
 }
 

@@ -30,7 +30,24 @@ struct Cov {
   int kind;
   double inv_ell;
   double amp;
+  double alpha;  // rational quadratic exponent
 };
+
+__host__ __device__ inline bool kind_indefinite(int kind) {
+  return kind == HODLR_K_MQ || kind == HODLR_K_BIHARMONIC;
+}
+
+// The radial functions of Sec. 5, t = r / ell. Kept out of line so that their pow and log
+// do not raise the register count of every kernel that evaluates the common covariances.
+static __device__ __noinline__ double cov_r_radial(int kind, double t, double amp, double alpha) {
+  switch (kind) {
+    case HODLR_K_RQ: return amp * pow(1.0 + t * t, -alpha);
+    case HODLR_K_IMQ: return amp / sqrt(1.0 + t * t);
+    case HODLR_K_MQ: return amp * sqrt(1.0 + t * t);
+    case HODLR_K_BIHARMONIC: return t > 0.0 ? amp * t * t * log(t) : 0.0;  // 0: the limit
+    default: return nan("");
+  }
+}
 
 __device__ __forceinline__ double cov_r(const Cov& c, double r) {
   switch (c.kind) {
@@ -44,20 +61,23 @@ __device__ __forceinline__ double cov_r(const Cov& c, double r) {
       double s = 1.7320508075688772 * r * c.inv_ell;  // sqrt(3) r / ell
       return c.amp * (1.0 + s) * exp(-s);
     }
-    default: {
+    case HODLR_K_MATERN52: {
       double s = 2.23606797749979 * r * c.inv_ell;  // sqrt(5) r / ell
       return c.amp * (1.0 + s + s * s * (1.0 / 3.0)) * exp(-s);
     }
+    default:
+      return cov_r_radial(c.kind, r * c.inv_ell, c.amp, c.alpha);
   }
 }
 
 // Hyperparameters in device memory, so that kernels (and captured graphs) read the current
 // setting: hyp[0] = 1/ell, hyp[1] = amplitude a, hyp[2] = sigma^2, hyp[3] = covariance
-// scale cr (1/ell, 1/ell, sqrt3/ell, sqrt5/ell for exp, SE, Matern-3/2, Matern-5/2).
-enum { kHypInvEll = 0, kHypAmp = 1, kHypSigma2 = 2, kHypScale = 3, kHypLen = 8 };
+// scale cr (1/ell, 1/ell, sqrt3/ell, sqrt5/ell for exp, SE, Matern-3/2, Matern-5/2; 1/ell
+// for the radial functions), hyp[4] = the rational quadratic's exponent alpha.
+enum { kHypInvEll = 0, kHypAmp = 1, kHypSigma2 = 2, kHypScale = 3, kHypAlpha = 4, kHypLen = 8 };
 
 __device__ __forceinline__ Cov cov_from(int kind, const double* __restrict__ hyp) {
-  return Cov{kind, hyp[kHypInvEll], hyp[kHypAmp]};
+  return Cov{kind, hyp[kHypInvEll], hyp[kHypAmp], hyp[kHypAlpha]};
 }
 
 // Sorted points in structure-of-arrays form: coordinate c of sorted point i is x[c * n + i].
@@ -82,7 +102,9 @@ __device__ __forceinline__ double dist(const Pts& p, int i, int j) {
 }
 
 // Device error word bits (ctx->dflags).
-enum : int { kFlagNotSpd = 1, kFlagRankCap = 2, kFlagTimeout = 4 };  // rank cap: also presize
+// kFlagNegDet: parity of the negative block determinants of an indefinite C (the sign of
+// det C), toggled by each one.
+enum : int { kFlagNotSpd = 1, kFlagRankCap = 2, kFlagTimeout = 4, kFlagNegDet = 8 };  // rank cap: also presize
 
 // ---------------------------------------------------------------------------------------
 // Context: everything one problem owns on the device. Layouts (n rows, column stride n):
@@ -102,6 +124,10 @@ struct Ctx {
   int d = 1;
   int kind = 0;
   double ell = 1, amp = 1, sigma2 = 0, eps = 1e-12;
+  double alpha = 1;               // rational quadratic exponent
+  bool indefinite = false;        // multiquadric / biharmonic: LU leaves, signed log |det|
+  int det_sign = 1;               // sign of det C after the last factorization
+  int32_t* leaf_perm = nullptr;   // LU row orders, kMaxLeaf per leaf (indefinite only)
   int leaf = 128, kappa = 0, max_rank = kDefaultMaxRank, max_nrhs = 16;
   int precision = 0;              // 0: FP64, 1: double-float leaf stage (mixed)
   int leaf_threads = 512;         // CTA size of the double-float leaf kernel (two CTAs per SM)

@@ -6,10 +6,14 @@
 //   factor mode: build C[I_leaf, I_leaf] from the sorted points (sigma^2 on the diagonal),
 //                factor it in place as L D L^T (the square-root-free Cholesky form, L unit
 //                lower, two pivots per step), store it, log det = sum log D_ii;
+//                for an indefinite C (multiquadric, biharmonic) instead P A = L D U~ (LU
+//                with partial pivoting, U = D U~ with U~ unit upper), the row order P
+//                stored beside it, log |det| = sum log |D_ii| and the sign from the row
+//                swaps and the signs of D_ii;
 //   solve mode:  load the stored factor.
 // Then every panel column (the ancestors' U/V rows in factor mode, and the right-hand sides)
-// is solved with L D L^T by one warp (lanes own rows lane + 32 m, two columns at a time; a
-// unit diagonal means every step is one shuffle and FMAs), and the warp also forms the
+// is solved by one warp (lanes own rows lane + 32 m, two columns at a time; unit triangular
+// factors make every step one shuffle and FMAs), and the warp also forms the
 // level-(kappa-1) partial products Phi_{kappa-1}^T x of the leaf's rows.
 #include <cuda_runtime.h>
 
@@ -39,6 +43,8 @@ struct LeafArgs {
   int64_t part_stride;
   double* leafL;
   double* leaf_logdet;
+  int32_t* leaf_perm;  // LU row order, kMaxLeaf per leaf (lu only)
+  int lu;              // 1: LU with partial pivoting (indefinite C), 0: L D L^T
   int32_t* flags;
   int64_t n;
 };
@@ -48,9 +54,11 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// Solve L D L^T x = b (L unit lower, stored below the diagonal of A) for NC columns held by
-// a warp: element i of column c in lane i % 32, slot i / 32 of x[c]. dinv holds 1 / D_ii.
-template <int NC>
+// Solve L D V x = b for NC columns held by a warp: element i of column c in lane i % 32,
+// slot i / 32 of x[c]. L is unit lower (below the diagonal of A), dinv holds 1 / D_ii and
+// V is unit upper: L^T (kUpper = false, read from below the diagonal) or the scaled LU
+// factor U~ (kUpper = true, above the diagonal).
+template <int NC, bool kUpper>
 __device__ __forceinline__ void warp_ldl_solve(const double* __restrict__ A,
                                                const double* __restrict__ dinv, int p, int lane,
                                                double (&x)[NC][4]) {
@@ -82,7 +90,7 @@ __device__ __forceinline__ void warp_ldl_solve(const double* __restrict__ A,
 #pragma unroll
     for (int c = 0; c < NC; ++c) x[c][m] *= di;
   }
-  // backward: L^T x = v
+  // backward: V x = v
 #pragma unroll
   for (int s = 3; s >= 0; --s) {
     for (int kk = 31; kk >= 0; --kk) {
@@ -95,13 +103,88 @@ __device__ __forceinline__ void warp_ldl_solve(const double* __restrict__ A,
       for (int m = 0; m <= s; ++m) {
         int i = m * 32 + lane;
         if (i < k) {
-          double lki = A[k * kLD + i];
+          double lki = kUpper ? A[i * kLD + k] : A[k * kLD + i];
 #pragma unroll
           for (int c = 0; c < NC; ++c) x[c][m] -= lki * xk[c];
         }
       }
     }
   }
+}
+
+// In-place LU with partial pivoting of the p x p block in A (stride kLD), right-looking:
+// at step k warp 0 picks the row of largest |A_ik|, i >= k (lowest index on ties), the
+// rows are swapped, and every warp updates its rows of the trailing block with its own
+// multiplier. On exit L (unit lower) is below the diagonal, D = diag(U) on it and
+// U~ = D^-1 U above it; perm[i] = original row now at position i; *nswap = row swaps;
+// *bad = 1 if a pivot was exactly zero (it is replaced by 1 to keep going).
+template <int kThreads>
+__device__ void lu_factor(double* A, int p, int* perm, int* prow, int* nswap, int* bad) {
+  int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int i = tid; i < p; i += kThreads) perm[i] = i;
+  if (tid == 0) *nswap = 0;
+  __syncthreads();
+  for (int k = 0; k < p; ++k) {
+    if (w == 0) {
+      double bv = -1.0;
+      int bi = k;
+      for (int i = k + lane; i < p; i += 32) {
+        double v = fabs(A[i * kLD + k]);
+        if (v > bv) {  // rows are visited in increasing order: ties keep the lower one
+          bv = v;
+          bi = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        *prow = bi;
+        if (bi != k) {
+          int t = perm[k];
+          perm[k] = perm[bi];
+          perm[bi] = t;
+          ++*nswap;
+        }
+      }
+    }
+    __syncthreads();
+    int pr = *prow;
+    if (pr != k)
+      for (int j = tid; j < p; j += kThreads) {
+        double t = A[k * kLD + j];
+        A[k * kLD + j] = A[pr * kLD + j];
+        A[pr * kLD + j] = t;
+      }
+    __syncthreads();
+    double akk = A[k * kLD + k];
+    if (akk == 0.0) {
+      akk = 1.0;
+      if (tid == 0) {
+        *bad = 1;
+        A[k * kLD + k] = 1.0;
+      }
+    }
+    const double inv = 1.0 / akk;
+    for (int i = k + 1 + w; i < p; i += kThreads / 32) {
+      double l = A[i * kLD + k] * inv;
+      __syncwarp();
+      for (int j = k + 1 + lane; j < p; j += 32) A[i * kLD + j] -= l * A[k * kLD + j];
+      if (lane == 0) A[i * kLD + k] = l;
+    }
+    __syncthreads();
+  }
+  // U~ = D^-1 U: scale each row above the diagonal by 1 / D_ii
+  for (int i = w; i < p; i += kThreads / 32) {
+    double inv = 1.0 / A[i * kLD + i];
+    for (int j = i + 1 + lane; j < p; j += 32) A[i * kLD + j] *= inv;
+  }
+  __syncthreads();
 }
 
 template <bool kFactor, int kLeafThreads>
@@ -113,6 +196,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
   __shared__ double red[kLeafThreads / 32];
   __shared__ double piv_inv[2], piv_t;
   __shared__ int bad;
+  __shared__ int perm[kMaxLeaf];
+  __shared__ int prow, nswap;
   int leaf = blockIdx.x;
   int id = a.leaf0 + leaf;
   int b = a.nb[id], p = a.ns[id];
@@ -128,7 +213,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
     __syncthreads();
     for (int e = tid; e < p * p; e += kLeafThreads) {
       int i = e / p, j = e - i * p;
-      if (j > i) continue;
+      if (j > i && !a.lu) continue;
       double r;
       if (a.pts.d == 1) {
         r = fabs(xl[i] - xl[j]);
@@ -148,6 +233,41 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
       A[i * kLD + j] = c;
     }
     __syncthreads();
+    if (a.lu) {
+      lu_factor<kLeafThreads>(A, p, perm, &prow, &nswap, &bad);
+      int32_t* pout = a.leaf_perm + (int64_t)leaf * kMaxLeaf;
+      for (int e = tid; e < p * p; e += kLeafThreads) {
+        int i = e / p, j = e - i * p;
+        Lout[i * kMaxLeaf + j] = A[i * kLD + j];
+      }
+      for (int i = tid; i < p; i += kLeafThreads) pout[i] = perm[i];
+      // log |det| = sum log |D_ii|; sign = (-1)^(row swaps) times the signs of D_ii
+      double s = 0.0;
+      int neg = 0;
+      for (int i = tid; i < p; i += kLeafThreads) {
+        double dii = A[i * kLD + i];
+        s += log(fabs(dii));
+        neg += dii < 0.0;
+      }
+      s = wsum(s);
+      neg = __reduce_add_sync(0xffffffffu, neg);
+      if (lane == 0) {
+        red[w] = s;
+        T0[w] = (double)neg;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        int ng = nswap;
+        for (int q = 0; q < kLeafThreads / 32; ++q) {
+          t += red[q];
+          ng += (int)T0[q];
+        }
+        a.leaf_logdet[leaf] = t;
+        if (bad) atomicOr(a.flags, kFlagNotSpd);
+        if (ng & 1) atomicXor(a.flags, kFlagNegDet);
+      }
+    } else {
     // L D L^T, right-looking, pivots k and k+1 per step: on exit A[i][j] (j < i) = L_ij and
     // A[k][k] = D_kk. The trailing update uses the unscaled columns kept in T0, T1:
     // A_ij -= L_ik (L_jk D_kk) + L_i,k+1 (L_j,k+1 D_k+1,k+1).
@@ -220,11 +340,14 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
       a.leaf_logdet[leaf] = t;
       if (bad) atomicOr(a.flags, kFlagNotSpd);
     }
+    }  // L D L^T
   } else {
     for (int e = tid; e < p * p; e += kLeafThreads) {
       int i = e / p, j = e - i * p;
-      if (j <= i) A[i * kLD + j] = Lout[i * kMaxLeaf + j];
+      if (j <= i || a.lu) A[i * kLD + j] = Lout[i * kMaxLeaf + j];
     }
+    if (a.lu)
+      for (int i = tid; i < p; i += kLeafThreads) perm[i] = a.leaf_perm[(int64_t)leaf * kMaxLeaf + i];
     __syncthreads();
   }
   for (int i = tid; i < p; i += kLeafThreads) dinv[i] = 1.0 / A[i * kLD + i];
@@ -243,10 +366,13 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         int i = m * 32 + lane;
-        x[c][m] = i < p ? col[c][i] : 0.0;
+        x[c][m] = i < p ? col[c][a.lu ? perm[i] : i] : 0.0;  // LU: rows in pivot order
       }
     }
-    warp_ldl_solve<NC>(A, dinv, p, lane, x);
+    if (a.lu)
+      warp_ldl_solve<NC, true>(A, dinv, p, lane, x);
+    else
+      warp_ldl_solve<NC, false>(A, dinv, p, lane, x);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       if (c0 + c >= ncol) break;
@@ -300,6 +426,8 @@ LeafArgs make_args(Ctx& c, int nrhs, bool factor) {
   a.part_stride = c.part_stride;
   a.leafL = c.leafL;
   a.leaf_logdet = c.leaf_logdet;
+  a.leaf_perm = c.leaf_perm;
+  a.lu = c.indefinite ? 1 : 0;
   a.flags = c.dflags;
   a.n = c.n;
   return a;
@@ -367,6 +495,8 @@ cudaError_t launch_leaf_single(const double* xs_soa, int n, int d, int kind, con
   a.part_stride = 0;
   a.leafL = L;
   a.leaf_logdet = logdet;
+  a.leaf_perm = nullptr;
+  a.lu = 0;
   a.flags = flags;
   a.n = n;
   return launch_leaf<true>(a, 1, 256, s);

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
         xl[c * kMaxLeaf + i] = ff_from_double(a.x[c * a.n + b + i] - a.x[c * a.n + b]);
     }
     __syncthreads();
-    const ff cr = ff_from_double(a.hyp[kHypScale]), amp = ff_from_double(a.hyp[kHypAmp]);
+    const CovFF cf = make_cov_ff(a.kind, a.hyp[kHypScale], a.hyp[kHypAmp], a.hyp[kHypAlpha]);
     const ff s2 = ff_from_double(a.hyp[kHypSigma2]);
     // lower triangle of the padded block
     for (int e = tid; e < P * (P + 1) / 2; e += kT) {
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
         } else {
           r = ff_from_double(dist(Pts{a.x, a.n, a.d}, b + i, b + j));  // d > 3: FP64 distance
         }
-        c = cov_ff(a.kind, r, cr, amp, tab);
+        c = cov_ff(cf, r, tab);
         if (i == j) c = ff_add(c, s2);
       } else {
         c = ff{i == j ? 1.0f : 0.0f, 0.0f};

@@ -422,6 +422,7 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
     na.z_stride = (int64_t)2 * r * na.wz;
     na.flags = c.dflags;
     na.zff = c.precision == 1;
+    na.signed_det = c.indefinite;
     if (r > 0) {
       HODLR_CUDA_TRY(launch_node(c, na, factor_mode));
     } else if (factor_mode) {
@@ -484,6 +485,7 @@ cudaError_t launch_level_first(Ctx& c, int nrhs, bool factor_mode) {
   na.z_stride = (int64_t)2 * r * na.wz;
   na.flags = c.dflags;
   na.zff = c.precision == 1;
+  na.signed_det = c.indefinite;
   if (r == 0) {
     if (factor_mode)
       HODLR_CUDA_TRY(cudaMemsetAsync(c.node_logdet + ((1 << j) - 1), 0, sizeof(double) << j, c.stream));
@@ -493,11 +495,13 @@ cudaError_t launch_level_first(Ctx& c, int nrhs, bool factor_mode) {
 }
 
 // Device hyperparameter slot from host values (stream-ordered, capturable).
-__global__ void k_set_hyp(double* hyp, int kind, double ell, double amp, double sigma2) {
+__global__ void k_set_hyp(double* hyp, int kind, double ell, double amp, double sigma2,
+                          double alpha) {
   hyp[kHypInvEll] = 1.0 / ell;
   hyp[kHypAmp] = amp;
   hyp[kHypSigma2] = sigma2;
   hyp[kHypScale] = cov_scale(kind, ell);
+  hyp[kHypAlpha] = alpha;
 }
 
 // The same from setting idx[0] of device arrays theta (ell, a pairs) and sigma2.
@@ -512,7 +516,7 @@ __global__ void k_load_setting(double* hyp, int kind, const double* theta, const
 }
 
 cudaError_t launch_set_hyp(Ctx& c, double ell, double amp, double sigma2) {
-  k_set_hyp<<<1, 1, 0, c.stream>>>(c.hyp, c.kind, ell, amp, sigma2);
+  k_set_hyp<<<1, 1, 0, c.stream>>>(c.hyp, c.kind, ell, amp, sigma2, c.alpha);
   ++c.launches;
   return cudaGetLastError();
 }

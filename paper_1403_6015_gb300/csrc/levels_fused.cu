@@ -334,6 +334,7 @@ cudaError_t launch_levels_fused(Ctx& c, int nrhs, bool factor_mode) {
       na.z_stride = (int64_t)2 * fa.rl * na.wz;
       na.flags = c.dflags;
       na.zff = c.precision == 1;
+      na.signed_det = c.indefinite;
       if (factor_mode && fa.rl == 0)
         HODLR_CUDA_TRY(cudaMemsetAsync(c.node_logdet + ((1 << l) - 1), 0, sizeof(double) << l, c.stream));
     }

@@ -77,6 +77,7 @@ __global__ void k_noalloc_prep(double* s, const double* __restrict__ x, const do
     hyp[hodlr::kHypAmp] = amp;
     hyp[hodlr::kHypSigma2] = sigma2;
     hyp[hodlr::kHypScale] = hodlr::cov_scale(kind, ell);
+    hyp[hodlr::kHypAlpha] = 1.0;
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     for (int c = 0; c < d; ++c) s[kOffX + c * n + i] = x[i * d + c];

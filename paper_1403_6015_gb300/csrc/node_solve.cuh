@@ -24,7 +24,15 @@ struct NodeArgs {
   int32_t* flags;
   int zff;              // 1 (mixed form): Z's panel columns (q < cj) as double-float pairs,
                         // its right-hand-side columns FP64; 0: all FP64
+  int signed_det;       // 1 (indefinite C): a negative det M toggles kFlagNegDet; 0: it is
+                        // an error (kFlagNotSpd)
 };
+
+// Record the sign of one block determinant in the device flags.
+__device__ __forceinline__ void record_sign(const NodeArgs& a, int sgn) {
+  if (sgn == 0 || (sgn < 0 && !a.signed_det)) atomicOr(a.flags, kFlagNotSpd);
+  else if (sgn < 0) atomicXor(a.flags, kFlagNegDet);
+}
 
 // Partial column of Z column q: ancestors' panel columns keep their index, the right-hand
 // sides sit after the node's own r columns in factor mode.
@@ -102,7 +110,7 @@ static __device__ void node_solve(const NodeArgs& a, int k, bool factor, double*
     for (int e = tid; e < m2; e += nthr) pg[e] = piv[e];
     if (tid == 0) {
       a.node_logdet[node] = lds;
-      if (sgn <= 0) atomicOr(a.flags, kFlagNotSpd);
+      record_sign(a, sgn);
     }
   } else {
     for (int e = tid; e < m2 * m2; e += nthr) M[e] = Mg[e];
@@ -242,7 +250,7 @@ static __device__ void node_solve_global(const NodeArgs& a, int k, bool factor, 
     }
     if (tid == 0) {
       a.node_logdet[node] = lds;
-      if (sgn <= 0) atomicOr(a.flags, kFlagNotSpd);
+      record_sign(a, sgn);
     }
   }
   __syncthreads();

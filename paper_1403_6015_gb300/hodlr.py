@@ -14,7 +14,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhodlr_gb300.so")
 
-KERNELS = {"exp": 0, "se": 1, "matern32": 2, "matern52": 3}
+KERNELS = {"exp": 0, "se": 1, "matern32": 2, "matern52": 3, "rq": 4, "imq": 5, "mq": 6,
+           "biharmonic": 7}
+INDEFINITE = ("mq", "biharmonic")  # LU leaves, signed log |det|, no log-likelihood
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTSPD", 4: "ERANK", 5: "ETIMEOUT",
           6: "ESTATE", 7: "ECUDA"}
 HODLR_OK, HODLR_EINVAL, HODLR_ENOMEM, HODLR_ENOTSPD, HODLR_ERANK = 0, 1, 2, 3, 4
@@ -35,7 +37,7 @@ class hodlr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rank_mode", ctypes.c_int),
                 ("max_rank", ctypes.c_int), ("max_nrhs", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("rq_alpha", ctypes.c_double)]
 
 
 _lib = None
@@ -61,6 +63,7 @@ def load():
     L.hodlr_factor_solve.argtypes = [_vp, _dp, _dp, ctypes.c_int, ctypes.c_int64]
     L.hodlr_solve.argtypes = [_vp, _dp, _dp, ctypes.c_int, ctypes.c_int64]
     L.hodlr_logdet.argtypes = [_vp, _dp]
+    L.hodlr_logdet_signed.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_int)]
     L.hodlr_loglik.argtypes = [_vp, _dp, _dp]
     L.hodlr_ranks.argtypes = [_vp, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     L.hodlr_tree.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _dp]
@@ -104,7 +107,7 @@ def load():
                  "hodlr_mlp_forward", "hodlr_mlp_gradient", "hodlr_mlp_train", "hodlr_mlp_save",
                  "hodlr_mlp_load", "hodlr_block_features", "hodlr_predict_ranks",
                  "hodlr_loglik_batched", "hodlr_refine_info", "hodlr_get_tuning",
-                 "hodlr_set_tuning", "hodlr_autotune", "hodlr_predict"):
+                 "hodlr_set_tuning", "hodlr_autotune", "hodlr_predict", "hodlr_logdet_signed"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -168,6 +171,11 @@ def hodlr_solve(ctx, y_addr, x_addr, nrhs, ld):
 
 def hodlr_logdet(ctx, out_addr):
     return load().hodlr_logdet(ctx, out_addr)
+
+
+def hodlr_logdet_signed(ctx, out_addr, sign: "ctypes.c_int"):
+    """log |det C| into out_addr (host or device), its sign into the ctypes int `sign`."""
+    return load().hodlr_logdet_signed(ctx, out_addr, ctypes.byref(sign))
 
 
 def hodlr_loglik(ctx, y_addr, out_addr):
@@ -345,7 +353,8 @@ class Hodlr:
 
     def __init__(self, x, kernel: str, theta, sigma2: float, leaf: int, eps: float,
                  max_rank: int = 64, max_nrhs: int = 16, stream=None, allow_rank_cap=False,
-                 precision: int = 0, refine_maxit: int = 0, refine_tol: float = 1e-10):
+                 precision: int = 0, refine_maxit: int = 0, refine_tol: float = 1e-10,
+                 rq_alpha: float = 1.0):
         if _is_torch(x):
             if x.dtype.itemsize != 8 or not x.is_contiguous():
                 raise ValueError("x must be a contiguous float64 tensor")
@@ -362,6 +371,7 @@ class Hodlr:
         o.precision = precision
         o.refine_maxit = refine_maxit
         o.refine_tol = refine_tol
+        o.rq_alpha = rq_alpha
         if stream is not None:
             o.stream = stream
         self.kernel = kernel
@@ -441,6 +451,13 @@ class Hodlr:
         buf = out if out is not None else np.zeros(1)
         self._check(hodlr_logdet(self._ctx, _addr(buf)), "logdet")
         return buf if out is not None else float(buf[0])
+
+    def logdet_signed(self):
+        """(log |det C|, sign of det C); the sign is -1 only for an indefinite kernel."""
+        buf = np.zeros(1)
+        sg = ctypes.c_int()
+        self._check(hodlr_logdet_signed(self._ctx, _addr(buf), sg), "logdet_signed")
+        return float(buf[0]), sg.value
 
     def loglik(self, y, out=None):
         if _is_torch(y):

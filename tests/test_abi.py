@@ -83,3 +83,21 @@ def test_build_rejects_bad_options():
         st, ctx = hodlr.hodlr_build(x, 64, 1, 0, [0.2, 1.0], 0.01, 16, 1e-12, o)
         assert st == hodlr.HODLR_EINVAL and not ctx
     assert hodlr.hodlr_default_opts().max_rank == 64
+    # the rational quadratic needs alpha > 0; the indefinite kernels (multiquadric,
+    # biharmonic) need the FP64 form; kernel codes end at 7; d at most 64
+    assert hodlr.hodlr_default_opts().rq_alpha == 1.0
+    for a in [0.0, -1.0, float("nan"), float("inf")]:
+        o = hodlr.hodlr_default_opts()
+        o.rq_alpha = a
+        st, ctx = hodlr.hodlr_build(x, 64, 1, hodlr.KERNELS["rq"], [0.2, 1.0], 0.01, 16, 1e-12, o)
+        assert st == hodlr.HODLR_EINVAL and not ctx
+    for kern in hodlr.INDEFINITE:
+        o = hodlr.hodlr_default_opts()
+        o.precision = 1
+        st, ctx = hodlr.hodlr_build(x, 64, 1, hodlr.KERNELS[kern], [0.2, 1.0], 0.01, 16, 1e-12, o)
+        assert st == hodlr.HODLR_EINVAL and not ctx
+    st, ctx = hodlr.hodlr_build(x, 64, 1, 8, [0.2, 1.0], 0.01, 16, 1e-12, None)
+    assert st == hodlr.HODLR_EINVAL and not ctx
+    x65 = np.zeros((2, 65))
+    st, ctx = hodlr.hodlr_build(x65, 2, 65, 0, [0.2, 1.0], 0.01, 16, 1e-12, None)
+    assert st == hodlr.HODLR_EINVAL and not ctx
