@@ -582,8 +582,11 @@ def run_supplementary(args):
     """Measurements beside the headline (untimed by it): the paper's phase split at n = 2^20
     (solve-only with 1 and 16 right-hand sides and log det given a factor, ordering), the
     mixed form with refinement on n = 2^22 (1-D squared-exponential ell = 0.05,
-    sigma^2 = 1e-3), and paper-shaped rows (n = 1e6 on [-3, 3], unit length scale) next to
-    the paper's single-core timings (context only)."""
+    sigma^2 = 1e-3), and rows shaped like the paper's tables (points on [-3, 3]^d, unit
+    length scale: the Gaussian, exponential, inverse multiquadric, biharmonic and
+    multiquadric at n = 1e6 in 1-D, the multiquadric at n = 1e5 in 2-D, the Gaussian at
+    n = 5000 in 32 and 64 dimensions) next to the paper's single-core timings (context
+    only)."""
     import torch
 
     from paper_1403_6015_gb300 import hodlr as H
@@ -669,19 +672,31 @@ def run_supplementary(args):
     # (3) paper-shaped rows: n = 1e6 on [-3, 3]; the paper's phases (Assembly = ordering +
     # compression, Factor, Solve, Det.) and the relative error of the solution of C x = b
     # with b made from a known x (b = C~ x through the library's own product)
-    paper = {"gaussian_2I+exp(-r^2)": ("se", 0.5 ** 0.5, 2.0, [14.1, 23.2, 0.834, 1.52]),
-             "exponential_I+exp(-r)": ("exp", 1.0, 1.0, [18.8, 8.05, 0.636, 1.35])}
-    n4 = 1000000
-    x4 = I.uniform_points(n4, 1, -3.0, 3.0, 1005)
-    xt = I.normal(n4, 1006)
+    # (name: kernel, ell, sigma^2, d, n, the paper's seconds for assembly/factor/solve/det)
+    paper = {"gaussian_2I+exp(-r^2)": ("se", 0.5 ** 0.5, 2.0, 1, 1000000, [14.1, 23.2, 0.834, 1.52]),
+             "exponential_I+exp(-r)": ("exp", 1.0, 1.0, 1, 1000000, [18.8, 8.05, 0.636, 1.35]),
+             "inverse_multiquadric_I+1/sqrt(1+r^2)": ("imq", 1.0, 1.0, 1, 1000000,
+                                                      [14.2, 26.8, 1.02, 1.49]),
+             "biharmonic_2I+r^2log(r)": ("biharmonic", 1.0, 2.0, 1, 1000000, [51.3, 81.9, 1.28, 3.40]),
+             "multiquadric_I+sqrt(1+r^2)": ("mq", 1.0, 1.0, 1, 1000000, [10.9, 17.1, 0.814, 1.94]),
+             "multiquadric_I+sqrt(1+r^2)_2d": ("mq", 1.0, 1.0, 2, 100000, [6.54, 6.95, 0.177, 0.31]),
+             "gaussian_2I+exp(-r^2)_d32_n5000": ("se", 0.5 ** 0.5, 2.0, 32, 5000, [0.15, 0.061, 0.004, 0.001]),
+             "gaussian_2I+exp(-r^2)_d64_n5000": ("se", 0.5 ** 0.5, 2.0, 64, 5000, [0.21, 0.059, 0.001, 0.001])}
     rows4 = {}
-    for name, (kern, ell, s2, ptimes) in paper.items():
-        r = {"n": n4, "kernel": kern, "ell": ell, "sigma2": s2, "leaf": LEAF, "eps": EPS,
-             "paper_s (one 1.3 GHz core)": dict(zip(["assembly", "factor", "solve", "det"], ptimes))}
-        for prec, fname in [(0, "fp64"), (1, "mixed")]:
+    for name, (kern, ell, s2, d4, n4, ptimes) in paper.items():
+        x4 = I.uniform_points(n4, d4, -3.0, 3.0, 1005 + d4)
+        xt = I.normal(n4, 1006)
+        r = {"n": n4, "d": d4, "kernel": kern, "ell": ell, "sigma2": s2, "leaf": LEAF, "eps": EPS,
+             "paper_s (one CPU core)": dict(zip(["assembly", "factor", "solve", "det"], ptimes))}
+        forms = [(0, "fp64")] if kern in H.INDEFINITE else [(0, "fp64"), (1, "mixed")]
+        for prec, fname in forms:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            h = H.Hodlr(x4, kern, [ell, 1.0], s2, LEAF, EPS, precision=prec)
+            try:
+                h = H.Hodlr(x4, kern, [ell, 1.0], s2, LEAF, EPS, precision=prec, max_rank=512)
+            except H.HodlrError as e:
+                r[fname] = {"error": str(e)}
+                continue
             torch.cuda.synchronize()
             asm_s = time.perf_counter() - t0
             b = h.matvec(xt)
@@ -695,15 +710,20 @@ def run_supplementary(args):
             torch.cuda.synchronize()
             sol_s = time.perf_counter() - t0
             t0 = time.perf_counter()
-            h.logdet()
+            _, sign = h.logdet_signed()
             det_s = time.perf_counter() - t0
+            kap = h.tree()[0]
+            rk = h.ranks()
             r[fname] = {"assembly_s": asm_s, "factor_s": fac_s, "solve_s": sol_s, "det_s": det_s,
                         "note": "assembly includes the host-to-device copy of x; solve "
                                 "includes host copies of b and x",
-                        "error": float(np.linalg.norm(xs - xt) / np.linalg.norm(xt))}
+                        "error": float(np.linalg.norm(xs - xt) / np.linalg.norm(xt)),
+                        "det_sign": sign,
+                        "top_ranks": [int(rk[(1 << j) - 1:(1 << (j + 1)) - 1].max())
+                                      for j in range(min(kap, 4))]}
             h.close()
         rows4[name] = r
-    out["paper_shaped_n1e6"] = rows4
+    out["paper_shaped"] = rows4
     return out
 
 
