@@ -68,7 +68,7 @@ def lib():
         L.oracle_tree_order.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _lp]
         L.oracle_hodlr_build.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp,
                                          ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                         ctypes.c_int, _ip]
+                                         ctypes.c_int, ctypes.c_int, _ip]
         L.oracle_hodlr_build.restype = ctypes.c_void_p
         L.oracle_hodlr_kappa.argtypes = [ctypes.c_void_p]
         L.oracle_hodlr_kappa.restype = ctypes.c_int
@@ -247,13 +247,18 @@ def tree_order(x, leaf: int) -> np.ndarray:
 class Hodlr:
     """O2: the plain CPU HODLR factorization (same call sequence as the C-ABI)."""
 
-    def __init__(self, x, kernel, theta, sigma2, leaf, eps, max_rank=64, allow_rank_cap=False):
+    def __init__(self, x, kernel, theta, sigma2, leaf, eps, max_rank=64, allow_rank_cap=False,
+                 compression: str = "aca"):
+        """compression: "aca" (adaptive cross approximation) or "chebyshev" (analytic
+        interpolation, 1-D)."""
         x = _f64(x)
         self.n, self.d = (x.shape[0], 1) if x.ndim == 1 else x.shape
         st = ctypes.c_int()
         th = _theta(theta)
         self._h = lib().oracle_hodlr_build(_d(x), self.n, self.d, KERNELS[kernel], _d(th), sigma2,
-                                           leaf, eps, max_rank, ctypes.byref(st))
+                                           leaf, eps, max_rank,
+                                           {"aca": 0, "chebyshev": 1}[compression],
+                                           ctypes.byref(st))
         if not self._h:
             raise OracleError(f"build: status {STATUS.get(st.value, st.value)}")
         self.status = st.value

@@ -659,10 +659,168 @@ static int orc_aca(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int64
 
 static int64_t orc_nid(int j, int64_t k) { return ((int64_t)1 << j) - 1 + k; }
 
+/* Analytic compression by Chebyshev interpolation (Sec. 3.1: A ~ E A~ P, A~ the kernel
+ * sampled at Chebyshev nodes of the two clusters, E and P interpolation matrices; the
+ * barycentric formula of Berrut and Trefethen 2004). 1-D only. Reading of the paper's
+ * "spectral analysis of the interpolating Chebyshev polynomial", which it does not spell
+ * out:
+ *   - nodes: q Chebyshev points of the first kind on each child's interval [first point,
+ *     last point], s_a = mid + half cos((2a + 1) pi / (2q));
+ *   - q from 8, 16, 32, 64: the first q for which the 2-D Chebyshev coefficients of the
+ *     interpolant, C = T A~ T^T with T_ja = (2/q) cos(j (2a + 1) pi / (2q)) (row j = 0
+ *     halved), have their last quarter (max(j, k) >= 3q/4) at most eps times the largest
+ *     coefficient; no q up to 64 passing is a failure (*ok = 0);
+ *   - rank: A~ is recompressed by a cross with full pivoting (the largest residual entry,
+ *     lowest row-major index on ties) until the residual's Frobenius norm is at most eps
+ *     times A~'s, capped at min(m_left, m_right, max_rank) (*ok = 0 at the cap);
+ *   - U = E A~_u and V = P A~_v, E_ia = L_a(x_i) the Lagrange basis of the left nodes at
+ *     the left points (barycentric weights (-1)^a sin((2a + 1) pi / (2q))), P likewise.
+ * Returns the rank; U (m_left x r) and V (m_right x r) column-major. */
+#define ORC_CHEB_QMAX 64
+
+static void orc_cheb_nodes(double a, double b, int q, double* s, double* w) {
+  for (int k = 0; k < q; ++k) {
+    double th = (2.0 * k + 1.0) * M_PI / (2.0 * q);
+    s[k] = 0.5 * (a + b) + 0.5 * (b - a) * cos(th);
+    w[k] = ((k & 1) ? -1.0 : 1.0) * sin(th);
+  }
+}
+
+/* Lagrange basis of the nodes s (weights w) at x: L[a] = (w_a / (x - s_a)) / sum_b (w_b /
+ * (x - s_b)); at a node (x == s_a, also every node of a zero-length interval) L = e_a. */
+static void orc_bary(double x, const double* s, const double* w, int q, double* L) {
+  for (int a = 0; a < q; ++a)
+    if (x == s[a]) {
+      for (int b = 0; b < q; ++b) L[b] = b == a ? 1.0 : 0.0;
+      return;
+    }
+  double den = 0.0;
+  for (int a = 0; a < q; ++a) {
+    L[a] = w[a] / (x - s[a]);
+    den += L[a];
+  }
+  for (int a = 0; a < q; ++a) L[a] /= den;
+}
+
+static int orc_cheb(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int64_t mr,
+                    double** Uo, double** Vo, int* ok) {
+  const int Q = ORC_CHEB_QMAX;
+  double s[ORC_CHEB_QMAX], ws[ORC_CHEB_QMAX], t[ORC_CHEB_QMAX], wt[ORC_CHEB_QMAX];
+  double* A = (double*)malloc(sizeof(double) * Q * Q);
+  double* W = (double*)malloc(sizeof(double) * Q * Q);
+  const double* x = H->xs; /* 1-D: sorted, so each child's interval is [first, last] */
+  if (ml == 0 || mr == 0) { /* an empty block: exact at rank 0 */
+    free(A); free(W);
+    *Uo = (double*)malloc(sizeof(double));
+    *Vo = (double*)malloc(sizeof(double));
+    *ok = 1;
+    return 0;
+  }
+  double a1 = x[bl], b1 = x[bl + ml - 1], a2 = x[br], b2 = x[br + mr - 1];
+  int q = 0;
+  *ok = 0;
+  for (int qq = 8; qq <= Q; qq *= 2) {
+    orc_cheb_nodes(a1, b1, qq, s, ws);
+    orc_cheb_nodes(a2, b2, qq, t, wt);
+    for (int i = 0; i < qq; ++i)
+      for (int j = 0; j < qq; ++j) {
+        double r = fabs(s[i] - t[j]);
+        A[i * qq + j] = orc_kernel(&H->cov, r, r * r);
+      }
+    /* C = T A T^T */
+    for (int jj = 0; jj < qq; ++jj)
+      for (int b = 0; b < qq; ++b) {
+        double acc = 0.0;
+        for (int a = 0; a < qq; ++a)
+          acc += cos(jj * (2.0 * a + 1.0) * M_PI / (2.0 * qq)) * A[a * qq + b];
+        W[jj * qq + b] = acc * (jj == 0 ? 1.0 : 2.0) / qq;
+      }
+    double cmax = 0.0, tail = 0.0;
+    for (int jj = 0; jj < qq; ++jj)
+      for (int kk = 0; kk < qq; ++kk) {
+        double acc = 0.0;
+        for (int b = 0; b < qq; ++b)
+          acc += W[jj * qq + b] * cos(kk * (2.0 * b + 1.0) * M_PI / (2.0 * qq));
+        double c = fabs(acc * (kk == 0 ? 1.0 : 2.0) / qq);
+        if (c > cmax) cmax = c;
+        if ((jj >= qq - qq / 4 || kk >= qq - qq / 4) && c > tail) tail = c;
+      }
+    if (tail <= H->eps * cmax) {
+      q = qq;
+      break;
+    }
+  }
+  int64_t cap64 = ml < mr ? ml : mr;
+  int rmax = (int)(cap64 < H->max_rank ? cap64 : H->max_rank);
+  double* Ua = (double*)malloc(sizeof(double) * Q * (rmax > 0 ? rmax : 1));
+  double* Va = (double*)malloc(sizeof(double) * Q * (rmax > 0 ? rmax : 1));
+  int r = 0;
+  if (q > 0) {
+    /* cross with full pivoting on A (q x q), residual in W */
+    double n0 = 0.0;
+    for (int e = 0; e < q * q; ++e) {
+      W[e] = A[e];
+      n0 += A[e] * A[e];
+    }
+    *ok = 1;
+    for (;;) {
+      double res = 0.0, best = -1.0;
+      int pi = 0, pj = 0;
+      for (int e = 0; e < q * q; ++e) {
+        res += W[e] * W[e];
+        if (fabs(W[e]) > best) {
+          best = fabs(W[e]);
+          pi = e / q;
+          pj = e % q;
+        }
+      }
+      if (res <= H->eps * H->eps * n0 || best == 0.0) break;
+      if (r == rmax) {
+        *ok = 0;
+        break;
+      }
+      double piv = W[pi * q + pj];
+      for (int a = 0; a < q; ++a) {
+        Ua[r * Q + a] = W[a * q + pj];
+        Va[r * Q + a] = W[pi * q + a] / piv;
+      }
+      for (int a = 0; a < q; ++a)
+        for (int b = 0; b < q; ++b) W[a * q + b] -= Ua[r * Q + a] * Va[r * Q + b];
+      ++r;
+    }
+  }
+  double* U = (double*)malloc(sizeof(double) * ml * (r > 0 ? r : 1));
+  double* V = (double*)malloc(sizeof(double) * mr * (r > 0 ? r : 1));
+  double L[ORC_CHEB_QMAX];
+  for (int64_t i = 0; i < ml && r > 0; ++i) {
+    orc_bary(x[bl + i], s, ws, q, L);
+    for (int l = 0; l < r; ++l) {
+      double acc = 0.0;
+      for (int a = 0; a < q; ++a) acc += L[a] * Ua[l * Q + a];
+      U[l * ml + i] = acc;
+    }
+  }
+  for (int64_t j = 0; j < mr && r > 0; ++j) {
+    orc_bary(x[br + j], t, wt, q, L);
+    for (int l = 0; l < r; ++l) {
+      double acc = 0.0;
+      for (int b = 0; b < q; ++b) acc += L[b] * Va[l * Q + b];
+      V[l * mr + j] = acc;
+    }
+  }
+  free(A); free(W); free(Ua); free(Va);
+  *Uo = U;
+  *Vo = V;
+  return r;
+}
+
+/* compression: 0 = adaptive cross approximation, 1 = Chebyshev interpolation (1-D). */
 void* oracle_hodlr_build(const double* x, int64_t n, int d, int kind, const double* theta,
-                         double sigma2, int leaf, double eps, int max_rank, int* status) {
+                         double sigma2, int leaf, double eps, int max_rank, int compression,
+                         int* status) {
   if (n < 1 || d < 1 || d > ORC_MAX_D || leaf < 1 || !(eps > 0) || sigma2 < 0 || max_rank < 1 ||
-      kind < 0 || kind > ORC_BH || (kind == ORC_RQ && !(theta[2] > 0))) {
+      kind < 0 || kind > ORC_BH || (kind == ORC_RQ && !(theta[2] > 0)) ||
+      compression < 0 || compression > 1 || (compression == 1 && d != 1)) {
     *status = ORC_EINVAL;
     return NULL;
   }
@@ -698,7 +856,8 @@ void* oracle_hodlr_build(const double* x, int64_t n, int d, int kind, const doub
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t id = 0; id < nint; ++id) {
     int64_t l = 2 * id + 1, r = 2 * id + 2;
-    H->rank[id] = orc_aca(H, H->nb[l], H->ns[l], H->nb[r], H->ns[r], &H->U[id], &H->V[id],
+    H->rank[id] = (compression == 1 ? orc_cheb : orc_aca)(H, H->nb[l], H->ns[l], H->nb[r],
+                                                         H->ns[r], &H->U[id], &H->V[id],
                           &H->aca_ok[id]);
   }
   int st = ORC_OK;

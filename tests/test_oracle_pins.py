@@ -474,6 +474,74 @@ def test_hodlr_positive_radial_vs_dense(kern, theta):
     np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-9 * np.abs(sol_d).max())
 
 
+# ---------------------------------------------------------------- Chebyshev compression --
+
+@pytest.mark.parametrize("kern,rank", [("exp", 1), ("matern32", 2), ("matern52", 3)])
+def test_chebyshev_exact_ranks(kern, rank):
+    """On sorted 1-D clusters these kernels are sums of 1 / 2 / 3 separable terms
+    (e^{x-y} times 1, (x - y), (x - y)^2), so the recompressed node samples have exactly
+    that rank, at every node, whatever q the coefficient test picked."""
+    x, _ = I.workload_1d(6000, 51)
+    H = O.Hodlr(x, kern, [0.1, 1.0], 0.01, 64, 1e-10, compression="chebyshev")
+    assert np.all(H.ranks() == rank)
+
+
+@pytest.mark.parametrize("kern,ell", [("se", 0.3), ("imq", 0.5), ("rq", 0.4), ("mq", 1.0)])
+def test_chebyshev_block_error(kern, ell):
+    """||B - U V^T||_F <= C eps ||B||_F for the top block and a deep one (Sec. 3.1's
+    interpolation error, C = 100 for the Lebesgue constants and the tail estimate)."""
+    x, _ = I.workload_1d(3000, 52, lo=-3.0, hi=3.0)
+    eps = 1e-10
+    H = O.Hodlr(x, kern, [ell, 1.0], 1.0, 32, eps, max_rank=256, compression="chebyshev")
+    xs = x[H.perm(), 0]
+    for node in (0, 6):
+        U, V = H.node_factors(node)
+        (bl, ml), (br, mr) = _node_children(H, node)
+        r = np.abs(xs[bl:bl + ml, None] - xs[None, br:br + mr])
+        B = O.kernel_values(kern, r.ravel(), ell, 1.0).reshape(r.shape)
+        err = np.linalg.norm(B - U @ V.T) / np.linalg.norm(B)
+        assert err <= 100 * eps, (node, err)
+
+
+def _node_children(H, node):
+    out = []
+    for c in (2 * node + 1, 2 * node + 2):
+        b, s = O.ctypes.c_int64(), O.ctypes.c_int64()
+        O.lib().oracle_hodlr_node_range(H._h, c, O.ctypes.byref(b), O.ctypes.byref(s))
+        out.append((b.value, s.value))
+    return out
+
+
+@pytest.mark.parametrize("kern,ell,s2", [("se", 0.3, 0.01), ("matern52", 0.3, 0.01),
+                                         ("imq", 0.5, 1.0), ("mq", 1.0, 1.0)])
+def test_chebyshev_hodlr_vs_dense(kern, ell, s2):
+    n = 3000
+    x, y = I.workload_1d(n, 53, lo=-3.0, hi=3.0)
+    x[17] = x[16]  # a duplicated point
+    H = O.Hodlr(x, kern, [ell, 1.0], s2, 32, 1e-12, max_rank=256, compression="chebyshev")
+    sol = H.factor_solve(y)
+    if kern in O.INDEFINITE:
+        sol_d, ld_d, sg = O.dense_lu_solve(x, kern, [ell, 1.0], s2, y)
+        assert H.logdet_sign() == sg
+    else:
+        sol_d, ld_d = O.dense_solve(x, kern, [ell, 1.0], s2, y)
+    assert abs(H.logdet() - ld_d) <= 1e-11 * abs(ld_d)
+    np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-8 * np.abs(sol_d).max())
+
+
+def test_chebyshev_reports_nonconvergence():
+    """r^2 log r is not smooth where the two clusters meet, and a length scale far below
+    the clusters' size needs more than 64 nodes: both report the rank cap status."""
+    x, _ = I.workload_1d(2000, 54, lo=-3.0, hi=3.0)
+    with pytest.raises(O.OracleError):
+        O.Hodlr(x, "biharmonic", [1.0, 1.0], 2.0, 32, 1e-12, compression="chebyshev")
+    with pytest.raises(O.OracleError):
+        O.Hodlr(x, "se", [0.01, 1.0], 0.01, 32, 1e-12, compression="chebyshev")
+    with pytest.raises(O.OracleError):  # 1-D only
+        O.Hodlr(I.workload_2d(500, 55)[0], "se", [0.3, 1.0], 0.01, 32, 1e-12,
+                compression="chebyshev")
+
+
 def test_hodlr_matvec_matches_dense():
     n = 800
     x, y = I.workload_1d(n, 95)
