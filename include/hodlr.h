@@ -86,6 +86,14 @@ typedef struct {
                        /*    corrections (no host check of the residual).                  */
   void* stream;        /* cudaStream_t for all device work; NULL = legacy default stream  */
   double rq_alpha;     /* exponent alpha > 0 of HODLR_K_RQ, default 1                      */
+  int compression;     /* 0: adaptive cross approximation (default); 1: Chebyshev          */
+                       /*    interpolation (Sec. 3.1's analytic A ~ E A~ P, barycentric    */
+                       /*    form): q = 8..64 nodes per cluster, the first q whose last    */
+                       /*    quarter of 2-D Chebyshev coefficients is below eps, then A~   */
+                       /*    recompressed to rank by a fully pivoted cross. d = 1 only; no  */
+                       /*    presize. A block needing more than 64 nodes (a kernel that is */
+                       /*    not smooth where the clusters meet, or ell much shorter than  */
+                       /*    the clusters) gets rank 0 and the build returns ERANK.         */
 } hodlr_opts;
 
 /* Fill *o with the defaults listed above. */

@@ -674,7 +674,12 @@ static int64_t orc_nid(int j, int64_t k) { return ((int64_t)1 << j) - 1 + k; }
  *     lowest row-major index on ties) until the residual's Frobenius norm is at most eps
  *     times A~'s, capped at min(m_left, m_right, max_rank) (*ok = 0 at the cap);
  *   - U = E A~_u and V = P A~_v, E_ia = L_a(x_i) the Lagrange basis of the left nodes at
- *     the left points (barycentric weights (-1)^a sin((2a + 1) pi / (2q))), P likewise.
+ *     the left points (barycentric weights (-1)^a sin((2a + 1) pi / (2q))), P likewise;
+ *   - a block that interpolation cannot represent within its caps (no q up to 64 passes,
+ *     or the cross reaches min(m_left, m_right)) is stored exactly when
+ *     m = min(m_left, m_right) <= max_rank: rank m, the identity on the smaller side and
+ *     the block's entries on the other (a small block has rank at most m, while its
+ *     interpolant can need more terms); otherwise *ok = 0.
  * Returns the rank; U (m_left x r) and V (m_right x r) column-major. */
 #define ORC_CHEB_QMAX 64
 
@@ -809,6 +814,22 @@ static int orc_cheb(const orc_hodlr* H, int64_t bl, int64_t ml, int64_t br, int6
     }
   }
   free(A); free(W); free(Ua); free(Va);
+  int64_t mmin = ml < mr ? ml : mr;
+  if (!*ok && mmin <= H->max_rank) { /* exact storage */
+    free(U);
+    free(V);
+    int m = (int)mmin;
+    U = (double*)malloc(sizeof(double) * ml * m);
+    V = (double*)malloc(sizeof(double) * mr * m);
+    for (int l = 0; l < m; ++l) {
+      for (int64_t i = 0; i < ml; ++i)
+        U[l * ml + i] = ml <= mr ? (i == l ? 1.0 : 0.0) : orc_kij(x, 1, &H->cov, bl + i, br + l);
+      for (int64_t j = 0; j < mr; ++j)
+        V[l * mr + j] = ml <= mr ? orc_kij(x, 1, &H->cov, bl + l, br + j) : (j == l ? 1.0 : 0.0);
+    }
+    *ok = 1;
+    r = m;
+  }
   *Uo = U;
   *Vo = V;
   return r;

@@ -78,6 +78,7 @@ void free_all(Ctx* c) {
   free_factor_buffers(c);
   dfree(c->nodes); dfree(c->xs); dfree(c->perm);
   dfree(c->item_node); dfree(c->item_start); dfree(c->node_item0); dfree(c->node_item1); dfree(c->raw);
+  dfree(c->cheb_q); dfree(c->cheb_coef);
   dfree(c->st_rank); dfree(c->st_row); dfree(c->st_col); dfree(c->st_done); dfree(c->st_ok);
   dfree(c->st_zero); dfree(c->st_phase); dfree(c->st_nused); dfree(c->st_used);
   dfree(c->st_delta); dfree(c->st_s2); dfree(c->aca_part); dfree(c->active);
@@ -172,6 +173,10 @@ hodlr_status setup_aca(Ctx* c) {
   TRY_CUDA(c, dalloc(&c->st_delta, nint), "alloc aca state");
   TRY_CUDA(c, dalloc(&c->st_s2, nint), "alloc aca state");
   TRY_CUDA(c, dalloc(&c->aca_part, c->n_items * (4 + 2 * c->max_rank)), "alloc aca partials");
+  if (c->compression == 1) {
+    TRY_CUDA(c, dalloc(&c->cheb_q, nint), "alloc chebyshev state");
+    TRY_CUDA(c, dalloc(&c->cheb_coef, (int64_t)hodlr::cheb_coef_elems(nint)), "alloc chebyshev state");
+  }
   TRY_CUDA(c, cudaMemcpyAsync(c->item_node, inode.data(), 4 * inode.size(), cudaMemcpyHostToDevice, c->stream), "upload");
   TRY_CUDA(c, cudaMemcpyAsync(c->item_start, istart.data(), 4 * istart.size(), cudaMemcpyHostToDevice, c->stream), "upload");
   TRY_CUDA(c, cudaMemcpyAsync(c->node_item0, i0.data(), 4 * i0.size(), cudaMemcpyHostToDevice, c->stream), "upload");
@@ -262,7 +267,10 @@ hodlr_status compress(Ctx* c) {
   bool cap = capturing(c);
   if (!cap) cudaEventRecord(c->ev[2], c->stream);
   int steps = 0;
-  TRY_CUDA(c, hodlr::launch_aca(*c, &steps), "aca");
+  if (c->compression == 1)
+    TRY_CUDA(c, hodlr::launch_cheb(*c), "chebyshev compression");
+  else
+    TRY_CUDA(c, hodlr::launch_aca(*c, &steps), "aca");
   if (!c->presized) {
     c->h_rank.assign(nint, 0);
     std::vector<int32_t> ok(nint, 1);
@@ -306,6 +314,7 @@ void hodlr_default_opts(hodlr_opts* o) {
   o->refine_maxit = 0;
   o->stream = nullptr;
   o->rq_alpha = 1.0;
+  o->compression = 0;
 }
 
 const char* hodlr_status_string(hodlr_status s) {
@@ -354,6 +363,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
       (int)kernel > HODLR_K_BIHARMONIC ||
       (kernel == HODLR_K_RQ && (!(opts.rq_alpha > 0) || !std::isfinite(opts.rq_alpha))) ||
       (hodlr::kind_indefinite(kernel) && opts.precision != 0) ||
+      (opts.compression != 0 && opts.compression != 1) || (opts.compression == 1 && d != 1) ||
       opts.max_rank < 1 || opts.max_rank > hodlr::kMaxRank || opts.max_nrhs < 1 ||
       (opts.precision != 0 && opts.precision != 1) || opts.refine_maxit < 0 ||
       (opts.refine_maxit > 0 && (!(opts.refine_tol > 0) || !std::isfinite(opts.refine_tol))))
@@ -364,6 +374,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   c->d = d;
   c->kind = (int)kernel;
   c->alpha = opts.rq_alpha;
+  c->compression = opts.compression;
   c->indefinite = hodlr::kind_indefinite(kernel);
   c->ell = theta[0];
   c->amp = theta[1];
@@ -451,7 +462,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   cudaEventElapsedTime(&c->phase_ms[1], c->ev[2], c->ev[3]);
   *out = reinterpret_cast<hodlr_ctx*>(c);
   if (c->rank_capped) {
-    c->last_error = "ACA reached max_rank before eps in at least one block";
+    c->last_error = "compression reached max_rank before eps (Chebyshev: needed more than 64 nodes) in at least one block";
     return HODLR_ERANK;
   }
   return HODLR_OK;
@@ -472,7 +483,7 @@ hodlr_status hodlr_rebuild(hodlr_ctx* ctx, const double* theta, double sigma2) {
   TRY_CUDA(c, cudaStreamSynchronize(c->stream), "rebuild");
   ++c->syncs;
   cudaEventElapsedTime(&c->phase_ms[1], c->ev[2], c->ev[3]);
-  if (c->rank_capped) return fail(c, HODLR_ERANK, "ACA reached max_rank before eps in at least one block");
+  if (c->rank_capped) return fail(c, HODLR_ERANK, "compression reached max_rank before eps (Chebyshev: needed more than 64 nodes) in at least one block");
   return HODLR_OK;
 }
 
@@ -723,6 +734,8 @@ hodlr_status hodlr_presize(hodlr_ctx* ctx, const int32_t* level_ranks, int nleve
   if (!c) return HODLR_EINVAL;
   if (c->indefinite && level_ranks)
     return fail(c, HODLR_EINVAL, "presize: not for an indefinite kernel (its sign needs a read-back)");
+  if (c->compression == 1 && level_ranks)
+    return fail(c, HODLR_EINVAL, "presize: not with Chebyshev compression");
   if (!level_ranks) {
     c->presized = false;
     c->graph_valid = false;

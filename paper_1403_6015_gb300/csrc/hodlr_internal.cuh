@@ -128,6 +128,9 @@ struct Ctx {
   bool indefinite = false;        // multiquadric / biharmonic: LU leaves, signed log |det|
   int det_sign = 1;               // sign of det C after the last factorization
   int32_t* leaf_perm = nullptr;   // LU row orders, kMaxLeaf per leaf (indefinite only)
+  int compression = 0;            // 0: cross approximation, 1: Chebyshev interpolation
+  int32_t* cheb_q = nullptr;      // Chebyshev nodes per cluster of each internal node
+  double* cheb_coef = nullptr;    // Chebyshev: factors of the sampled blocks
   int leaf = 128, kappa = 0, max_rank = kDefaultMaxRank, max_nrhs = 16;
   int precision = 0;              // 0: FP64, 1: double-float leaf stage (mixed)
   int leaf_threads = 512;         // CTA size of the double-float leaf kernel (two CTAs per SM)
@@ -244,6 +247,8 @@ struct Ctx {
 cudaError_t launch_sort_1d(Ctx& c, const double* x_dev_rowmajor);
 cudaError_t launch_sort_kd(Ctx& c, const double* x_dev_rowmajor);
 cudaError_t launch_aca(Ctx& c, int* steps_out);
+cudaError_t launch_cheb(Ctx& c);
+size_t cheb_coef_elems(int nint);
 cudaError_t launch_pack(Ctx& c);
 cudaError_t launch_exp_table(Ctx& c);
 cudaError_t launch_xrel(Ctx& c);

@@ -37,7 +37,8 @@ class hodlr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rank_mode", ctypes.c_int),
                 ("max_rank", ctypes.c_int), ("max_nrhs", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("rq_alpha", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("rq_alpha", ctypes.c_double),
+                ("compression", ctypes.c_int)]
 
 
 _lib = None
@@ -354,7 +355,7 @@ class Hodlr:
     def __init__(self, x, kernel: str, theta, sigma2: float, leaf: int, eps: float,
                  max_rank: int = 64, max_nrhs: int = 16, stream=None, allow_rank_cap=False,
                  precision: int = 0, refine_maxit: int = 0, refine_tol: float = 1e-10,
-                 rq_alpha: float = 1.0):
+                 rq_alpha: float = 1.0, compression: str = "aca"):
         if _is_torch(x):
             if x.dtype.itemsize != 8 or not x.is_contiguous():
                 raise ValueError("x must be a contiguous float64 tensor")
@@ -372,6 +373,7 @@ class Hodlr:
         o.refine_maxit = refine_maxit
         o.refine_tol = refine_tol
         o.rq_alpha = rq_alpha
+        o.compression = {"aca": 0, "chebyshev": 1}[compression]
         if stream is not None:
             o.stream = stream
         self.kernel = kernel

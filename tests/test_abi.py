@@ -98,6 +98,13 @@ def test_build_rejects_bad_options():
         assert st == hodlr.HODLR_EINVAL and not ctx
     st, ctx = hodlr.hodlr_build(x, 64, 1, 8, [0.2, 1.0], 0.01, 16, 1e-12, None)
     assert st == hodlr.HODLR_EINVAL and not ctx
+    # Chebyshev compression: codes 0/1 only, points in 1-D only
+    for comp, xx, d in [(2, x, 1), (-1, x, 1), (1, np.zeros((64, 2)), 2)]:
+        o = hodlr.hodlr_default_opts()
+        o.compression = comp
+        st, ctx = hodlr.hodlr_build(xx, 64, d, 1, [0.2, 1.0], 0.01, 16, 1e-12, o)
+        assert st == hodlr.HODLR_EINVAL and not ctx
+    assert hodlr.hodlr_default_opts().compression == 0
     x65 = np.zeros((2, 65))
     st, ctx = hodlr.hodlr_build(x65, 2, 65, 0, [0.2, 1.0], 0.01, 16, 1e-12, None)
     assert st == hodlr.HODLR_EINVAL and not ctx

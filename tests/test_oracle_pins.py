@@ -529,6 +529,18 @@ def test_chebyshev_hodlr_vs_dense(kern, ell, s2):
     np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-8 * np.abs(sol_d).max())
 
 
+@pytest.mark.parametrize("n", [3, 5, 11, 40])
+def test_chebyshev_small_blocks_stored_exactly(n):
+    """Leaf size 1: 1 x 2 or 2 x 2 blocks, whose interpolants need more terms than the
+    blocks' own rank, are stored exactly; the result is the dense one."""
+    x, y = I.workload_1d(n, 65 + n)
+    sol_d, ld_d = O.dense_solve(x, "se", [0.5, 1.0], 0.1, y)
+    H = O.Hodlr(x, "se", [0.5, 1.0], 0.1, 1, 1e-13, compression="chebyshev")
+    sol = H.factor_solve(y)
+    assert abs(H.logdet() - ld_d) <= 1e-12 * max(1.0, abs(ld_d))
+    np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-10 * np.abs(sol_d).max())
+
+
 def test_chebyshev_reports_nonconvergence():
     """r^2 log r is not smooth where the two clusters meet, and a length scale far below
     the clusters' size needs more than 64 nodes: both report the rank cap status."""
