@@ -630,6 +630,30 @@ def run_supplementary(args):
         h.close()
     out["phases_n2p20_mixed"] = ph
 
+    # (1b) the analytic compression (Chebyshev interpolation) against the cross
+    # approximation on the same evaluation: compression time, ranks, log-likelihood
+    cheb = {}
+    for kern, ell in KERNELS + [("se", 0.3)]:
+        row = {}
+        for comp in ("aca", "chebyshev"):
+            h = H.Hodlr(xd, kern, [ell, 1.0], SIGMA2, LEAF, EPS, precision=1, compression=comp)
+            comp_ms = ms_of(lambda: h.rebuild([ell, 1.0], SIGMA2))
+
+            def ev():
+                h.rebuild([ell, 1.0], SIGMA2)
+                return h.loglik(yd)
+            ev_ms = ms_of(ev)
+            k2 = h.tree()[0]
+            rk = h.ranks()
+            row[comp] = {"compression_ms": comp_ms, "eval_ms": ev_ms, "loglik": ev(),
+                         "level_ranks": [int(rk[(1 << j) - 1:(1 << (j + 1)) - 1].max())
+                                         for j in range(k2)]}
+            h.close()
+        row["loglik_rel_diff"] = abs(row["aca"]["loglik"] - row["chebyshev"]["loglik"]) / abs(
+            row["aca"]["loglik"])
+        cheb[f"{kern}_ell{ell}"] = row
+    out["chebyshev_vs_aca_n2p20_mixed"] = cheb
+
     # (2) mixed precision + refinement at n = 2^22 (1-D squared-exponential)
     n3 = 1 << 22
     x3, y3 = I.workload_1d(n3, 1003)

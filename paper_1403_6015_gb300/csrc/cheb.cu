@@ -10,14 +10,18 @@
 //                  memory products with a cosine table); the first q whose last quarter of
 //                  coefficients is at most eps times the largest is kept; then a cross with
 //                  full pivoting on A~ down to a residual of eps ||A~||_F gives the rank r
-//                  and the q x r factors of A~ = A~_u A~_v^T. A block that interpolation
+//                  and the q x r factors of A~ = A~_u A~_v^T, turned into Chebyshev
+//                  coefficients (c = T A~_u, the same transform). A block that interpolation
 //                  cannot represent within its caps (no q passes, or the cross reaches
 //                  min(m_L, m_R)) is stored exactly when m = min(m_L, m_R) <= max_rank
 //                  (rank m: identity on the smaller side, the block's entries on the
 //                  other; q = -1 marks it), else its rank is 0 and ok = 0.
 //   k_cheb_expand  one CTA per (leaf, level): the leaf's rows of the level's U (left child)
-//                  or V (right child): the Lagrange basis of the child's nodes at each point
-//                  times A~_u (or A~_v).
+//                  or V (right child): the interpolating polynomial evaluated in the
+//                  Chebyshev basis, T_k(u) by the three-term recurrence at u = the point
+//                  mapped to [-1, 1], times the coefficients. This is the polynomial the
+//                  barycentric form gives (Lagrange basis at the same nodes), with no
+//                  division per point and node.
 #include <cuda_runtime.h>
 
 #include "ff.cuh"
@@ -44,18 +48,17 @@ struct ChebArgs {
   int32_t* rank;   // per internal node
   int32_t* ok;     // 1 if converged below the caps
   int32_t* qn;     // nodes per cluster chosen, 0 if none up to kChebQ, -1: stored exactly
-  double* coef;    // per node: A~_u then A~_v, each kChebQ x kChebQ, column l at l * kChebQ
+  double* coef;    // per node: Chebyshev coefficients of A~_u then of A~_v, each
+                   // kChebQ x kChebQ, column l at l * kChebQ
   double* raw;
   int64_t raw_off[32];
   int ff_out;      // 1: store the panels as double-float pairs (mixed form)
 };
 
-// q Chebyshev points of the first kind on [lo, hi] and their barycentric weights.
-__device__ __forceinline__ void cheb_point(double lo, double hi, int q, int k, double* s,
-                                           double* w) {
+// Chebyshev point k of the first kind (of q) on [lo, hi].
+__device__ __forceinline__ double cheb_point(double lo, double hi, int q, int k) {
   double th = (2.0 * k + 1.0) * kPi / (2.0 * q);
-  *s = 0.5 * (lo + hi) + 0.5 * (hi - lo) * cos(th);
-  if (w) *w = ((k & 1) ? -1.0 : 1.0) * sin(th);
+  return 0.5 * (lo + hi) + 0.5 * (hi - lo) * cos(th);
 }
 
 // Block-wide max of v (all threads get it).
@@ -83,9 +86,10 @@ __device__ double block_sum(double v, double* red) {
 }
 
 __global__ void __launch_bounds__(kChebThreads) k_cheb_node(ChebArgs a) {
-  extern __shared__ double sm[];  // A (q x q), W (q x q)
+  extern __shared__ double sm[];  // A (q x q, then A~_u), W (q x q residual), V (A~_v)
   double* A = sm;
   double* W = sm + kChebQ * kChebQ;
+  double* V = sm + 2 * kChebQ * kChebQ;
   __shared__ double s[kChebQ], t[kChebQ], ctab[4 * kChebQ], us[kChebQ], vs[kChebQ];
   __shared__ double red[kW], redb[kW];
   __shared__ int redi[kW];
@@ -105,8 +109,8 @@ __global__ void __launch_bounds__(kChebThreads) k_cheb_node(ChebArgs a) {
   int q = 0;
   for (int qq = 8; qq <= kChebQ; qq *= 2) {
     for (int k = tid; k < qq; k += kChebThreads) {
-      cheb_point(a1, b1, qq, k, &s[k], nullptr);
-      cheb_point(a2, b2, qq, k, &t[k], nullptr);
+      s[k] = cheb_point(a1, b1, qq, k);
+      t[k] = cheb_point(a2, b2, qq, k);
     }
     for (int m = tid; m < 4 * qq; m += kChebThreads) ctab[m] = cos(m * kPi / (2.0 * qq));
     __syncthreads();
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(kChebThreads) k_cheb_node(ChebArgs a) {
     W[e] = A[e];
     n0 += A[e] * A[e];
   }
-  n0 = block_sum(n0, red);
+  n0 = block_sum(n0, red);  // (its barriers also end the reads of A: it now holds A~_u)
   double* cu = a.coef + (int64_t)id * 2 * kChebQ * kChebQ;
   double* cv = cu + kChebQ * kChebQ;
   int r = 0, okv = 1;
@@ -207,8 +211,8 @@ __global__ void __launch_bounds__(kChebThreads) k_cheb_node(ChebArgs a) {
       double u = W[k * q + pj], v = W[pi * q + k] / piv;
       us[k] = u;
       vs[k] = v;
-      cu[r * kChebQ + k] = u;
-      cv[r * kChebQ + k] = v;
+      A[r * kChebQ + k] = u;
+      V[r * kChebQ + k] = v;
     }
     __syncthreads();
     for (int e = tid; e < q * q; e += kChebThreads) {
@@ -218,20 +222,30 @@ __global__ void __launch_bounds__(kChebThreads) k_cheb_node(ChebArgs a) {
     __syncthreads();
     ++r;
   }
+  const bool exact = !okv && mmin <= a.max_rank;
   if (tid == 0) {
-    bool exact = !okv && mmin <= a.max_rank;
     a.qn[id] = exact ? -1 : q;
     a.rank[id] = exact ? mmin : r;
     a.ok[id] = exact ? 1 : okv;
   }
+  if (exact) return;
+  // Chebyshev coefficients of each factor column: c_kl = (2/q) sum_a cos(k th_a) F_al,
+  // row 0 halved (ctab still holds the cosines of the accepted q)
+  for (int e = tid; e < 2 * r * q; e += kChebThreads) {
+    int side = e / (r * q), f = e - side * r * q;
+    int l = f / q, k = f - l * q;
+    const double* F = side ? V : A;
+    double acc = 0.0;
+    for (int aa = 0; aa < q; ++aa) acc += ctab[(k * (2 * aa + 1)) % (4 * q)] * F[l * kChebQ + aa];
+    (side ? cv : cu)[l * kChebQ + k] = acc * (k == 0 ? 1.0 : 2.0) / q;
+  }
 }
 
 __global__ void __launch_bounds__(kMaxLeaf) k_cheb_expand(ChebArgs a) {
-  extern __shared__ double sm[];  // coefficients (q x r, column l at l * kChebQ), L (128 x 65)
+  extern __shared__ double sm[];  // coefficients (q x r, column l at l * kChebQ), T (128 x 65)
   double* cf = sm;
   double* L = sm + kChebQ * kChebQ;
   constexpr int kLS = kChebQ + 1;
-  __shared__ double s[kChebQ], wt[kChebQ];
   const int leaf = blockIdx.x, j = blockIdx.y, tid = threadIdx.x;
   const int K = a.kappa;
   const int anc = (leaf >> (K - j)) + (1 << j) - 1;                 // node at level j
@@ -265,7 +279,8 @@ __global__ void __launch_bounds__(kMaxLeaf) k_cheb_expand(ChebArgs a) {
     return;
   }
   const double lo = a.xs[cb], hi = a.xs[cb + cm - 1];
-  for (int k = tid; k < q; k += kMaxLeaf) cheb_point(lo, hi, q, k, &s[k], &wt[k]);
+  const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+  const double inv_half = half > 0.0 ? 1.0 / half : 0.0;  // a zero-length interval: u = 0
   const double* src = a.coef + (int64_t)anc * 2 * kChebQ * kChebQ + (left ? 0 : kChebQ * kChebQ);
   for (int e = tid; e < r * kChebQ; e += kMaxLeaf) {
     int l = e / kChebQ, k = e - l * kChebQ;
@@ -273,25 +288,17 @@ __global__ void __launch_bounds__(kMaxLeaf) k_cheb_expand(ChebArgs a) {
   }
   __syncthreads();
   if (tid >= p) return;
-  const double x = a.xs[b + tid];
-  double* Li = L + tid * kLS;
-  int hit = -1;
-  for (int k = 0; k < q; ++k)
-    if (x == s[k]) {
-      hit = k;
-      break;
-    }
-  if (hit >= 0) {
-    for (int k = 0; k < q; ++k) Li[k] = k == hit ? 1.0 : 0.0;
-  } else {
-    double den = 0.0;
-    for (int k = 0; k < q; ++k) {
-      double v = wt[k] / (x - s[k]);
-      Li[k] = v;
-      den += v;
-    }
-    double inv = 1.0 / den;
-    for (int k = 0; k < q; ++k) Li[k] *= inv;
+  double u = (a.xs[b + tid] - mid) * inv_half;
+  u = fmin(1.0, fmax(-1.0, u));
+  double* Li = L + tid * kLS;  // T_k(u), k < q
+  double t0 = 1.0, t1 = u;
+  Li[0] = 1.0;
+  if (q > 1) Li[1] = u;
+  for (int k = 2; k < q; ++k) {
+    double t2 = 2.0 * u * t1 - t0;
+    Li[k] = t2;
+    t0 = t1;
+    t1 = t2;
   }
   for (int l = 0; l < r; ++l) {
     double acc = 0.0;
@@ -330,7 +337,7 @@ cudaError_t launch_cheb(Ctx& c) {
   a.raw = c.raw;
   for (int j = 0; j < 32; ++j) a.raw_off[j] = j < c.kappa ? c.h_raw_off[j] : 0;
   a.ff_out = c.precision == 1;
-  const size_t smem_node = sizeof(double) * 2 * kChebQ * kChebQ;
+  const size_t smem_node = sizeof(double) * 3 * kChebQ * kChebQ;
   const size_t smem_exp = sizeof(double) * (kChebQ * kChebQ + kMaxLeaf * (kChebQ + 1));
   HODLR_CUDA_TRY(cudaFuncSetAttribute(k_cheb_node, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_node));
   HODLR_CUDA_TRY(cudaFuncSetAttribute(k_cheb_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_exp));
