@@ -42,7 +42,7 @@ FP64_PEAK = 152 * 2 * 2 * 2.07e9  # SMs x FP64 FMA/clk/SM x 2 flop x max SM cloc
 # DRAM bytes (read + write) of one launch of each form's leaf kernel at n = 2^20, from the
 # ncu captures summarised in profiles/ (scaled from the n = 2^18 capture by the number of
 # leaves); None until a capture matches the current kernel.
-LEAF_TRAFFIC_BYTES = {0: None, 1: 4 * (59.030784 + 125.38752) * 1e6}
+LEAF_TRAFFIC_BYTES = {0: None, 1: 4 * (59.3728 + 130.24128) * 1e6}
 
 
 def config():
