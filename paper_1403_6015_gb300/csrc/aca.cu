@@ -57,13 +57,16 @@ struct AcaArgs {
 };
 
 // Entry k(x_i, x_j) of an off-diagonal block: FP64, or (mixed form) double-float
-// evaluation of the covariance from the FP64 distance.
-template <bool kFF>
+// evaluation of the covariance from the FP64 distance. kGen = false: the kernels
+// specialised for points in one or two dimensions and the four covariances of Table 1
+// (the common case, whose code stays free of the general paths); true: any d and kind.
+template <bool kFF, bool kGen>
 __device__ __forceinline__ double block_entry(const AcaArgs& a, const Cov& cov, int i, int j,
                                               const ff* tab, const CovFF& cf) {
-  double r = dist(a.pts, i, j);
-  if (!kFF) return cov_r(cov, r);
-  return ff_to_double(cov_ff(cf, ff_from_double(r), tab));
+  double r = kGen ? dist(a.pts, i, j) : dist12(a.pts, i, j);
+  if (!kFF) return kGen ? cov_r(cov, r) : cov_r_table1(cov, r);
+  ff v = kGen ? cov_ff(cf, ff_from_double(r), tab) : cov_ff_table1(cf, ff_from_double(r), tab);
+  return ff_to_double(v);
 }
 
 // The same entry as a double-float (mixed form), for i in the left and j in the right
@@ -71,6 +74,7 @@ __device__ __forceinline__ double block_entry(const AcaArgs& a, const Cov& cov, 
 // node's split point (the first point of its right child): in 1-D the left child's are
 // <= 0 and the right child's >= 0, so r = x_j - x_i is a same-sign double-float sum whose
 // error is relative to r itself, also for the closest pairs across the split; no FP64.
+template <bool kGen>
 __device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int lev, int i, int j,
                                             const ff* tab, const CovFF& cf) {
   const int64_t n = a.pts.n;
@@ -82,13 +86,14 @@ __device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int lev, int i, i
   } else {
     ff u = ff_sub(xr[j], xr[i]), v = ff_sub(xr[n + j], xr[n + i]);
     ff s = ff_add(ff_mul(u, u), ff_mul(v, v));
-    for (int c = 2; c < a.pts.d; ++c) {
-      ff w = ff_sub(xr[c * n + j], xr[c * n + i]);
-      s = ff_add(s, ff_mul(w, w));
-    }
+    if (kGen)
+      for (int c = 2; c < a.pts.d; ++c) {
+        ff w = ff_sub(xr[c * n + j], xr[c * n + i]);
+        s = ff_add(s, ff_mul(w, w));
+      }
     r = ff_sqrt(s);
   }
-  return cov_ff(cf, r, tab);
+  return kGen ? cov_ff(cf, r, tab) : cov_ff_table1(cf, r, tab);
 }
 
 __device__ __forceinline__ int level_of(int id) { return 31 - __clz(id + 1); }
@@ -178,7 +183,7 @@ __global__ void k_aca_init(AcaArgs a) {
 }
 
 // A: residual row of the current pivot row, stored unnormalised in column k of the V rows.
-template <bool kFF>
+template <bool kFF, bool kGen>
 __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   int item = blockIdx.x;
   int id = a.item_node[item];
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
     for (int q = 0; q < kPer; ++q) {
       int b = start + q * kAcaThreads + threadIdx.x;
       if (b < mr) {
-        double v = block_entry<false>(a, cov, bl + i, br + b, tab, cf);
+        double v = block_entry<false, kGen>(a, cov, bl + i, br + b, tab, cf);
         for (int l = 0; l < k; ++l) v -= uik[l] * raw[l * n + br + b];
         raw[(int64_t)k * n + br + b] = v;
         amax_merge(bv, bi, v, b);
@@ -230,7 +235,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
     for (int q = 0; q < kPer; ++q) {
       int b = start + q * kAcaThreads + threadIdx.x;
       if (b < mr) {
-        ff v = block_entry_ff(a, level_of(id), bl + i, br + b, tab, cf);
+        ff v = block_entry_ff<kGen>(a, level_of(id), bl + i, br + b, tab, cf);
         for (int l = 0; l < k; ++l) v = ff_fms(v, uik[l], rawf[l * n + br + b]);
         rawf[(int64_t)k * n + br + b] = v;
         amax_merge_f(bv, bi, v.hi, b);
@@ -329,7 +334,7 @@ __global__ void k_aca_pivot_row(AcaArgs a) {
 
 // C: residual column u (stored in column k of the U rows), normalised row v, and this tile's
 // contributions to |u|^2, |v|^2, u_l.u, v_l.v and argmax over unused rows of |u|.
-template <bool kFF>
+template <bool kFF, bool kGen>
 __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   int item = blockIdx.x;
   int id = a.item_node[item];
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
       uu[q] = 0.0;
       vv[q] = 0.0;
       if (t < ml) {
-        double u = block_entry<false>(a, cov, bl + t, br + j, tab, cf);
+        double u = block_entry<false, kGen>(a, cov, bl + t, br + j, tab, cf);
         for (int l = 0; l < k; ++l) u -= raw[l * n + bl + t] * vjk[l];
         raw[(int64_t)k * n + bl + t] = u;
         uu[q] = u;
@@ -427,7 +432,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
       uu[q] = 0.0f;
       vv[q] = 0.0f;
       if (t < ml) {
-        ff u = block_entry_ff(a, level_of(id), bl + t, br + j, tab, cf);
+        ff u = block_entry_ff<kGen>(a, level_of(id), bl + t, br + j, tab, cf);
         for (int l = 0; l < k; ++l) u = ff_fms(u, rawf[l * n + bl + t], vjk[l]);
         rawf[(int64_t)k * n + bl + t] = u;
         uu[q] = u.hi;
@@ -495,7 +500,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
 // as the tiled kernels (argmax, |u|^2, |v|^2, u_l.u, v_l.v).
 constexpr int kSmallPer = kSmallNode / 32;  // elements per lane
 
-template <bool kFF>
+template <bool kFF, bool kGen>
 __global__ void __launch_bounds__(kAcaThreads) k_aca_row_small(AcaArgs a, int item0, int nitem) {
   __shared__ ff tab[64];
   if (kFF) {
@@ -521,7 +526,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row_small(AcaArgs a, int it
     for (int q = 0; q < kSmallPer; ++q) {
       int b = q * 32 + lane;
       if (b < mr) {
-        double v = block_entry<false>(a, cov, bl + i, br + b, tab, CovFF{});
+        double v = block_entry<false, kGen>(a, cov, bl + i, br + b, tab, CovFF{});
         for (int l = 0; l < k; ++l) v -= raw[l * n + bl + i] * raw[l * n + br + b];
         raw[(int64_t)k * n + br + b] = v;
         amax_merge(bv, bi, v, b);
@@ -537,7 +542,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row_small(AcaArgs a, int it
     for (int q = 0; q < kSmallPer; ++q) {
       int b = q * 32 + lane;
       if (b < mr) {
-        ff v = block_entry_ff(a, lev, bl + i, br + b, tab, cf);
+        ff v = block_entry_ff<kGen>(a, lev, bl + i, br + b, tab, cf);
         for (int l = 0; l < k; ++l) v = ff_fms(v, rawf[l * n + bl + i], rawf[l * n + br + b]);
         rawf[(int64_t)k * n + br + b] = v;
         amax_merge_f(bv, bi, v.hi, b);
@@ -552,7 +557,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row_small(AcaArgs a, int it
   }
 }
 
-template <bool kFF>
+template <bool kFF, bool kGen>
 __global__ void __launch_bounds__(kAcaThreads) k_aca_col_small(AcaArgs a, int item0, int nitem) {
   __shared__ ff tab[64];
   if (kFF) {
@@ -586,7 +591,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_small(AcaArgs a, int it
       uu[q] = 0.0;
       vv[q] = 0.0;
       if (t < ml) {
-        double u = block_entry<false>(a, cov, bl + t, br + j, tab, CovFF{});
+        double u = block_entry<false, kGen>(a, cov, bl + t, br + j, tab, CovFF{});
         for (int l = 0; l < k; ++l) u -= raw[l * n + bl + t] * raw[l * n + br + j];
         raw[(int64_t)k * n + bl + t] = u;
         uu[q] = u;
@@ -638,7 +643,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_small(AcaArgs a, int it
       uu[q] = 0.0f;
       vv[q] = 0.0f;
       if (t < ml) {
-        ff u = block_entry_ff(a, lev, bl + t, br + j, tab, cf);
+        ff u = block_entry_ff<kGen>(a, lev, bl + t, br + j, tab, cf);
         for (int l = 0; l < k; ++l) u = ff_fms(u, rawf[l * n + bl + t], rawf[l * n + br + j]);
         rawf[(int64_t)k * n + bl + t] = u;
         uu[q] = u.hi;
@@ -787,6 +792,23 @@ __global__ void k_pack(PackArgs p) {
 
 }  // namespace
 
+// Launch K<kFF, kGen> for the context's form (double-float or FP64) and case (gen: any d
+// and kind; else the kernels specialised for d <= 2 and Table 1's covariances).
+#define ACA_LAUNCH(K, grid, smem, ...)                                               \
+  do {                                                                               \
+    if (c.precision == 1) {                                                          \
+      if (gen)                                                                       \
+        K<true, true><<<grid, kAcaThreads, smem, c.stream>>>(__VA_ARGS__);           \
+      else                                                                           \
+        K<true, false><<<grid, kAcaThreads, smem, c.stream>>>(__VA_ARGS__);          \
+    } else {                                                                         \
+      if (gen)                                                                       \
+        K<false, true><<<grid, kAcaThreads, smem, c.stream>>>(__VA_ARGS__);          \
+      else                                                                           \
+        K<false, false><<<grid, kAcaThreads, smem, c.stream>>>(__VA_ARGS__);         \
+    }                                                                                \
+  } while (0)
+
 cudaError_t launch_aca(Ctx& c, int* steps_out) {
   int nint = (1 << c.kappa) - 1;
   *steps_out = 0;
@@ -828,41 +850,33 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   const size_t smem_col = sizeof(double) * (c.max_rank + (size_t)(2 + 2 * c.max_rank) * (kAcaThreads / 32)) +
                           sizeof(int) * (2 * c.max_rank + 2);
   if (smem_col > 48 * 1024) {
-    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));
-    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));
   }
   // adaptive: until no block is active (host check per step); presized: a fixed number of
   // steps (rank + 1 per block, one spare for a zero pivot) and a device-side check
   int max_steps = c.presized ? maxpre + 2 : 2 * c.max_rank + 4;
+  // the specialised kernels cover points in one or two dimensions and Table 1's kernels
+  const bool gen = c.d > 2 || c.kind > HODLR_K_MATERN52;
   for (int s = 0; s < max_steps; ++s) {
     if (!c.presized) HODLR_CUDA_TRY(cudaMemsetAsync(c.active, 0, sizeof(int32_t), c.stream));
     if (nbig > 0) {
-      if (c.precision == 1)
-        k_aca_row<true><<<(unsigned)nbig, kAcaThreads, smem_row, c.stream>>>(a);
-      else
-        k_aca_row<false><<<(unsigned)nbig, kAcaThreads, smem_row, c.stream>>>(a);
+      ACA_LAUNCH(k_aca_row, (unsigned)nbig, smem_row, a);
       ++c.launches;
     }
     if (nsmall > 0) {
-      if (c.precision == 1)
-        k_aca_row_small<true><<<sgrid, kAcaThreads, 0, c.stream>>>(a, (int)nbig, (int)nsmall);
-      else
-        k_aca_row_small<false><<<sgrid, kAcaThreads, 0, c.stream>>>(a, (int)nbig, (int)nsmall);
+      ACA_LAUNCH(k_aca_row_small, sgrid, 0, a, (int)nbig, (int)nsmall);
       ++c.launches;
     }
     k_aca_pivot_row<<<wblocks, 256, 0, c.stream>>>(a);
     if (nbig > 0) {
-      if (c.precision == 1)
-        k_aca_col<true><<<(unsigned)nbig, kAcaThreads, smem_col, c.stream>>>(a);
-      else
-        k_aca_col<false><<<(unsigned)nbig, kAcaThreads, smem_col, c.stream>>>(a);
+      ACA_LAUNCH(k_aca_col, (unsigned)nbig, smem_col, a);
       ++c.launches;
     }
     if (nsmall > 0) {
-      if (c.precision == 1)
-        k_aca_col_small<true><<<sgrid, kAcaThreads, 0, c.stream>>>(a, (int)nbig, (int)nsmall);
-      else
-        k_aca_col_small<false><<<sgrid, kAcaThreads, 0, c.stream>>>(a, (int)nbig, (int)nsmall);
+      ACA_LAUNCH(k_aca_col_small, sgrid, 0, a, (int)nbig, (int)nsmall);
       ++c.launches;
     }
     k_aca_pivot_col<<<wblocks, 256, 0, c.stream>>>(a);

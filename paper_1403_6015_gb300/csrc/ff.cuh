@@ -188,7 +188,8 @@ static __device__ __noinline__ ff cov_ff_radial(const CovFF& k, ff s, const ff* 
   return ff{nanf(""), 0.0f};
 }
 
-__device__ __forceinline__ ff cov_ff(const CovFF& k, ff r, const ff* tab) {
+// The four covariances of Table 1 alone (kernels specialised for the common case).
+__device__ __forceinline__ ff cov_ff_table1(const CovFF& k, ff r, const ff* tab) {
   ff s = ff_mul(r, k.cr);
   const ff one = {1.0f, 0.0f};
   switch (k.kind) {
@@ -198,14 +199,19 @@ __device__ __forceinline__ ff cov_ff(const CovFF& k, ff r, const ff* tab) {
       return ff_mul(k.amp, ff_exp(ff_mulf(ff_mul(s, s), -0.5f), tab));
     case 2:  // Matern-3/2
       return ff_mul(k.amp, ff_mul(ff_add(one, s), ff_exp(ff_neg(s), tab)));
-    case 3: {  // Matern-5/2
+    default: {  // Matern-5/2
       const ff third = {0.3333333432674408f, -9.934107481068821e-09f};
       ff poly = ff_add(ff_add(one, s), ff_mul(ff_mul(s, s), third));
       return ff_mul(k.amp, ff_mul(poly, ff_exp(ff_neg(s), tab)));
     }
-    default:  // rational quadratic exp(-alpha log(1 + t^2)), inverse multiquadric
-      return cov_ff_radial(k, s, tab);
   }
+}
+
+// Any kind with a double-float form (rational quadratic exp(-alpha log(1 + t^2)) and
+// inverse multiquadric out of line).
+__device__ __forceinline__ ff cov_ff(const CovFF& k, ff r, const ff* tab) {
+  if (k.kind <= 3) return cov_ff_table1(k, r, tab);
+  return cov_ff_radial(k, ff_mul(r, k.cr), tab);
 }
 
 // 2^(j/64), j = 0..63, as double-floats (from the FP64 exp2), for ff_exp.

@@ -49,7 +49,9 @@ static __device__ __noinline__ double cov_r_radial(int kind, double t, double am
   }
 }
 
-__device__ __forceinline__ double cov_r(const Cov& c, double r) {
+// The four covariances of Table 1 (exponential, squared-exponential, Matern-3/2,
+// Matern-5/2) alone: what kernels specialised for the common case evaluate.
+__device__ __forceinline__ double cov_r_table1(const Cov& c, double r) {
   switch (c.kind) {
     case HODLR_K_EXP:
       return c.amp * exp(-r * c.inv_ell);
@@ -61,13 +63,17 @@ __device__ __forceinline__ double cov_r(const Cov& c, double r) {
       double s = 1.7320508075688772 * r * c.inv_ell;  // sqrt(3) r / ell
       return c.amp * (1.0 + s) * exp(-s);
     }
-    case HODLR_K_MATERN52: {
+    default: {  // Matern-5/2
       double s = 2.23606797749979 * r * c.inv_ell;  // sqrt(5) r / ell
       return c.amp * (1.0 + s + s * s * (1.0 / 3.0)) * exp(-s);
     }
-    default:
-      return cov_r_radial(c.kind, r * c.inv_ell, c.amp, c.alpha);
   }
+}
+
+// Any covariance kind.
+__device__ __forceinline__ double cov_r(const Cov& c, double r) {
+  if (c.kind <= HODLR_K_MATERN52) return cov_r_table1(c, r);
+  return cov_r_radial(c.kind, r * c.inv_ell, c.amp, c.alpha);
 }
 
 // Hyperparameters in device memory, so that kernels (and captured graphs) read the current
@@ -86,6 +92,14 @@ struct Pts {
   int64_t n;
   int d;
 };
+
+// Distance for points in one or two dimensions only (kernels specialised for that case).
+__device__ __forceinline__ double dist12(const Pts& p, int i, int j) {
+  if (p.d == 1) return fabs(p.x[i] - p.x[j]);
+  double a = p.x[i] - p.x[j];
+  double b = p.x[p.n + i] - p.x[p.n + j];
+  return sqrt(a * a + b * b);
+}
 
 __device__ __forceinline__ double dist(const Pts& p, int i, int j) {
   if (p.d == 1) return fabs(p.x[i] - p.x[j]);
