@@ -849,7 +849,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   const size_t smem_row = sizeof(double) * c.max_rank;
   const size_t smem_col = sizeof(double) * (c.max_rank + (size_t)(2 + 2 * c.max_rank) * (kAcaThreads / 32)) +
                           sizeof(int) * (2 * c.max_rank + 2);
-  if (smem_col > 48 * 1024) {
+  if (smem_col > kSmemOptIn) {
     HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));
     HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));
     HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col));

@@ -82,7 +82,7 @@ cudaError_t launch_node(Ctx& c, const NodeArgs& na, bool factor_mode) {
   int r = na.r;
   if (r <= kSmemRank) {
     size_t smem = sizeof(double) * 4 * r * r;
-    if (smem > 48 * 1024)
+    if (smem > kSmemOptIn)
       HODLR_CUDA_TRY(cudaFuncSetAttribute(k_node, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_node<<<1u << na.j, 128, smem, c.stream>>>(na, factor_mode);
   } else {
@@ -385,7 +385,7 @@ cudaError_t launch_scatter_rhs(Ctx& c, double* x, int64_t ld, int nrhs) {
 template <class T>
 cudaError_t launch_sweep(const SweepArgs& sa, unsigned grid, size_t smem, cudaStream_t st) {
   if (smem <= 200 * 1024) {
-    if (smem > 48 * 1024)
+    if (smem > kSmemOptIn)
       HODLR_CUDA_TRY(cudaFuncSetAttribute(k_sweep<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_sweep<true, T><<<grid, kSweepThreads, smem, st>>>(sa);
   } else {

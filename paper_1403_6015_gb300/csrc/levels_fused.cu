@@ -342,11 +342,11 @@ cudaError_t launch_levels_fused(Ctx& c, int nrhs, bool factor_mode) {
     size_t smem = sizeof(double) * 4 * fa.rl * fa.rl;
     unsigned grid = (unsigned)((nleaf + kG - 1) / kG);
     if (c.precision == 1) {
-      if (smem > 48 * 1024)
+      if (smem > kSmemOptIn)
         HODLR_CUDA_TRY(cudaFuncSetAttribute(k_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_level<true><<<grid, kLT, smem, c.stream>>>(fa);
     } else {
-      if (smem > 48 * 1024)
+      if (smem > kSmemOptIn)
         HODLR_CUDA_TRY(cudaFuncSetAttribute(k_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_level<false><<<grid, kLT, smem, c.stream>>>(fa);
     }

@@ -115,3 +115,57 @@ def test_presize_rejects_bad_input(H):
     with pytest.raises(H.HodlrError):
         h.presize(np.full(6, 64, dtype=np.int32))  # rank + 1 must fit max_rank
     h.presize(None)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sweep_graph_general_case(H, precision):
+    """The captured sweep on a problem the specialised compression kernels do not cover
+    (3-D points, inverse multiquadric): the general instantiation is chosen at launch and
+    captured with the rest; every setting equals its adaptive evaluation."""
+    import torch
+    n, nset = 1 << 13, 6
+    x, y = I.workload_3d(n, 1007)
+    y = np.ascontiguousarray(y).reshape(-1)
+    ell = np.array([2.0, 2.2, 2.4, 2.6, 2.8, 3.0])
+    s2 = np.array([0.5, 0.3, 0.2, 0.2, 0.1, 0.1])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.from_numpy(y).cuda()
+        theta = torch.from_numpy(np.stack([ell, np.ones(nset)], 1).copy()).cuda()
+        sig = torch.from_numpy(s2.copy()).cuda()
+        status = torch.full((nset,), -1, dtype=torch.int32, device="cuda")
+    stream.synchronize()
+    h = H.Hodlr(xd, "imq", [ell[0], 1.0], s2[0], 64, 1e-8, max_rank=256, precision=precision,
+                stream=stream.cuda_stream)
+    kappa, _ = h.tree()
+    r = h.ranks()
+    prof = np.array([r[(1 << j) - 1:(1 << (j + 1)) - 1].max() for j in range(kappa)]) + 4
+    h.presize(np.minimum(prof, 255).astype(np.int32))
+    out = h.loglik_sweep(theta, sig, yd, status=status)
+    stream.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    got = out.cpu().numpy()
+    for b in range(nset):
+        ref = H.Hodlr(x, "imq", [ell[b], 1.0], s2[b], 64, 1e-8, max_rank=256,
+                      precision=precision).loglik(y)
+        assert rel(got[b], ref) <= 1e-12, (b, got[b], ref)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_presized_node_step_at_rank_39(H, precision):
+    """A node matrix of rank 39 takes 4 x 39^2 x 8 = 48,672 bytes of dynamic shared
+    memory: with the kernel's static arrays just over the 48 KB a launch may use without
+    opting in. Presized padding to 39 (fused sweep), and to 67 at the top with 39 below
+    (unfused sweep), must still give the adaptive log-likelihood."""
+    x, y = I.workload_1d(1 << 14, 1008)
+    th, s2 = [0.3, 1.0], 1e-2
+    ref = H.Hodlr(x, "se", th, s2, 64, 1e-12, max_rank=128, precision=precision).loglik(y)
+    h = H.Hodlr(x, "se", th, s2, 64, 1e-12, max_rank=128, precision=precision)
+    kappa, _ = h.tree()
+    for prof in ([39] * kappa, [67] + [39] * (kappa - 1)):
+        h.presize(np.array(prof, dtype=np.int32))
+        h.rebuild(th, s2)
+        got = h.loglik(y)
+        assert h.status_flags() == 0
+        assert rel(got, ref) <= 1e-12, (prof[:2], got, ref)
