@@ -1,0 +1,49 @@
+"""Launch-configuration boundaries. A presized context pads every level to the given rank
+with zero columns, which leaves every product of the factorization unchanged, so its
+log-likelihood must equal the adaptive one. Padding to ranks around each switch and
+shared-memory threshold of the level sweep exercises them all on one small problem: the
+node step's shared-memory matrix (4 r^2 doubles, opt-in above 40 KB: r = 38, 39, 40), the
+fused sweep's limit (r <= 64) and the global-memory node step above it (65), and the
+staged (ranks up to 200 KB of rows) and unstaged level sweeps (127, 200)."""
+import numpy as np
+import pytest
+
+from paper_1403_6015_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_1403_6015_gb300 import build_lib, hodlr
+    build_lib.build()
+    hodlr.load()
+    return hodlr
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("r", [1, 38, 39, 40, 63, 64, 65, 127, 200])
+def test_presized_padding_any_rank(H, precision, r):
+    x, y = I.workload_1d(1 << 13, 1010)
+    th, s2 = [0.3, 1.0], 1e-2
+    ref = H.Hodlr(x, "se", th, s2, 64, 1e-12, max_rank=256, precision=precision).loglik(y)
+    h = H.Hodlr(x, "se", th, s2, 64, 1e-12, max_rank=256, precision=precision)
+    kappa, _ = h.tree()
+    # the deepest blocks are 64 x 64: a level's padding beyond its blocks' size is legal
+    prof = np.full(kappa, max(r, int(h.ranks().max())), dtype=np.int32)
+    h.presize(prof)
+    h.rebuild(th, s2)
+    got = h.loglik(y)
+    assert h.status_flags() == 0
+    assert rel(got, ref) <= 1e-12, (r, got, ref)
+    # and the solve alone with the stored factor (the mixed form's solutions carry its
+    # double-float rounding, ~4e-11 of the largest entry here, summed in another order by
+    # the unfused sweep than by the fused one)
+    sol = h.solve(y)
+    sol_ref = H.Hodlr(x, "se", th, s2, 64, 1e-12, max_rank=256, precision=precision).factor_solve(y)
+    tol = 1e-11 if precision == 0 else 1e-9
+    np.testing.assert_allclose(sol, sol_ref, rtol=0, atol=tol * np.abs(sol_ref).max())
