@@ -47,3 +47,18 @@ def test_presized_padding_any_rank(H, precision, r):
     sol_ref = H.Hodlr(x, "se", th, s2, 64, 1e-12, max_rank=256, precision=precision).factor_solve(y)
     tol = 1e-11 if precision == 0 else 1e-9
     np.testing.assert_allclose(sol, sol_ref, rtol=0, atol=tol * np.abs(sol_ref).max())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("max_rank", [2, 283, 284, 337, 338, 340, 341, 512])
+def test_compression_any_max_rank(H, precision, max_rank):
+    """The compression's column kernel takes 144 bytes of shared memory per unit of
+    max_rank (plus 136), crossing the opt-in threshold near max_rank 284 and 48 KB near
+    340; ranks here are small, so the result must not depend on max_rank. (The smallest
+    cap is 2: the cross takes one step past its last kept term to confirm convergence, so
+    even these rank-1 blocks report the cap at max_rank 1.)"""
+    x, y = I.workload_1d(1 << 13, 1011)
+    th, s2 = [0.2, 1.0], 1e-2
+    ref = H.Hodlr(x, "exp", th, s2, 64, 1e-12, precision=precision).loglik(y)
+    got = H.Hodlr(x, "exp", th, s2, 64, 1e-12, max_rank=max_rank, precision=precision).loglik(y)
+    assert rel(got, ref) <= 1e-13, (max_rank, got, ref)
