@@ -69,7 +69,7 @@ typedef struct {
                        /*    pipe (~2^-48 unit roundoff), everything else FP64; it keeps  */
                        /*    per-level relative coordinates, kappa x d x n x 8 bytes     */
   int rank_mode;       /* 0: adaptive ACA ranks                                            */
-  int max_rank;        /* cap on the ACA rank of one off-diagonal block (1..512), default  */
+  int max_rank;        /* cap on the ACA rank of one off-diagonal block (1..1024), default */
                        /*    64. Levels whose rank exceeds 64 factor their node matrices  */
                        /*    in global memory and use the unfused level sweep; memory     */
                        /*    grows with max_rank (ACA columns n x min(max_rank, m/2) per  */

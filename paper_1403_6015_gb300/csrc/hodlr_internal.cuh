@@ -19,7 +19,7 @@ constexpr int kMaxDim = 64;        // largest point dimension d
 // cudaFuncAttributeMaxDynamicSharedMemorySize: without it static plus dynamic must stay
 // within 48 KB, and the kernels' static arrays take up to about 1 KB.
 constexpr size_t kSmemOptIn = 40 * 1024;
-constexpr int kMaxRank = 512;      // hard cap on a block's rank (opts.max_rank)
+constexpr int kMaxRank = 1024;     // hard cap on a block's rank (opts.max_rank)
 constexpr int kDefaultMaxRank = 64;  // default opts.max_rank
 constexpr int kSmemRank = 64;      // ranks up to this use the shared-memory node step
                                    // (2r x 2r in smem) and the fused level sweep

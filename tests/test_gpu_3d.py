@@ -90,3 +90,29 @@ def test_3d_default_rank_cap_reports(H):
     x, _ = I.workload_3d(3000, 96)
     with pytest.raises(H.HodlrError):
         H.Hodlr(x, "matern32", [1.0, 1.0], 0.01, 32, 1e-10)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_3d_ranks_above_512(H, precision):
+    """3-D Matern-3/2 (ell = 1, eps = 1e-10): top-level ranks above 600, under the cap of
+    1024; the node matrices of those levels (2r > 1200) are factored in global memory."""
+    n = 3000
+    x, y = I.workload_3d(n, 97)
+    y = np.ascontiguousarray(y).reshape(-1)
+    th, s2 = [1.0, 1.0], 0.01
+    h = H.Hodlr(x, "matern32", th, s2, 32, 1e-10, max_rank=1024, precision=precision)
+    sol = h.factor_solve(y)
+    ld = h.logdet()
+    o = O.Hodlr(x, "matern32", th, s2, 32, 1e-10, max_rank=1024)
+    o.factor_solve(y)
+    kappa, _ = h.tree()
+    lv, lv_o = level_max(h.ranks(), kappa), level_max(o.ranks(), o.kappa)
+    assert lv[0] > 512
+    assert np.all(np.abs(lv - lv_o) <= np.maximum(2, 0.03 * lv_o)), (lv, lv_o)
+    _, ld_d = O.dense_solve(x, "matern32", th, s2, y)
+    print(f"matern32 3-D prec {precision}: ranks {lv.tolist()} logdet vs oracle "
+          f"{rel(ld, o.logdet()):.2e} vs dense {rel(ld, ld_d):.2e}")
+    assert rel(ld, o.logdet()) <= (1e-12 if precision == 0 else 1e-11)
+    assert rel(ld, ld_d) <= 1e-10
+    res_own = np.linalg.norm(y - h.matvec(sol)) / np.linalg.norm(y)
+    assert res_own <= (3e-11 if precision == 0 else 3e-10), res_own
