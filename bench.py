@@ -36,6 +36,7 @@ EPS = 1e-12
 SIGMA2 = 1e-2
 KERNELS = [("matern32", 0.1), ("exp", 0.2)]
 SEED = 1002
+COMPRESSION = "aca"  # cross approximation; --compression chebyshev for profiling captures
 METRIC = "GP log-likelihood evals/sec (solve+logdet) at n=2^20, 1 GB300, at 1e-10 rel err"
 FP64_PEAK = 152 * 2 * 2 * 2.07e9  # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
 
@@ -50,7 +51,7 @@ def config():
                         "sigma^2=1e-2, leaf 128, eps=1e-12, nrhs=1",
             "n": N, "leaf": LEAF, "eps": EPS, "sigma2": SIGMA2,
             "kernels": [f"{k}:ell={e}" for k, e in KERNELS],
-            "evals_per_step": len(KERNELS),
+            "evals_per_step": len(KERNELS), "compression": COMPRESSION,
             "l2": "inputs larger than L2 (1 GB leaf factors + 0.2 GB panels per eval)"}
 
 
@@ -176,7 +177,8 @@ def measure_form(args, precision, x, y, xd, yd, stream, world, rank, local, dev)
 
     from paper_1403_6015_gb300 import hodlr as H
     ctxs = [H.Hodlr(xd, kern, [ell, 1.0], SIGMA2, LEAF, EPS, max_rank=16, max_nrhs=1,
-                    stream=stream.cuda_stream, precision=precision) for kern, ell in KERNELS]
+                    stream=stream.cuda_stream, precision=precision, compression=args.compression)
+            for kern, ell in KERNELS]
     outs = torch.zeros(len(KERNELS), dtype=torch.float64, device=dev)
     # launch configuration per context, chosen by the library's autotuner (untimed)
     tuning = {}
@@ -797,7 +799,7 @@ def run_reference(args):
 
 
 def main():
-    global N
+    global N, COMPRESSION
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -812,8 +814,11 @@ def main():
     ap.add_argument("--n", type=int, default=N, help="points (profiling captures only)")
     ap.add_argument("--precision", type=int, default=-1,
                     help="-1: both forms (default), 0: FP64 only, 1: mixed only")
+    ap.add_argument("--compression", default="aca", choices=["aca", "chebyshev"],
+                    help="compression of the timed evaluations (profiling captures)")
     args = ap.parse_args()
     N = args.n
+    COMPRESSION = args.compression
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -241,6 +241,9 @@ __global__ void __launch_bounds__(kChebThreads) k_cheb_node(ChebArgs a) {
   }
 }
 
+// kFF (mixed form): the recurrence and the sums in double-float on the FP32 pipe (the
+// panels are stored as double-floats anyway); otherwise FP64.
+template <bool kFF>
 __global__ void __launch_bounds__(kMaxLeaf) k_cheb_expand(ChebArgs a) {
   extern __shared__ double sm[];  // coefficients (q x r, column l at l * kChebQ), T (128 x 65)
   double* cf = sm;
@@ -284,12 +287,38 @@ __global__ void __launch_bounds__(kMaxLeaf) k_cheb_expand(ChebArgs a) {
   const double* src = a.coef + (int64_t)anc * 2 * kChebQ * kChebQ + (left ? 0 : kChebQ * kChebQ);
   for (int e = tid; e < r * kChebQ; e += kMaxLeaf) {
     int l = e / kChebQ, k = e - l * kChebQ;
-    if (k < q) cf[e] = src[e];
+    if (k < q) {
+      if (kFF)
+        reinterpret_cast<ff*>(cf)[e] = ff_from_double(src[e]);
+      else
+        cf[e] = src[e];
+    }
   }
   __syncthreads();
   if (tid >= p) return;
   double u = (a.xs[b + tid] - mid) * inv_half;
   u = fmin(1.0, fmax(-1.0, u));
+  if (kFF) {
+    const ff* cff = reinterpret_cast<const ff*>(cf);
+    ff* Lf = reinterpret_cast<ff*>(L) + tid * kLS;  // T_k(u), k < q
+    const ff uf = ff_from_double(u), u2 = ff{2.0f * uf.hi, 2.0f * uf.lo};
+    ff t0 = {1.0f, 0.0f}, t1 = uf;
+    Lf[0] = t0;
+    if (q > 1) Lf[1] = uf;
+    for (int k = 2; k < q; ++k) {
+      ff t2 = ff_neg(ff_fms(t0, u2, t1));  // 2 u T_{k-1} - T_{k-2}
+      Lf[k] = t2;
+      t0 = t1;
+      t1 = t2;
+    }
+    ff* rawf = reinterpret_cast<ff*>(raw);
+    for (int l = 0; l < r; ++l) {
+      ff acc = {0.0f, 0.0f};
+      for (int k = 0; k < q; ++k) acc = ff_fma(acc, Lf[k], cff[l * kChebQ + k]);
+      rawf[(int64_t)l * a.n + b + tid] = acc;
+    }
+    return;
+  }
   double* Li = L + tid * kLS;  // T_k(u), k < q
   double t0 = 1.0, t1 = u;
   Li[0] = 1.0;
@@ -303,11 +332,7 @@ __global__ void __launch_bounds__(kMaxLeaf) k_cheb_expand(ChebArgs a) {
   for (int l = 0; l < r; ++l) {
     double acc = 0.0;
     for (int k = 0; k < q; ++k) acc += Li[k] * cf[l * kChebQ + k];
-    int64_t o = (int64_t)l * a.n + b + tid;
-    if (a.ff_out)
-      reinterpret_cast<ff*>(raw)[o] = ff_from_double(acc);
-    else
-      raw[o] = acc;
+    raw[(int64_t)l * a.n + b + tid] = acc;
   }
 }
 
@@ -340,9 +365,13 @@ cudaError_t launch_cheb(Ctx& c) {
   const size_t smem_node = sizeof(double) * 3 * kChebQ * kChebQ;
   const size_t smem_exp = sizeof(double) * (kChebQ * kChebQ + kMaxLeaf * (kChebQ + 1));
   HODLR_CUDA_TRY(cudaFuncSetAttribute(k_cheb_node, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_node));
-  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_cheb_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_exp));
+  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_cheb_expand<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_exp));
+  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_cheb_expand<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_exp));
   k_cheb_node<<<nint, kChebThreads, smem_node, c.stream>>>(a);
-  k_cheb_expand<<<dim3(1u << c.kappa, c.kappa), kMaxLeaf, smem_exp, c.stream>>>(a);
+  if (a.ff_out)
+    k_cheb_expand<true><<<dim3(1u << c.kappa, c.kappa), kMaxLeaf, smem_exp, c.stream>>>(a);
+  else
+    k_cheb_expand<false><<<dim3(1u << c.kappa, c.kappa), kMaxLeaf, smem_exp, c.stream>>>(a);
   c.launches += 2;
   return cudaGetLastError();
 }
