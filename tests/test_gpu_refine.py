@@ -118,3 +118,31 @@ def test_sweep_runs_fixed_corrections(H):
         ld, q = O.matern_kalman(x[perm, 0], 5, ell[b], 1.0, s2[b], y[perm])
         exact = -0.5 * q - 0.5 * ld - 0.5 * n * np.log(2 * np.pi)
         assert abs(got[b] - exact) <= 1e-9 * abs(exact), (b, got[b], exact)
+
+
+def test_mixed_refined_at_n2p22():
+    """The mixed form with refinement at its full size: n = 2^22 points, squared-exponential
+    ell = 0.05, sigma^2 = 1e-3, leaf 128, eps = 1e-12 (top-level rank 14). cond(C) is about
+    3e8 here, so the FP64 rounding of C x itself is ~1e-8 of y. The log-likelihood
+    (about -2.1e9, dominated by y^T C^-1 y) is compared with the FP64 form at 1e-9 (the same
+    operations in FP64: measured 2.6e-10) and with the oracle's HODLR, which rounds in
+    another order, at cond(C) u ~ 3e-8 (bound 1e-7, measured 2.3e-8); exact residual rows of
+    the dense C at 1e-7 (measured 4e-8)."""
+    from paper_1403_6015_gb300 import build_lib, hodlr as H
+    build_lib.build()
+    H.load()
+    n = 1 << 22
+    x, y = I.workload_1d(n, 1003)
+    th, s2 = [0.05, 1.0], 1e-3
+    hm = H.Hodlr(x, "se", th, s2, 128, 1e-12, max_rank=64, precision=1, refine_maxit=2,
+                 refine_tol=1e-13)
+    ll_m = hm.loglik(y)
+    ll_d = H.Hodlr(x, "se", th, s2, 128, 1e-12, max_rank=64, precision=0).loglik(y)
+    assert abs(ll_m - ll_d) <= 1e-9 * abs(ll_d), (ll_m, ll_d)
+    ll_o = O.Hodlr(x, "se", th, s2, 128, 1e-12).loglik(y)
+    assert abs(ll_m - ll_o) <= 1e-7 * abs(ll_o), (ll_m, ll_o)
+    hm.rebuild(th, s2)
+    sol = hm.factor_solve(y)
+    rows = np.unique(np.linspace(0, n - 1, 16).astype(np.int64))
+    cx = O.dense_matvec_rows(x, "se", th, s2, sol, rows)
+    assert np.abs(cx - y[rows]).max() <= 1e-7 * np.abs(y).max()
