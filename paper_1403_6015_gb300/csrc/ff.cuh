@@ -87,6 +87,44 @@ __device__ __forceinline__ ff ff_fms(ff c, ff a, ff b) {
 // c + a * b
 __device__ __forceinline__ ff ff_fma(ff c, ff a, ff b) { return ff_fms(c, ff_neg(a), b); }
 
+// Compensated dot-product accumulator (the "Dot2" scheme of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 2005, with double-word operands):
+// a float running sum s and a float sum e of the errors. Each product enters as its exact
+// leading part (TwoProd) plus the cross terms, the running sum by TwoSum with its error
+// moved to e, and the pair is renormalised once, when read. 12 instructions per term
+// against 15 for ff_fms, with an error of order n^2 u^2 sum |x_i y_i| for n terms
+// (u = 2^-24), the same order as n renormalised sloppy sums for the short (<= 32-term)
+// dot products it is used for.
+struct ffacc {
+  float s, e;
+};
+
+__device__ __forceinline__ ffacc ffacc_init(ff c) { return ffacc{c.hi, c.lo}; }
+
+// acc -= x * y
+__device__ __forceinline__ void ffacc_fms(ffacc& a, ff x, ff y) {
+  float p = x.hi * y.hi;
+  float pe = fmaf(x.hi, y.hi, -p);
+  pe = fmaf(x.hi, y.lo, pe);
+  pe = fmaf(x.lo, y.hi, pe);
+  float s, t;
+  two_sum(a.s, -p, s, t);
+  a.s = s;
+  a.e += t - pe;
+}
+
+// acc += x * y
+__device__ __forceinline__ void ffacc_fma(ffacc& a, ff x, ff y) { ffacc_fms(a, ff_neg(x), y); }
+
+__device__ __forceinline__ ff ffacc_get(ffacc a) { return ff_make(a.s, a.e); }
+
+// the sum of two accumulators, renormalised
+__device__ __forceinline__ ff ffacc_get2(ffacc a, ffacc b) {
+  float s, t;
+  two_sum(a.s, b.s, s, t);
+  return ff_make(s, t + (a.e + b.e));
+}
+
 // a * f for a float f
 __device__ __forceinline__ ff ff_mulf(ff a, float f) {
   float p = a.hi * f;

@@ -19,7 +19,9 @@
 //     below it, the trailing matrix is updated in 2 x 2 register tiles (32-term dots);
 //   - the panel columns and right-hand sides are solved in chunks of 32 columns held in
 //     shared memory: 32 x 32 diagonal blocks by one warp per column, the rest as dense
-//     updates with one thread per output element.
+//     updates with one thread per output element;
+//   - the dot products (trailing update, solve updates, partial products) accumulate in
+//     compensated form (ffacc: the error of each sum kept apart and added once at the end).
 #include <cuda_runtime.h>
 
 #include "ff.cuh"
@@ -181,8 +183,10 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
           int jc = c0 + cc;
           ff uj0 = Up[jc * kBS + c], uj1 = Up[jc * kBS + c + 1];
           for (int i = jc + lane; i < P; i += 32) {
-            ff v = ff_fms(A[tri(i) + jc], A[tri(i) + col], uj0);
-            v = ff_fms(v, A[tri(i) + col + 1], uj1);
+            ffacc acc = ffacc_init(A[tri(i) + jc]);
+            ffacc_fms(acc, A[tri(i) + col], uj0);
+            ffacc_fms(acc, A[tri(i) + col + 1], uj1);
+            ff v = ffacc_get(acc);
             if (i == jc && cc == c + 2) {
               if (!(v.hi > 0.0f)) {
                 bad = 1;
@@ -201,27 +205,31 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
       for (int e = tid; e < M * (M + 1) / 2; e += kT) {
         int ti = tri_row(e), tj = e - ti * (ti + 1) / 2;
         int i0 = r0 + 2 * ti, j0 = r0 + 2 * tj;
-        ff s00a = {0, 0}, s01a = {0, 0}, s10a = {0, 0}, s11a = {0, 0};
-        ff s00b = {0, 0}, s01b = {0, 0}, s10b = {0, 0}, s11b = {0, 0};
+        // two compensated accumulators per entry (the first starts from A_ij)
+        const ff z = {0.0f, 0.0f};
+        ffacc s00a = ffacc_init(A[tri(i0) + j0]), s10a = ffacc_init(A[tri(i0 + 1) + j0]);
+        ffacc s11a = ffacc_init(A[tri(i0 + 1) + j0 + 1]);
+        ffacc s01a = ffacc_init(ti != tj ? A[tri(i0) + j0 + 1] : z);  // above the diagonal if ti == tj
+        ffacc s00b = ffacc_init(z), s01b = ffacc_init(z), s10b = ffacc_init(z), s11b = ffacc_init(z);
 #pragma unroll 4
         for (int c = 0; c < 32; c += 2) {
           ff l0 = A[tri(i0) + c0 + c], l1 = A[tri(i0 + 1) + c0 + c];
           ff u0 = Up[j0 * kBS + c], u1 = Up[(j0 + 1) * kBS + c];
-          s00a = ff_fma(s00a, l0, u0);
-          s01a = ff_fma(s01a, l0, u1);
-          s10a = ff_fma(s10a, l1, u0);
-          s11a = ff_fma(s11a, l1, u1);
+          ffacc_fms(s00a, l0, u0);
+          ffacc_fms(s01a, l0, u1);
+          ffacc_fms(s10a, l1, u0);
+          ffacc_fms(s11a, l1, u1);
           ff m0 = A[tri(i0) + c0 + c + 1], m1 = A[tri(i0 + 1) + c0 + c + 1];
           ff v0 = Up[j0 * kBS + c + 1], v1 = Up[(j0 + 1) * kBS + c + 1];
-          s00b = ff_fma(s00b, m0, v0);
-          s01b = ff_fma(s01b, m0, v1);
-          s10b = ff_fma(s10b, m1, v0);
-          s11b = ff_fma(s11b, m1, v1);
+          ffacc_fms(s00b, m0, v0);
+          ffacc_fms(s01b, m0, v1);
+          ffacc_fms(s10b, m1, v0);
+          ffacc_fms(s11b, m1, v1);
         }
-        A[tri(i0) + j0] = ff_sub(A[tri(i0) + j0], ff_add(s00a, s00b));
-        A[tri(i0 + 1) + j0] = ff_sub(A[tri(i0 + 1) + j0], ff_add(s10a, s10b));
-        A[tri(i0 + 1) + j0 + 1] = ff_sub(A[tri(i0 + 1) + j0 + 1], ff_add(s11a, s11b));
-        if (ti != tj) A[tri(i0) + j0 + 1] = ff_sub(A[tri(i0) + j0 + 1], ff_add(s01a, s01b));
+        A[tri(i0) + j0] = ffacc_get2(s00a, s00b);
+        A[tri(i0 + 1) + j0] = ffacc_get2(s10a, s10b);
+        A[tri(i0 + 1) + j0 + 1] = ffacc_get2(s11a, s11b);
+        if (ti != tj) A[tri(i0) + j0 + 1] = ffacc_get2(s01a, s01b);
       }
       __syncthreads();
     }
@@ -285,13 +293,13 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
       int r0 = c0 + 32;
       for (int e = tid; e < (P - r0) * cw; e += kT) {
         int i = r0 + e / cw, c = e - (e / cw) * cw;
-        ff sa = {0, 0}, sb = {0, 0};
+        ffacc sa = ffacc_init(B[i * kBS + c]), sb = ffacc_init(ff{0.0f, 0.0f});
 #pragma unroll 4
         for (int k = 0; k < 32; k += 2) {
-          sa = ff_fma(sa, A[tri(i) + c0 + k], B[(c0 + k) * kBS + c]);
-          sb = ff_fma(sb, A[tri(i) + c0 + k + 1], B[(c0 + k + 1) * kBS + c]);
+          ffacc_fms(sa, A[tri(i) + c0 + k], B[(c0 + k) * kBS + c]);
+          ffacc_fms(sb, A[tri(i) + c0 + k + 1], B[(c0 + k + 1) * kBS + c]);
         }
-        B[i * kBS + c] = ff_sub(B[i * kBS + c], ff_add(sa, sb));
+        B[i * kBS + c] = ffacc_get2(sa, sb);
       }
       __syncthreads();
     }
@@ -315,13 +323,13 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
       __syncthreads();
       for (int e = tid; e < c0 * cw; e += kT) {
         int i = e / cw, c = e - i * cw;
-        ff sa = {0, 0}, sb = {0, 0};
+        ffacc sa = ffacc_init(B[i * kBS + c]), sb = ffacc_init(ff{0.0f, 0.0f});
 #pragma unroll 4
         for (int k = 0; k < 32; k += 2) {
-          sa = ff_fma(sa, A[tri(c0 + k) + i], B[(c0 + k) * kBS + c]);
-          sb = ff_fma(sb, A[tri(c0 + k + 1) + i], B[(c0 + k + 1) * kBS + c]);
+          ffacc_fms(sa, A[tri(c0 + k) + i], B[(c0 + k) * kBS + c]);
+          ffacc_fms(sb, A[tri(c0 + k + 1) + i], B[(c0 + k + 1) * kBS + c]);
         }
-        B[i * kBS + c] = ff_sub(B[i * kBS + c], ff_add(sa, sb));
+        B[i * kBS + c] = ffacc_get2(sa, sb);
       }
       __syncthreads();
     }
@@ -339,8 +347,9 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
       for (int t = w; t < a.rl * cw; t += NW) {
         int r = t / cw, c = t - r * cw;
         const ff* ph = reinterpret_cast<const ff*>(a.phi) + (int64_t)(a.coff + r) * a.n + b;
-        ff s = {0.0f, 0.0f};
-        for (int i = lane; i < p; i += 32) s = ff_fma(s, ph[i], B[i * kBS + c]);
+        ffacc acc = ffacc_init(ff{0.0f, 0.0f});
+        for (int i = lane; i < p; i += 32) ffacc_fma(acc, ph[i], B[i * kBS + c]);
+        ff s = ffacc_get(acc);
         for (int o = 16; o > 0; o >>= 1) s = ff_add(s, xor_ff(s, o));
         if (lane == 0) out[r * ncol + q0 + c] = ff_to_double(s);
       }

@@ -39,7 +39,13 @@ def test_presized_padding_any_rank(H, precision, r):
     h.rebuild(th, s2)
     got = h.loglik(y)
     assert h.status_flags() == 0
-    assert rel(got, ref) <= 1e-12, (r, got, ref)
+    # padded ranks above 64 run the global-memory node step instead of the fused sweep: a
+    # different FP64 summation order, carried through the leaf solutions (unit roundoff
+    # 2^-53 in the FP64 form, 2^-48 in the double-float leaves of the mixed form; this
+    # squared-exponential problem has cond(C) near 1e6; 2.0e-12 seen for the mixed form at
+    # r = 65)
+    tol_ll = 1e-12 if precision == 0 else 1e-11
+    assert rel(got, ref) <= tol_ll, (r, got, ref)
     # and the solve alone with the stored factor (the mixed form's solutions carry its
     # double-float rounding, ~4e-11 of the largest entry here, summed in another order by
     # the unfused sweep than by the fused one)
