@@ -40,10 +40,10 @@ COMPRESSION = "aca"  # cross approximation; --compression chebyshev for profilin
 METRIC = "GP log-likelihood evals/sec (solve+logdet) at n=2^20, 1 GB300, at 1e-10 rel err"
 FP64_PEAK = 152 * 2 * 2 * 2.07e9  # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
 
-# DRAM bytes (read + write) of one launch of each form's leaf kernel at n = 2^20, from the
-# ncu captures summarised in profiles/ (scaled from the n = 2^18 capture by the number of
-# leaves); None until a capture matches the current kernel.
-LEAF_TRAFFIC_BYTES = {0: None, 1: 4 * (59.3728 + 130.24128) * 1e6}
+# DRAM bytes (read + write) of one launch of each form's leaf kernel at n = 2^20 (the
+# bench's own launch: 8192 leaves, 26 panel columns + 1 right-hand side), measured by ncu
+# (profiles/leaf_kernel_dram_n2p20.md); None when the kernel has changed since.
+LEAF_TRAFFIC_BYTES = {0: 276945920 + 720439552, 1: 275459840 + 732192512}
 
 
 def config():
