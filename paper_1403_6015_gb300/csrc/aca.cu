@@ -755,9 +755,10 @@ __global__ void k_aca_check(AcaArgs a, int32_t* flags) {
   if (!a.done[id] || (!a.ok[id] && !full) || a.rank[id] > pre) atomicOr(flags, kFlagRankCap);
 }
 
-// Compact panels: level j's columns [coff_j, coff_j + r_j) of phi and pan take the node's
-// first rank columns of the raw panel and zeros beyond (zero columns leave every product
-// of the factorization unchanged).
+// Compact panels: level j's columns [coff_j, coff_j + r_j) of phi take the node's first
+// rank columns of the raw panel and zeros beyond (zero columns leave every product of the
+// factorization unchanged). The working panel is written by the leaf stage, which reads
+// its columns from phi.
 struct PackArgs {
   const double* raw;
   int64_t raw_off[32];
@@ -766,7 +767,6 @@ struct PackArgs {
   const int32_t* nb;
   const int32_t* rank;
   double* phi;
-  double* pan;
   int64_t n;
 };
 
@@ -781,12 +781,9 @@ __global__ void k_pack(PackArgs p) {
   // are 0 in both)
   const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p.raw + p.raw_off[j]);
   unsigned long long* phi = reinterpret_cast<unsigned long long*>(p.phi);
-  unsigned long long* pan = reinterpret_cast<unsigned long long*>(p.pan);
   for (int c = 0; c < p.rl[j]; ++c) {
     unsigned long long v = c < r ? src[c * p.n + i] : 0ull;
-    int64_t o = (int64_t)(p.coff[j] + c) * p.n + i;
-    phi[o] = v;
-    pan[o] = v;
+    phi[(int64_t)(p.coff[j] + c) * p.n + i] = v;
   }
 }
 
@@ -944,7 +941,6 @@ cudaError_t launch_pack(Ctx& c) {
   p.nb = c.nodes;
   p.rank = c.rank_dev;
   p.phi = c.phi;
-  p.pan = c.pan;
   p.n = c.n;
   dim3 g((unsigned)((c.n + 255) / 256), (unsigned)c.kappa);
   k_pack<<<g, 256, 0, c.stream>>>(p);

@@ -601,10 +601,8 @@ static hodlr_status factor_impl(Ctx* c, int nrhs) {
   c->solve_timed = false;
   bool cap = capturing(c);
   if (!cap) cudaEventRecord(c->ev[4], c->stream);
-  if (c->R > 0 && c->kappa > 0) {
-    // the working panel starts from the original U/V (a previous factor modified it)
-    TRY_CUDA(c, cudaMemcpyAsync(c->pan, c->phi, sizeof(double) * c->n * c->R, cudaMemcpyDeviceToDevice, c->stream), "panel");
-  }
+  // the leaf stage reads the original U/V from phi and writes the working panel (every
+  // column, every point), so no copy of phi is needed first
   if (!c->presized) TRY_CUDA(c, cudaMemsetAsync(c->dflags, 0, 4, c->stream), "flags");
   if (!cap) cudaEventRecord(c->ev[6], c->stream);
   if (c->precision == 1)

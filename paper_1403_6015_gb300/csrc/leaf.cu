@@ -362,11 +362,13 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       int cc = c0 + c < ncol ? c0 + c : c0;  // a missing second column repeats the first
+      // panel columns are read from Phi (the packed U/V) and written, solved, to the panel
       col[c] = cc < a.cP ? a.pan + (int64_t)cc * a.n + b : a.Y + (int64_t)(cc - a.cP) * a.n + b;
+      const double* src = cc < a.cP ? a.phi + (int64_t)cc * a.n + b : col[c];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         int i = m * 32 + lane;
-        x[c][m] = i < p ? col[c][a.lu ? perm[i] : i] : 0.0;  // LU: rows in pivot order
+        x[c][m] = i < p ? src[a.lu ? perm[i] : i] : 0.0;  // LU: rows in pivot order
       }
     }
     if (a.lu)

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
   int ncol = a.cP + a.nrhs;
   for (int q0 = 0; q0 < ncol; q0 += kCW) {
     int cw = ncol - q0 < kCW ? ncol - q0 : kCW;
-    const ff* panf = reinterpret_cast<const ff*>(a.pan);
+    const ff* panf = reinterpret_cast<const ff*>(a.phi);  // panel columns read from Phi
     for (int e = tid; e < P * cw; e += kT) {
       int c = e / P, i = e - c * P;
       int q = q0 + c;

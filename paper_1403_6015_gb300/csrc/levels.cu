@@ -263,17 +263,30 @@ __global__ void k_sum_blocks(const double* __restrict__ v, const double* __restr
 
 constexpr int kRedBlocks = 256;
 
+// One warp: lane l sums the partials l, l + 32, ... in index order, then a fixed xor
+// butterfly combines the 32 lane sums (each pair added the same way on both lanes), so the
+// result is the same on every lane and on every run.
 __global__ void k_finish(const double* __restrict__ pl, const double* __restrict__ pn,
                          const double* __restrict__ pq, double* scal, int64_t n, int mode) {
   // mode 0: logdet only; mode 1: logdet and quadratic form -> log-likelihood
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double a = 0.0, b = 0.0;
-  for (int i = 0; i < kRedBlocks; ++i) a += pl[i];
-  for (int i = 0; i < kRedBlocks; ++i) b += pn[i];
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  int l = threadIdx.x;
+  double a = 0.0, b = 0.0, q = 0.0;
+#pragma unroll
+  for (int i = l; i < kRedBlocks; i += 32) {
+    a += pl[i];
+    b += pn[i];
+    if (mode == 1) q += pq[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+  }
+  if (l != 0) return;
   scal[0] = a + b;
   if (mode == 1) {
-    double q = 0.0;
-    for (int i = 0; i < kRedBlocks; ++i) q += pq[i];
     scal[1] = q;
     scal[2] = -0.5 * q - 0.5 * scal[0] - 0.5 * (double)n * log(2.0 * 3.14159265358979323846);
   }

@@ -46,27 +46,69 @@ __global__ void k_hist(const uint64_t* __restrict__ key, int64_t n, int shift, i
   counts[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of m entries by one block of 1024 threads.
-__global__ void k_scan(uint32_t* __restrict__ a, int64_t m) {
-  __shared__ uint32_t s[1024];
-  int t = threadIdx.x;
-  int64_t per = (m + 1023) / 1024;
-  int64_t b = t * per, e = b + per < m ? b + per : m;
-  uint32_t sum = 0;
-  for (int64_t i = b; i < e; ++i) sum += a[i];
-  s[t] = sum;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    uint32_t v = t >= off ? s[t - off] : 0u;
+// Exclusive scan of m entries by one block of 1024 threads, in tiles of 1024 x kScanT
+// entries: a tile is loaded coalesced into shared memory (padded by one word per 32 so
+// that each thread's kScanT contiguous entries sit in distinct banks), every thread sums
+// its entries, the 1024 sums are scanned by warp shuffles and then across the 32 warp
+// totals, and the tile is written back coalesced, offset by the running carry of the
+// tiles before it.
+constexpr int kScanT = 8;
+constexpr int kScanTile = 1024 * kScanT;
+
+__device__ __forceinline__ int scan_pad(int j) { return j + (j >> 5); }
+
+__global__ void __launch_bounds__(1024) k_scan(uint32_t* __restrict__ a, int64_t m) {
+  __shared__ uint32_t s[kScanTile + kScanTile / 32];
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry_next;
+  int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < m; base += kScanTile) {
+#pragma unroll
+    for (int q = 0; q < kScanT; ++q) {
+      int j = q * 1024 + t;
+      s[scan_pad(j)] = base + j < m ? a[base + j] : 0u;
+    }
     __syncthreads();
-    s[t] += v;
+    uint32_t v[kScanT], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanT; ++q) {
+      v[q] = s[scan_pad(t * kScanT + q)];
+      sum += v[q];
+    }
+    uint32_t x = sum;  // inclusive scan of the thread sums within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
     __syncthreads();
-  }
-  uint32_t run = s[t] - sum;
-  for (int64_t i = b; i < e; ++i) {
-    uint32_t v = a[i];
-    a[i] = run;
-    run += v;
+    if (w == 0) {
+      uint32_t y = wsum[lane], z = y;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t u = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += u;
+      }
+      wsum[lane] = z - y;  // exclusive prefix of the warp totals
+    }
+    __syncthreads();
+    uint32_t run = carry + wsum[w] + (x - sum);
+#pragma unroll
+    for (int q = 0; q < kScanT; ++q) {
+      s[scan_pad(t * kScanT + q)] = run;
+      run += v[q];
+    }
+    if (t == 1023) carry_next = run;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kScanT; ++q) {
+      int j = q * 1024 + t;
+      if (base + j < m) a[base + j] = s[scan_pad(j)];
+    }
+    carry = carry_next;
+    __syncthreads();  // the next tile overwrites s and carry_next
   }
 }
 
