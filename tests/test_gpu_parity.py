@@ -37,7 +37,10 @@ def dense_C(x, kern, th, s2):
 
 # ------------------------------------------------------------------ ordering -------------
 
-@pytest.mark.parametrize("n,leaf", [(1, 8), (100, 8), (4097, 64), (1 << 17, 128)])
+# 2^17 points fill exactly one tile of the radix sort's digit-count scan (256 counts per
+# 4096 keys, 8192 counts per tile); 405 561 and 2^20 span 3.1 and 8 tiles.
+@pytest.mark.parametrize("n,leaf", [(1, 8), (100, 8), (4097, 64), (1 << 17, 128), (405561, 128),
+                                    (1 << 20, 128)])
 def test_sort_1d_bit_exact(H, n, leaf):
     x, _ = I.workload_1d(n, 7 + n)
     if n > 10:
@@ -48,7 +51,7 @@ def test_sort_1d_bit_exact(H, n, leaf):
     np.testing.assert_array_equal(perm, O.tree_order(x, leaf))
 
 
-@pytest.mark.parametrize("n,leaf", [(50, 8), (3001, 20), (1 << 15, 64)])
+@pytest.mark.parametrize("n,leaf", [(50, 8), (3001, 20), (1 << 15, 64), (300007, 128)])
 def test_sort_2d_kd_bit_exact(H, n, leaf):
     x, _ = I.workload_2d(n, 11 + n)
     h = H.Hodlr(x, "se", [0.3, 1.0], 0.01, leaf, 1e-8, allow_rank_cap=True)
