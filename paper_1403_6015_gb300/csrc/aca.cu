@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   CovFF cf{};
   if (kFF) {
     for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
-    cf = make_cov_ff(a.kind, a.hyp[kHypScale], cov.amp, cov.alpha);
+    cf = load_cov_ff(a.kind, a.hyp);
   }
   int k = a.rank[id], i = a.row[id];
   int bl = a.nb[2 * id + 1], br = a.nb[2 * id + 2], mr = a.ns[2 * id + 2];
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   const Cov cov = cov_from(a.kind, a.hyp);
   if (kFF) {
     for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
-    cf = make_cov_ff(a.kind, a.hyp[kHypScale], cov.amp, cov.alpha);
+    cf = load_cov_ff(a.kind, a.hyp);
   }
   __shared__ double wv[kAcaThreads / 32];
   __shared__ int wi[kAcaThreads / 32];
@@ -421,9 +421,11 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   } else {
     ff* rawf = reinterpret_cast<ff*>(raw);
     ff* vjk = reinterpret_cast<ff*>(dsm);
+    __shared__ ff inv_s;  // 1 / delta, converted by one thread (FP64 pipe)
     for (int l = threadIdx.x; l < k; l += kAcaThreads) vjk[l] = rawf[l * n + br + j];
+    if (threadIdx.x == 0) inv_s = ff_rcp(ff_from_double(delta));
     __syncthreads();
-    const ff inv = ff_rcp(ff_from_double(delta));
+    const ff inv = inv_s;
     float uu[kPer], vv[kPer];  // high words, for the dot products of the stopping test
     float nu2 = 0.0f, nv2 = 0.0f, bv = 0.0f;
 #pragma unroll
@@ -535,7 +537,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row_small(AcaArgs a, int it
     warp_amax(bv, bi);
     fv = bv;
   } else {
-    const CovFF cf = make_cov_ff(a.kind, a.hyp[kHypScale], cov.amp, cov.alpha);
+    const CovFF cf = load_cov_ff(a.kind, a.hyp);
     ff* rawf = reinterpret_cast<ff*>(raw);
     float bv = 0.0f;
 #pragma unroll
@@ -632,7 +634,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_small(AcaArgs a, int it
       out[3] = nv2;
     }
   } else {
-    const CovFF cf = make_cov_ff(a.kind, a.hyp[kHypScale], cov.amp, cov.alpha);
+    const CovFF cf = load_cov_ff(a.kind, a.hyp);
     ff* rawf = reinterpret_cast<ff*>(raw);
     const ff inv = ff_rcp(ff_from_double(delta));
     float uu[kSmallPer], vv[kSmallPer];

@@ -889,6 +889,7 @@ __global__ void k_lane_load(double* hyp, int kind, const double* theta, const do
   hyp[hodlr::kHypAmp] = amp;
   hyp[hodlr::kHypSigma2] = sigma2[b];
   hyp[hodlr::kHypScale] = hodlr::cov_scale(kind, ell);
+  hodlr::set_hyp_ff(hyp);
 }
 
 __global__ void k_lane_store(const double* scal, int32_t* flags, int32_t* round, double* out,

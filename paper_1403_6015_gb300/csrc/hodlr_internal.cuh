@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/hodlr.h"
+#include "ff.cuh"
 
 namespace hodlr {
 
@@ -84,10 +85,29 @@ __device__ __forceinline__ double cov_r(const Cov& c, double r) {
 // setting: hyp[0] = 1/ell, hyp[1] = amplitude a, hyp[2] = sigma^2, hyp[3] = covariance
 // scale cr (1/ell, 1/ell, sqrt3/ell, sqrt5/ell for exp, SE, Matern-3/2, Matern-5/2; 1/ell
 // for the radial functions), hyp[4] = the rational quadratic's exponent alpha.
-enum { kHypInvEll = 0, kHypAmp = 1, kHypSigma2 = 2, kHypScale = 3, kHypAlpha = 4, kHypLen = 8 };
+enum {
+  kHypInvEll = 0, kHypAmp = 1, kHypSigma2 = 2, kHypScale = 3, kHypAlpha = 4,
+  kHypCrFF = 5, kHypAmpFF = 6, kHypAlphaFF = 7, kHypLen = 8
+};
 
 __device__ __forceinline__ Cov cov_from(int kind, const double* __restrict__ hyp) {
   return Cov{kind, hyp[kHypInvEll], hyp[kHypAmp], hyp[kHypAlpha]};
+}
+
+// Slots kHypCrFF.. hold the double-float kernels' covariance parameters (the factor applied
+// to r, the amplitude, the rational quadratic's exponent) as double-float pairs. They are
+// converted once, by the kernel that writes the slots, instead of by every thread that
+// reads them: FP64-to-float conversions run on the FP64 pipe, 1/64 of the FP32 rate.
+__device__ __forceinline__ void set_hyp_ff(double* hyp) {
+  ff* h = reinterpret_cast<ff*>(hyp);
+  h[kHypCrFF] = ff_from_double(hyp[kHypScale]);
+  h[kHypAmpFF] = ff_from_double(hyp[kHypAmp]);
+  h[kHypAlphaFF] = ff_from_double(hyp[kHypAlpha]);
+}
+
+__device__ __forceinline__ CovFF load_cov_ff(int kind, const double* __restrict__ hyp) {
+  const ff* h = reinterpret_cast<const ff*>(hyp);
+  return CovFF{kind, h[kHypCrFF], h[kHypAmpFF], h[kHypAlphaFF]};
 }
 
 // Sorted points in structure-of-arrays form: coordinate c of sorted point i is x[c * n + i].

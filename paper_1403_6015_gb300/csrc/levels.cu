@@ -515,6 +515,7 @@ __global__ void k_set_hyp(double* hyp, int kind, double ell, double amp, double 
   hyp[kHypSigma2] = sigma2;
   hyp[kHypScale] = cov_scale(kind, ell);
   hyp[kHypAlpha] = alpha;
+  set_hyp_ff(hyp);
 }
 
 // The same from setting idx[0] of device arrays theta (ell, a pairs) and sigma2.
@@ -526,6 +527,7 @@ __global__ void k_load_setting(double* hyp, int kind, const double* theta, const
   hyp[kHypAmp] = amp;
   hyp[kHypSigma2] = sigma2[b];
   hyp[kHypScale] = cov_scale(kind, ell);
+  set_hyp_ff(hyp);
 }
 
 cudaError_t launch_set_hyp(Ctx& c, double ell, double amp, double sigma2) {
