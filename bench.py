@@ -159,12 +159,14 @@ def accuracy(x, y, perm, kern, ell, ll, logdet, sol):
             "residual_rows": float(np.abs(Cx - y[rows]).max() / np.abs(y).max())}
 
 
-# Double-float (mixed form) leaf kernel: FP64-equivalent peak of the FP32 pipe. One
-# double-float multiply-add (TwoProd by FMA, TwoSum, FastTwoSum) is 14 FP32 instructions.
-FF_PEAK = 152 * 128 * 2.07e9 / 14 * 2
+# Double-float (mixed form) leaf kernel: FP64-equivalent peak of the FP32 pipe. The
+# cheapest double-float multiply-add the kernel executes, a term of a compensated dot
+# product (TwoProd by FMA with the cross terms, TwoSum, error accumulation), is 12 FP32
+# instructions; the sequential updates (TwoProd, TwoSum, FastTwoSum) take 15.
+FF_PEAK = 152 * 128 * 2.07e9 / 12 * 2
 FORMS = {1: ("mixed", "f64/f32x2", "k_leaf_ff<512,true> (double-float leaf block build + "
                                    "L D L^T + panel solves)", FF_PEAK,
-             "FP32 pipe in double-float multiply-adds: 152 SMs x 128 lanes x 2.07 GHz / 14 "
+             "FP32 pipe in double-float multiply-adds: 152 SMs x 128 lanes x 2.07 GHz / 12 "
              "instructions x 2 flop"),
          0: ("fp64", "f64", "k_leaf<true,512> (leaf block build + L D L^T + panel solves)",
              FP64_PEAK, "FP64 derived: 152 SMs x 2 FMA/clk x 2.07 GHz x 2 flop")}
