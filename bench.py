@@ -755,17 +755,67 @@ def run_supplementary(args):
     return out
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo on x86, lscpu on Arm, else the machine)."""
+    import platform
+    import subprocess
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(x, y):
     """The oracle (plain FP64 CPU HODLR, OpenMP over the nodes of a level) on one full step
-    of the same workload: one log-likelihood evaluation of each kernel at n = 2^20."""
+    of the same workload: one log-likelihood evaluation of each kernel at n = 2^20, on all
+    host cores (the reported value) and on one core; then, on all cores, the paper's
+    per-phase split (Assembly = ordering + compression, Factor, Solve, Det.)."""
+    import os
     import oracle as O
+    cores = os.cpu_count() or 1
+    O.set_num_threads(0)
+    threads = O.num_threads()
     t0 = time.perf_counter()
     for kern, ell in KERNELS:
         O.Hodlr(x, kern, [ell, 1.0], SIGMA2, LEAF, EPS).loglik(y)
     dt = time.perf_counter() - t0
-    return {"value": len(KERNELS) / dt, "unit": "evals/s", "cores": O.num_threads(),
+    phases = {}
+    for kern, ell in KERNELS:
+        t = [time.perf_counter()]
+        h = O.Hodlr(x, kern, [ell, 1.0], SIGMA2, LEAF, EPS)
+        t.append(time.perf_counter())
+        h.factor()
+        t.append(time.perf_counter())
+        h.solve(y)
+        t.append(time.perf_counter())
+        h.logdet()
+        t.append(time.perf_counter())
+        phases[kern] = {k: t[i + 1] - t[i] for i, k in enumerate(["assembly_s", "factor_s",
+                                                                  "solve_s", "det_s"])}
+    O.set_num_threads(1)
+    t0 = time.perf_counter()
+    for kern, ell in KERNELS:
+        O.Hodlr(x, kern, [ell, 1.0], SIGMA2, LEAF, EPS).loglik(y)
+    d1 = time.perf_counter() - t0
+    O.set_num_threads(0)
+    return {"value": len(KERNELS) / dt, "unit": "evals/s", "cores": threads,
             "kind": "oracle", "sample": "one full step: one loglik per kernel at n=2^20 "
-                                        f"({dt:.1f} s)"}
+                                        f"({dt:.1f} s on {threads} threads)",
+            "cpu_model": cpu_model(), "host_cores": cores,
+            "single_thread": {"value": len(KERNELS) / d1, "unit": "evals/s", "cores": 1,
+                              "sample": f"the same step on one thread ({d1:.1f} s)"},
+            "phases_all_cores": phases}
 
 
 def run_reference(args):
@@ -794,7 +844,8 @@ def run_reference(args):
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(),
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": O.num_threads(),
-                             "kind": "oracle", "sample": "full workload, every step"},
+                             "kind": "oracle", "sample": "full workload, every step",
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

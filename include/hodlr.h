@@ -336,10 +336,14 @@ hodlr_status hodlr_refine_info(hodlr_ctx* ctx, int32_t* corrections, double* res
  *          NaN if C is not positive definite;
  *   stream cudaStream_t (NULL = legacy default stream); the call is stream-ordered and
  *          does not synchronise.
+ *   kernel the four covariances of Table 1 only (HODLR_K_EXP, HODLR_K_SE,
+ *          HODLR_K_MATERN32, HODLR_K_MATERN52); any other kind returns HODLR_EINVAL.
  * Limits: 1 <= n <= 128; larger n returns HODLR_EINVAL, as do host pointers.
- * Scratch: a fixed 135,296-byte array in device global memory that every GPU loading the
+ * Scratch: a fixed 136,384-byte array in device global memory that every GPU loading the
  * library holds until exit. The first call on a device looks up its address (with that
- * device current), so make that first call before any stream capture. All calls on a
+ * device current), so make that first call before any stream capture; calls outside a
+ * capture look it up again, so the address stays valid across a device reset, but a
+ * capture begun after a reset must again follow one uncaptured call. All calls on a
  * device share the array: calls that overlap on the GPU race. */
 hodlr_status hodlr_loglik_small_noalloc(const double* x, int64_t n, int d, hodlr_kernel kernel,
                                         const double* theta, double sigma2, const double* y,

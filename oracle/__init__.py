@@ -46,6 +46,7 @@ def lib():
         build()
         L = ctypes.CDLL(_LIB)
         L.oracle_num_threads.restype = ctypes.c_int
+        L.oracle_set_num_threads.argtypes = [ctypes.c_int]
         L.oracle_kernel_values.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, _dp, _dp]
         L.oracle_dense_lu_solve.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp,
                                             ctypes.c_double, _dp, ctypes.c_int, ctypes.c_int64, _dp,
@@ -111,6 +112,12 @@ def _check(st: int, what: str):
 
 def num_threads() -> int:
     return lib().oracle_num_threads()
+
+
+def set_num_threads(t: int) -> None:
+    """Threads of the oracle's OpenMP loops (t < 1: all host cores); results do not depend
+    on it."""
+    lib().oracle_set_num_threads(int(t))
 
 
 def _theta(theta) -> np.ndarray:

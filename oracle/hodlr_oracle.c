@@ -43,6 +43,16 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* Threads used by the parallel loops that follow (t < 1: all host cores). Timing only;
+ * every result is independent of the thread count. */
+void oracle_set_num_threads(int t) {
+#ifdef _OPENMP
+  omp_set_num_threads(t >= 1 ? t : omp_get_num_procs());
+#else
+  (void)t;
+#endif
+}
+
 /* ------------------------------------------------------------------------------------
  * Covariance functions. k(r) = a f(r / ell), r the Euclidean distance (Table 1 with a
  * length scale ell and amplitude a; Matern nu = 3/2 and 5/2 in their closed forms), and
@@ -1047,7 +1057,7 @@ static int orc_factor_impl(orc_hodlr* H, double* y, int nrhs) {
     }
   }
   if (bad) return ORC_ENOTSPD;
-  /* log det: fixed-order pairwise sums of the leaf terms and of the node terms. */
+  /* log det: sequential sums, in a fixed order, of the leaf terms and of the node terms. */
   double sl = 0.0, sn = 0.0;
   for (int64_t k = 0; k < nleaf; ++k) sl += H->leaflogdet[k];
   for (int64_t id = 0; id < nint; ++id) sn += H->nodelogdet[id];

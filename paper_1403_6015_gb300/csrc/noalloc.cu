@@ -9,11 +9,16 @@
 // their buffers in hodlr_build; this one uses a fixed array in device global memory that
 // the library defines once per loaded module.
 //
-// The scratch: a file-scope __device__ array of kNoAllocBytes (135,296 bytes). Every GPU
+// The scratch: a file-scope __device__ array of kNoAllocBytes (136,384 bytes). Every GPU
 // that loads the library holds one copy until the process exits. Host code cannot use the
 // array's name as a device address; the first call on a device (with that device current)
-// asks the runtime for the address with cudaGetSymbolAddress and keeps it for later calls
-// on that device. That first call should therefore come before any stream capture.
+// asks the runtime for the address with cudaGetSymbolAddress and keeps it for calls made
+// while a stream capture is under way. That first call should therefore come before any
+// stream capture. Calls outside a capture look the address up again, so that a device
+// reset (which reloads the module and can move the array) never leaves a stale address
+// in use; a capture begun after a reset must again follow one uncaptured call.
+// Covariances: the four of Table 1 (exponential, squared-exponential, Matern-3/2,
+// Matern-5/2) only; the radial kinds return HODLR_EINVAL.
 // All calls on a device share the array: calls whose work overlaps on the GPU (different
 // streams, no ordering between them) race and give wrong results. Each call first clears
 // the words that must start at zero.
@@ -39,6 +44,7 @@ constexpr int kOffInt = kOffLd + 8;                            // int32 words: n
 constexpr int kOffHyp = kOffInt + 8;                           // hyperparameter slot
 constexpr int kNoAllocDoubles = kOffHyp + 8;
 constexpr size_t kNoAllocBytes = sizeof(double) * kNoAllocDoubles;
+static_assert(kNoAllocBytes == 136384, "the documented scratch size");
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
@@ -46,14 +52,21 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};
 
-// Device address of the scratch on the current device (set up once per device).
-cudaError_t scratch_address(double** out) {
+// Device address of the scratch on the current device. Looked up on every call made
+// outside a stream capture (so that it follows a device reset); under capture the address
+// kept from the last uncaptured call on this device is used.
+cudaError_t scratch_address(cudaStream_t st, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;  // treat as capturing: use the kept address
+  }
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone || !g_addr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
@@ -125,12 +138,12 @@ extern "C" hodlr_status hodlr_loglik_small_noalloc(const double* x, int64_t n, i
       !std::isfinite(theta[1]) || !(sigma2 >= 0) || !std::isfinite(sigma2) || !x || !y || !out)
     return HODLR_EINVAL;
   if (!on_device(x) || !on_device(y) || !on_device(out)) return HODLR_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
   double* s = nullptr;
-  if (scratch_address(&s) != cudaSuccess) {
+  if (scratch_address(st, &s) != cudaSuccess) {
     cudaGetLastError();
     return HODLR_ECUDA;
   }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   int32_t* iw = reinterpret_cast<int32_t*>(s + kOffInt);
   k_noalloc_prep<<<1, 128, 0, st>>>(s, x, y, (int)n, d, (int)kernel, theta[0], theta[1], sigma2);
   cudaError_t e = cudaGetLastError();

@@ -1,9 +1,11 @@
 """Batched evaluation: one CUDA graph forks a round of evaluations into several presized
 contexts (lanes) on their own streams; every result must equal the adaptive single
-evaluation of the same setting."""
+evaluation of the same setting and, for the Matern covariances in 1-D, the exact
+log-likelihood of the oracle's Kalman filter (the state-space form cited in Sec. 2.3)."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1403_6015_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -15,6 +17,13 @@ def H():
     build_lib.build()
     hodlr.load()
     return hodlr
+
+
+def kalman_loglik(x, y, nu2, ell, s2):
+    """Exact Gaussian log-likelihood of Matern nu = nu2/2 (amplitude 1) on 1-D points."""
+    order = np.argsort(x[:, 0], kind="stable")
+    ld, q = O.matern_kalman(x[order, 0], nu2, ell, 1.0, s2, y[order])
+    return -0.5 * q - 0.5 * ld - 0.5 * len(y) * np.log(2.0 * np.pi)
 
 
 def settings(nset, seed):
@@ -51,6 +60,8 @@ def test_batched_sweep_lanes(H, precision):
     for b in range(nset):
         r = H.Hodlr(x, "matern52", [ell[b], 1.0], s2[b], 128, 1e-12, precision=precision).loglik(y)
         assert abs(got[b] - r) <= 1e-12 * abs(r), (b, got[b], r)
+        k = kalman_loglik(x, y, 5, ell[b], s2[b])
+        assert abs(got[b] - k) <= 1e-9 * abs(k), (b, ell[b], s2[b], got[b], k)
 
 
 def test_batched_uneven_instances(H):
@@ -85,6 +96,53 @@ def test_batched_uneven_instances(H):
         for b in range(nset):
             r = H.Hodlr(x, "matern32", [ell[b], 1.0], s2[b], 64, 1e-12).loglik(y)
             assert abs(got[b] - r) <= 1e-12 * abs(r)
+            k = kalman_loglik(x, y, 3, ell[b], s2[b])
+            assert abs(got[b] - k) <= 1e-9 * abs(k), (b, ell[b], s2[b], got[b], k)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_uneven_matern52_instances_vs_kalman(H, precision):
+    """The uneven-instance workload as the bench runs it: 64 independent problems with n
+    log-uniform in [2^12, 2^18], Matern-5/2 (exact rank 3), leaf 128, eps 1e-12, two
+    (ell, sigma^2) settings each (ell log-uniform in [0.05, 2], sigma^2 in [1e-4, 1]), one
+    presized lane per problem on 16 lane streams, every result against the exact Kalman
+    log-likelihood."""
+    import torch
+    ninst, per = 64, 2
+    un = I.uniform01(3003, ninst)
+    sizes = np.round(np.exp(np.log(4096.0) + un * (np.log(262144.0) - np.log(4096.0)))).astype(int)
+    assert sizes.max() > 200000 and sizes.min() < 5000
+    origin = torch.cuda.Stream()
+    pool = [torch.cuda.Stream() for _ in range(16)]
+    lanes, keep = [], []
+    for i, ni in enumerate(sizes):
+        x, y = I.workload_1d(int(ni), 3100 + i)
+        ell, s2 = settings(per, 3300 + i)
+        h = H.Hodlr(x, "matern52", [ell[0], 1.0], s2[0], 128, 1e-12, precision=precision,
+                    stream=pool[i % len(pool)].cuda_stream)
+        h.presize(np.full(h.tree()[0], 4, dtype=np.int32))
+        theta = torch.from_numpy(np.stack([ell, np.ones(per)], 1).copy()).cuda()
+        sig = torch.from_numpy(s2.copy()).cuda()
+        yd = torch.from_numpy(y).cuda()
+        out = torch.zeros(per, dtype=torch.float64, device="cuda")
+        st = torch.full((per,), -1, dtype=torch.int32, device="cuda")
+        lanes.append(H.hodlr_batch_lane(h._ctx, theta.data_ptr(), sig.data_ptr(), yd.data_ptr(),
+                                        out.data_ptr(), st.data_ptr(), 0, 1, per))
+        keep.append((h, x, y, ell, s2, theta, sig, yd, out, st))
+    torch.cuda.synchronize()
+    assert H.hodlr_loglik_batched(lanes, origin.cuda_stream) == H.HODLR_OK
+    torch.cuda.synchronize()
+    worst = 0.0
+    for h, x, y, ell, s2, theta, sig, yd, out, st in keep:
+        assert (st.cpu().numpy() == 0).all()
+        got = out.cpu().numpy()
+        for b in range(per):
+            k = kalman_loglik(x, y, 5, ell[b], s2[b])
+            e = abs(got[b] - k) / abs(k)
+            worst = max(worst, e)
+            assert e <= 1e-9, (len(y), ell[b], s2[b], got[b], k)
+        h.close()
+    print(f"uneven Matern-5/2 instances, precision {precision}: worst rel. error {worst:.2e}")
 
 
 def test_batched_lanes_sharing_streams(H):

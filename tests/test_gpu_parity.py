@@ -291,3 +291,22 @@ def test_matern32_vs_kalman_full_size(H, n):
     Cx = O.dense_matvec_rows(x, "matern32", th, s2, sol, rows)
     res = np.abs(Cx - y[rows]).max() / np.abs(y).max()
     assert res <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nrhs16_full_size_every_column(H, precision):
+    """The fused factor-solve with 16 right-hand sides at n = 2^20 (the exponential kernel,
+    ell=0.2, sigma^2=1e-2, leaf 128, eps=1e-12), in both forms: every column of C^-1 Y
+    against the Ornstein-Uhlenbeck closed form, and the log det."""
+    n, nrhs = 1 << 20, 16
+    x, Y = I.workload_1d(n, 1001, nrhs)
+    th, s2 = [0.2, 1.0], 1e-2
+    h = H.Hodlr(x, "exp", th, s2, 128, 1e-12, max_nrhs=nrhs, precision=precision)
+    sol = h.factor_solve(Y)
+    assert sol.shape == (n, nrhs)
+    _, perm = h.tree()
+    sol_c, ld_c = O.ou_closed_form(x[perm, 0], th[0], th[1], s2, Y[perm])
+    assert rel(h.logdet(), ld_c) <= 1e-10
+    for c in range(nrhs):
+        err = np.linalg.norm(sol[perm, c] - sol_c[:, c]) / np.linalg.norm(sol_c[:, c])
+        assert err <= 1e-9, (c, err)
