@@ -287,17 +287,24 @@ hodlr_status hodlr_counters(hodlr_ctx* ctx, int64_t* out2);
  *   leaf_threads  CTA size of this context's leaf kernel: FP64 form 256, 512 or 1024;
  *                 mixed form 512 (two leaves per SM) or 1024 (one).
  *   sweep_mode    0: one launch per level when every level's reductions fit a block and
- *                 no rank exceeds 64, else the segmented sweep; 1: always segmented. */
+ *                 no rank exceeds 64, else the segmented sweep; 1: always segmented.
+ *   leaf_kernel   mixed form only: 0 = every leaf operation in double-float on the FP32
+ *                 pipe; 1 = the trailing updates of the leaf factorization and the
+ *                 off-diagonal block updates of its solves as exact bf16-slice products
+ *                 on the tensor cores (512 threads, two leaves per SM; leaf_threads is
+ *                 then ignored). Must be 0 in the FP64 form. */
 typedef struct {
   int leaf_threads;
   int sweep_mode;
+  int leaf_kernel;
 } hodlr_tuning;
 
 /* Read or set the launch configuration. Errors: EINVAL (a value outside the lists). */
 hodlr_status hodlr_get_tuning(hodlr_ctx* ctx, hodlr_tuning* out);
 hodlr_status hodlr_set_tuning(hodlr_ctx* ctx, const hodlr_tuning* t);
 
-/* Autotuner: time every candidate configuration (leaf CTA sizes x sweep modes) on this
+/* Autotuner: time every candidate configuration (leaf CTA sizes x sweep modes, and in the
+ * mixed form the tensor-core leaf kernel x sweep modes) on this
  * context's own problem (one fused factorization with the right-hand side y, n doubles,
  * host or device), each reps times after one untimed run, with CUDA events on
  * opts.stream; keep the fastest (lowest median) and write it to *best (may be NULL) and

@@ -388,6 +388,7 @@ hodlr_status hodlr_build(const double* x, int64_t n, int d, hodlr_kernel kernel,
   c->refine_maxit = opts.refine_maxit;
   if (const char* e = std::getenv("HODLR_LEAF_THREADS")) c->leaf_threads = std::atoi(e);
   if (const char* e = std::getenv("HODLR_LEAF_THREADS64")) c->leaf_threads64 = std::atoi(e);
+  if (const char* e = std::getenv("HODLR_LEAF_TC")) c->leaf_tc = std::atoi(e) != 0;
   if (const char* e = std::getenv("HODLR_NO_FUSED")) c->no_fused = std::atoi(e) != 0;
   c->stream = (cudaStream_t)opts.stream;
   c->kappa = kappa_for(n, leaf);
@@ -1054,8 +1055,10 @@ hodlr_status hodlr_matvec(hodlr_ctx* ctx, const double* x, double* y) {
 
 static bool valid_tuning(const Ctx* c, const hodlr_tuning* t) {
   if (!t || (t->sweep_mode != 0 && t->sweep_mode != 1)) return false;
+  if (t->leaf_kernel != 0 && t->leaf_kernel != 1) return false;
   if (c->precision == 1) return t->leaf_threads == 512 || t->leaf_threads == 1024;
-  return t->leaf_threads == 256 || t->leaf_threads == 512 || t->leaf_threads == 1024;
+  return t->leaf_kernel == 0 &&
+         (t->leaf_threads == 256 || t->leaf_threads == 512 || t->leaf_threads == 1024);
 }
 
 hodlr_status hodlr_get_tuning(hodlr_ctx* ctx, hodlr_tuning* out) {
@@ -1063,15 +1066,18 @@ hodlr_status hodlr_get_tuning(hodlr_ctx* ctx, hodlr_tuning* out) {
   if (!c || !out) return HODLR_EINVAL;
   out->leaf_threads = c->precision == 1 ? c->leaf_threads : c->leaf_threads64;
   out->sweep_mode = c->no_fused ? 1 : 0;
+  out->leaf_kernel = c->precision == 1 && c->leaf_tc ? 1 : 0;
   return HODLR_OK;
 }
 
 hodlr_status hodlr_set_tuning(hodlr_ctx* ctx, const hodlr_tuning* t) {
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!c) return HODLR_EINVAL;
-  if (!valid_tuning(c, t)) return fail(c, HODLR_EINVAL, "set_tuning: leaf_threads or sweep_mode");
+  if (!valid_tuning(c, t))
+    return fail(c, HODLR_EINVAL, "set_tuning: leaf_threads, sweep_mode or leaf_kernel");
   if (c->precision == 1) c->leaf_threads = t->leaf_threads;
   else c->leaf_threads64 = t->leaf_threads;
+  c->leaf_tc = c->precision == 1 && t->leaf_kernel == 1;
   c->no_fused = t->sweep_mode == 1;
   c->graph_valid = false;  // captured graphs hold the old launch shapes
   return HODLR_OK;
@@ -1087,8 +1093,10 @@ hodlr_status hodlr_autotune(hodlr_ctx* ctx, const double* y, int reps, hodlr_tun
   int64_t ldd;
   hodlr_status s = stage_in(c, y, 1, c->n, &yd, &ldd);
   if (s != HODLR_OK) return s;
-  std::vector<int> threads = c->precision == 1 ? std::vector<int>{512, 1024}
-                                               : std::vector<int>{256, 512, 1024};
+  // candidates: (leaf_threads, leaf_kernel); the tensor-core leaf kernel has one CTA size
+  std::vector<std::pair<int, int>> cands =
+      c->precision == 1 ? std::vector<std::pair<int, int>>{{512, 0}, {1024, 0}, {512, 1}}
+                        : std::vector<std::pair<int, int>>{{256, 0}, {512, 0}, {1024, 0}};
   hodlr_tuning saved;
   hodlr_get_tuning(ctx, &saved);
   hodlr_tuning win = saved;
@@ -1100,8 +1108,8 @@ hodlr_status hodlr_autotune(hodlr_ctx* ctx, const double* y, int reps, hodlr_tun
     return fail(c, HODLR_ECUDA, "autotune: events");
   }
   for (int mode = 0; mode < 2 && s == HODLR_OK; ++mode)
-    for (int th : threads) {
-      hodlr_tuning t{th, mode};
+    for (const auto& cand : cands) {
+      hodlr_tuning t{cand.first, mode, cand.second};
       hodlr_set_tuning(ctx, &t);
       std::vector<float> ms;
       for (int r = 0; r <= reps && s == HODLR_OK; ++r) {

@@ -172,6 +172,7 @@ struct Ctx {
   int leaf = 128, kappa = 0, max_rank = kDefaultMaxRank, max_nrhs = 16;
   int precision = 0;              // 0: FP64, 1: double-float leaf stage (mixed)
   int leaf_threads = 512;         // CTA size of the double-float leaf kernel (two CTAs per SM)
+  bool leaf_tc = false;           // mixed form: leaf updates on the tensor cores (k_leaf_tc)
   int leaf_threads64 = 512;       // CTA size of the FP64 leaf kernel (measured best)
   bool no_fused = false;          // force the segmented level sweep
   cudaStream_t stream = nullptr;
