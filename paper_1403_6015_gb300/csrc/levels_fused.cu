@@ -44,12 +44,6 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-__device__ __forceinline__ ff wsum_ff(ff v) {
-  for (int o = 16; o > 0; o >>= 1)
-    v = ff_add(v, ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
-  return v;
-}
-
 // Mixed form, a right-hand-side column: FP64 arithmetic (the solution keeps FP64
 // accuracy), the double-float panel values converted as they are read; Z's right-hand-side
 // columns are FP64.
@@ -98,6 +92,84 @@ __device__ __forceinline__ void leaf_column_rhs(const FusedArgs& a, int leaf, in
   }
 }
 
+// Read-only loads: the level's own Ut/Vt columns, Phi and the level's Z are not written by
+// this launch (it writes the coarser levels' columns, the right-hand sides and the other Z
+// buffer), so they may take the non-coherent path and be scheduled ahead of the stores.
+__device__ __forceinline__ ff ldg_ff(const ff* p) {
+  float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return ff{v.x, v.y};
+}
+
+// Finish two partial sums of one warp at once (a reduce-scatter): after exchanging across
+// lane ^ 16, lanes 0..15 carry s0 and lanes 16..31 carry s1, and four more xor steps leave
+// the totals in lanes 0 and 16. Fixed order: deterministic.
+__device__ __forceinline__ double wsum2(double s0, double s1, int lane) {
+  const bool hi = (lane & 16) != 0;
+  double mine = hi ? s1 : s0, other = hi ? s0 : s1;
+  mine += __shfl_xor_sync(0xffffffffu, other, 16);
+  for (int o = 8; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  return mine;
+}
+
+// FP64 form, two columns q and q1 of [panel | right-hand sides] of one leaf.
+__device__ __forceinline__ void leaf_pair_f64(const FusedArgs& a, int leaf, int b, int p, int q,
+                                              bool two, int wz, int sh, int zs, int lane) {
+  const int q1 = two ? q + 1 : q;
+  double* c0p = q < a.cP ? a.pan + (int64_t)q * a.n + b : a.Y + (int64_t)(q - a.cP) * a.n + b;
+  double* c1p = q1 < a.cP ? a.pan + (int64_t)q1 * a.n + b : a.Y + (int64_t)(q1 - a.cP) * a.n + b;
+  double x0[4], x1[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    int i = m * 32 + lane;
+    x0[m] = i < p ? c0p[i] : 0.0;
+    x1[m] = (two && i < p) ? c1p[i] : 0.0;
+  }
+  if (a.ru > 0) {
+    int side = (leaf >> (sh - 1)) & 1;
+    const double* Zs = a.Zu + (int64_t)(leaf >> sh) * zs + (int64_t)side * a.ru * wz;
+    for (int c = 0; c < a.ru; ++c) {
+      double z0 = __ldg(Zs + c * wz + q), z1 = __ldg(Zs + c * wz + q1);
+      const double* tl = a.pan + (int64_t)(a.cu + c) * a.n + b;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) {
+          double t = __ldg(tl + i);
+          x0[m] -= t * z0;
+          x1[m] -= t * z1;
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int i = m * 32 + lane;
+      if (i < p) {
+        c0p[i] = x0[m];
+        if (two) c1p[i] = x1[m];
+      }
+    }
+  }
+  if (a.u > 0 && a.rl > 0) {
+    double* out = a.part + (int64_t)leaf * a.part_stride;
+    for (int c = 0; c < a.rl; ++c) {
+      const double* ph = a.phi + (int64_t)(a.cl + c) * a.n + b;
+      double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int i = m * 32 + lane;
+        if (i < p) {
+          double h = __ldg(ph + i);
+          s0 += h * x0[m];
+          s1 += h * x1[m];
+        }
+      }
+      double t = wsum2(s0, s1, lane);
+      if (lane == 0) out[c * wz + q] = t;
+      if (two && lane == 16) out[c * wz + q1] = t;
+    }
+  }
+}
+
 // Mixed form, a panel column: the panels and Z's panel columns are double-float pairs; the
 // update and the partial products run on the FP32 pipe.
 __device__ __forceinline__ void leaf_column_ff(const FusedArgs& a, int leaf, int b, int p, int q,
@@ -118,12 +190,12 @@ __device__ __forceinline__ void leaf_column_ff(const FusedArgs& a, int leaf, int
     int side = (leaf >> (sh - 1)) & 1;
     const ff* Zs = reinterpret_cast<const ff*>(a.Zu) + (int64_t)(leaf >> sh) * zs + (int64_t)side * a.ru * wz;
     for (int c = 0; c < a.ru; ++c) {
-      ff z = Zs[c * wz + q];
+      ff z = ldg_ff(Zs + c * wz + q);
       const ff* tl = panf + (int64_t)(a.cu + c) * a.n + b;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         int i = m * 32 + lane;
-        if (i < p) x[m] = ff_fms(x[m], tl[i], z);
+        if (i < p) x[m] = ff_fms(x[m], ldg_ff(tl + i), z);
       }
     }
 #pragma unroll
@@ -140,9 +212,10 @@ __device__ __forceinline__ void leaf_column_ff(const FusedArgs& a, int leaf, int
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         int i = m * 32 + lane;
-        if (i < p) s = ff_fma(s, ph[i], x[m]);
+        if (i < p) s = ff_fma(s, ldg_ff(ph + i), x[m]);
       }
-      s = wsum_ff(s);
+      for (int o = 16; o > 0; o >>= 1)
+        s = ff_add(s, ff{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)});
       if (lane == 0) out[c * wz + q] = ff_to_double(s);
     }
   }
@@ -162,56 +235,22 @@ __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
   int wz = a.cP + a.nrhs;
   int sh = a.kappa - a.u;  // leaves per level-u half-node = 2^(sh - 1); per node = 2^sh
   int zs = 2 * a.ru * wz;
-  for (int t = w; t < nl * wz; t += kLT / 32) {
-    if (kFF) {
-      int g = t / wz, q = t - g * wz;
-      int leaf = leaf_base + g;
-      int id = a.leaf0 + leaf;
-      leaf_column_ff(a, leaf, a.nb[id], a.ns[id], q, wz, sh, zs, lane);
-      continue;
-    }
-    int g = t / wz, q = t - g * wz;
+  // tasks. FP64 form: pairs of columns of one leaf (the level's columns read once for two,
+  // one reduce-scatter for both partial sums). Mixed form: one column of one leaf per
+  // task, twice as many warps in flight for the longer double-float chains (measured
+  // faster than pairs there).
+  const int npair = kFF ? 0 : (wz + 1) >> 1;
+  const int ntask = kFF ? wz : npair;
+  for (int t = w; t < nl * ntask; t += kLT / 32) {
+    int g = t / ntask, k = t - g * ntask;
     int leaf = leaf_base + g;
     int id = a.leaf0 + leaf;
     int b = a.nb[id], p = a.ns[id];
-    double* col = q < a.cP ? a.pan + (int64_t)q * a.n + b : a.Y + (int64_t)(q - a.cP) * a.n + b;
-    double x[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      int i = m * 32 + lane;
-      x[m] = i < p ? col[i] : 0.0;
-    }
-    if (a.ru > 0) {
-      int side = (leaf >> (sh - 1)) & 1;
-      const double* Zs = a.Zu + (int64_t)(leaf >> sh) * zs + (int64_t)side * a.ru * wz;
-      for (int c = 0; c < a.ru; ++c) {
-        double z = Zs[c * wz + q];
-        const double* tl = a.pan + (int64_t)(a.cu + c) * a.n + b;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          int i = m * 32 + lane;
-          if (i < p) x[m] -= tl[i] * z;
-        }
-      }
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        int i = m * 32 + lane;
-        if (i < p) col[i] = x[m];
-      }
-    }
-    if (a.u > 0 && a.rl > 0) {
-      double* out = a.part + (int64_t)leaf * a.part_stride;
-      for (int c = 0; c < a.rl; ++c) {
-        const double* ph = a.phi + (int64_t)(a.cl + c) * a.n + b;
-        double s = 0.0;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          int i = m * 32 + lane;
-          if (i < p) s += ph[i] * x[m];
-        }
-        s = wsum(s);
-        if (lane == 0) out[c * wz + q] = s;
-      }
+    if (kFF) {
+      leaf_column_ff(a, leaf, b, p, k, wz, sh, zs, lane);
+    } else {
+      int q = 2 * k;
+      leaf_pair_f64(a, leaf, b, p, q, q + 1 < wz, wz, sh, zs, lane);
     }
   }
   if (a.u == 0 || a.rl == 0) return;
