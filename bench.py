@@ -513,6 +513,12 @@ def run_sweeps(args):
     RM.sweep_with_predictor(h, net, ell, s2, yd, margin=1, lanes=lanes, stream=origin.cuda_stream)
     (gotl, stl), tl = timed(lambda: RM.sweep_with_predictor(h, net, ell, s2, yd, margin=1, lanes=lanes,
                                                             stream=origin.cuda_stream))
+    # the baseline at equal batching: the same 8 lanes and settings, presized from one
+    # adaptive probe at the smallest ell (no network; margin 0: the probe's ranks bound
+    # every setting's here, and it measured fastest)
+    RM.sweep_with_probe(h, ell, s2, yd, margin=0, lanes=lanes, stream=origin.cuda_stream)
+    (gotb, stb), tb = timed(lambda: RM.sweep_with_probe(h, ell, s2, yd, margin=0, lanes=lanes,
+                                                        stream=origin.cuda_stream))
     for c in lanes:
         c.close()
     out["predictor_se"] = {
@@ -521,11 +527,67 @@ def run_sweeps(args):
         "predicted_lanes": 8, "predicted_lanes_evals_per_s": nset / tl, "lanes_gain": ta / tl,
         "lanes_fallbacks": stl["fallbacks"],
         "lanes_max_rel_diff": float(np.max(np.abs(gotl - ref) / np.abs(ref))),
+        "probe_lanes_evals_per_s": nset / tb, "gain_equal_batching": tb / tl,
+        "probe_fallbacks": stb["fallbacks"], "probe_level_ranks": stb["probe_level_ranks"],
+        "probe_max_rel_diff": float(np.max(np.abs(gotb - ref) / np.abs(ref))),
+        "presized_rank_sum": {"predictor": stl["presized_rank_sum"],
+                              "probe": stb["presized_rank_sum"]},
         "groups": st["groups"], "fallbacks": st["fallbacks"],
         "max_rel_diff": float(np.max(np.abs(got - ref) / np.abs(ref))),
         "train": {"pairs": int(X.shape[0]), "final_mse": loss, "seconds": t_train,
                   "steps": 1500}}
     h.close()
+
+    # (2b) where the network replaces a probe per problem: 64 independent problems of uneven
+    # size (n log-uniform in [2^12, 2^16]), squared-exponential, eps 1e-10, two settings
+    # each, all in one batched launch. Baseline at equal batching: each problem presized
+    # from one adaptive compression at its smallest ell (an adaptive evaluation with host
+    # synchronisations per problem); predictor: each problem presized by the network.
+    ninst, per = 64, 2
+    un = I.uniform01(3013, ninst)
+    sizes = np.round(np.exp(np.log(4096.0) + un * (np.log(65536.0) - np.log(4096.0)))).astype(int)
+    pool = [torch.cuda.Stream() for _ in range(16)]
+    origin = torch.cuda.Stream()
+    ictx, iset, iys = [], [], []
+    for i, ni in enumerate(sizes):
+        xi, yi = I.workload_1d(int(ni), 3200 + i)
+        e_i, s_i = sweep_settings(per, 3400 + i)
+        ictx.append(H.Hodlr(xi, "se", [e_i[0], 1.0], s_i[0], 128, 1e-10,
+                            stream=pool[i % len(pool)].cuda_stream))
+        iset.append((e_i, s_i))
+        iys.append(torch.from_numpy(yi).cuda())
+    torch.cuda.synchronize()
+
+    def adaptive_inst():
+        res = []
+        for hi, (e_i, s_i), yi in zip(ictx, iset, iys):
+            hi.presize(None)
+            v = np.zeros(per)
+            for b in range(per):
+                hi.rebuild([float(e_i[b]), 1.0], float(s_i[b]))
+                v[b] = hi.loglik(yi)
+            res.append(v)
+        return res
+    adaptive_inst()
+    ref_i, ta_i = timed(adaptive_inst)
+    RM.instances_with_probe(ictx, iset, iys, origin.cuda_stream, margin=0)
+    (got_b, st_b), tb_i = timed(lambda: RM.instances_with_probe(ictx, iset, iys, origin.cuda_stream,
+                                                                margin=0))
+    RM.instances_with_predictor(ictx, net, iset, iys, origin.cuda_stream, margin=1)
+    (got_p, st_p), tp_i = timed(lambda: RM.instances_with_predictor(ictx, net, iset, iys,
+                                                                    origin.cuda_stream, margin=1))
+    relmax = lambda got: max(float(np.max(np.abs(a - b) / np.abs(b))) for a, b in zip(got, ref_i))
+    out["predictor_instances"] = {
+        "instances": ninst, "settings_per_instance": per, "n_min": int(sizes.min()),
+        "n_max": int(sizes.max()), "kernel": "se", "eps": 1e-10, "leaf": 128, "form": "fp64",
+        "adaptive_evals_per_s": ninst * per / ta_i,
+        "probe_evals_per_s": ninst * per / tb_i, "predicted_evals_per_s": ninst * per / tp_i,
+        "gain_equal_batching": tb_i / tp_i, "probe_fallbacks": st_b["fallbacks"],
+        "predictor_fallbacks": st_p["fallbacks"],
+        "presized_rank_sum": {"predictor": st_p["presized_rank_sum"], "probe": st_b["presized_rank_sum"]},
+        "max_rel_diff": {"probe": relmax(got_b), "predictor": relmax(got_p)}}
+    for hi in ictx:
+        hi.close()
     net.close()
 
     # (3) the predictor at scale: 2-D n = 2^20 U[0,1]^2, squared-exponential ell = 0.1,

@@ -204,12 +204,16 @@ typedef struct {
 
 /* Batched evaluation (many settings of one problem, or many independent problems of uneven
  * size): every lane evaluates its settings in rounds; one round of all lanes is captured as
- * a single CUDA graph that forks from `stream` (cudaStream_t, not a lane's) into the lanes'
- * streams, runs them concurrently and joins, and the graph is replayed for the remaining
- * rounds. The first round runs directly (it sets kernel attributes). Lanes must use
- * distinct contexts; lanes whose contexts share a stream run one after another on it. No
- * lane's stream may be `stream` itself. Stream-ordered on `stream`. Errors (message in the
- * offending lane's hodlr_last_error): EINVAL, ENOMEM, ECUDA. */
+ * a single CUDA graph and replayed for the remaining rounds. A round forks from `stream`
+ * (cudaStream_t, not a lane's) into the lanes' streams for their compressions and
+ * right-hand sides, joins into one persistent leaf-stage launch per form (FP64, mixed) in
+ * which every CTA takes (lane, leaf) work items from a device counter until the leaves of
+ * all lanes are factored and solved (Sec. 3.2's leaf factor K_kappa), and forks again for
+ * each lane's level sweep, log det and log-likelihood before joining. The first round
+ * runs directly (it sets kernel attributes). Lanes must use distinct contexts; lanes whose
+ * contexts share a stream run one after another on it. No lane's stream may be `stream`
+ * itself. The leaf work list lives in the first lane's context. Stream-ordered on `stream`.
+ * Errors (message in the offending lane's hodlr_last_error): EINVAL, ENOMEM, ECUDA. */
 hodlr_status hodlr_loglik_batched(const hodlr_batch_lane* lanes, int nlanes, void* stream);
 
 /* ---- Learned rank predictor (not in the paper; sizes presized mode from features) ------

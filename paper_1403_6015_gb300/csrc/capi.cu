@@ -88,6 +88,11 @@ void free_all(Ctx* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
   dfree(c->sweep_idx);
+  if (c->batch_args) cudaFree(c->batch_args);
+  c->batch_args = nullptr;
+  c->batch_cap = 0;
+  c->batch_first_cap = 0;
+  dfree(c->batch_first);
   dfree(c->boxes);
   dfree(c->feat);
   if (c->h_active) cudaFreeHost(c->h_active);
@@ -905,7 +910,9 @@ __global__ void k_lane_store(const double* scal, int32_t* flags, int32_t* round,
   round[0] = (int32_t)(r + 1);
 }
 
-static hodlr_status lane_eval(const hodlr_batch_lane& L) {
+// A lane's part of a round before the leaf stage: its setting into the hyperparameter
+// slot, the compression, the right-hand side.
+static hodlr_status lane_pre(const hodlr_batch_lane& L) {
   Ctx* c = reinterpret_cast<Ctx*>(L.ctx);
   k_lane_load<<<1, 1, 0, c->stream>>>(c->hyp, c->kind, L.theta, L.sigma2, c->sweep_idx, L.first,
                                       L.stride, L.count);
@@ -914,15 +921,132 @@ static hodlr_status lane_eval(const hodlr_batch_lane& L) {
   if (s != HODLR_OK) return s;
   TRY_CUDA(c, gather_rhs(c, L.y, c->n, 1), "gather");
   c->factored = false;
-  s = factor_impl(c, 1);
-  if (s != HODLR_OK) return s;
-  s = refine(c, 1, true);
+  return HODLR_OK;
+}
+
+// A lane's part after the leaf stage: level sweep, log det, refinement, log-likelihood,
+// and the result into the caller's output.
+static hodlr_status lane_post(const hodlr_batch_lane& L) {
+  Ctx* c = reinterpret_cast<Ctx*>(L.ctx);
+  TRY_CUDA(c, sweep(c, 1, true), "levels");
+  TRY_CUDA(c, hodlr::launch_logdet_sum(*c), "logdet");
+  c->factored = true;
+  c->nrhs_fused = 1;
+  hodlr_status s = refine(c, 1, true);
   if (s != HODLR_OK) return s;
   TRY_CUDA(c, hodlr::launch_quad_loglik(*c), "loglik");
   k_lane_store<<<1, 1, 0, c->stream>>>(c->scal, c->dflags, c->sweep_idx, L.out, L.status, L.first,
                                        L.stride, L.count);
   ++c->launches;
   TRY_CUDA(c, cudaGetLastError(), "store");
+  return HODLR_OK;
+}
+
+// The leaf stage of every lane of one round: per form (FP64, mixed), one persistent
+// launch whose CTAs take (lane, leaf) items from a device counter; its argument blocks
+// and leaf offsets sit in the first lane's context (written before the rounds).
+struct BatchLeaves {
+  int nprob[2] = {0, 0};
+  int total[2] = {0, 0};
+  size_t args_off[2] = {0, 0};  // byte offset of each form's argument blocks in batch_args
+  int first_off[2] = {0, 0};    // int offset of each form's offsets in batch_first
+  int counter_off = 0;          // two counters after the offsets
+};
+
+static hodlr_status plan_leaves(const hodlr_batch_lane* lanes, int nlanes, cudaStream_t origin,
+                                BatchLeaves* plan) {
+  Ctx* c0 = reinterpret_cast<Ctx*>(lanes[0].ctx);
+  const size_t asz[2] = {hodlr::leaf_args_bytes(), hodlr::leaf_args_bytes_ff()};
+  std::vector<unsigned char> hargs;
+  std::vector<int32_t> hfirst;
+  for (int f = 0; f < 2; ++f) {
+    plan->args_off[f] = hargs.size();
+    plan->first_off[f] = (int)hfirst.size();
+    int tot = 0;
+    for (int i = 0; i < nlanes; ++i) {
+      Ctx* c = reinterpret_cast<Ctx*>(lanes[i].ctx);
+      if (c->precision != f) continue;
+      size_t at = hargs.size();
+      hargs.resize(at + asz[f]);
+      if (f == 1) hodlr::leaf_args_fill_ff(*c, 1, hargs.data() + at);
+      else hodlr::leaf_args_fill(*c, 1, hargs.data() + at);
+      hfirst.push_back(tot);
+      tot += 1 << c->kappa;
+      ++plan->nprob[f];
+    }
+    hfirst.push_back(tot);
+    plan->total[f] = tot;
+  }
+  plan->counter_off = (int)hfirst.size();
+  hfirst.push_back(0);
+  hfirst.push_back(0);
+  int64_t need = (int64_t)hargs.size();
+  if (need > c0->batch_cap || (int64_t)hfirst.size() > c0->batch_first_cap) {
+    if (c0->batch_args) cudaFree(c0->batch_args);
+    c0->batch_args = nullptr;
+    c0->batch_cap = 0;
+    c0->batch_first_cap = 0;
+    dfree(c0->batch_first);
+    int64_t nf = std::max<int64_t>((int64_t)hfirst.size(), 2 * (int64_t)nlanes + 8);
+    if (cudaMalloc(&c0->batch_args, (size_t)std::max<int64_t>(need, 1)) != cudaSuccess ||
+        cudaMalloc(&c0->batch_first, sizeof(int32_t) * (size_t)nf) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c0, HODLR_ENOMEM, "batched: leaf work list");
+    }
+    c0->batch_cap = std::max<int64_t>(need, 1);
+    c0->batch_first_cap = nf;
+  }
+  TRY_CUDA(c0, cudaMemcpyAsync(c0->batch_args, hargs.data(), hargs.size(), cudaMemcpyHostToDevice, origin),
+           "batched: leaf work list");
+  TRY_CUDA(c0, cudaMemcpyAsync(c0->batch_first, hfirst.data(), sizeof(int32_t) * hfirst.size(),
+                               cudaMemcpyHostToDevice, origin), "batched: leaf work list");
+  return HODLR_OK;
+}
+
+static hodlr_status leaves_round(const hodlr_batch_lane* lanes, const BatchLeaves& plan,
+                                 cudaStream_t origin) {
+  Ctx* c0 = reinterpret_cast<Ctx*>(lanes[0].ctx);
+  for (int f = 0; f < 2; ++f) {
+    if (plan.nprob[f] == 0) continue;
+    int32_t* counter = c0->batch_first + plan.counter_off + f;
+    TRY_CUDA(c0, cudaMemsetAsync(counter, 0, sizeof(int32_t), origin), "batched: leaf counter");
+    const void* args = static_cast<unsigned char*>(c0->batch_args) + plan.args_off[f];
+    const int32_t* first = c0->batch_first + plan.first_off[f];
+    cudaError_t e = f == 1 ? hodlr::launch_leaf_factor_multi_ff(args, first, plan.nprob[f], plan.total[f],
+                                                                counter, c0->sms, origin)
+                           : hodlr::launch_leaf_factor_multi(args, first, plan.nprob[f], plan.total[f],
+                                                             counter, c0->sms, origin);
+    TRY_CUDA(c0, e, "batched: leaf stage");
+    ++c0->launches;
+  }
+  return HODLR_OK;
+}
+
+// One round: every lane's compression and right-hand side on its own stream (fork), the
+// persistent leaf launches on the origin stream (join), every lane's sweep and
+// log-likelihood on its own stream again (fork), joined into the origin stream.
+static hodlr_status batched_round(const hodlr_batch_lane* lanes, int nlanes, cudaStream_t origin,
+                                  const BatchLeaves& plan, std::vector<cudaEvent_t>& ev) {
+  cudaEventRecord(ev[nlanes], origin);
+  for (int i = 0; i < nlanes; ++i) {
+    Ctx* c = reinterpret_cast<Ctx*>(lanes[i].ctx);
+    cudaStreamWaitEvent(c->stream, ev[nlanes], 0);
+    hodlr_status s = lane_pre(lanes[i]);
+    if (s != HODLR_OK) return s;
+    cudaEventRecord(ev[i], c->stream);
+    cudaStreamWaitEvent(origin, ev[i], 0);
+  }
+  hodlr_status s = leaves_round(lanes, plan, origin);
+  if (s != HODLR_OK) return s;
+  cudaEventRecord(ev[nlanes + 1], origin);
+  for (int i = 0; i < nlanes; ++i) {
+    Ctx* c = reinterpret_cast<Ctx*>(lanes[i].ctx);
+    cudaStreamWaitEvent(c->stream, ev[nlanes + 1], 0);
+    s = lane_post(lanes[i]);
+    if (s != HODLR_OK) return s;
+    cudaEventRecord(ev[i], c->stream);
+    cudaStreamWaitEvent(origin, ev[i], 0);
+  }
   return HODLR_OK;
 }
 
@@ -948,7 +1072,7 @@ hodlr_status hodlr_loglik_batched(const hodlr_batch_lane* lanes, int nlanes, voi
       return fail(c, HODLR_ENOMEM, "batched: counter");
     rounds = std::max(rounds, L.count);
   }
-  std::vector<cudaEvent_t> ev(nlanes + 1, nullptr);
+  std::vector<cudaEvent_t> ev(nlanes + 2, nullptr);
   for (auto& e : ev)
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
@@ -960,23 +1084,24 @@ hodlr_status hodlr_loglik_batched(const hodlr_batch_lane* lanes, int nlanes, voi
     for (auto& f : ev)
       if (f) cudaEventDestroy(f);
   };
-  // round counters to zero, ordered before the graph on the origin stream
+  // round counters to zero and the leaf work list, ordered before the rounds on origin
   for (int i = 0; i < nlanes; ++i) {
     Ctx* c = reinterpret_cast<Ctx*>(lanes[i].ctx);
     cudaMemsetAsync(c->sweep_idx, 0, sizeof(int32_t), origin);
   }
+  BatchLeaves plan;
+  hodlr_status ps = plan_leaves(lanes, nlanes, origin, &plan);
+  if (ps != HODLR_OK) {
+    cleanup();
+    return ps;
+  }
   // one direct round first (sets kernel attributes outside the capture)
-  cudaEventRecord(ev[nlanes], origin);
-  for (int i = 0; i < nlanes; ++i) {
-    Ctx* c = reinterpret_cast<Ctx*>(lanes[i].ctx);
-    cudaStreamWaitEvent(c->stream, ev[nlanes], 0);
-    hodlr_status s = lane_eval(lanes[i]);
+  {
+    hodlr_status s = batched_round(lanes, nlanes, origin, plan, ev);
     if (s != HODLR_OK) {
       cleanup();
       return s;
     }
-    cudaEventRecord(ev[i], c->stream);
-    cudaStreamWaitEvent(origin, ev[i], 0);
   }
   if (rounds > 1) {
     cudaGraph_t g = nullptr;
@@ -984,14 +1109,7 @@ hodlr_status hodlr_loglik_batched(const hodlr_batch_lane* lanes, int nlanes, voi
     cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed);
     hodlr_status s = HODLR_OK;
     if (e == cudaSuccess) {
-      cudaEventRecord(ev[nlanes], origin);
-      for (int i = 0; i < nlanes && s == HODLR_OK; ++i) {
-        Ctx* c = reinterpret_cast<Ctx*>(lanes[i].ctx);
-        cudaStreamWaitEvent(c->stream, ev[nlanes], 0);
-        s = lane_eval(lanes[i]);
-        cudaEventRecord(ev[i], c->stream);
-        cudaStreamWaitEvent(origin, ev[i], 0);
-      }
+      s = batched_round(lanes, nlanes, origin, plan, ev);
       e = cudaStreamEndCapture(origin, &g);
     }
     if (s == HODLR_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);

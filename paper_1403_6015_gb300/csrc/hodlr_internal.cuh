@@ -173,6 +173,12 @@ struct Ctx {
   int precision = 0;              // 0: FP64, 1: double-float leaf stage (mixed)
   int leaf_threads = 512;         // CTA size of the double-float leaf kernel (two CTAs per SM)
   bool leaf_tc = false;           // mixed form: leaf updates on the tensor cores (k_leaf_tc)
+  // batched evaluation with this context as its first lane: the persistent leaf launch's
+  // argument blocks and leaf offsets (device), grown as needed
+  void* batch_args = nullptr;
+  int32_t* batch_first = nullptr;  // offsets, then one counter per form
+  int64_t batch_cap = 0;           // bytes of batch_args
+  int64_t batch_first_cap = 0;     // ints of batch_first
   int leaf_threads64 = 512;       // CTA size of the FP64 leaf kernel (measured best)
   bool no_fused = false;          // force the segmented level sweep
   cudaStream_t stream = nullptr;
@@ -295,6 +301,18 @@ cudaError_t launch_gather_rhs(Ctx& c, const double* y, int64_t ld, int nrhs);
 cudaError_t launch_scatter_rhs(Ctx& c, double* x, int64_t ld, int nrhs);
 cudaError_t launch_leaf_factor(Ctx& c, int nrhs);
 cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs);
+// Batched evaluation: one persistent factor launch over the leaves of many contexts of one
+// form. args: device array of nprob argument blocks (leaf_args_fill / leaf_args_fill_ff,
+// leaf_args_bytes / leaf_args_bytes_ff each), first: device array of nprob + 1 leaf
+// offsets (first[nprob] = total), counter: device int, zero before the launch.
+size_t leaf_args_bytes();
+size_t leaf_args_bytes_ff();
+void leaf_args_fill(Ctx& c, int nrhs, void* out);
+void leaf_args_fill_ff(Ctx& c, int nrhs, void* out);
+cudaError_t launch_leaf_factor_multi(const void* args, const int32_t* first, int nprob, int total,
+                                     int32_t* counter, int sms, cudaStream_t s);
+cudaError_t launch_leaf_factor_multi_ff(const void* args, const int32_t* first, int nprob,
+                                        int total, int32_t* counter, int sms, cudaStream_t s);
 cudaError_t launch_leaf_solve_ff(Ctx& c, int nrhs);
 cudaError_t launch_leaf_solve(Ctx& c, int nrhs);
 cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode);

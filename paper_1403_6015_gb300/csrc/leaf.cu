@@ -17,6 +17,9 @@
 // level-(kappa-1) partial products Phi_{kappa-1}^T x of the leaf's rows.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstring>
+
 #include "hodlr_internal.cuh"
 
 namespace hodlr {
@@ -188,7 +191,7 @@ __device__ void lu_factor(double* A, int p, int* perm, int* prow, int* nswap, in
 }
 
 template <bool kFactor, int kLeafThreads>
-__global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
+__device__ __forceinline__ void leaf_body(const LeafArgs& a, int leaf) {
   extern __shared__ double A[];  // [kMaxLeaf][kLD]
   __shared__ double xl[3 * kMaxLeaf];
   __shared__ double dinv[kMaxLeaf];
@@ -198,7 +201,6 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
   __shared__ int bad;
   __shared__ int perm[kMaxLeaf];
   __shared__ int prow, nswap;
-  int leaf = blockIdx.x;
   int id = a.leaf0 + leaf;
   int b = a.nb[id], p = a.ns[id];
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -408,6 +410,37 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
   }
 }
 
+template <bool kFactor, int kLeafThreads>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs a) {
+  leaf_body<kFactor, kLeafThreads>(a, blockIdx.x);
+}
+
+// Persistent factor launch over the leaves of many problems (batched evaluation): every
+// CTA takes work items (problem, leaf) from a device counter until all are done; item t
+// belongs to the problem whose first item, first[problem], is the largest <= t.
+template <int kLeafThreads>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf_multi(const LeafArgs* __restrict__ args,
+                                                            const int32_t* __restrict__ first,
+                                                            int nprob, int32_t* counter) {
+  __shared__ int item_s;
+  const int total = first[nprob];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (first[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    leaf_body<true, kLeafThreads>(args[lo], item - first[lo]);
+    __syncthreads();
+  }
+}
+
 LeafArgs make_args(Ctx& c, int nrhs, bool factor) {
   LeafArgs a;
   a.pts = Pts{c.xs, c.n, c.d};
@@ -453,6 +486,23 @@ cudaError_t launch_leaf(const LeafArgs& a, unsigned grid, int threads, cudaStrea
       HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf<kFactor, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_leaf<kFactor, 256><<<grid, 256, smem, s>>>(a);
   }
+  return cudaGetLastError();
+}
+
+size_t leaf_args_bytes() { return sizeof(LeafArgs); }
+
+void leaf_args_fill(Ctx& c, int nrhs, void* out) {
+  LeafArgs a = make_args(c, nrhs, true);
+  memcpy(out, &a, sizeof(a));
+}
+
+cudaError_t launch_leaf_factor_multi(const void* args, const int32_t* first, int nprob, int total,
+                                     int32_t* counter, int sms, cudaStream_t s) {
+  size_t smem = sizeof(double) * kMaxLeaf * kLD;
+  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_multi<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  unsigned grid = (unsigned)std::min(total, sms);
+  if (grid == 0) return cudaSuccess;
+  k_leaf_multi<512><<<grid, 512, smem, s>>>(static_cast<const LeafArgs*>(args), first, nprob, counter);
   return cudaGetLastError();
 }
 

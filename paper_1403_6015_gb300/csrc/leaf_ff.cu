@@ -24,6 +24,9 @@
 //     compensated form (ffacc: the error of each sum kept apart and added once at the end).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstring>
+
 #include "ff.cuh"
 #include "hodlr_internal.cuh"
 #include "tc.cuh"
@@ -78,7 +81,7 @@ __device__ __forceinline__ int tri_row(int e) {
 }
 
 template <int kT, bool kFactor>
-__global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
+__device__ __forceinline__ void leaf_ff_body(const LeafFFArgs& a, int leaf) {
   extern __shared__ ff sm[];
   ff* A = sm;                          // packed lower triangle, kTri
   ff* Up = A + kTri;                   // [kMaxLeaf][kBS] unscaled panel columns (factor)
@@ -90,7 +93,6 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
   __shared__ double red[kT / 32];
   __shared__ int bad;
   constexpr int NW = kT / 32;
-  int leaf = blockIdx.x;
   int id = a.leaf0 + leaf;
   int b = a.nb[id], p = a.ns[id];
   int P = (p + 31) & ~31, NB = P / 32;
@@ -355,6 +357,37 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
         if (lane == 0) out[r * ncol + q0 + c] = ff_to_double(s);
       }
     }
+    __syncthreads();
+  }
+}
+
+template <int kT, bool kFactor>
+__global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff(LeafFFArgs a) {
+  leaf_ff_body<kT, kFactor>(a, blockIdx.x);
+}
+
+// Persistent factor launch over the leaves of many problems (batched evaluation): every
+// CTA takes work items (problem, leaf) from a device counter until all are done; item t
+// belongs to the problem whose first item, first[problem], is the largest <= t.
+template <int kT>
+__global__ void __launch_bounds__(kT, 1024 / kT) k_leaf_ff_multi(const LeafFFArgs* __restrict__ args,
+                                                                const int32_t* __restrict__ first,
+                                                                int nprob, int32_t* counter) {
+  __shared__ int item_s;
+  const int total = first[nprob];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = item_s;
+    __syncthreads();  // every thread has read the item before thread 0 takes the next
+    if (item >= total) break;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (first[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    leaf_ff_body<kT, true>(args[lo], item - first[lo]);
     __syncthreads();
   }
 }
@@ -889,6 +922,23 @@ cudaError_t launch_tc(const LeafFFArgs& a, unsigned grid, cudaStream_t s) {
 }
 
 }  // namespace
+
+size_t leaf_args_bytes_ff() { return sizeof(LeafFFArgs); }
+
+void leaf_args_fill_ff(Ctx& c, int nrhs, void* out) {
+  LeafFFArgs a = make_ff_args(c, nrhs, true);
+  memcpy(out, &a, sizeof(a));
+}
+
+cudaError_t launch_leaf_factor_multi_ff(const void* args, const int32_t* first, int nprob,
+                                        int total, int32_t* counter, int sms, cudaStream_t s) {
+  size_t smem = sizeof(ff) * (kTri + kMaxLeaf * kBS);
+  HODLR_CUDA_TRY(cudaFuncSetAttribute(k_leaf_ff_multi<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  unsigned grid = (unsigned)std::min(total, 2 * sms);
+  if (grid == 0) return cudaSuccess;
+  k_leaf_ff_multi<512><<<grid, 512, smem, s>>>(static_cast<const LeafFFArgs*>(args), first, nprob, counter);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_leaf_factor_ff(Ctx& c, int nrhs) {
   ++c.launches;

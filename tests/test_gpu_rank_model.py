@@ -151,3 +151,63 @@ def test_sweep_with_predictor_on_lanes(H, RM, trained):
     for b in range(len(ell)):
         r = H.Hodlr(x, "se", [ell[b], 1.0], s2[b], 64, 1e-10).loglik(y)
         assert abs(got[b] - r) <= 1e-12 * abs(r), (b, got[b], r)
+
+
+def test_predictor_against_probe_at_equal_batching(H, RM, trained):
+    """The predictor against the network-free baseline on the same lanes and settings: the
+    baseline presizes every setting from one adaptive probe at the smallest ell. Both give
+    the adaptive results, and the predictor presizes less in total (its grouped profiles
+    follow each setting's ranks; the probe pads every setting to the largest ranks)."""
+    import torch
+    net = trained[0]
+    n = 1 << 14
+    x, y = I.workload_1d(n, 954)
+    u = I.uniform01(98, 32)
+    ell = np.exp(np.log(0.05) + u[:16] * (np.log(2.0) - np.log(0.05)))
+    s2 = np.exp(np.log(1e-4) + u[16:] * (np.log(1.0) - np.log(1e-4)))
+    yd = torch.from_numpy(y).cuda()
+    stream = torch.cuda.Stream()
+    h = H.Hodlr(x, "se", [ell[0], 1.0], s2[0], 64, 1e-10, stream=stream.cuda_stream)
+    origin = torch.cuda.Stream()
+    lanes = [H.Hodlr(x, "se", [ell[0], 1.0], s2[0], 64, 1e-10, stream=torch.cuda.Stream().cuda_stream)
+             for _ in range(3)]
+    torch.cuda.synchronize()
+    got_p, st_p = RM.sweep_with_predictor(h, net, ell, s2, yd, margin=1, lanes=lanes,
+                                          stream=origin.cuda_stream)
+    got_b, st_b = RM.sweep_with_probe(h, ell, s2, yd, margin=1, lanes=lanes,
+                                      stream=origin.cuda_stream)
+    for b in range(len(ell)):
+        r = H.Hodlr(x, "se", [ell[b], 1.0], s2[b], 64, 1e-10).loglik(y)
+        assert abs(got_p[b] - r) <= 1e-12 * abs(r), (b, got_p[b], r)
+        assert abs(got_b[b] - r) <= 1e-12 * abs(r), (b, got_b[b], r)
+    assert st_p["presized_rank_sum"] < st_b["presized_rank_sum"], (st_p, st_b)
+
+
+def test_predictor_presizes_uneven_instances(H, RM, trained):
+    """Independent problems of uneven size: the network presizes each one (no adaptive
+    compression), and the batched results equal the adaptive ones; the probe baseline
+    (one adaptive compression per problem) gives the same results."""
+    import torch
+    net = trained[0]
+    sizes = [4500, 9000, 20000, 33000]
+    origin = torch.cuda.Stream()
+    ctxs, sets, ys, raw = [], [], [], []
+    for i, ni in enumerate(sizes):
+        x, y = I.workload_1d(ni, 960 + i)
+        u = I.uniform01(99 + i, 4)
+        e = np.exp(np.log(0.05) + u[:2] * (np.log(2.0) - np.log(0.05)))
+        s2 = np.exp(np.log(1e-4) + u[2:] * (np.log(1.0) - np.log(1e-4)))
+        ctxs.append(H.Hodlr(x, "se", [e[0], 1.0], s2[0], 128, 1e-10,
+                            stream=torch.cuda.Stream().cuda_stream))
+        sets.append((e, s2))
+        ys.append(torch.from_numpy(y).cuda())
+        raw.append((x, y))
+    torch.cuda.synchronize()
+    got_p, st_p = RM.instances_with_predictor(ctxs, net, sets, ys, origin.cuda_stream, margin=1)
+    got_b, st_b = RM.instances_with_probe(ctxs, sets, ys, origin.cuda_stream, margin=0)
+    assert st_p["fallbacks"] == 0
+    for (x, y), (e, s2), gp, gb in zip(raw, sets, got_p, got_b):
+        for b in range(2):
+            r = H.Hodlr(x, "se", [e[b], 1.0], s2[b], 128, 1e-10).loglik(y)
+            assert abs(gp[b] - r) <= 1e-12 * abs(r)
+            assert abs(gb[b] - r) <= 1e-12 * abs(r)
