@@ -913,6 +913,34 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def profile_batched():
+    """One batched call for launch-list captures: 4 presized lanes of one n = 65536 point set
+    (Matern-5/2, leaf 128, eps 1e-12, mixed form), 16 settings, so 4 rounds."""
+    import torch
+
+    from paper_1403_6015_gb300 import hodlr as H
+    from paper_1403_6015_gb300 import inputs as I
+    n, nset, L = 65536, 16, 4
+    x, y = I.workload_1d(n, 1003)
+    ell, s2 = sweep_settings(nset, 2004)
+    ctxs = []
+    for s in [torch.cuda.Stream() for _ in range(L)]:
+        h = H.Hodlr(x, "matern52", [ell[0], 1.0], s2[0], 128, 1e-12, precision=1, stream=s.cuda_stream)
+        h.presize(np.full(h.tree()[0], 4, dtype=np.int32))
+        ctxs.append(h)
+    theta = torch.from_numpy(np.stack([ell, np.ones(nset)], 1).copy()).cuda()
+    sig = torch.from_numpy(s2.copy()).cuda()
+    yd = torch.from_numpy(y).cuda()
+    out = torch.zeros(nset, dtype=torch.float64, device="cuda")
+    status = torch.zeros(nset, dtype=torch.int32, device="cuda")
+    origin = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    H.loglik_batched(ctxs, theta, sig, yd, out, status, stream=origin.cuda_stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_batched": {"lanes": L, "settings": nset,
+                                          "status_ok": bool((status.cpu().numpy() == 0).all())}}))
+
+
 def main():
     global N, COMPRESSION
     ap = argparse.ArgumentParser()
@@ -931,12 +959,17 @@ def main():
                     help="-1: both forms (default), 0: FP64 only, 1: mixed only")
     ap.add_argument("--compression", default="aca", choices=["aca", "chebyshev"],
                     help="compression of the timed evaluations (profiling captures)")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="run one small batched call (4 lanes, 16 Matern-5/2 settings, "
+                         "n=65536, mixed form) and exit: the case of the batched launch list")
     args = ap.parse_args()
     N = args.n
     COMPRESSION = args.compression
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile_batched:
+        profile_batched()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
