@@ -18,8 +18,8 @@
 //     per pair; the next pair's first pivot is computed by the thread that updates it);
 //     below it, the trailing matrix is updated in 2 x 2 register tiles (32-term dots);
 //   - the panel columns and right-hand sides are solved in chunks of 32 columns held in
-//     shared memory: 32 x 32 diagonal blocks by one warp per column, the rest as dense
-//     updates with one thread per output element;
+//     shared memory: 32 x 32 diagonal blocks by one warp per two columns (diag_fwd2,
+//     diag_bwd2), the rest as dense updates with one thread per output element;
 //   - the dot products (trailing update, solve updates, partial products) accumulate in
 //     compensated form (ffacc: the error of each sum kept apart and added once at the end).
 #include <cuda_runtime.h>
@@ -78,6 +78,45 @@ __device__ __forceinline__ int tri_row(int e) {
   while (i * (i + 1) / 2 > e) --i;
   while ((i + 1) * (i + 2) / 2 <= e) ++i;
   return i;
+}
+
+// Unit lower 32 x 32 diagonal-block solves for two columns per warp: half h (lane / 16) of
+// the warp holds column h of the pair, lane l = lane % 16 its rows l (top) and 16 + l
+// (bottom). Forward (L w = b): a 16-step chain over the top rows whose every step also
+// applies the new value to the 16 bottom rows (the dense 16 x 16 block, no idle lanes),
+// then a 16-step chain over the bottom rows. Backward (L^T x = v) mirrors it. Each row
+// receives its terms in the same order as a 32-step chain, so the results are the same,
+// with half the critical path and a quarter fewer double-float operations.
+template <class LF>
+__device__ __forceinline__ void diag_fwd2(ff& top, ff& bot, int lane, LF L) {
+  const int l = lane & 15, base = lane & 16;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    ff xk = shfl_ff(top, base + k);
+    if (l > k) top = ff_fms(top, L(l, k), xk);
+    bot = ff_fms(bot, L(16 + l, k), xk);
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    ff xk = shfl_ff(bot, base + k);
+    if (l > k) bot = ff_fms(bot, L(16 + l, 16 + k), xk);
+  }
+}
+
+template <class LF>
+__device__ __forceinline__ void diag_bwd2(ff& top, ff& bot, int lane, LF L) {
+  const int l = lane & 15, base = lane & 16;
+#pragma unroll
+  for (int k = 15; k >= 0; --k) {
+    ff xk = shfl_ff(bot, base + k);
+    if (l < k) bot = ff_fms(bot, L(16 + k, 16 + l), xk);
+    top = ff_fms(top, L(16 + k, l), xk);
+  }
+#pragma unroll
+  for (int k = 15; k >= 0; --k) {
+    ff xk = shfl_ff(top, base + k);
+    if (l < k) top = ff_fms(top, L(k, l), xk);
+  }
 }
 
 template <int kT, bool kFactor>
@@ -284,13 +323,14 @@ __device__ __forceinline__ void leaf_ff_body(const LeafFFArgs& a, int leaf) {
     // forward: L w = b
     for (int J = 0; J < NB; ++J) {
       int c0 = 32 * J;
-      for (int c = w; c < cw; c += NW) {
-        ff xv = B[(c0 + lane) * kBS + c];
-        for (int k = 0; k < 32; ++k) {
-          ff xk = shfl_ff(xv, k);
-          if (lane > k) xv = ff_fms(xv, A[tri(c0 + lane) + c0 + k], xk);
+      for (int c2 = w; 2 * c2 < cw; c2 += NW) {
+        const int c = 2 * c2 + (lane >> 4), l = lane & 15;  // c <= 31 < kBS: in bounds
+        ff top = B[(c0 + l) * kBS + c], bot = B[(c0 + 16 + l) * kBS + c];
+        diag_fwd2(top, bot, lane, [&](int i, int k) { return A[tri(c0 + i) + c0 + k]; });
+        if (c < cw) {
+          B[(c0 + l) * kBS + c] = top;
+          B[(c0 + 16 + l) * kBS + c] = bot;
         }
-        B[(c0 + lane) * kBS + c] = xv;
       }
       __syncthreads();
       int r0 = c0 + 32;
@@ -315,13 +355,14 @@ __device__ __forceinline__ void leaf_ff_body(const LeafFFArgs& a, int leaf) {
     // backward: L^T x = v
     for (int J = NB - 1; J >= 0; --J) {
       int c0 = 32 * J;
-      for (int c = w; c < cw; c += NW) {
-        ff xv = B[(c0 + lane) * kBS + c];
-        for (int k = 31; k >= 0; --k) {
-          ff xk = shfl_ff(xv, k);
-          if (lane < k) xv = ff_fms(xv, A[tri(c0 + k) + c0 + lane], xk);
+      for (int c2 = w; 2 * c2 < cw; c2 += NW) {
+        const int c = 2 * c2 + (lane >> 4), l = lane & 15;
+        ff top = B[(c0 + l) * kBS + c], bot = B[(c0 + 16 + l) * kBS + c];
+        diag_bwd2(top, bot, lane, [&](int i, int k) { return A[tri(c0 + i) + c0 + k]; });
+        if (c < cw) {
+          B[(c0 + l) * kBS + c] = top;
+          B[(c0 + 16 + l) * kBS + c] = bot;
         }
-        B[(c0 + lane) * kBS + c] = xv;
       }
       __syncthreads();
       for (int e = tid; e < c0 * cw; e += kT) {
@@ -738,13 +779,14 @@ __global__ void __launch_bounds__(512, 2) k_leaf_tc(LeafFFArgs a) {
         LJJ[i * kBS + k] = (k < i && c0 + i < p) ? Lst[(c0 + i) * kMaxLeaf + c0 + k] : zero;
       }
       __syncthreads();
-      for (int c = w; c < cw; c += NW) {
-        ff xv = X[(c0 + lane) * kBS + c];
-        for (int k = 0; k < 32; ++k) {
-          ff xk = shfl_ff(xv, k);
-          if (lane > k) xv = ff_fms(xv, LJJ[lane * kBS + k], xk);
+      for (int c2 = w; 2 * c2 < cw; c2 += NW) {
+        const int c = 2 * c2 + (lane >> 4), l = lane & 15;
+        ff top = X[(c0 + l) * kBS + c], bot = X[(c0 + 16 + l) * kBS + c];
+        diag_fwd2(top, bot, lane, [&](int i, int k) { return LJJ[i * kBS + k]; });
+        if (c < cw) {
+          X[(c0 + l) * kBS + c] = top;
+          X[(c0 + 16 + l) * kBS + c] = bot;
         }
-        X[(c0 + lane) * kBS + c] = xv;
       }
       __syncthreads();
       if (m > 0) {
@@ -800,13 +842,14 @@ __global__ void __launch_bounds__(512, 2) k_leaf_tc(LeafFFArgs a) {
         LJJ[i * kBS + k] = (k < i && c0 + i < p) ? Lst[(c0 + i) * kMaxLeaf + c0 + k] : zero;
       }
       __syncthreads();
-      for (int c = w; c < cw; c += NW) {
-        ff xv = X[(c0 + lane) * kBS + c];
-        for (int k = 31; k >= 0; --k) {
-          ff xk = shfl_ff(xv, k);
-          if (lane < k) xv = ff_fms(xv, LJJ[k * kBS + lane], xk);
+      for (int c2 = w; 2 * c2 < cw; c2 += NW) {
+        const int c = 2 * c2 + (lane >> 4), l = lane & 15;
+        ff top = X[(c0 + l) * kBS + c], bot = X[(c0 + 16 + l) * kBS + c];
+        diag_bwd2(top, bot, lane, [&](int i, int k) { return LJJ[i * kBS + k]; });
+        if (c < cw) {
+          X[(c0 + l) * kBS + c] = top;
+          X[(c0 + 16 + l) * kBS + c] = bot;
         }
-        X[(c0 + lane) * kBS + c] = xv;
       }
       __syncthreads();
       if (c0 > 0) {
