@@ -12,7 +12,8 @@
 //                swaps and the signs of D_ii;
 //   solve mode:  load the stored factor.
 // Then every panel column (the ancestors' U/V rows in factor mode, and the right-hand sides)
-// is solved by one warp (lanes own rows lane + 32 m, two columns at a time; unit triangular
+// is solved by one warp, two columns at a time (L D L^T: one column per 16-lane half, lanes
+// own rows l + 16 m; LU: both columns in all lanes, rows lane + 32 m; unit triangular
 // factors make every step one shuffle and FMAs), and the warp also forms the
 // level-(kappa-1) partial products Phi_{kappa-1}^T x of the leaf's rows.
 #include <cuda_runtime.h>
@@ -51,6 +52,14 @@ struct LeafArgs {
   int32_t* flags;
   int64_t n;
 };
+
+// Row of the lower-triangle element with linear index e (row-major, diagonal included).
+__device__ __forceinline__ int tri_row(int e) {
+  int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (i * (i + 1) / 2 > e) --i;
+  while ((i + 1) * (i + 2) / 2 <= e) ++i;
+  return i;
+}
 
 __device__ __forceinline__ double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -110,6 +119,50 @@ __device__ __forceinline__ void warp_ldl_solve(const double* __restrict__ A,
 #pragma unroll
           for (int c = 0; c < NC; ++c) x[c][m] -= lki * xk[c];
         }
+      }
+    }
+  }
+}
+
+// The same solve with L^T (L D L^T factor) for two columns per warp, one per 16-lane half:
+// lane l = lane % 16 of half h holds rows 16 j + l (j = 0..7) of column h in x[j]. Every
+// 16-row diagonal chunk leaves at most 15 of a half's lanes idle per step (instead of 31
+// of 32), and one shuffle serves one column instead of two.
+__device__ __forceinline__ void half_ldl_solve(const double* __restrict__ A,
+                                               const double* __restrict__ dinv, int p, int lane,
+                                               double (&x)[8]) {
+  const int l = lane & 15, base = lane & 16;
+  // forward: L w = b
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    for (int kk = 0; kk < 16; ++kk) {
+      int k = s * 16 + kk;
+      if (k >= p) break;
+      double wk = __shfl_sync(0xffffffffu, x[s], base + kk);
+#pragma unroll
+      for (int m = s; m < 8; ++m) {
+        int i = m * 16 + l;
+        if (i > k && i < p) x[m] -= A[i * kLD + k] * wk;
+      }
+    }
+  }
+  // v = D^-1 w
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    int i = m * 16 + l;
+    x[m] *= i < p ? dinv[i] : 0.0;
+  }
+  // backward: L^T x = v
+#pragma unroll
+  for (int s = 7; s >= 0; --s) {
+    for (int kk = 15; kk >= 0; --kk) {
+      int k = s * 16 + kk;
+      if (k >= p) continue;
+      double xk = __shfl_sync(0xffffffffu, x[s], base + kk);
+#pragma unroll
+      for (int m = 0; m <= s; ++m) {
+        int i = m * 16 + l;
+        if (i < k) x[m] -= A[k * kLD + i] * xk;
       }
     }
   }
@@ -313,14 +366,16 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, int leaf) {
       }
       __syncthreads();
       if (two) {
-        for (int j = k + 2 + w; j < p; j += kLeafThreads / 32) {
-          double t0 = T0[j], t1 = T1[j];
-          for (int i = j + lane; i < p; i += 32) {
-            double v = A[i * kLD + j];
-            v -= A[i * kLD + k] * t0;
-            v -= A[i * kLD + k + 1] * t1;
-            A[i * kLD + j] = v;
-          }
+        // the trailing lower triangle (rows and columns >= k + 2) flattened over all
+        // threads, element e at row tri_row(e): no idle lanes but in the last pass
+        const int m = p - k - 2;
+        for (int e = tid; e < m * (m + 1) / 2; e += kLeafThreads) {
+          int ii = tri_row(e), jj = e - ii * (ii + 1) / 2;
+          int i = k + 2 + ii, j = k + 2 + jj;
+          double v = A[i * kLD + j];
+          v -= A[i * kLD + k] * T0[j];
+          v -= A[i * kLD + k + 1] * T1[j];
+          A[i * kLD + j] = v;
         }
       }
       __syncthreads();
@@ -358,6 +413,46 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, int leaf) {
   int ncol = a.cP + a.nrhs;
   int wtot = ncol;  // partial row width
   constexpr int NC = 2;
+  if (!a.lu) {
+    // L D L^T: two columns per warp in the half-warp layout (half_ldl_solve)
+    const int l = lane & 15;
+    for (int c0 = w * 2; c0 < ncol; c0 += 2 * (kLeafThreads / 32)) {
+      const int c = c0 + (lane >> 4);
+      const bool valid = c < ncol;
+      const int cc = valid ? c : c0;  // a missing second column repeats the first
+      double* col = cc < a.cP ? a.pan + (int64_t)cc * a.n + b : a.Y + (int64_t)(cc - a.cP) * a.n + b;
+      const double* src = cc < a.cP ? a.phi + (int64_t)cc * a.n + b : col;
+      double x[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        int i = m * 16 + l;
+        x[m] = i < p ? src[i] : 0.0;
+      }
+      half_ldl_solve(A, dinv, p, lane, x);
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          int i = m * 16 + l;
+          if (i < p) col[i] = x[m];
+        }
+      }
+      if (a.kappa > 0) {
+        double* out = a.part + (int64_t)leaf * a.part_stride;
+        for (int r = 0; r < a.rl; ++r) {
+          const double* ph = a.phi + (int64_t)(a.coff + r) * a.n + b;
+          double sum = 0.0;
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            int i = m * 16 + l;
+            if (i < p) sum += ph[i] * x[m];
+          }
+          for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+          if (l == 0 && valid) out[r * wtot + c] = sum;
+        }
+      }
+    }
+    return;
+  }
   for (int c0 = w * NC; c0 < ncol; c0 += NC * (kLeafThreads / 32)) {
     double* col[NC];
     double x[NC][4];
@@ -373,10 +468,7 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, int leaf) {
         x[c][m] = i < p ? src[a.lu ? perm[i] : i] : 0.0;  // LU: rows in pivot order
       }
     }
-    if (a.lu)
-      warp_ldl_solve<NC, true>(A, dinv, p, lane, x);
-    else
-      warp_ldl_solve<NC, false>(A, dinv, p, lane, x);
+    warp_ldl_solve<NC, true>(A, dinv, p, lane, x);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       if (c0 + c >= ncol) break;
