@@ -43,7 +43,7 @@ FP64_PEAK = 152 * 2 * 2 * 2.07e9  # SMs x FP64 FMA/clk/SM x 2 flop x max SM cloc
 # DRAM bytes (read + write) of one launch of each form's leaf kernel at n = 2^20 (the
 # bench's own launch: 8192 leaves, 26 panel columns + 1 right-hand side), measured by ncu
 # (profiles/leaf_kernel_dram_n2p20.md); None when the kernel has changed since.
-LEAF_TRAFFIC_BYTES = {0: 259804160 + 723923712, 1: 258695424 + 735551232}
+LEAF_TRAFFIC_BYTES = {0: 259840768 + 723815680, 1: 258910976 + 735765504}
 
 
 def config():
