@@ -296,19 +296,24 @@ hodlr_status hodlr_counters(hodlr_ctx* ctx, int64_t* out2);
  *                 pipe; 1 = the trailing updates of the leaf factorization and the
  *                 off-diagonal block updates of its solves as exact bf16-slice products
  *                 on the tensor cores (512 threads, two leaves per SM; leaf_threads is
- *                 then ignored). Must be 0 in the FP64 form. */
+ *                 then ignored). Must be 0 in the FP64 form.
+ *   sweep_tile    tile shape of the one-launch-per-level sweep (sweep_mode 0): leaves and
+ *                 threads per block, 0: 4 x 256, 1: 2 x 128, 2: 8 x 256, 3: 8 x 512,
+ *                 4: 2 x 64, 5: 1 x 64, 6: 1 x 128. */
 typedef struct {
   int leaf_threads;
   int sweep_mode;
   int leaf_kernel;
+  int sweep_tile;
 } hodlr_tuning;
 
 /* Read or set the launch configuration. Errors: EINVAL (a value outside the lists). */
 hodlr_status hodlr_get_tuning(hodlr_ctx* ctx, hodlr_tuning* out);
 hodlr_status hodlr_set_tuning(hodlr_ctx* ctx, const hodlr_tuning* t);
 
-/* Autotuner: time every candidate configuration (leaf CTA sizes x sweep modes, and in the
- * mixed form the tensor-core leaf kernel x sweep modes) on this
+/* Autotuner: time every candidate configuration (leaf CTA sizes and, in the mixed form,
+ * the tensor-core leaf kernel, each with the segmented sweep and with every tile shape of
+ * the one-launch-per-level sweep) on this
  * context's own problem (one fused factorization with the right-hand side y, n doubles,
  * host or device), each reps times after one untimed run, with CUDA events on
  * opts.stream; keep the fastest (lowest median) and write it to *best (may be NULL) and

@@ -1174,6 +1174,7 @@ hodlr_status hodlr_matvec(hodlr_ctx* ctx, const double* x, double* y) {
 static bool valid_tuning(const Ctx* c, const hodlr_tuning* t) {
   if (!t || (t->sweep_mode != 0 && t->sweep_mode != 1)) return false;
   if (t->leaf_kernel != 0 && t->leaf_kernel != 1) return false;
+  if (t->sweep_tile < 0 || t->sweep_tile > 6) return false;
   if (c->precision == 1) return t->leaf_threads == 512 || t->leaf_threads == 1024;
   return t->leaf_kernel == 0 &&
          (t->leaf_threads == 256 || t->leaf_threads == 512 || t->leaf_threads == 1024);
@@ -1185,6 +1186,7 @@ hodlr_status hodlr_get_tuning(hodlr_ctx* ctx, hodlr_tuning* out) {
   out->leaf_threads = c->precision == 1 ? c->leaf_threads : c->leaf_threads64;
   out->sweep_mode = c->no_fused ? 1 : 0;
   out->leaf_kernel = c->precision == 1 && c->leaf_tc ? 1 : 0;
+  out->sweep_tile = c->sweep_tile;
   return HODLR_OK;
 }
 
@@ -1197,6 +1199,7 @@ hodlr_status hodlr_set_tuning(hodlr_ctx* ctx, const hodlr_tuning* t) {
   else c->leaf_threads64 = t->leaf_threads;
   c->leaf_tc = c->precision == 1 && t->leaf_kernel == 1;
   c->no_fused = t->sweep_mode == 1;
+  c->sweep_tile = t->sweep_tile;
   c->graph_valid = false;  // captured graphs hold the old launch shapes
   return HODLR_OK;
 }
@@ -1225,9 +1228,13 @@ hodlr_status hodlr_autotune(hodlr_ctx* ctx, const double* y, int reps, hodlr_tun
     if (e0) cudaEventDestroy(e0);
     return fail(c, HODLR_ECUDA, "autotune: events");
   }
-  for (int mode = 0; mode < 2 && s == HODLR_OK; ++mode)
+  // sweep configurations: the segmented sweep, then the fused sweep's tile shapes
+  std::vector<std::pair<int, int>> sweeps = {{1, 0}, {0, 0}, {0, 1}, {0, 2}, {0, 3}, {0, 4},
+                                             {0, 5}, {0, 6}};
+  for (const auto& sw : sweeps)
     for (const auto& cand : cands) {
-      hodlr_tuning t{cand.first, mode, cand.second};
+      if (s != HODLR_OK) break;
+      hodlr_tuning t{cand.first, sw.first, cand.second, sw.second};
       hodlr_set_tuning(ctx, &t);
       std::vector<float> ms;
       for (int r = 0; r <= reps && s == HODLR_OK; ++r) {

@@ -181,6 +181,7 @@ struct Ctx {
   int64_t batch_first_cap = 0;     // ints of batch_first
   int leaf_threads64 = 512;       // CTA size of the FP64 leaf kernel (measured best)
   bool no_fused = false;          // force the segmented level sweep
+  int sweep_tile = 0;             // tile shape of the fused sweep (leaves, threads per block)
   cudaStream_t stream = nullptr;
   int device = 0;
   int sms = 152;

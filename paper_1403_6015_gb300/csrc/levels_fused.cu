@@ -17,8 +17,10 @@
 namespace hodlr {
 namespace {
 
-constexpr int kLT = 256;  // threads per block
-constexpr int kG = 4;     // leaves per block
+// Tile shapes of the fused sweep: leaves per block and threads per block.
+constexpr int kSweepTiles = 7;
+constexpr int kTileG[kSweepTiles] = {4, 2, 8, 8, 2, 1, 1};
+constexpr int kTileT[kSweepTiles] = {256, 128, 256, 512, 64, 64, 128};
 
 struct FusedArgs {
   const int32_t* nb;
@@ -221,8 +223,9 @@ __device__ __forceinline__ void leaf_column_ff(const FusedArgs& a, int leaf, int
   }
 }
 
-template <bool kFF>
-__global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
+// G leaves per block, T threads (the tile shape, chosen per problem by the autotuner).
+template <bool kFF, int G, int T>
+__global__ void __launch_bounds__(T) k_level(FusedArgs a) {
   extern __shared__ double M[];  // node step, (2 rl)^2
   __shared__ int piv[2 * kSmemRank];
   __shared__ double lds;
@@ -230,8 +233,8 @@ __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
   __shared__ int flag;
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   int nleaf = 1 << a.kappa;
-  int leaf_base = blockIdx.x * kG;
-  int nl = nleaf - leaf_base < kG ? nleaf - leaf_base : kG;
+  int leaf_base = blockIdx.x * G;
+  int nl = nleaf - leaf_base < G ? nleaf - leaf_base : G;
   int wz = a.cP + a.nrhs;
   int sh = a.kappa - a.u;  // leaves per level-u half-node = 2^(sh - 1); per node = 2^sh
   int zs = 2 * a.ru * wz;
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
   // faster than pairs there).
   const int npair = kFF ? 0 : (wz + 1) >> 1;
   const int ntask = kFF ? wz : npair;
-  for (int t = w; t < nl * ntask; t += kLT / 32) {
+  for (int t = w; t < nl * ntask; t += T / 32) {
     int g = t / ntask, k = t - g * ntask;
     int leaf = leaf_base + g;
     int id = a.leaf0 + leaf;
@@ -260,17 +263,17 @@ __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
   // Where a half-node spans several blocks, each block first sums its own leaves'
   // partials (fixed order) into its first leaf's slot, so the last block of the half sums
   // one value per block instead of one per leaf.
-  const bool pre = hl >= 2 * kG;  // then this block's kG leaves lie inside one half-node
+  const bool pre = hl >= 2 * G;  // then this block's G leaves lie inside one half-node
   __syncthreads();
   if (pre) {
     double* p0 = a.part + (int64_t)leaf_base * a.part_stride;
-    for (int e = tid; e < E; e += kLT) {
+    for (int e = tid; e < E; e += T) {
       double s = p0[e];
       for (int t = 1; t < nl; ++t) s += p0[(int64_t)t * a.part_stride + e];
       p0[e] = s;
     }
   }
-  const int step = pre ? kG : 1;   // leaf stride between the slots to sum
+  const int step = pre ? G : 1;   // leaf stride between the slots to sum
   const int nsl = hl / step;       // slots per half-node
   __threadfence();
   __syncthreads();
@@ -291,14 +294,14 @@ __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
     const int64_t sst = (int64_t)step * a.part_stride;
     if (nsl >= 32) {
       // one warp per entry: lanes stride over the half's slots, then a fixed xor tree
-      for (int e = w; e < E; e += kLT / 32) {
+      for (int e = w; e < E; e += T / 32) {
         double s = 0.0;
         for (int t = lane; t < nsl; t += 32) s += __ldcg(pbase + (int64_t)t * sst + e);
         s = wsum(s);
         if (lane == 0) hs[e] = s;
       }
     } else {
-      for (int e = tid; e < E; e += kLT) {
+      for (int e = tid; e < E; e += T) {
         double s = 0.0;
         for (int t = 0; t < nsl; ++t) s += __ldcg(pbase + (int64_t)t * sst + e);
         hs[e] = s;
@@ -318,6 +321,14 @@ __global__ void __launch_bounds__(kLT) k_level(FusedArgs a) {
     node_solve(a.na, node, a.factor != 0, M, piv, &lds, &sgn);
     if (tid == 0) a.cnt[(1 << a.u) + node] = 0;
   }
+}
+
+template <bool kFF, int G, int T>
+cudaError_t launch_level(const FusedArgs& fa, unsigned grid, size_t smem, cudaStream_t s) {
+  if (smem > kSmemOptIn)
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_level<kFF, G, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_level<kFF, G, T><<<grid, T, smem, s>>>(fa);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -379,15 +390,23 @@ cudaError_t launch_levels_fused(Ctx& c, int nrhs, bool factor_mode) {
     }
     if (wz == 0 && (l < 0 || fa.rl == 0)) continue;
     size_t smem = sizeof(double) * 4 * fa.rl * fa.rl;
-    unsigned grid = (unsigned)((nleaf + kG - 1) / kG);
-    if (c.precision == 1) {
-      if (smem > kSmemOptIn)
-        HODLR_CUDA_TRY(cudaFuncSetAttribute(k_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_level<true><<<grid, kLT, smem, c.stream>>>(fa);
-    } else {
-      if (smem > kSmemOptIn)
-        HODLR_CUDA_TRY(cudaFuncSetAttribute(k_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_level<false><<<grid, kLT, smem, c.stream>>>(fa);
+    const int tile = c.sweep_tile >= 0 && c.sweep_tile < kSweepTiles ? c.sweep_tile : 0;
+    unsigned grid = (unsigned)((nleaf + kTileG[tile] - 1) / kTileG[tile]);
+    switch (tile * 2 + (c.precision == 1 ? 1 : 0)) {
+      case 0: HODLR_CUDA_TRY((launch_level<false, 4, 256>(fa, grid, smem, c.stream))); break;
+      case 1: HODLR_CUDA_TRY((launch_level<true, 4, 256>(fa, grid, smem, c.stream))); break;
+      case 2: HODLR_CUDA_TRY((launch_level<false, 2, 128>(fa, grid, smem, c.stream))); break;
+      case 3: HODLR_CUDA_TRY((launch_level<true, 2, 128>(fa, grid, smem, c.stream))); break;
+      case 4: HODLR_CUDA_TRY((launch_level<false, 8, 256>(fa, grid, smem, c.stream))); break;
+      case 5: HODLR_CUDA_TRY((launch_level<true, 8, 256>(fa, grid, smem, c.stream))); break;
+      case 6: HODLR_CUDA_TRY((launch_level<false, 8, 512>(fa, grid, smem, c.stream))); break;
+      case 7: HODLR_CUDA_TRY((launch_level<true, 8, 512>(fa, grid, smem, c.stream))); break;
+      case 8: HODLR_CUDA_TRY((launch_level<false, 2, 64>(fa, grid, smem, c.stream))); break;
+      case 9: HODLR_CUDA_TRY((launch_level<true, 2, 64>(fa, grid, smem, c.stream))); break;
+      case 10: HODLR_CUDA_TRY((launch_level<false, 1, 64>(fa, grid, smem, c.stream))); break;
+      case 11: HODLR_CUDA_TRY((launch_level<true, 1, 64>(fa, grid, smem, c.stream))); break;
+      case 12: HODLR_CUDA_TRY((launch_level<false, 1, 128>(fa, grid, smem, c.stream))); break;
+      default: HODLR_CUDA_TRY((launch_level<true, 1, 128>(fa, grid, smem, c.stream)));
     }
     ++c.launches;
     HODLR_CUDA_TRY(cudaGetLastError());

@@ -31,7 +31,7 @@ class hodlr_batch_lane(ctypes.Structure):
 
 class hodlr_tuning(ctypes.Structure):
     _fields_ = [("leaf_threads", ctypes.c_int), ("sweep_mode", ctypes.c_int),
-                ("leaf_kernel", ctypes.c_int)]
+                ("leaf_kernel", ctypes.c_int), ("sweep_tile", ctypes.c_int)]
 
 
 class hodlr_opts(ctypes.Structure):
@@ -550,12 +550,16 @@ class Hodlr:
         t = hodlr_tuning()
         self._check(hodlr_get_tuning(self._ctx, t), "get_tuning")
         return {"leaf_threads": t.leaf_threads, "sweep_mode": t.sweep_mode,
-                "leaf_kernel": t.leaf_kernel}
+                "leaf_kernel": t.leaf_kernel, "sweep_tile": t.sweep_tile}
 
-    def set_tuning(self, leaf_threads: int, sweep_mode: int = 0, leaf_kernel: int | None = None):
+    def set_tuning(self, leaf_threads: int, sweep_mode: int = 0, leaf_kernel: int | None = None,
+                   sweep_tile: int | None = None):
+        cur = self.tuning()
         if leaf_kernel is None:
-            leaf_kernel = self.tuning()["leaf_kernel"]
-        t = hodlr_tuning(leaf_threads, sweep_mode, leaf_kernel)
+            leaf_kernel = cur["leaf_kernel"]
+        if sweep_tile is None:
+            sweep_tile = cur["sweep_tile"]
+        t = hodlr_tuning(leaf_threads, sweep_mode, leaf_kernel, sweep_tile)
         self._check(hodlr_set_tuning(self._ctx, t), "set_tuning")
 
     def autotune(self, y, reps: int = 3, cache: str | None = None) -> dict:
@@ -578,14 +582,14 @@ class Hodlr:
                 table = {}
             if key in table:
                 self.set_tuning(table[key]["leaf_threads"], table[key]["sweep_mode"],
-                                table[key].get("leaf_kernel", 0))
+                                table[key].get("leaf_kernel", 0), table[key].get("sweep_tile", 0))
                 return dict(table[key], cached=True)
         yy = y.contiguous() if _is_torch(y) else _f64_host(y).reshape(-1)
         best = hodlr_tuning()
         ms = ctypes.c_float()
         self._check(hodlr_autotune(self._ctx, _addr(yy), reps, best, ms), "autotune")
         res = {"leaf_threads": best.leaf_threads, "sweep_mode": best.sweep_mode,
-               "leaf_kernel": best.leaf_kernel, "ms": ms.value}
+               "leaf_kernel": best.leaf_kernel, "sweep_tile": best.sweep_tile, "ms": ms.value}
         if key is not None:
             table[key] = res
             with open(cache, "w") as f:
