@@ -196,3 +196,39 @@ def test_batched_rejects_bad_lanes(H):
     assert "differ from the caller" in H.hodlr_last_error(h._ctx)
     assert H.hodlr_loglik_batched([lane, lane], origin.cuda_stream) == H.HODLR_EINVAL
     assert "two lanes" in H.hodlr_last_error(h._ctx)
+
+
+def test_batched_lanes_of_both_forms_in_one_call(H):
+    """One batched call whose lanes mix the FP64 and the mixed form (two persistent leaf
+    launches per round, one per form) and uneven sizes, including a problem that is a
+    single leaf: every result equals the adaptive evaluation of its own form."""
+    import torch
+    origin = torch.cuda.Stream()
+    specs = [(120, 0), (5000, 1), (20000, 0), (33000, 1), (9000, 1), (70000, 0)]
+    nset = 3
+    lanes, keep = [], []
+    for i, (n, prec) in enumerate(specs):
+        x, y = I.workload_1d(n, 1300 + i)
+        ell, s2 = settings(nset, 500 + i)
+        h = H.Hodlr(x, "matern32", [ell[0], 1.0], s2[0], 128, 1e-12, precision=prec,
+                    stream=torch.cuda.Stream().cuda_stream)
+        h.presize(np.full(max(h.tree()[0], 1), 3, dtype=np.int32)[:h.tree()[0]])
+        theta = torch.from_numpy(np.stack([ell, np.ones(nset)], 1).copy()).cuda()
+        sig = torch.from_numpy(s2.copy()).cuda()
+        yd = torch.from_numpy(y).cuda()
+        out = torch.zeros(nset, dtype=torch.float64, device="cuda")
+        st = torch.full((nset,), -1, dtype=torch.int32, device="cuda")
+        lanes.append(H.hodlr_batch_lane(h._ctx, theta.data_ptr(), sig.data_ptr(), yd.data_ptr(),
+                                        out.data_ptr(), st.data_ptr(), 0, 1, nset))
+        keep.append((h, x, y, ell, s2, prec, theta, sig, yd, out, st))
+    torch.cuda.synchronize()
+    assert H.hodlr_loglik_batched(lanes, origin.cuda_stream) == H.HODLR_OK
+    torch.cuda.synchronize()
+    for h, x, y, ell, s2, prec, theta, sig, yd, out, st in keep:
+        assert (st.cpu().numpy() == 0).all()
+        got = out.cpu().numpy()
+        for b in range(nset):
+            r = H.Hodlr(x, "matern32", [ell[b], 1.0], s2[b], 128, 1e-12, precision=prec).loglik(y)
+            assert abs(got[b] - r) <= 1e-12 * abs(r), (len(y), prec, b, got[b], r)
+            k = kalman_loglik(x, y, 3, ell[b], s2[b])
+            assert abs(got[b] - k) <= 1e-9 * abs(k), (len(y), prec, b, got[b], k)
