@@ -69,11 +69,15 @@ typedef struct {
                        /*    pipe (~2^-48 unit roundoff), everything else FP64; it keeps  */
                        /*    per-level relative coordinates, kappa x d x n x 8 bytes     */
   int rank_mode;       /* 0: adaptive ACA ranks                                            */
-  int max_rank;        /* cap on the ACA rank of one off-diagonal block (1..1024), default */
+  int max_rank;        /* cap on the ACA rank of one off-diagonal block (1..8192), default */
                        /*    64. Levels whose rank exceeds 64 factor their node matrices  */
-                       /*    in global memory and use the unfused level sweep; memory     */
-                       /*    grows with max_rank (ACA columns n x min(max_rank, m/2) per  */
-                       /*    level, leaf partials 2^kappa x r x (R + max_nrhs))           */
+                       /*    in global memory and use the unfused level sweep; from rank  */
+                       /*    128 the node step is a blocked LU over many CTAs (a          */
+                       /*    cooperative launch per panel) and the sweep a set of batched */
+                       /*    FP64 products. Memory grows with max_rank (ACA columns        */
+                       /*    n x min(max_rank, m/2) per level) and with the ranks reached  */
+                       /*    (node matrices 2^j (2 r_j)^2 per level, half-node sums        */
+                       /*    2^(j+1) r_j (R + max_nrhs), R the sum of the level ranks)      */
   int max_nrhs;        /* right-hand sides carried through a fused factor, default 16     */
   double refine_tol;   /* iterative refinement (not in the paper): stop when              */
                        /*    ||y - C~ x||_2 <= refine_tol ||y||_2, C~ the FP64 HODLR       */

@@ -84,6 +84,7 @@ void free_all(Ctx* c) {
   dfree(c->st_delta); dfree(c->st_s2); dfree(c->aca_part); dfree(c->active);
   dfree(c->Y); dfree(c->ysort); dfree(c->leafL); dfree(c->leaf_logdet); dfree(c->node_logdet); dfree(c->leaf_perm);
   dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->ry); dfree(c->rw); dfree(c->exp_tab); dfree(c->xrel); dfree(c->Mlu); dfree(c->Mpiv);
+  dfree(c->big_i32); dfree(c->big_slots); dfree(c->big_perm);
   dfree(c->hyp);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
@@ -199,9 +200,17 @@ hodlr_status size_buffers(Ctx* c) {
   for (int j = 0; j < K; ++j) c->h_coff[j + 1] = c->h_coff[j] + c->h_rl[j];
   c->R = c->h_coff[K];
   int64_t nleaf = (int64_t)1 << K;
-  int rmax_level = 0;
-  for (int j = 0; j < K; ++j) rmax_level = std::max(rmax_level, c->h_rl[j]);
-  int64_t pstride = std::max<int64_t>(1, (int64_t)rmax_level * (c->R + c->max_nrhs));
+  // per-leaf partials of level j (r_j x (c_j + r_j + max_nrhs) each) for the levels whose
+  // half sums are segmented sums: the finest, and those below a sweep step not in product
+  // form; the others get their half sums directly (2^(j+1) r_j w_j values)
+  int64_t pstride = 1, direct_el = 0;
+  bool big = false;
+  for (int j = 0; j < K; ++j) {
+    const int64_t rw = (int64_t)c->h_rl[j] * (c->h_coff[j] + c->h_rl[j] + c->max_nrhs);
+    if (j + 1 < K && hodlr::gemm_step(c->h_rl, j + 1)) direct_el = std::max(direct_el, rw << (j + 1));
+    else pstride = std::max(pstride, rw);
+    big |= c->h_rl[j] >= hodlr::kBlockRank;
+  }
   pstride = std::max<int64_t>(pstride, c->R);  // the matvec stores R partials per leaf
   int64_t zel = 1, hel = 1, mlu = 0, piv = 0;
   c->h_mlu_off.assign(K, 0);
@@ -217,6 +226,7 @@ hodlr_status size_buffers(Ctx* c) {
     hel += ((int64_t)2 << j) * r;
   }
   hel = std::max<int64_t>(hel, (nleaf + 1) * pstride);
+  hel = std::max<int64_t>(hel, direct_el);
   // the fused sweep's last block of a level-j half sums 2^(K-j-1) partials of r_j w_j values
   c->fused_work = 0;
   for (int j = 0; j < K; ++j)
@@ -239,6 +249,23 @@ hodlr_status size_buffers(Ctx* c) {
     c->part_stride = pstride;
     c->z_elems = zel;
     c->half_elems = hel;
+  }
+  if (big) {
+    // blocked node steps: per node sign and barrier counter, published panel candidates,
+    // the substitution's row orders (2 r_j per node of the largest level)
+    TRY_CUDA(c, hodlr::big_setup(*c), "large-rank setup");
+    int64_t perm_el = 1;
+    for (int j = 0; j < K; ++j) perm_el = std::max<int64_t>(perm_el, ((int64_t)2 << j) * c->h_rl[j]);
+    if (!c->big_i32) {
+      c->big_nodes = std::max<int64_t>(nleaf / 2, 1);
+      TRY_CUDA(c, dalloc(&c->big_i32, 2 * c->big_nodes), "alloc large-rank scratch");
+      TRY_CUDA(c, dalloc(&c->big_slots, hodlr::big_slot_elems(c->coop_cap)), "alloc large-rank scratch");
+    }
+    if (c->big_perm_cap < perm_el) {
+      dfree(c->big_perm);
+      TRY_CUDA(c, dalloc(&c->big_perm, perm_el), "alloc large-rank scratch");
+      c->big_perm_cap = perm_el;
+    }
   }
   if (c->mlu_cap < mlu || c->piv_cap < piv) {
     dfree(c->Mlu);
@@ -528,6 +555,10 @@ static hodlr_status check_flags(Ctx* c) {
   TRY_CUDA(c, cudaMemcpyAsync(&fl, c->dflags, 4, cudaMemcpyDeviceToHost, c->stream), "flags");
   TRY_CUDA(c, cudaStreamSynchronize(c->stream), "flags");
   ++c->syncs;
+  if (fl & hodlr::kFlagTimeout) {
+    c->factored = false;
+    return fail(c, HODLR_ETIMEOUT, "a bounded device wait (grid barrier of a large-rank LU panel) gave up");
+  }
   if (fl & hodlr::kFlagNotSpd) {
     c->factored = false;
     return fail(c, HODLR_ENOTSPD, c->indefinite ? "a leaf pivot or node determinant was zero"

@@ -20,10 +20,12 @@ constexpr int kMaxDim = 64;        // largest point dimension d
 // cudaFuncAttributeMaxDynamicSharedMemorySize: without it static plus dynamic must stay
 // within 48 KB, and the kernels' static arrays take up to about 1 KB.
 constexpr size_t kSmemOptIn = 40 * 1024;
-constexpr int kMaxRank = 1024;     // hard cap on a block's rank (opts.max_rank)
+constexpr int kMaxRank = 8192;     // hard cap on a block's rank (opts.max_rank)
 constexpr int kDefaultMaxRank = 64;  // default opts.max_rank
 constexpr int kSmemRank = 64;      // ranks up to this use the shared-memory node step
                                    // (2r x 2r in smem) and the fused level sweep
+constexpr int kBlockRank = 128;    // ranks from this up: blocked node step over many CTAs and
+                                   // the sweep in product form (levels_big.cu)
 constexpr int kAcaTile = 1024;     // columns (rows) of one ACA work item
 constexpr int kSmallNode = 256;    // nodes whose children both fit: one warp per node
 
@@ -139,6 +141,13 @@ __device__ __forceinline__ double dist(const Pts& p, int i, int j) {
   return sqrt(s);
 }
 
+// Sweep step of level u (update of level u, half-node sums of level u - 1) in product form:
+// when either level's rank is large. Level j's half sums then come straight from step j + 1,
+// without per-leaf partials.
+inline bool gemm_step(const std::vector<int>& rl, int u) {
+  return rl[u] >= kBlockRank || (u >= 1 && rl[u - 1] >= kBlockRank);
+}
+
 // Device error word bits (ctx->dflags).
 // kFlagNegDet: parity of the negative block determinants of an indefinite C (the sign of
 // det C), toggled by each one.
@@ -248,6 +257,14 @@ struct Ctx {
   double* Z = nullptr;            // two buffers of z_elems: Z of levels with even / odd index
   int64_t z_elems = 0;
   int32_t* cnt = nullptr;         // arrival counters of the fused level sweep
+  // large-rank levels (levels_big.cu): per node sign and barrier counter (big_nodes each),
+  // the panel kernel's published candidates, the substitution's row orders
+  int32_t* big_i32 = nullptr;
+  int64_t big_nodes = 0;
+  double* big_slots = nullptr;
+  int32_t* big_perm = nullptr;
+  int64_t big_perm_cap = 0;
+  int coop_cap = 0;               // co-resident CTAs of the cooperative panel launch
   int64_t fused_work = 0;         // largest per-block reduction of the fused sweep (values)
   int64_t half_elems = 0;
   double* scal = nullptr;         // [0] logdet, [1] quad, [2] loglik
@@ -319,6 +336,11 @@ cudaError_t launch_leaf_solve(Ctx& c, int nrhs);
 cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode);
 cudaError_t launch_level_first(Ctx& c, int nrhs, bool factor_mode);
 cudaError_t launch_levels_fused(Ctx& c, int nrhs, bool factor_mode);
+struct NodeArgs;
+cudaError_t big_setup(Ctx& c);
+int64_t big_slot_elems(int coop_cap);
+cudaError_t launch_node_blocked(Ctx& c, const NodeArgs& na, bool factor);
+cudaError_t launch_sweep_gemm(Ctx& c, int u, int nrhs, bool factor_mode);
 cudaError_t launch_logdet_sum(Ctx& c);
 cudaError_t launch_quad_loglik(Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double* xin_sorted, double* yout_sorted);

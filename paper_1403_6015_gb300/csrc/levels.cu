@@ -76,10 +76,11 @@ __global__ void __launch_bounds__(kNodeBigThreads) k_node_big(NodeArgs a, bool f
   node_solve_global(a, blockIdx.x, factor, wv, wi, &pv, &lds, &sgn);
 }
 
-// Node step of every node of level na.j: M in shared memory up to rank kSmemRank, else in
-// global memory.
+// Node step of every node of level na.j: M in shared memory up to rank kSmemRank, in
+// global memory with one CTA per node below kBlockRank, else blocked over many CTAs.
 cudaError_t launch_node(Ctx& c, const NodeArgs& na, bool factor_mode) {
   int r = na.r;
+  if (r >= kBlockRank) return launch_node_blocked(c, na, factor_mode);
   if (r <= kSmemRank) {
     size_t smem = sizeof(double) * 4 * r * r;
     if (smem > kSmemOptIn)
@@ -410,6 +411,8 @@ cudaError_t launch_sweep(const SweepArgs& sa, unsigned grid, size_t smem, cudaSt
 // Sweep of all internal levels after the leaf stage has written the level-(kappa-1)
 // partials. factor_mode: build and factor M per node (panel columns included); otherwise
 // reuse the stored LU factors and carry only the right-hand sides.
+// Levels whose sweep step is in product form (gemm_step) hand the next level its half sums
+// directly (stride r_j w_j); the others go through per-leaf partials and segmented sums.
 cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
   int K = c.kappa;
   int64_t nleaf = (int64_t)1 << K;
@@ -419,10 +422,12 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
     int cP = factor_mode ? cj + r : 0;  // panel columns in the level-j partials
     int w = cP + nrhs;
     int h = 1 << (K - j - 1);
-    HODLR_CUDA_TRY(segsum(c.part, c.part_stride, r * w, nleaf, h, c.part2, c.half, c.stream, &c.launches));
+    const bool direct = j + 1 < K && gemm_step(c.h_rl, j + 1);
+    if (!direct)
+      HODLR_CUDA_TRY(segsum(c.part, c.part_stride, r * w, nleaf, h, c.part2, c.half, c.stream, &c.launches));
     NodeArgs na;
     na.half = c.half;
-    na.stride = c.part_stride;
+    na.stride = direct ? (int64_t)r * w : c.part_stride;
     na.j = j;
     na.r = r;
     na.w = w;
@@ -466,6 +471,10 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
     sa.part_stride = c.part_stride;
     sa.n = c.n;
     if (sa.cP + nrhs == 0) continue;  // nothing left to update (root level, no right-hand side)
+    if (gemm_step(c.h_rl, j)) {
+      HODLR_CUDA_TRY(launch_sweep_gemm(c, j, nrhs, factor_mode));
+      continue;
+    }
     size_t smem = sizeof(double) * kMaxLeaf * (sa.ru + sa.rl);
     if (c.precision == 1)
       HODLR_CUDA_TRY(launch_sweep<ff>(sa, (unsigned)nleaf, smem, c.stream));

@@ -77,7 +77,7 @@ def test_build_rejects_bad_options():
         o.refine_tol = tol
         st, ctx = hodlr.hodlr_build(x, 64, 1, 0, [0.2, 1.0], 0.01, 16, 1e-12, o)
         assert st == hodlr.HODLR_EINVAL and not ctx
-    for mr in [0, 1025]:
+    for mr in [0, 8193]:
         o = hodlr.hodlr_default_opts()
         o.max_rank = mr
         st, ctx = hodlr.hodlr_build(x, 64, 1, 0, [0.2, 1.0], 0.01, 16, 1e-12, o)
