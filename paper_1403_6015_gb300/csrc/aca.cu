@@ -60,6 +60,8 @@ struct AcaArgs {
   int32_t* active;
   int nint;
   int pre[32];         // presized rank of each level (0: adaptive)
+  int wide0, wide1;    // item range of the wide nodes (rank cap above kWideRank)
+  const int32_t* wide_nodes;  // their ids
 };
 
 // Entry k(x_i, x_j) of an off-diagonal block: FP64, or (mixed form) double-float
@@ -781,11 +783,47 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_small(AcaArgs a, int it
   }
 }
 
-// D: one warp per node combines the tiles, updates the norm estimate and decides.
+// Norm update and stopping decision of node id after its step k (one thread): |S_k|^2 +=
+// 2 cross + |u|^2 |v|^2; stop when |u||v| <= eps |S_k| (the term dropped), when no unused
+// row is left, or at the rank cap; else the next pivot row is bi.
+__device__ void col_decide(const AcaArgs& a, int id, int k, int bi, double nu2, double nv2,
+                           double cross) {
+  double s2 = a.s2[id] + 2.0 * cross + nu2 * nv2;
+  a.s2[id] = s2;
+  if (sqrt(nu2 * nv2) <= a.eps * sqrt(s2)) {
+    a.done[id] = 1;
+    a.ok[id] = 1;
+    return;
+  }
+  int r = k + 1;
+  a.rank[id] = r;
+  if (bi < 0) {
+    a.done[id] = 1;
+    a.ok[id] = 1;
+    return;
+  }
+  a.row[id] = bi;
+  int rmax = rmax_of(a, id);
+  if (r >= rmax) {
+    int ml = a.ns[2 * id + 1], mr = a.ns[2 * id + 2];
+    a.done[id] = 1;
+    a.ok[id] = rmax == (ml < mr ? ml : mr);
+    return;
+  }
+  atomicAdd(a.active, 1);
+}
+
+__device__ __forceinline__ bool is_wide(const AcaArgs& a, int id) {
+  const int i0 = a.node_item0[id];
+  return i0 >= a.wide0 && i0 < a.wide1;
+}
+
+// D: one warp per node combines the tiles, updates the norm estimate and decides (wide
+// nodes: k_aca_pivot_col_wide).
 __global__ void k_aca_pivot_col(AcaArgs a) {
   int id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (id >= a.nint || a.done[id]) return;
+  if (id >= a.nint || is_wide(a, id) || a.done[id]) return;
   if (!a.phase[id]) {
     if (lane == 0) atomicAdd(a.active, 1);
     return;
@@ -815,30 +853,229 @@ __global__ void k_aca_pivot_col(AcaArgs a) {
     cross += du * dv;
   }
   cross = warp_sum(cross);
-  if (lane != 0) return;
-  double s2 = a.s2[id] + 2.0 * cross + nu2 * nv2;
-  a.s2[id] = s2;
-  if (sqrt(nu2 * nv2) <= a.eps * sqrt(s2)) {
-    a.done[id] = 1;
-    a.ok[id] = 1;
+  if (lane == 0) col_decide(a, id, k, bi, nu2, nv2, cross);
+}
+
+// ---- wide nodes: rank cap above kWideRank ----------------------------------------------
+// Work items of kWideTile rows, so that a block of a top-level node spreads over many CTAs.
+// The sum over the cross's earlier vectors is split over the warps (warp w takes l = w,
+// w + 8, ...; the eight partial sums are added in warp order); the dot products u_l.u and
+// v_l.v of a tile run with threads over l and the tile's rows in order. FP64 arithmetic in
+// both forms (the mixed form's double-float columns are converted on load and store).
+static_assert(kWideTile == 32, "one row of a wide item per lane");
+
+template <bool kFF>
+__device__ __forceinline__ double rld(const double* raw, int64_t i) {
+  return kFF ? ff_to_double(reinterpret_cast<const ff*>(raw)[i]) : raw[i];
+}
+
+// Stores v and returns the value stored (the mixed form rounds it to a double-float).
+template <bool kFF>
+__device__ __forceinline__ double rst(double* raw, int64_t i, double v) {
+  if (!kFF) {
+    raw[i] = v;
+    return v;
+  }
+  const ff f = ff_from_double(v);
+  reinterpret_cast<ff*>(raw)[i] = f;
+  return ff_to_double(f);
+}
+
+template <bool kFF, bool kGen>
+__device__ __forceinline__ double entry_wide(const AcaArgs& a, const Cov& cov, int id, int i,
+                                             int j, const ff* tab, const CovFF& cf) {
+  if (kFF) return ff_to_double(block_entry_ff<kGen>(a, level_of(id), i, j, tab, cf));
+  return block_entry<false, kGen>(a, cov, i, j, tab, cf);
+}
+
+// A for a wide item: residual row entries b = start + lane of the right child.
+template <bool kFF, bool kGen>
+__global__ void __launch_bounds__(kAcaThreads) k_aca_row_wide(AcaArgs a, int item0) {
+  constexpr int kW = kAcaThreads / 32;
+  const int item = item0 + blockIdx.x;
+  const int id = a.item_node[item];
+  if (a.done[id]) return;
+  __shared__ double uik[kRankChunk];
+  __shared__ double red[kW][kWideTile];
+  __shared__ ff tab[64];
+  const Cov cov = cov_from(a.kind, a.hyp);
+  CovFF cf{};
+  if (kFF) {
+    for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
+    cf = load_cov_ff(a.kind, a.hyp);
+  }
+  const int k = a.rank[id], i = a.row[id];
+  const int bl = a.nb[2 * id + 1], br = a.nb[2 * id + 2], mr = a.ns[2 * id + 2];
+  const int64_t n = a.pts.n;
+  double* raw = a.raw + a.raw_off[level_of(id)];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = a.item_start[item] + lane;
+  double acc = 0.0;
+  for (int l0 = 0; l0 < k; l0 += kRankChunk) {
+    const int l1 = min(k, l0 + kRankChunk);
+    __syncthreads();
+    for (int l = l0 + threadIdx.x; l < l1; l += kAcaThreads) uik[l - l0] = rld<kFF>(raw, l * n + bl + i);
+    __syncthreads();
+    if (b < mr)
+      for (int l = l0 + w; l < l1; l += kW) acc += uik[l - l0] * rld<kFF>(raw, l * n + br + b);
+  }
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w != 0) return;
+  double bv = 0.0;
+  int bi = -1;
+  if (b < mr) {
+    double s = 0.0;
+    for (int q = 0; q < kW; ++q) s += red[q][lane];
+    const double v = rst<kFF>(raw, (int64_t)k * n + br + b, entry_wide<kFF, kGen>(a, cov, id, bl + i, br + b, tab, cf) - s);
+    amax_merge(bv, bi, v, b);
+  }
+  warp_amax(bv, bi);
+  if (lane == 0) {
+    a.part[(int64_t)item * a.part_stride + 0] = bv;
+    a.part[(int64_t)item * a.part_stride + 1] = (double)bi;
+  }
+}
+
+// C for a wide item: rows t = start + lane of u (left child) and of v (right child), their
+// norms and unused-row argmax, then the tile's u_l.u and v_l.v for every l < k.
+template <bool kFF, bool kGen>
+__global__ void __launch_bounds__(kAcaThreads) k_aca_col_wide(AcaArgs a, int item0) {
+  constexpr int kW = kAcaThreads / 32;
+  const int item = item0 + blockIdx.x;
+  const int id = a.item_node[item];
+  if (a.done[id] || !a.phase[id]) return;
+  __shared__ double vjk[kRankChunk];
+  __shared__ int used_s[kUsedChunk];
+  __shared__ double red[kW][kWideTile];
+  __shared__ double us[kWideTile], vs[kWideTile];
+  __shared__ int isu_s[kWideTile];
+  __shared__ ff tab[64];
+  const Cov cov = cov_from(a.kind, a.hyp);
+  CovFF cf{};
+  if (kFF) {
+    for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
+    cf = load_cov_ff(a.kind, a.hyp);
+  }
+  const int k = a.rank[id], j = a.col[id];
+  const double delta = a.delta[id];
+  const int bl = a.nb[2 * id + 1], ml = a.ns[2 * id + 1];
+  const int br = a.nb[2 * id + 2], mr = a.ns[2 * id + 2];
+  const int nu = a.nused[id];
+  const int64_t n = a.pts.n;
+  double* raw = a.raw + a.raw_off[level_of(id)];
+  const int start = a.item_start[item];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = start + lane;
+  if (threadIdx.x < kWideTile) isu_s[threadIdx.x] = 0;
+  for (int s0 = 0; s0 < nu; s0 += kUsedChunk) {
+    const int s1 = min(nu - s0, kUsedChunk);
+    __syncthreads();
+    for (int q = threadIdx.x; q < s1; q += kAcaThreads) used_s[q] = a.used[(int64_t)id * a.used_stride + s0 + q];
+    __syncthreads();
+    bool f = false;
+    for (int q = w; q < s1; q += kW) f |= used_s[q] == t;
+    if (f) isu_s[lane] = 1;
+  }
+  double acc = 0.0;
+  for (int l0 = 0; l0 < k; l0 += kRankChunk) {
+    const int l1 = min(k, l0 + kRankChunk);
+    __syncthreads();
+    for (int l = l0 + threadIdx.x; l < l1; l += kAcaThreads) vjk[l - l0] = rld<kFF>(raw, l * n + br + j);
+    __syncthreads();
+    if (t < ml)
+      for (int l = l0 + w; l < l1; l += kW) acc += rld<kFF>(raw, l * n + bl + t) * vjk[l - l0];
+  }
+  red[w][lane] = acc;
+  __syncthreads();
+  double* out = a.part + (int64_t)item * a.part_stride;
+  if (w == 0) {
+    double u = 0.0, v = 0.0, bv = 0.0;
+    int bi = -1;
+    if (t < ml) {
+      double s = 0.0;
+      for (int q = 0; q < kW; ++q) s += red[q][lane];
+      u = rst<kFF>(raw, (int64_t)k * n + bl + t, entry_wide<kFF, kGen>(a, cov, id, bl + t, br + j, tab, cf) - s);
+      if (!isu_s[lane]) amax_merge(bv, bi, u, t);
+    }
+    if (t < mr) {
+      const int64_t e = (int64_t)k * n + br + t;
+      v = rst<kFF>(raw, e, rld<kFF>(raw, e) * (1.0 / delta));
+    }
+    us[lane] = u;
+    vs[lane] = v;
+    const double nu2 = warp_sum(u * u), nv2 = warp_sum(v * v);
+    warp_amax(bv, bi);
+    if (lane == 0) {
+      out[0] = bv;
+      out[1] = (double)bi;
+      out[2] = nu2;
+      out[3] = nv2;
+    }
+  }
+  __syncthreads();
+  const int tu = min(kWideTile, ml - start), tv = min(kWideTile, mr - start);
+  for (int l = threadIdx.x; l < k; l += kAcaThreads) {
+    double du = 0.0, dv = 0.0;
+    const int64_t col = (int64_t)l * n;
+    for (int q = 0; q < tu; ++q) du += rld<kFF>(raw, col + bl + start + q) * us[q];
+    for (int q = 0; q < tv; ++q) dv += rld<kFF>(raw, col + br + start + q) * vs[q];
+    out[4 + l] = du;
+    out[4 + a.max_rank + l] = dv;
+  }
+}
+
+// D for a wide node: one block; the argmax and norms as in k_aca_pivot_col, the sum over l
+// with threads over l (tiles in item order), then the warps' sums in order.
+__global__ void __launch_bounds__(256) k_aca_pivot_col_wide(AcaArgs a) {
+  const int id = a.wide_nodes[blockIdx.x];
+  if (a.done[id]) return;
+  if (!a.phase[id]) {
+    if (threadIdx.x == 0) atomicAdd(a.active, 1);
     return;
   }
-  int r = k + 1;
-  a.rank[id] = r;
-  if (bi < 0) {
-    a.done[id] = 1;
-    a.ok[id] = 1;
-    return;
+  __shared__ double red[8];
+  __shared__ double s_nu2, s_nv2;
+  __shared__ int s_bi;
+  const int k = a.rank[id];
+  const int i0 = a.node_item0[id], i1 = a.node_item1[id];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w == 0) {
+    double bv = 0.0, nu2 = 0.0, nv2 = 0.0;
+    int bi = -1;
+    for (int it = i0 + lane; it < i1; it += 32) {
+      const double* p = a.part + (int64_t)it * a.part_stride;
+      amax_merge(bv, bi, p[0], (int)p[1]);
+      nu2 += p[2];
+      nv2 += p[3];
+    }
+    warp_amax(bv, bi);
+    nu2 = warp_sum(nu2);
+    nv2 = warp_sum(nv2);
+    if (lane == 0) {
+      s_nu2 = nu2;
+      s_nv2 = nv2;
+      s_bi = bi;
+    }
   }
-  a.row[id] = bi;
-  int rmax = rmax_of(a, id);
-  if (r >= rmax) {
-    int ml = a.ns[2 * id + 1], mr = a.ns[2 * id + 2];
-    a.done[id] = 1;
-    a.ok[id] = rmax == (ml < mr ? ml : mr);
-    return;
+  double cross = 0.0;
+  for (int l = threadIdx.x; l < k; l += 256) {
+    double du = 0.0, dv = 0.0;
+    for (int it = i0; it < i1; ++it) {
+      const double* p = a.part + (int64_t)it * a.part_stride;
+      du += p[4 + l];
+      dv += p[4 + a.max_rank + l];
+    }
+    cross += du * dv;
   }
-  atomicAdd(a.active, 1);
+  cross = warp_sum(cross);
+  if (lane == 0) red[w] = cross;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double c = 0.0;
+    for (int q = 0; q < 8; ++q) c += red[q];
+    col_decide(a, id, k, s_bi, s_nu2, s_nv2, c);
+  }
 }
 
 // Presized mode: flag every block that did not converge within its level's rank.
@@ -934,10 +1171,14 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   a.xrel = reinterpret_cast<const ff*>(c.xrel);
   a.active = c.active;
   a.nint = nint;
+  a.wide0 = (int)c.n_big_items;
+  a.wide1 = (int)(c.n_big_items + c.n_wide_items);
+  a.wide_nodes = c.wide_nodes;
   k_aca_init<<<(nint + 255) / 256, 256, 0, c.stream>>>(a);
   ++c.launches;
   int wblocks = (nint * 32 + 255) / 256;
-  const int64_t nbig = c.n_big_items, nsmall = c.n_items - c.n_big_items;
+  const int64_t nbig = c.n_big_items, nwide = c.n_wide_items;
+  const int64_t nsmall = c.n_items - nbig - nwide, small0 = nbig + nwide;
   const unsigned sgrid = (unsigned)((nsmall + kAcaThreads / 32 - 1) / (kAcaThreads / 32));
   const size_t smem_row = 0, smem_col = 0;  // static, independent of the rank
   // adaptive: until no block is active (host check per step); presized: a fixed number of
@@ -951,8 +1192,12 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
       ACA_LAUNCH(k_aca_row, (unsigned)nbig, smem_row, a);
       ++c.launches;
     }
+    if (nwide > 0) {
+      ACA_LAUNCH(k_aca_row_wide, (unsigned)nwide, 0, a, (int)nbig);
+      ++c.launches;
+    }
     if (nsmall > 0) {
-      ACA_LAUNCH(k_aca_row_small, sgrid, 0, a, (int)nbig, (int)nsmall);
+      ACA_LAUNCH(k_aca_row_small, sgrid, 0, a, (int)small0, (int)nsmall);
       ++c.launches;
     }
     k_aca_pivot_row<<<wblocks, 256, 0, c.stream>>>(a);
@@ -960,11 +1205,19 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
       ACA_LAUNCH(k_aca_col, (unsigned)nbig, smem_col, a);
       ++c.launches;
     }
+    if (nwide > 0) {
+      ACA_LAUNCH(k_aca_col_wide, (unsigned)nwide, 0, a, (int)nbig);
+      ++c.launches;
+    }
     if (nsmall > 0) {
-      ACA_LAUNCH(k_aca_col_small, sgrid, 0, a, (int)nbig, (int)nsmall);
+      ACA_LAUNCH(k_aca_col_small, sgrid, 0, a, (int)small0, (int)nsmall);
       ++c.launches;
     }
     k_aca_pivot_col<<<wblocks, 256, 0, c.stream>>>(a);
+    if (c.n_wide_nodes > 0) {
+      k_aca_pivot_col_wide<<<(unsigned)c.n_wide_nodes, 256, 0, c.stream>>>(a);
+      ++c.launches;
+    }
     c.launches += 2;
     HODLR_CUDA_TRY(cudaGetLastError());
     *steps_out = s + 1;

@@ -77,7 +77,7 @@ void free_factor_buffers(Ctx* c) {
 void free_all(Ctx* c) {
   free_factor_buffers(c);
   dfree(c->nodes); dfree(c->xs); dfree(c->perm);
-  dfree(c->item_node); dfree(c->item_start); dfree(c->node_item0); dfree(c->node_item1); dfree(c->raw);
+  dfree(c->item_node); dfree(c->item_start); dfree(c->wide_nodes); dfree(c->node_item0); dfree(c->node_item1); dfree(c->raw);
   dfree(c->cheb_q); dfree(c->cheb_coef);
   dfree(c->st_rank); dfree(c->st_row); dfree(c->st_col); dfree(c->st_done); dfree(c->st_ok);
   dfree(c->st_zero); dfree(c->st_phase); dfree(c->st_nused); dfree(c->st_used);
@@ -130,18 +130,23 @@ hodlr_status setup_aca(Ctx* c) {
   if (nint == 0) return HODLR_OK;
   const int32_t* nb = c->h_nodes.data();
   const int32_t* ns = nb + ((int64_t)2 << K);
-  // work items: first the 1024-column tiles of the nodes with a child above kSmallNode
-  // points (one block each), then one item per small node (one warp each); node id owns
-  // items [i0[id], i1[id])
-  std::vector<int32_t> inode, istart, i0(nint + 1), i1(nint + 1, 0);
-  for (int pass = 0; pass < 2; ++pass) {
+  // work items: first the kAcaTile-row tiles of the nodes with a child above kSmallNode
+  // points (one block each), then the kWideTile-row tiles of the wide nodes (rank cap above
+  // kWideRank), then one item per small node (one warp each); node id owns items
+  // [i0[id], i1[id])
+  std::vector<int32_t> inode, istart, i0(nint + 1), i1(nint + 1, 0), wide;
+  for (int pass = 0; pass < 3; ++pass) {
     if (pass == 1) c->n_big_items = (int64_t)inode.size();
+    if (pass == 2) c->n_wide_items = (int64_t)inode.size() - c->n_big_items;
     for (int id = 0; id < nint; ++id) {
       int32_t m = std::max(ns[2 * id + 1], ns[2 * id + 2]);
       bool small = m <= hodlr::kSmallNode;
-      if (small != (pass == 1)) continue;
+      bool wd = !small && std::min(std::min(ns[2 * id + 1], ns[2 * id + 2]), c->max_rank) > hodlr::kWideRank;
+      if ((pass == 0 && (small || wd)) || (pass == 1 && !wd) || (pass == 2 && !small)) continue;
+      if (wd) wide.push_back(id);
+      const int tile = wd ? hodlr::kWideTile : hodlr::kAcaTile;
       i0[id] = (int32_t)inode.size();
-      for (int32_t s = 0; s < m || s == 0; s += hodlr::kAcaTile) {
+      for (int32_t s = 0; s < m || s == 0; s += tile) {
         inode.push_back(id);
         istart.push_back(s);
         if (small) break;
@@ -149,6 +154,7 @@ hodlr_status setup_aca(Ctx* c) {
       i1[id] = (int32_t)inode.size();
     }
   }
+  c->n_wide_nodes = (int)wide.size();
   i0[nint] = i1[nint] = (int32_t)inode.size();
   c->n_items = (int64_t)inode.size();
   c->h_raw_off.assign(K, 0);
@@ -179,6 +185,9 @@ hodlr_status setup_aca(Ctx* c) {
   TRY_CUDA(c, dalloc(&c->st_delta, nint), "alloc aca state");
   TRY_CUDA(c, dalloc(&c->st_s2, nint), "alloc aca state");
   TRY_CUDA(c, dalloc(&c->aca_part, c->n_items * (4 + 2 * c->max_rank)), "alloc aca partials");
+  TRY_CUDA(c, dalloc(&c->wide_nodes, (int64_t)wide.size()), "alloc items");
+  if (!wide.empty())
+    TRY_CUDA(c, cudaMemcpyAsync(c->wide_nodes, wide.data(), 4 * wide.size(), cudaMemcpyHostToDevice, c->stream), "upload");
   if (c->compression == 1) {
     TRY_CUDA(c, dalloc(&c->cheb_q, nint), "alloc chebyshev state");
     TRY_CUDA(c, dalloc(&c->cheb_coef, (int64_t)hodlr::cheb_coef_elems(nint)), "alloc chebyshev state");

@@ -28,6 +28,8 @@ constexpr int kBlockRank = 128;    // ranks from this up: blocked node step over
                                    // the sweep in product form (levels_big.cu)
 constexpr int kAcaTile = 1024;     // columns (rows) of one ACA work item
 constexpr int kSmallNode = 256;    // nodes whose children both fit: one warp per node
+constexpr int kWideRank = 256;     // nodes whose rank cap min(m_left, m_right, max_rank)
+constexpr int kWideTile = 32;      // exceeds this: ACA work items of 32 rows (one per lane)
 
 // ---------------------------------------------------------------------------------------
 // Covariance functions (Table 1 with length scale ell and amplitude a; Matern nu = 3/2 and
@@ -208,7 +210,10 @@ struct Ctx {
   int32_t* item_start = nullptr;  // first row/column of the item's tile
   int32_t* node_item0 = nullptr;  // first item of each internal node (nint + 1 entries)
   int32_t* node_item1 = nullptr;  // one past its last item
-  int64_t n_big_items = 0;        // items [0, n_big_items): tiles; the rest: small nodes
+  int64_t n_big_items = 0;        // items [0, n_big_items): tiles of kAcaTile rows; then
+  int64_t n_wide_items = 0;       // n_wide_items tiles of kWideTile rows; the rest: small nodes
+  int32_t* wide_nodes = nullptr;  // ids of the nodes with wide items
+  int n_wide_nodes = 0;
   std::vector<int64_t> h_raw_off; // offset (in doubles) of level j's raw panel
   std::vector<int> h_rcap;        // raw columns of level j
   double* raw = nullptr;

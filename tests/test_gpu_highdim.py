@@ -59,11 +59,12 @@ def test_high_dim_vs_oracle_and_dense(H, n, d, half, precision):
         assert lv[0] == n // 2  # full rank: the top block is n/2 x n/2
     if precision == 0 or d == 8:
         assert np.all(np.abs(lv - lv_o) <= 2), (lv, lv_o)
-    else:
-        # In [-3, 3]^32 the off-diagonal entries are about exp(-192): the FP64 form
-        # compresses them to eps of their own norm, the mixed form's double-floats (FP32
-        # exponent range) hold them as zero. Either is exact to rounding against 2I.
-        assert np.all(lv <= lv_o + 2), (lv, lv_o)
+    # In [-3, 3]^32 the off-diagonal entries lie between about exp(-50) and exp(-192): the
+    # FP64 form compresses them to eps of their own norm; the mixed form's double-floats
+    # (FP32 exponent range) lose their low words there or hold them as zero, so its ranks
+    # are not the FP64 form's (the 1024-row tiles' FP32 norms underflow and stop at rank 0,
+    # the 32-row tiles of nodes with a rank cap above 256 take FP64 norms and see the
+    # entries' rounding). Either is exact to rounding against 2I: the checks below.
     sol_d, ld_d = O.dense_solve(x, "se", th, S2, y)
     print(f"d {d} prec {precision}: ranks {lv.tolist()} logdet vs oracle {rel(ld, ld_o):.2e} "
           f"vs dense {rel(ld, ld_d):.2e}, solution vs dense "
