@@ -841,18 +841,35 @@ __global__ void k_aca_pivot_col(AcaArgs a) {
   warp_amax(bv, bi);
   nu2 = warp_sum(nu2);
   nv2 = warp_sum(nv2);
-  // sum_l (u_l.u)(v_l.v): lane l mod 32 takes l, summing the tiles in item order
+  // sum_l (u_l.u)(v_l.v), in whichever of two fixed orders costs fewer dependent adds: many
+  // tiles and a small rank (the top levels of a large problem): lanes over tiles and one warp
+  // sum per l; else lane l mod 32 takes l and sums the tiles in item order
   double cross = 0.0;
-  for (int l = lane; l < k; l += 32) {
-    double du = 0.0, dv = 0.0;
-    for (int it = i0; it < i1; ++it) {
-      const double* p = a.part + (int64_t)it * a.part_stride;
-      du += p[4 + l];
-      dv += p[4 + a.max_rank + l];
+  const int items = i1 - i0;
+  if (k * ((items + 31) / 32 + 5) <= ((k + 31) / 32) * items) {
+    for (int l = 0; l < k; ++l) {
+      double du = 0.0, dv = 0.0;
+      for (int it = i0 + lane; it < i1; it += 32) {
+        const double* p = a.part + (int64_t)it * a.part_stride;
+        du += p[4 + l];
+        dv += p[4 + a.max_rank + l];
+      }
+      du = warp_sum(du);
+      dv = warp_sum(dv);
+      cross += du * dv;
     }
-    cross += du * dv;
+  } else {
+    for (int l = lane; l < k; l += 32) {
+      double du = 0.0, dv = 0.0;
+      for (int it = i0; it < i1; ++it) {
+        const double* p = a.part + (int64_t)it * a.part_stride;
+        du += p[4 + l];
+        dv += p[4 + a.max_rank + l];
+      }
+      cross += du * dv;
+    }
+    cross = warp_sum(cross);
   }
-  cross = warp_sum(cross);
   if (lane == 0) col_decide(a, id, k, bi, nu2, nv2, cross);
 }
 
@@ -863,6 +880,7 @@ __global__ void k_aca_pivot_col(AcaArgs a) {
 // v_l.v of a tile run with threads over l and the tile's rows in order. FP64 arithmetic in
 // both forms (the mixed form's double-float columns are converted on load and store).
 static_assert(kWideTile == 32, "one row of a wide item per lane");
+constexpr int kCrossL = 128;  // l values per CTA of the wide cross term
 
 template <bool kFF>
 __device__ __forceinline__ double rld(const double* raw, int64_t i) {
@@ -1025,57 +1043,64 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_wide(AcaArgs a, int ite
   }
 }
 
-// D for a wide node: one block; the argmax and norms as in k_aca_pivot_col, the sum over l
-// with threads over l (tiles in item order), then the warps' sums in order.
-__global__ void __launch_bounds__(256) k_aca_pivot_col_wide(AcaArgs a) {
-  const int id = a.wide_nodes[blockIdx.x];
-  if (a.done[id]) return;
-  if (!a.phase[id]) {
-    if (threadIdx.x == 0) atomicAdd(a.active, 1);
-    return;
-  }
-  __shared__ double red[8];
-  __shared__ double s_nu2, s_nv2;
-  __shared__ int s_bi;
+// Cross term of a wide node, spread over CTAs: CTA (c, node) takes l in [c kCrossL,
+// (c + 1) kCrossL), each thread one l summing the tiles in item order, and folds
+// (u_l.u)(v_l.v) over its l's (warp sums, then the warps in order) into cross_part.
+__global__ void __launch_bounds__(kCrossL) k_aca_cross_wide(AcaArgs a, double* cross_part, int nchunk) {
+  const int id = a.wide_nodes[blockIdx.y];
+  if (a.done[id] || !a.phase[id]) return;
   const int k = a.rank[id];
+  const int l = blockIdx.x * kCrossL + threadIdx.x;
+  if (blockIdx.x * kCrossL >= k) return;
   const int i0 = a.node_item0[id], i1 = a.node_item1[id];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (w == 0) {
-    double bv = 0.0, nu2 = 0.0, nv2 = 0.0;
-    int bi = -1;
-    for (int it = i0 + lane; it < i1; it += 32) {
-      const double* p = a.part + (int64_t)it * a.part_stride;
-      amax_merge(bv, bi, p[0], (int)p[1]);
-      nu2 += p[2];
-      nv2 += p[3];
-    }
-    warp_amax(bv, bi);
-    nu2 = warp_sum(nu2);
-    nv2 = warp_sum(nv2);
-    if (lane == 0) {
-      s_nu2 = nu2;
-      s_nv2 = nv2;
-      s_bi = bi;
-    }
-  }
-  double cross = 0.0;
-  for (int l = threadIdx.x; l < k; l += 256) {
+  double c = 0.0;
+  if (l < k) {
     double du = 0.0, dv = 0.0;
     for (int it = i0; it < i1; ++it) {
       const double* p = a.part + (int64_t)it * a.part_stride;
       du += p[4 + l];
       dv += p[4 + a.max_rank + l];
     }
-    cross += du * dv;
+    c = du * dv;
   }
-  cross = warp_sum(cross);
-  if (lane == 0) red[w] = cross;
+  __shared__ double red[kCrossL / 32];
+  c = warp_sum(c);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double c = 0.0;
-    for (int q = 0; q < 8; ++q) c += red[q];
-    col_decide(a, id, k, s_bi, s_nu2, s_nv2, c);
+    double s = 0.0;
+    for (int q = 0; q < kCrossL / 32; ++q) s += red[q];
+    cross_part[(int64_t)blockIdx.y * nchunk + blockIdx.x] = s;
   }
+}
+
+// D for a wide node: one warp; the argmax and norms as in k_aca_pivot_col, the cross term
+// from k_aca_cross_wide's chunks in order.
+__global__ void __launch_bounds__(32) k_aca_pivot_col_wide(AcaArgs a, const double* cross_part, int nchunk) {
+  const int id = a.wide_nodes[blockIdx.x];
+  if (a.done[id]) return;
+  const int lane = threadIdx.x;
+  if (!a.phase[id]) {
+    if (lane == 0) atomicAdd(a.active, 1);
+    return;
+  }
+  const int k = a.rank[id];
+  const int i0 = a.node_item0[id], i1 = a.node_item1[id];
+  double bv = 0.0, nu2 = 0.0, nv2 = 0.0;
+  int bi = -1;
+  for (int it = i0 + lane; it < i1; it += 32) {
+    const double* p = a.part + (int64_t)it * a.part_stride;
+    amax_merge(bv, bi, p[0], (int)p[1]);
+    nu2 += p[2];
+    nv2 += p[3];
+  }
+  warp_amax(bv, bi);
+  nu2 = warp_sum(nu2);
+  nv2 = warp_sum(nv2);
+  if (lane != 0) return;
+  double c = 0.0;
+  for (int q = 0; q * kCrossL < k; ++q) c += cross_part[(int64_t)blockIdx.x * nchunk + q];
+  col_decide(a, id, k, bi, nu2, nv2, c);
 }
 
 // Presized mode: flag every block that did not converge within its level's rank.
@@ -1178,6 +1203,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   ++c.launches;
   int wblocks = (nint * 32 + 255) / 256;
   const int64_t nbig = c.n_big_items, nwide = c.n_wide_items;
+  const int nchunk = (c.max_rank + kCrossL - 1) / kCrossL;  // cross-term chunks per wide node
   const int64_t nsmall = c.n_items - nbig - nwide, small0 = nbig + nwide;
   const unsigned sgrid = (unsigned)((nsmall + kAcaThreads / 32 - 1) / (kAcaThreads / 32));
   const size_t smem_row = 0, smem_col = 0;  // static, independent of the rank
@@ -1215,8 +1241,9 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
     }
     k_aca_pivot_col<<<wblocks, 256, 0, c.stream>>>(a);
     if (c.n_wide_nodes > 0) {
-      k_aca_pivot_col_wide<<<(unsigned)c.n_wide_nodes, 256, 0, c.stream>>>(a);
-      ++c.launches;
+      k_aca_cross_wide<<<dim3((unsigned)nchunk, (unsigned)c.n_wide_nodes), kCrossL, 0, c.stream>>>(a, c.wide_cross, nchunk);
+      k_aca_pivot_col_wide<<<(unsigned)c.n_wide_nodes, 32, 0, c.stream>>>(a, c.wide_cross, nchunk);
+      c.launches += 2;
     }
     c.launches += 2;
     HODLR_CUDA_TRY(cudaGetLastError());

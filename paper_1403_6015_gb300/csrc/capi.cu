@@ -77,7 +77,7 @@ void free_factor_buffers(Ctx* c) {
 void free_all(Ctx* c) {
   free_factor_buffers(c);
   dfree(c->nodes); dfree(c->xs); dfree(c->perm);
-  dfree(c->item_node); dfree(c->item_start); dfree(c->wide_nodes); dfree(c->node_item0); dfree(c->node_item1); dfree(c->raw);
+  dfree(c->item_node); dfree(c->item_start); dfree(c->wide_nodes); dfree(c->wide_cross); dfree(c->node_item0); dfree(c->node_item1); dfree(c->raw);
   dfree(c->cheb_q); dfree(c->cheb_coef);
   dfree(c->st_rank); dfree(c->st_row); dfree(c->st_col); dfree(c->st_done); dfree(c->st_ok);
   dfree(c->st_zero); dfree(c->st_phase); dfree(c->st_nused); dfree(c->st_used);
@@ -186,6 +186,7 @@ hodlr_status setup_aca(Ctx* c) {
   TRY_CUDA(c, dalloc(&c->st_s2, nint), "alloc aca state");
   TRY_CUDA(c, dalloc(&c->aca_part, c->n_items * (4 + 2 * c->max_rank)), "alloc aca partials");
   TRY_CUDA(c, dalloc(&c->wide_nodes, (int64_t)wide.size()), "alloc items");
+  TRY_CUDA(c, dalloc(&c->wide_cross, (int64_t)wide.size() * ((c->max_rank + 127) / 128)), "alloc items");
   if (!wide.empty())
     TRY_CUDA(c, cudaMemcpyAsync(c->wide_nodes, wide.data(), 4 * wide.size(), cudaMemcpyHostToDevice, c->stream), "upload");
   if (c->compression == 1) {

@@ -213,6 +213,7 @@ struct Ctx {
   int64_t n_big_items = 0;        // items [0, n_big_items): tiles of kAcaTile rows; then
   int64_t n_wide_items = 0;       // n_wide_items tiles of kWideTile rows; the rest: small nodes
   int32_t* wide_nodes = nullptr;  // ids of the nodes with wide items
+  double* wide_cross = nullptr;   // their cross-term chunks, ceil(max_rank / 128) each
   int n_wide_nodes = 0;
   std::vector<int64_t> h_raw_off; // offset (in doubles) of level j's raw panel
   std::vector<int> h_rcap;        // raw columns of level j
