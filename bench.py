@@ -1077,6 +1077,25 @@ def profile_batched():
                                           "status_ok": bool((status.cpu().numpy() == 0).all())}}))
 
 
+def profile_dense_row(name):
+    """One factorization of a dense-limit row for launch-list and kernel captures: the
+    3-D n = 10 000 or the d = 4 n = 5000 Gaussian row of Sec. 5 (the stored oracle inputs,
+    FP64 form, leaf 128, eps 1e-12, max_rank n/2): build, factor with the right-hand side,
+    log det against the oracle's stored value."""
+    from paper_1403_6015_gb300 import hodlr as H
+    from paper_1403_6015_gb300 import inputs as I
+    with open(os.path.join(ROOT, "tests", "golden", f"fullrank_{name}.json")) as f:
+        g = json.load(f)
+    n = g["n"]
+    x = I.uniform_points(n, g["d"], g["box"][0], g["box"][1], g["seed_points"])
+    y = I.normal(n, g["seed_y"])
+    h = H.Hodlr(x, "se", [g["ell"], g["amp"]], g["sigma2"], g["leaf"], g["eps"], max_rank=n // 2)
+    h.factor_solve(y)
+    ld = h.logdet()
+    print(json.dumps({"profile_dense_row": name, "logdet_rel_err": abs(ld - g["logdet"]) / abs(g["logdet"]),
+                      "phase_ms": h.phase_ms()}))
+
+
 def main():
     global N, COMPRESSION
     ap = argparse.ArgumentParser()
@@ -1095,6 +1114,8 @@ def main():
                     help="-1: both forms (default), 0: FP64 only, 1: mixed only")
     ap.add_argument("--compression", default="aca", choices=["aca", "chebyshev"],
                     help="compression of the timed evaluations (profiling captures)")
+    ap.add_argument("--profile-dense-row", choices=["d3", "d4"], default=None,
+                    help="one factorization of a dense-limit Gaussian row (for captures)")
     ap.add_argument("--profile-batched", action="store_true",
                     help="run one small batched call (4 lanes, 16 Matern-5/2 settings, "
                          "n=65536, mixed form) and exit: the case of the batched launch list")
@@ -1103,6 +1124,11 @@ def main():
     COMPRESSION = args.compression
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.profile_dense_row:
+        from paper_1403_6015_gb300 import build_lib
+        build_lib.build()
+        profile_dense_row(args.profile_dense_row)
+        return
     if args.profile_batched:
         profile_batched()
     elif args.impl == "reference":

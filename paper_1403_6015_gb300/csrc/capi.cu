@@ -219,7 +219,7 @@ hodlr_status size_buffers(Ctx* c) {
     const int64_t rw = (int64_t)c->h_rl[j] * (c->h_coff[j] + c->h_rl[j] + c->max_nrhs);
     if (j + 1 < K && hodlr::gemm_step(c->h_rl, j + 1)) direct_el = std::max(direct_el, rw << (j + 1));
     else pstride = std::max(pstride, rw);
-    big |= c->h_rl[j] >= hodlr::kBlockRank;
+    big |= c->h_rl[j] > hodlr::kSmemRank;  // a blocked node step (levels_big.cu)
   }
   pstride = std::max<int64_t>(pstride, c->R);  // the matvec stores R partials per leaf
   int64_t zel = 1, hel = 1, mlu = 0, piv = 0;

@@ -24,8 +24,8 @@ constexpr int kMaxRank = 8192;     // hard cap on a block's rank (opts.max_rank)
 constexpr int kDefaultMaxRank = 64;  // default opts.max_rank
 constexpr int kSmemRank = 64;      // ranks up to this use the shared-memory node step
                                    // (2r x 2r in smem) and the fused level sweep
-constexpr int kBlockRank = 128;    // ranks from this up: blocked node step over many CTAs and
-                                   // the sweep in product form (levels_big.cu)
+constexpr int kBlockRank = 128;    // ranks from this up: the sweep in product form
+                                   // (levels_big.cu; node steps above kSmemRank are blocked)
 constexpr int kAcaTile = 1024;     // columns (rows) of one ACA work item
 constexpr int kSmallNode = 256;    // nodes whose children both fit: one warp per node
 constexpr int kWideRank = 256;     // nodes whose rank cap min(m_left, m_right, max_rank)

@@ -8,8 +8,8 @@
 // Work is expressed over leaf row tiles so all levels have the same parallelism:
 //   per-leaf partials  Phi_j[leaf]^T Q[leaf]       (written by the previous sweep step)
 //   k_segsum           fixed-order sums over each node half
-//   k_node             M, LU, log det, Z per node (M in shared memory, ranks <= 64)
-//   k_node_big         the same with M in global memory (ranks above 64)
+//   k_node             M, LU, log det, Z per node (M in shared memory, ranks <= 64; larger
+//                      ranks: the blocked node step of levels_big.cu)
 //   k_sweep            update of level u on each leaf fused with the partials of level u-1
 #include <cuda_runtime.h>
 
@@ -65,30 +65,15 @@ __global__ void __launch_bounds__(128) k_node(NodeArgs a, bool factor) {
   node_solve(a, blockIdx.x, factor, M, piv, &lds, &sgn);
 }
 
-constexpr int kNodeBigThreads = 512;
-
-__global__ void __launch_bounds__(kNodeBigThreads) k_node_big(NodeArgs a, bool factor) {
-  __shared__ double wv[kNodeBigThreads / 32];
-  __shared__ int wi[kNodeBigThreads / 32];
-  __shared__ int pv;
-  __shared__ double lds;
-  __shared__ int sgn;
-  node_solve_global(a, blockIdx.x, factor, wv, wi, &pv, &lds, &sgn);
-}
-
-// Node step of every node of level na.j: M in shared memory up to rank kSmemRank, in
-// global memory with one CTA per node below kBlockRank, else blocked over many CTAs.
+// Node step of every node of level na.j: M in shared memory up to rank kSmemRank (one CTA
+// per node), else in global memory, factored and solved blocked over many CTAs.
 cudaError_t launch_node(Ctx& c, const NodeArgs& na, bool factor_mode) {
   int r = na.r;
-  if (r >= kBlockRank) return launch_node_blocked(c, na, factor_mode);
-  if (r <= kSmemRank) {
-    size_t smem = sizeof(double) * 4 * r * r;
-    if (smem > kSmemOptIn)
-      HODLR_CUDA_TRY(cudaFuncSetAttribute(k_node, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_node<<<1u << na.j, 128, smem, c.stream>>>(na, factor_mode);
-  } else {
-    k_node_big<<<1u << na.j, kNodeBigThreads, 0, c.stream>>>(na, factor_mode);
-  }
+  if (r > kSmemRank) return launch_node_blocked(c, na, factor_mode);
+  size_t smem = sizeof(double) * 4 * r * r;
+  if (smem > kSmemOptIn)
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_node, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_node<<<1u << na.j, 128, smem, c.stream>>>(na, factor_mode);
   ++c.launches;
   return cudaGetLastError();
 }

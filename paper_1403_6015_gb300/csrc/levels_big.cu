@@ -14,16 +14,17 @@
 //              theorem, Sec. 4), then Z = M^-1 [V^T P_R; U^T P_L] by blocked forward and
 //              back substitution (k_z_fill applies the pivots, k_z_diag solves a diagonal
 //              block, k_gemm updates the rows below or above it).
-//   sweep      the level-u update P -= Ut Z of each leaf's rows (k_gemm, one product per
-//              leaf), then the half-node sums Phi_{u-1}^T P of the next level as one product
-//              per half-node (k_gemm over the half-node's rows), in place of per-leaf
-//              partials and their segmented sums.
+//   sweep      the level-u update P -= Ut Z (k_gemm, one product per half of a level-u
+//              node: its rows share one block of Z), then the half-node sums Phi_{u-1}^T P
+//              of the next level as one product per half-node (k_gemm over the half-node's
+//              rows), in place of per-leaf partials and their segmented sums.
 // All arithmetic is FP64, also in the mixed form (its double-float panels are converted on
 // load and store), and every sum runs in a fixed order: results are deterministic.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "ff.cuh"
 #include "hodlr_internal.cuh"
@@ -37,8 +38,8 @@ constexpr int kBM = 64, kBN = 64, kBK = 16, kGemmThreads = 256;
 
 enum GemmMode : int {
   kUniform = 0,   // problem t at fixed offsets t * a_bs, t * b_bs, t * c_bs
-  kLeafRows = 1,  // problem t = leaf t: rows nb[id0 + t] .. + ns[id0 + t] of A and C;
-                  // B = the Z block of the leaf's level-u node and side
+  kNodeRows = 1,  // problem t = node id0 + t: rows nb[id0 + t] .. + ns[id0 + t] of A and C;
+                  // B = the Z block of its ancestor (t >> sh) and side ((t >> (sh - 1)) & 1)
   kHalfRows = 2   // problem t = half-node t: the sum runs over its rows nb[id0 + t] ..
 };
 
@@ -49,14 +50,14 @@ struct GemmArgs {
   const void* b;
   void* c;
   int64_t ai, ak, bk, bj, ci, cj;
-  int m, n, k;              // kLeafRows: m is the problem's leaf size; kHalfRows: k likewise
+  int m, n, k;              // kNodeRows: m is the problem's node size; kHalfRows: k likewise
   int mode;
   int64_t a_bs, b_bs, c_bs;
   const int32_t* nb;
   const int32_t* ns;
   int id0;
-  int sh;                   // kLeafRows: leaves per level-u node = 2^sh
-  int64_t z_stride, z_side; // kLeafRows: Z of node (t >> sh), side ((t >> (sh-1)) & 1)
+  int sh;                   // kNodeRows: problems per Z block's node = 2^sh
+  int64_t z_stride, z_side; // kNodeRows: Z of node (t >> sh), side ((t >> (sh-1)) & 1)
 };
 
 __device__ __forceinline__ double ldv(const double* p, int64_t i) { return p[i]; }
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
   const int t = blockIdx.z;
   int m = g.m, K = g.k;
   int64_t oa = (int64_t)t * g.a_bs, ob = (int64_t)t * g.b_bs, oc = (int64_t)t * g.c_bs;
-  if (g.mode == kLeafRows) {
+  if (g.mode == kNodeRows) {
     const int id = g.id0 + t;
     const int b = g.nb[id];
     m = g.ns[id];
@@ -215,6 +216,7 @@ struct PanelArgs {
   double* slots;        // per launched node: 2 (parity) x (G + 1) x kSlot doubles
   int32_t* flags;
   int m2, c0, nb, G, rpc, node0;
+  int G_wait;           // CTAs the barrier waits for: G (more only to test the timeout path)
   int last, signed_det;
 };
 
@@ -281,7 +283,12 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_panel(PanelArgs a) {
   const int r_lo = c0 + g * a.rpc;
   const int nrow = max(0, min(a.rpc, m2 - r_lo));
   constexpr int kLd = kNB + 1;
-  if (__ldcg(a.flags) & kFlagTimeout) return;  // an earlier barrier gave up: no more waits
+  int32_t* pivn = a.piv + (int64_t)node * a.m2;
+  if (__ldcg(a.flags) & kFlagTimeout) {  // an earlier barrier gave up: no more waits; the
+    if (g == 0)                          // pivots stay valid row indices for the kernels after
+      for (int t = threadIdx.x; t < a.nb; t += kPanelThreads) pivn[a.c0 + t] = a.c0 + t;
+    return;
+  }
   double* M = a.M + (int64_t)node * a.m_bs;
   uint32_t* ctr = a.bar + node;
   for (int e = tid; e < nrow * nb; e += kPanelThreads) {
@@ -326,7 +333,11 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_panel(PanelArgs a) {
       if (sbi >= 0) sl[(int64_t)g * kSlot + 2 + tid] = S[(sbi - r_lo) * kLd + tid];
       if (c >= r_lo && c < r_lo + nrow) sl[(int64_t)G * kSlot + 2 + tid] = S[(c - r_lo) * kLd + tid];
     }
-    if (!grid_barrier(ctr, a.bar_base + (uint32_t)(t + 1) * G, a.flags, &ok_s)) return;
+    if (!grid_barrier(ctr, a.bar_base + (uint32_t)(t + 1) * a.G_wait, a.flags, &ok_s)) {
+      if (g == 0)
+        for (int q = t + tid; q < nb; q += kPanelThreads) pivn[c0 + q] = c0 + q;
+      return;
+    }
     // the pivot, the same in every CTA
     if (w == 0) {
       double fv = -1.0;
@@ -368,7 +379,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_panel(PanelArgs a) {
     }
     const double d = urow[t];
     if (g == 0 && tid == 0) {
-      a.piv[(int64_t)node * m2 + c] = p;
+      pivn[c] = p;
       if (p != c) sgn = -sgn;
       if (d == 0.0) sgn = 0;
       else {
@@ -416,7 +427,10 @@ __global__ void __launch_bounds__(128) k_lu_rows(double* Mall, int64_t m_bs, con
     const int i = e / nb, j = e - i * nb;
     L[i][j] = M[(int64_t)(c0 + i) * m2 + c0 + j];
   }
-  for (int e = threadIdx.x; e < nb; e += blockDim.x) pv[e] = piv[c0 + e];
+  for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+    const int p = piv[c0 + e];
+    pv[e] = (unsigned)p < (unsigned)m2 ? p : c0 + e;  // a pivot outside M: keep the row
+  }
   __syncthreads();
   int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= c0) col += nb;  // skip the panel's own columns
@@ -459,7 +473,8 @@ __global__ void k_z_perm(const int32_t* __restrict__ pivall, int m2, int32_t* __
   __syncthreads();
   if (threadIdx.x == 0)
     for (int c = 0; c < m2; ++c) {
-      const int p = piv[c];
+      int p = piv[c];
+      if ((unsigned)p >= (unsigned)m2) p = c;  // a pivot outside M: keep the row
       const int v = pm[c];
       pm[c] = pm[p];
       pm[p] = v;
@@ -574,6 +589,10 @@ cudaError_t launch_node_blocked(Ctx& c, const NodeArgs& na, bool factor) {
   int32_t* sign = c.big_i32;
   uint32_t* bar = reinterpret_cast<uint32_t*>(c.big_i32 + c.big_nodes);
   if (factor) {
+    // HODLR_TEST_BARRIER_EXTRA=k: each barrier waits for k CTAs that are never launched, so
+    // that a test can check the bounded wait and the ETIMEOUT status (0 in normal use)
+    const char* ev = getenv("HODLR_TEST_BARRIER_EXTRA");
+    const int barrier_extra = ev ? std::max(0, atoi(ev)) : 0;
     k_m_build<<<dim3(grid_for(m_bs, 256), nodes), 256, 0, c.stream>>>(na, m_bs);
     ++c.launches;
     HODLR_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(uint32_t) * nodes, c.stream));
@@ -601,6 +620,7 @@ cudaError_t launch_node_blocked(Ctx& c, const NodeArgs& na, bool factor) {
         pa.c0 = c0;
         pa.nb = nb;
         pa.G = G;
+        pa.G_wait = G + barrier_extra;
         pa.rpc = rpc;
         pa.node0 = k0;
         pa.last = c0 + nb == m2;
@@ -610,7 +630,7 @@ cudaError_t launch_node_blocked(Ctx& c, const NodeArgs& na, bool factor) {
                                                    dim3(kPanelThreads), args, smem, c.stream));
         ++c.launches;
       }
-      base += (uint32_t)(nb * G);
+      base += (uint32_t)(nb * (G + barrier_extra));
       if (m2 > nb) {
         k_lu_rows<<<dim3((unsigned)((m2 - nb + 127) / 128), nodes), 128, 0, c.stream>>>(
             na.Mlu, m_bs, na.Mpiv, m2, c0, nb);
@@ -665,14 +685,14 @@ cudaError_t launch_node_blocked(Ctx& c, const NodeArgs& na, bool factor) {
   return cudaGetLastError();
 }
 
-// Sweep step of level u in product form: every leaf's rows P -= Ut Z (panel columns
-// [0, cP) and the right-hand sides), then, for u > 0, the half-node sums of level u - 1,
+// Sweep step of level u in product form: the rows of each half of a level-u node
+// P -= Ut Z_side (panel columns [0, cP) and the right-hand sides), then, for u > 0, the
+// half-node sums of level u - 1,
 // half + t hs with rows c < r_{u-1} and columns q < cP + nrhs (hs = r_{u-1} (cP + nrhs)).
 template <class T>
 static cudaError_t sweep_gemm_t(Ctx& c, int u, int nrhs, bool factor_mode) {
   const int K = c.kappa;
   const int64_t n = c.n;
-  const int nleaf = 1 << K;
   const int ru = c.h_rl[u], cu = c.h_coff[u];
   const int cP = factor_mode ? cu : 0, wz = cP + nrhs;
   const int rl = u > 0 ? c.h_rl[u - 1] : 0, cl = u > 0 ? c.h_coff[u - 1] : 0;
@@ -681,8 +701,12 @@ static cudaError_t sweep_gemm_t(Ctx& c, int u, int nrhs, bool factor_mode) {
   const int32_t* nb = c.nodes;
   const int32_t* ns = c.nodes + ((int64_t)2 << K);
   if (ru > 0 && wz > 0) {
+    // the halves of the level-u nodes are the level-(u + 1) nodes, 2^(u+1) of them
+    const int halves = 2 << u, id0 = halves - 1;
+    int mh = 0;
+    for (int t = 0; t < halves; ++t) mh = std::max(mh, c.h_nodes[((size_t)2 << K) + id0 + t]);
     GemmArgs g{};
-    g.mode = kLeafRows;
+    g.mode = kNodeRows;
     g.a = pan + (int64_t)cu * n;
     g.ai = 1;
     g.ak = n;
@@ -693,22 +717,22 @@ static cudaError_t sweep_gemm_t(Ctx& c, int u, int nrhs, bool factor_mode) {
     g.k = ru;
     g.nb = nb;
     g.ns = ns;
-    g.id0 = nleaf - 1;
-    g.sh = K - u;
+    g.id0 = id0;
+    g.sh = 1;
     g.z_stride = (int64_t)2 * ru * wz;
     g.z_side = (int64_t)ru * wz;
     if (cP > 0) {
       g.b = reinterpret_cast<const T*>(c.Z);
       g.c = pan;
       g.n = cP;
-      HODLR_CUDA_TRY((gemm<T, T, T, true>(g, c.max_leaf_size, nleaf, c.stream)));
+      HODLR_CUDA_TRY((gemm<T, T, T, true>(g, mh, halves, c.stream)));
       ++c.launches;
     }
     if (nrhs > 0) {
       g.b = c.Z + cP;
       g.c = c.Y;
       g.n = nrhs;
-      HODLR_CUDA_TRY((gemm<T, double, double, true>(g, c.max_leaf_size, nleaf, c.stream)));
+      HODLR_CUDA_TRY((gemm<T, double, double, true>(g, mh, halves, c.stream)));
       ++c.launches;
     }
   }

@@ -149,144 +149,5 @@ static __device__ void node_solve(const NodeArgs& a, int k, bool factor, double*
   }
 }
 
-// The node step for ranks above the shared-memory limit: the same M, LU with partial
-// pivoting, log|det| and Z, with M held in global memory (the level's Mlu slot, read
-// through L2) and every step spread over the whole block: a block-wide pivot search (the
-// largest |M(i,c)|, lowest row index on ties, as in node_solve), the row swap, the
-// multipliers, and a trailing update with one warp per row and lanes over columns.
-// Shared scratch: wv/wi (one entry per warp), the chosen pivot, lds/sgn.
-static __device__ void node_solve_global(const NodeArgs& a, int k, bool factor, double* wv,
-                                         int* wi, int* pv, double* lds_p, int* sgn_p) {
-  double& lds = *lds_p;
-  int& sgn = *sgn_p;
-  int node = (1 << a.j) - 1 + k;
-  int r = a.r, m2 = 2 * r, tid = threadIdx.x, nthr = blockDim.x;
-  int lane = tid & 31, w = tid >> 5, nw = nthr >> 5;
-  const double* L = a.half + (int64_t)(2 * k) * a.stride;
-  const double* Rt = a.half + (int64_t)(2 * k + 1) * a.stride;
-  double* M = a.Mlu + (int64_t)k * m2 * m2;
-  int32_t* piv = a.Mpiv + (int64_t)k * m2;
-  if (factor) {
-    for (int64_t e = tid; e < (int64_t)m2 * m2; e += nthr) {
-      int row = (int)(e / m2), col = (int)(e - (int64_t)row * m2);
-      double v;
-      if (row < r && col < r) v = row == col ? 1.0 : 0.0;
-      else if (row >= r && col >= r) v = row == col ? 1.0 : 0.0;
-      else if (row < r) v = __ldcg(Rt + row * a.w + a.cj + (col - r));   // V^T Vt
-      else v = __ldcg(L + (row - r) * a.w + a.cj + col);                 // U^T Ut
-      M[e] = v;
-    }
-    if (tid == 0) {
-      lds = 0.0;
-      sgn = 1;
-    }
-    __syncthreads();
-    for (int c = 0; c < m2; ++c) {
-      double bv = -1.0;
-      int bi = -1;
-      for (int i = c + tid; i < m2; i += nthr) {
-        double v = fabs(M[(int64_t)i * m2 + c]);
-        if (v > bv) {
-          bv = v;
-          bi = i;
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) {
-          bv = ov;
-          bi = oi;
-        }
-      }
-      if (lane == 0) {
-        wv[w] = bv;
-        wi[w] = bi;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        double fv = -1.0;
-        int fi = -1;
-        for (int q = 0; q < nw; ++q)
-          if (wi[q] >= 0 && (fi < 0 || wv[q] > fv || (wv[q] == fv && wi[q] < fi))) {
-            fv = wv[q];
-            fi = wi[q];
-          }
-        if (fi < 0) fi = c;  // every candidate NaN: keep the diagonal, as the serial search
-        *pv = fi;
-        piv[c] = fi;
-        if (fi != c) sgn = -sgn;
-      }
-      __syncthreads();
-      int p = *pv;
-      if (p != c)
-        for (int jj = tid; jj < m2; jj += nthr) {
-          double t = M[(int64_t)c * m2 + jj];
-          M[(int64_t)c * m2 + jj] = M[(int64_t)p * m2 + jj];
-          M[(int64_t)p * m2 + jj] = t;
-        }
-      __syncthreads();
-      double d = M[(int64_t)c * m2 + c];
-      if (tid == 0) {
-        if (d == 0.0) sgn = 0;
-        else {
-          if (d < 0) sgn = -sgn;
-          lds += log(fabs(d));
-        }
-      }
-      for (int i = c + 1 + tid; i < m2; i += nthr) {
-        double* e = M + (int64_t)i * m2 + c;
-        *e = d != 0.0 ? *e / d : 0.0;
-      }
-      __syncthreads();
-      for (int i = c + 1 + w; i < m2; i += nw) {
-        double l = M[(int64_t)i * m2 + c];
-        if (l == 0.0) continue;  // subtracting 0 * x leaves the row unchanged
-        double* mi = M + (int64_t)i * m2;
-        const double* mc = M + (int64_t)c * m2;
-        for (int jj = c + 1 + lane; jj < m2; jj += 32) mi[jj] -= l * mc[jj];
-      }
-      __syncthreads();
-    }
-    if (tid == 0) {
-      a.node_logdet[node] = lds;
-      record_sign(a, sgn);
-    }
-  }
-  __syncthreads();
-  // Z = M^-1 [V^T P_R; U^T P_L], one thread per column (M rows read by the whole warp)
-  double* Zn = a.Z + (int64_t)k * a.z_stride;
-  for (int q = tid; q < a.wz; q += nthr) {
-    int pc = zcol(a, q);
-    for (int row = 0; row < r; ++row) {
-      Zn[(int64_t)row * a.wz + q] = __ldcg(Rt + row * a.w + pc);
-      Zn[(int64_t)(r + row) * a.wz + q] = __ldcg(L + row * a.w + pc);
-    }
-    for (int c = 0; c < m2; ++c) {
-      int p = piv[c];
-      if (p != c) {
-        double t = Zn[(int64_t)c * a.wz + q];
-        Zn[(int64_t)c * a.wz + q] = Zn[(int64_t)p * a.wz + q];
-        Zn[(int64_t)p * a.wz + q] = t;
-      }
-    }
-    for (int i = 1; i < m2; ++i) {
-      double s = Zn[(int64_t)i * a.wz + q];
-      const double* mi = M + (int64_t)i * m2;
-      for (int c = 0; c < i; ++c) s -= mi[c] * Zn[(int64_t)c * a.wz + q];
-      Zn[(int64_t)i * a.wz + q] = s;
-    }
-    for (int i = m2 - 1; i >= 0; --i) {
-      double s = Zn[(int64_t)i * a.wz + q];
-      const double* mi = M + (int64_t)i * m2;
-      for (int c = i + 1; c < m2; ++c) s -= mi[c] * Zn[(int64_t)c * a.wz + q];
-      Zn[(int64_t)i * a.wz + q] = s / mi[i];
-    }
-    if (a.zff && q < a.cj)  // a panel column, in place: this thread owns column q
-      for (int i = 0; i < m2; ++i)
-        reinterpret_cast<ff*>(Zn)[(int64_t)i * a.wz + q] = ff_from_double(Zn[(int64_t)i * a.wz + q]);
-  }
-}
-
 
 }  // namespace hodlr

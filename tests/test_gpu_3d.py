@@ -41,7 +41,7 @@ def test_sort_3d_kd_bit_exact(H, n, leaf):
 @pytest.mark.parametrize("kern,ell,eps,ld_tol", [("se", 0.5, 1e-12, 1e-12),
                                                  ("matern52", 2.0, 1e-10, 1e-10)])
 def test_3d_vs_oracle_and_dense(H, kern, ell, eps, ld_tol, precision):
-    """Top-level ranks above 300: the global-memory node step and the unstaged sweep."""
+    """Top-level ranks above 300: the blocked node step and the sweep in product form."""
     n = 3000
     x, y = I.workload_3d(n, 94)
     y = np.ascontiguousarray(y).reshape(-1)

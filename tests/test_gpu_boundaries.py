@@ -3,9 +3,8 @@ with zero columns, which leaves every product of the factorization unchanged, so
 log-likelihood must equal the adaptive one. Padding to ranks around each switch and
 shared-memory threshold of the level sweep exercises them all on one small problem: the
 node step's shared-memory matrix (4 r^2 doubles, opt-in above 40 KB: r = 38, 39, 40), the
-fused sweep's limit (r <= 64) and the global-memory node step above it (65, 127), and from
-r = 128 the blocked node step over many CTAs with the level sweep as batched products
-(128, 200)."""
+fused sweep's limit (r <= 64) and the blocked node step over many CTAs above it (65, 127),
+and from r = 128 the level sweep as batched products as well (128, 200)."""
 import numpy as np
 import pytest
 
@@ -40,7 +39,7 @@ def test_presized_padding_any_rank(H, precision, r):
     h.rebuild(th, s2)
     got = h.loglik(y)
     assert h.status_flags() == 0
-    # padded ranks above 64 run the global-memory node step instead of the fused sweep: a
+    # padded ranks above 64 run the blocked node step instead of the fused sweep: a
     # different FP64 summation order, carried through the leaf solutions (unit roundoff
     # 2^-53 in the FP64 form, 2^-48 in the double-float leaves of the mixed form; this
     # squared-exponential problem has cond(C) near 1e6; 2.0e-12 seen for the mixed form at
@@ -52,10 +51,10 @@ def test_presized_padding_any_rank(H, precision, r):
     # the unfused sweep than by the fused one)
     sol = h.solve(y)
     sol_ref = H.Hodlr(x, "se", th, s2, 64, 1e-12, max_rank=256, precision=precision).factor_solve(y)
-    # from r = 128 the blocked LU and the K-chunked products sum in yet another order: 2.4e-11
-    # of the largest entry measured in the FP64 form, while every path (fused, global-memory,
+    # above r = 64 the blocked LU and its K-chunked products sum in yet another order: 2.4e-11
+    # of the largest entry measured in the FP64 form at r = 128, while every path (fused,
     # blocked) lies 5.3e-10 to 5.5e-10 from the dense solution of this cond ~ 1e6 problem
-    tol = (1e-11 if r < 128 else 1e-10) if precision == 0 else 1e-9
+    tol = (1e-11 if r <= 64 else 1e-10) if precision == 0 else 1e-9
     np.testing.assert_allclose(sol, sol_ref, rtol=0, atol=tol * np.abs(sol_ref).max())
 
 

@@ -8,6 +8,7 @@ oracle values of the paper's n = 5000 (d = 4) and n = 10 000 (d = 3) rows (writt
 tests/golden/make_fullrank_golden.py), and against dense Cholesky."""
 import json
 import os
+import time
 
 import numpy as np
 import pytest
@@ -134,3 +135,28 @@ def test_paper_rows_vs_stored_oracle(H, name):
     assert rel(y @ sol, g["quad"]) <= 1e-10
     assert rel(ld, ld_d) <= 1e-10
     np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-10 * np.abs(sol_d).max())
+
+
+def test_barrier_timeout_reports_etimeout(H, monkeypatch):
+    """The large-rank LU panel's CTAs meet at a grid barrier whose wait is bounded (2 s, then
+    a flag). HODLR_TEST_BARRIER_EXTRA=1 makes each barrier wait for one CTA that is never
+    launched: the factorization must return ETIMEOUT within a few seconds (later panels see
+    the flag and skip their waits), fault nothing, and leave the context usable."""
+    n, d = 1000, 8
+    x = I.uniform_points(n, d, -3.0 / np.sqrt(8.0), 3.0 / np.sqrt(8.0), 2120)
+    y = I.normal(n, 2121)
+    th = [ELL, 1.0]
+    h = H.Hodlr(x, "se", th, S2, 128, EPS, max_rank=n // 2)
+    monkeypatch.setenv("HODLR_TEST_BARRIER_EXTRA", "1")
+    t0 = time.perf_counter()
+    with pytest.raises(H.HodlrError) as e:
+        h.factor_solve(y)
+    dt = time.perf_counter() - t0
+    monkeypatch.delenv("HODLR_TEST_BARRIER_EXTRA")
+    assert e.value.status == H.HODLR_ETIMEOUT
+    assert 1.5 < dt < 30.0, dt
+    h.rebuild(th, S2)
+    sol = h.factor_solve(y)
+    ld_d, sol_d = dense_chol(x, y)
+    assert rel(h.logdet(), ld_d) <= 1e-12
+    np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-11 * np.abs(sol_d).max())

@@ -57,7 +57,7 @@ def test_high_rank_2d(H, problem, ell, precision):
     h = H.Hodlr(x, "se", [ell, 1.0], S2, 128, EPS, max_rank=300, precision=precision)
     kappa, _ = h.tree()
     lv = level_max(h.ranks(), kappa)
-    assert lv[0] > 64  # the global-memory node step
+    assert lv[0] > 64  # the blocked node step
     if ell == 0.1:
         assert lv[0] + lv[1] > 200  # the unstaged level sweep
     o = O.Hodlr(x, "se", [ell, 1.0], S2, 128, EPS, max_rank=300)
