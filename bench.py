@@ -43,6 +43,7 @@ FP64_PEAK = 152 * 2 * 2 * 2.07e9  # SMs x FP64 FMA/clk/SM x 2 flop x max SM cloc
 # DRAM bytes (read + write) of one launch of each form's leaf kernel at n = 2^20 (the
 # bench's own launch: 8192 leaves, 26 panel columns + 1 right-hand side), measured by ncu
 # (profiles/leaf_kernel_dram_n2p20.md); None when the kernel has changed since.
+DENSE_SAMPLE_N = 1200  # the dense-limit case timed on both the oracle and the GPU
 LEAF_TRAFFIC_BYTES = {0: 259840768 + 723815680, 1: 258910976 + 735765504}
 
 
@@ -896,6 +897,7 @@ def dense_limit_rows(H, I, torch):
     oracle's stored value (tests/golden, written by its own script) or dense Cholesky, and
     the factorization's algorithmic FP64 rate against the derived FP64 peak."""
     rows = {
+        "gaussian_d4_n1200_oracle_sample": (None, DENSE_SAMPLE_N, 4, 3.0, 2100, None),
         "gaussian_3d_n10000": ("d3", 10000, 3, 3.0, 2003, [15.4, 17.3, 0.113, 0.91]),
         "gaussian_d4_n5000": ("d4", 5000, 4, 3.0, 2004, [9.67, 21.25, 0.073, 0.088]),
         "gaussian_scaled_d8_n5000": (None, 5000, 8, 3.0 / np.sqrt(8.0), 2008, [40.8, 138.4, 0.186, 0.359]),
@@ -904,8 +906,11 @@ def dense_limit_rows(H, I, torch):
     for name, (gname, n, d, half, seed, ptimes) in rows.items():
         x = I.uniform_points(n, d, -half, half, seed)
         y = I.normal(n, seed + 1)
-        r = {"n": n, "d": d, "cube_half_width": half, "leaf": LEAF, "eps": EPS, "max_rank": n // 2,
-             "paper_s (laptop, one core)": dict(zip(["assembly", "factor", "solve", "det"], ptimes))}
+        r = {"n": n, "d": d, "cube_half_width": half, "leaf": LEAF, "eps": EPS, "max_rank": n // 2}
+        if ptimes:
+            r["paper_s (laptop, one core)"] = dict(zip(["assembly", "factor", "solve", "det"], ptimes))
+        else:
+            r["note"] = "the case cpu_baseline.dense_limit_sample times on the oracle"
         if gname:
             with open(os.path.join(ROOT, "tests", "golden", f"fullrank_{gname}.json")) as f:
                 g = json.load(f)
@@ -981,6 +986,7 @@ def cpu_baseline(x, y):
     per-phase split (Assembly = ordering + compression, Factor, Solve, Det.)."""
     import os
     import oracle as O
+    from paper_1403_6015_gb300 import inputs as I
     cores = os.cpu_count() or 1
     O.set_num_threads(0)
     threads = O.num_threads()
@@ -1007,13 +1013,26 @@ def cpu_baseline(x, y):
         O.Hodlr(x, kern, [ell, 1.0], SIGMA2, LEAF, EPS).loglik(y)
     d1 = time.perf_counter() - t0
     O.set_num_threads(0)
+    # a dense-limit sample: the d = 4 Gaussian row's cube at n = 1200 (every level of full or
+    # nearly full rank), one build + factor + solve + log det; the GPU's time on the same
+    # case is in the supplementary dense_limit_rows
+    xd = I.uniform_points(DENSE_SAMPLE_N, 4, -3.0, 3.0, 2100)
+    yd = I.normal(DENSE_SAMPLE_N, 2101)
+    t0 = time.perf_counter()
+    hd = O.Hodlr(xd, "se", [0.5 ** 0.5, 1.0], 2.0, LEAF, EPS, max_rank=DENSE_SAMPLE_N // 2)
+    hd.factor_solve(yd)
+    hd.logdet()
+    dd = time.perf_counter() - t0
     return {"value": len(KERNELS) / dt, "unit": "evals/s", "cores": threads,
             "kind": "oracle", "sample": "one full step: one loglik per kernel at n=2^20 "
                                         f"({dt:.1f} s on {threads} threads)",
             "cpu_model": cpu_model(), "host_cores": cores,
             "single_thread": {"value": len(KERNELS) / d1, "unit": "evals/s", "cores": 1,
                               "sample": f"the same step on one thread ({d1:.1f} s)"},
-            "phases_all_cores": phases}
+            "phases_all_cores": phases,
+            "dense_limit_sample": {"seconds": dd, "cores": threads,
+                                   "sample": f"C = 2I + exp(-r^2), n = {DENSE_SAMPLE_N} points uniform in "
+                                             "[-3, 3]^4, leaf 128, eps 1e-12: build, factor, solve, log det"}}
 
 
 def run_reference(args):

@@ -1031,15 +1031,32 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_wide(AcaArgs a, int ite
       out[3] = nv2;
     }
   }
-  __syncthreads();
+  // u_l.u and v_l.v over this tile's rows: kAcaThreads values of l at a time, their columns
+  // staged through shared memory (each warp loads whole 32-row columns, coalesced), then
+  // thread l sums its column in row order
+  extern __shared__ double tile[];  // kAcaThreads x (kWideTile + 1)
+  constexpr int kLd = kWideTile + 1;
   const int tu = min(kWideTile, ml - start), tv = min(kWideTile, mr - start);
-  for (int l = threadIdx.x; l < k; l += kAcaThreads) {
-    double du = 0.0, dv = 0.0;
-    const int64_t col = (int64_t)l * n;
-    for (int q = 0; q < tu; ++q) du += rld<kFF>(raw, col + bl + start + q) * us[q];
-    for (int q = 0; q < tv; ++q) dv += rld<kFF>(raw, col + br + start + q) * vs[q];
-    out[4 + l] = du;
-    out[4 + a.max_rank + l] = dv;
+  for (int lb = 0; lb < k; lb += kAcaThreads) {
+    const int nl = min(kAcaThreads, k - lb);
+    const int l = lb + threadIdx.x;
+    __syncthreads();
+    for (int ll = w; ll < nl; ll += kW)
+      tile[ll * kLd + lane] = lane < tu ? rld<kFF>(raw, (int64_t)(lb + ll) * n + bl + start + lane) : 0.0;
+    __syncthreads();
+    double du = 0.0;
+    if (threadIdx.x < nl)
+      for (int q = 0; q < tu; ++q) du += tile[threadIdx.x * kLd + q] * us[q];
+    __syncthreads();
+    for (int ll = w; ll < nl; ll += kW)
+      tile[ll * kLd + lane] = lane < tv ? rld<kFF>(raw, (int64_t)(lb + ll) * n + br + start + lane) : 0.0;
+    __syncthreads();
+    if (threadIdx.x < nl) {
+      double dv = 0.0;
+      for (int q = 0; q < tv; ++q) dv += tile[threadIdx.x * kLd + q] * vs[q];
+      out[4 + l] = du;
+      out[4 + a.max_rank + l] = dv;
+    }
   }
 }
 
@@ -1207,6 +1224,14 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   const int64_t nsmall = c.n_items - nbig - nwide, small0 = nbig + nwide;
   const unsigned sgrid = (unsigned)((nsmall + kAcaThreads / 32 - 1) / (kAcaThreads / 32));
   const size_t smem_row = 0, smem_col = 0;  // static, independent of the rank
+  // the wide column kernel's dot-product tile: kAcaThreads columns of kWideTile + 1 doubles
+  const size_t smem_wide = sizeof(double) * kAcaThreads * (kWideTile + 1);
+  if (nwide > 0) {
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col_wide<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide));
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col_wide<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide));
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col_wide<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide));
+    HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col_wide<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide));
+  }
   // adaptive: until no block is active (host check per step); presized: a fixed number of
   // steps (rank + 1 per block, one spare for a zero pivot) and a device-side check
   int max_steps = c.presized ? maxpre + 2 : 2 * c.max_rank + 4;
@@ -1232,7 +1257,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
       ++c.launches;
     }
     if (nwide > 0) {
-      ACA_LAUNCH(k_aca_col_wide, (unsigned)nwide, 0, a, (int)nbig);
+      ACA_LAUNCH(k_aca_col_wide, (unsigned)nwide, smem_wide, a, (int)nbig);
       ++c.launches;
     }
     if (nsmall > 0) {
