@@ -881,6 +881,7 @@ __global__ void k_aca_pivot_col(AcaArgs a) {
 // both forms (the mixed form's double-float columns are converted on load and store).
 static_assert(kWideTile == 32, "one row of a wide item per lane");
 constexpr int kCrossL = 128;  // l values per CTA of the wide cross term
+constexpr int kWideThreads = 512;  // CTA of the wide row and column kernels (16 warps)
 
 template <bool kFF>
 __device__ __forceinline__ double rld(const double* raw, int64_t i) {
@@ -908,8 +909,8 @@ __device__ __forceinline__ double entry_wide(const AcaArgs& a, const Cov& cov, i
 
 // A for a wide item: residual row entries b = start + lane of the right child.
 template <bool kFF, bool kGen>
-__global__ void __launch_bounds__(kAcaThreads) k_aca_row_wide(AcaArgs a, int item0) {
-  constexpr int kW = kAcaThreads / 32;
+__global__ void __launch_bounds__(kWideThreads) k_aca_row_wide(AcaArgs a, int item0) {
+  constexpr int kW = kWideThreads / 32;
   const int item = item0 + blockIdx.x;
   const int id = a.item_node[item];
   if (a.done[id]) return;
@@ -919,7 +920,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row_wide(AcaArgs a, int ite
   const Cov cov = cov_from(a.kind, a.hyp);
   CovFF cf{};
   if (kFF) {
-    for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
+    for (int q = threadIdx.x; q < 64; q += kWideThreads) tab[q] = a.tab[q];
     cf = load_cov_ff(a.kind, a.hyp);
   }
   const int k = a.rank[id], i = a.row[id];
@@ -932,7 +933,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row_wide(AcaArgs a, int ite
   for (int l0 = 0; l0 < k; l0 += kRankChunk) {
     const int l1 = min(k, l0 + kRankChunk);
     __syncthreads();
-    for (int l = l0 + threadIdx.x; l < l1; l += kAcaThreads) uik[l - l0] = rld<kFF>(raw, l * n + bl + i);
+    for (int l = l0 + threadIdx.x; l < l1; l += kWideThreads) uik[l - l0] = rld<kFF>(raw, l * n + bl + i);
     __syncthreads();
     if (b < mr)
       for (int l = l0 + w; l < l1; l += kW) acc += uik[l - l0] * rld<kFF>(raw, l * n + br + b);
@@ -958,8 +959,8 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_row_wide(AcaArgs a, int ite
 // C for a wide item: rows t = start + lane of u (left child) and of v (right child), their
 // norms and unused-row argmax, then the tile's u_l.u and v_l.v for every l < k.
 template <bool kFF, bool kGen>
-__global__ void __launch_bounds__(kAcaThreads) k_aca_col_wide(AcaArgs a, int item0) {
-  constexpr int kW = kAcaThreads / 32;
+__global__ void __launch_bounds__(kWideThreads) k_aca_col_wide(AcaArgs a, int item0) {
+  constexpr int kW = kWideThreads / 32;
   const int item = item0 + blockIdx.x;
   const int id = a.item_node[item];
   if (a.done[id] || !a.phase[id]) return;
@@ -972,7 +973,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_wide(AcaArgs a, int ite
   const Cov cov = cov_from(a.kind, a.hyp);
   CovFF cf{};
   if (kFF) {
-    for (int q = threadIdx.x; q < 64; q += kAcaThreads) tab[q] = a.tab[q];
+    for (int q = threadIdx.x; q < 64; q += kWideThreads) tab[q] = a.tab[q];
     cf = load_cov_ff(a.kind, a.hyp);
   }
   const int k = a.rank[id], j = a.col[id];
@@ -989,7 +990,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_wide(AcaArgs a, int ite
   for (int s0 = 0; s0 < nu; s0 += kUsedChunk) {
     const int s1 = min(nu - s0, kUsedChunk);
     __syncthreads();
-    for (int q = threadIdx.x; q < s1; q += kAcaThreads) used_s[q] = a.used[(int64_t)id * a.used_stride + s0 + q];
+    for (int q = threadIdx.x; q < s1; q += kWideThreads) used_s[q] = a.used[(int64_t)id * a.used_stride + s0 + q];
     __syncthreads();
     bool f = false;
     for (int q = w; q < s1; q += kW) f |= used_s[q] == t;
@@ -999,7 +1000,7 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_wide(AcaArgs a, int ite
   for (int l0 = 0; l0 < k; l0 += kRankChunk) {
     const int l1 = min(k, l0 + kRankChunk);
     __syncthreads();
-    for (int l = l0 + threadIdx.x; l < l1; l += kAcaThreads) vjk[l - l0] = rld<kFF>(raw, l * n + br + j);
+    for (int l = l0 + threadIdx.x; l < l1; l += kWideThreads) vjk[l - l0] = rld<kFF>(raw, l * n + br + j);
     __syncthreads();
     if (t < ml)
       for (int l = l0 + w; l < l1; l += kW) acc += rld<kFF>(raw, l * n + bl + t) * vjk[l - l0];
@@ -1031,14 +1032,14 @@ __global__ void __launch_bounds__(kAcaThreads) k_aca_col_wide(AcaArgs a, int ite
       out[3] = nv2;
     }
   }
-  // u_l.u and v_l.v over this tile's rows: kAcaThreads values of l at a time, their columns
+  // u_l.u and v_l.v over this tile's rows: kWideThreads values of l at a time, their columns
   // staged through shared memory (each warp loads whole 32-row columns, coalesced), then
   // thread l sums its column in row order
-  extern __shared__ double tile[];  // kAcaThreads x (kWideTile + 1)
+  extern __shared__ double tile[];  // kWideThreads x (kWideTile + 1)
   constexpr int kLd = kWideTile + 1;
   const int tu = min(kWideTile, ml - start), tv = min(kWideTile, mr - start);
-  for (int lb = 0; lb < k; lb += kAcaThreads) {
-    const int nl = min(kAcaThreads, k - lb);
+  for (int lb = 0; lb < k; lb += kWideThreads) {
+    const int nl = min(kWideThreads, k - lb);
     const int l = lb + threadIdx.x;
     __syncthreads();
     for (int ll = w; ll < nl; ll += kW)
@@ -1166,20 +1167,21 @@ __global__ void k_pack(PackArgs p) {
 
 // Launch K<kFF, kGen> for the context's form (double-float or FP64) and case (gen: any d
 // and kind; else the kernels specialised for d <= 2 and Table 1's covariances).
-#define ACA_LAUNCH(K, grid, smem, ...)                                               \
+#define ACA_LAUNCH_T(K, grid, threads, smem, ...)                                    \
   do {                                                                               \
     if (c.precision == 1) {                                                          \
       if (gen)                                                                       \
-        K<true, true><<<grid, kAcaThreads, smem, c.stream>>>(__VA_ARGS__);           \
+        K<true, true><<<grid, threads, smem, c.stream>>>(__VA_ARGS__);               \
       else                                                                           \
-        K<true, false><<<grid, kAcaThreads, smem, c.stream>>>(__VA_ARGS__);          \
+        K<true, false><<<grid, threads, smem, c.stream>>>(__VA_ARGS__);              \
     } else {                                                                         \
       if (gen)                                                                       \
-        K<false, true><<<grid, kAcaThreads, smem, c.stream>>>(__VA_ARGS__);          \
+        K<false, true><<<grid, threads, smem, c.stream>>>(__VA_ARGS__);              \
       else                                                                           \
-        K<false, false><<<grid, kAcaThreads, smem, c.stream>>>(__VA_ARGS__);         \
+        K<false, false><<<grid, threads, smem, c.stream>>>(__VA_ARGS__);             \
     }                                                                                \
   } while (0)
+#define ACA_LAUNCH(K, grid, smem, ...) ACA_LAUNCH_T(K, grid, kAcaThreads, smem, __VA_ARGS__)
 
 cudaError_t launch_aca(Ctx& c, int* steps_out) {
   int nint = (1 << c.kappa) - 1;
@@ -1224,8 +1226,8 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   const int64_t nsmall = c.n_items - nbig - nwide, small0 = nbig + nwide;
   const unsigned sgrid = (unsigned)((nsmall + kAcaThreads / 32 - 1) / (kAcaThreads / 32));
   const size_t smem_row = 0, smem_col = 0;  // static, independent of the rank
-  // the wide column kernel's dot-product tile: kAcaThreads columns of kWideTile + 1 doubles
-  const size_t smem_wide = sizeof(double) * kAcaThreads * (kWideTile + 1);
+  // the wide column kernel's dot-product tile: kWideThreads columns of kWideTile + 1 doubles
+  const size_t smem_wide = sizeof(double) * kWideThreads * (kWideTile + 1);
   if (nwide > 0) {
     HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col_wide<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide));
     HODLR_CUDA_TRY(cudaFuncSetAttribute(k_aca_col_wide<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide));
@@ -1244,7 +1246,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
       ++c.launches;
     }
     if (nwide > 0) {
-      ACA_LAUNCH(k_aca_row_wide, (unsigned)nwide, 0, a, (int)nbig);
+      ACA_LAUNCH_T(k_aca_row_wide, (unsigned)nwide, kWideThreads, 0, a, (int)nbig);
       ++c.launches;
     }
     if (nsmall > 0) {
@@ -1257,7 +1259,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
       ++c.launches;
     }
     if (nwide > 0) {
-      ACA_LAUNCH(k_aca_col_wide, (unsigned)nwide, smem_wide, a, (int)nbig);
+      ACA_LAUNCH_T(k_aca_col_wide, (unsigned)nwide, kWideThreads, smem_wide, a, (int)nbig);
       ++c.launches;
     }
     if (nsmall > 0) {
