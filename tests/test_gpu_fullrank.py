@@ -160,3 +160,42 @@ def test_barrier_timeout_reports_etimeout(H, monkeypatch):
     ld_d, sol_d = dense_chol(x, y)
     assert rel(h.logdet(), ld_d) <= 1e-12
     np.testing.assert_allclose(sol, sol_d, rtol=0, atol=1e-11 * np.abs(sol_d).max())
+
+
+def test_full_rank_sweep_and_batched_lanes(H):
+    """The graph-captured hyperparameter sweep and the batched lanes on a full-rank problem
+    (scaled d = 8 cube, blocks of full rank 500): the captured evaluations include the
+    cooperative LU panel launches. Presized to the full rank (max_rank n/2 + 1 allows it),
+    every setting must report status 0 and equal the adaptive log-likelihood."""
+    torch = pytest.importorskip("torch")
+    n, d = 1000, 8
+    x = I.uniform_points(n, d, -3.0 / np.sqrt(8.0), 3.0 / np.sqrt(8.0), 2130)
+    y = I.normal(n, 2131)
+    ells = np.array([0.6, ELL, 0.8, 0.9])
+    s2s = np.array([2.0, 2.0, 1.5, 1.0])
+    mr = n // 2 + 1
+    ref = np.array([H.Hodlr(x, "se", [e, 1.0], s2, 128, EPS, max_rank=mr).loglik(y)
+                    for e, s2 in zip(ells, s2s)])
+    th = torch.tensor(np.stack([ells, np.ones(4)], 1), dtype=torch.float64, device="cuda")
+    sg = torch.tensor(s2s, dtype=torch.float64, device="cuda")
+    yd = torch.tensor(y, dtype=torch.float64, device="cuda")
+
+    def presized():
+        h = H.Hodlr(x, "se", [ells[0], 1.0], s2s[0], 128, EPS, max_rank=mr,
+                    stream=torch.cuda.Stream().cuda_stream)
+        h.presize(np.array([min(int(v), mr - 1) for v in h.level_ranks()], dtype=np.int32))
+        return h
+
+    h = presized()
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    out = h.loglik_sweep(th, sg, yd, status=st)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all(), st
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=0)
+    ctxs = [presized() for _ in range(2)]
+    out2 = torch.zeros(4, dtype=torch.float64, device="cuda")
+    st2 = torch.zeros(4, dtype=torch.int32, device="cuda")
+    H.loglik_batched(ctxs, th, sg, yd, out2, st2, stream=torch.cuda.Stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert (st2.cpu().numpy() == 0).all(), st2
+    np.testing.assert_allclose(out2.cpu().numpy(), ref, rtol=1e-12, atol=0)
