@@ -310,3 +310,23 @@ def test_nrhs16_full_size_every_column(H, precision):
     for c in range(nrhs):
         err = np.linalg.norm(sol[perm, c] - sol_c[:, c]) / np.linalg.norm(sol_c[:, c])
         assert err <= 1e-9, (c, err)
+
+
+@pytest.mark.parametrize("kern,ell", [("exp", 0.002), ("se", 0.003), ("matern32", 0.02), ("matern52", 0.02)])
+def test_fp64_covariance_entries_to_the_last_bits(H, kern, ell):
+    """The FP64 covariances evaluate exp by a table-driven method of their own (Tang's, one
+    unit in the last place). On a single-leaf problem C v is the dense product of those
+    entries with v, so it must match the oracle's dense rows (libm exp, compensated sums) to
+    a few units of roundoff in sum |C_ij v_j|. The short length scales take the arguments
+    of exp from 0 down past -745, through the subnormal range into underflow."""
+    n = 128
+    x = np.sort(I.uniform_points(n, 1, -1.0, 1.0, 2200 + len(kern)).reshape(-1))
+    v = I.normal(n, 2201)
+    s2 = 1e-2
+    h = H.Hodlr(x, kern, [ell, 1.0], s2, 128, 1e-12)
+    assert h.tree()[0] == 0  # one leaf: every entry is evaluated, nothing compressed
+    got = h.matvec(v)
+    ref = O.dense_matvec_rows(x, kern, [ell, 1.0], s2, v, np.arange(n))
+    C = O.kernel_values(kern, np.abs(x[:, None] - x[None, :]), ell, 1.0)
+    scale = np.abs(C) @ np.abs(v) + s2 * np.abs(v)
+    assert np.all(np.abs(got - ref) <= 8 * 2.0 ** -52 * scale), np.max(np.abs(got - ref) / scale)
