@@ -1154,6 +1154,55 @@ def dense_3d_column(sizes=(20000, 50000, 100000)):
     print(json.dumps({"dense_3d_column": out}))
 
 
+def dimension_tables(n=5000, dims=(1, 2, 4, 8, 16, 32, 64)):
+    """The paper's two d-dimensional Gaussian tables (Sec. 5: C = 2I + exp(-r^2), n = 5000,
+    points uniform in the unscaled cube [-3, 3]^d and in the scaled cube
+    [-3/sqrt(d), 3/sqrt(d)]^d), FP64 form, leaf 128, eps 1e-12, max_rank n/2: assembly,
+    factor, solve and det timed per call, log det against dense Cholesky (LAPACK)."""
+    import scipy.linalg as sl
+    from scipy.spatial.distance import cdist
+    from paper_1403_6015_gb300 import hodlr as H
+    from paper_1403_6015_gb300 import inputs as I
+    paper = {"unscaled": {1: [0.02, 0.087, 0.002, 0.001], 2: [1.17, 2.043, 0.027, 0.014],
+                          4: [9.67, 21.25, 0.073, 0.088], 8: [10.4, 7.773, 0.041, 0.039],
+                          16: [0.09, 0.168, 0.002, 0.002], 32: [0.15, 0.061, 0.004, 0.001],
+                          64: [0.21, 0.059, 0.001, 0.001]},
+             "scaled": {1: [0.02, 0.087, 0.002, 0.001], 2: [0.70, 1.157, 0.017, 0.005],
+                        4: [33.6, 108.2, 0.165, 0.360], 8: [40.8, 138.4, 0.186, 0.359],
+                        16: [41.9, 138.7, 0.182, 0.358], 32: [43.4, 174.1, 0.174, 0.354],
+                        64: [42.2, 142.2, 0.181, 0.346]}}
+    out = {}
+    # one build first, so that no row carries the process's first-use set-up
+    H.Hodlr(I.uniform_points(n, 1, -3.0, 3.0, 2400), "se", [0.5 ** 0.5, 1.0], 2.0, LEAF, EPS).close()
+    for table in ["unscaled", "scaled"]:
+        out[table] = {}
+        for d in dims:
+            half = 3.0 if table == "unscaled" else 3.0 / np.sqrt(d)
+            x = I.uniform_points(n, d, -half, half, 2400 + d)
+            y = I.normal(n, 2401)
+            t0 = time.perf_counter()
+            h = H.Hodlr(x, "se", [0.5 ** 0.5, 1.0], 2.0, LEAF, EPS, max_rank=n // 2)
+            t1 = time.perf_counter()
+            h.factor()
+            t2 = time.perf_counter()
+            h.solve(y)
+            t3 = time.perf_counter()
+            ld = h.logdet()
+            t4 = time.perf_counter()
+            kap, _ = h.tree()
+            rk = h.ranks()
+            h.close()
+            C = np.exp(-cdist(x, x, "sqeuclidean"))
+            C[np.diag_indices_from(C)] += 2.0
+            ldd = 2.0 * np.log(np.diag(sl.cho_factor(C, lower=True)[0])).sum()
+            out[table][str(d)] = {
+                "assembly_s": t1 - t0, "factor_s": t2 - t1, "solve_s": t3 - t2, "det_s": t4 - t3,
+                "total_s": t4 - t0, "logdet_rel_err_vs_dense": abs(ld - ldd) / abs(ldd),
+                "level_max_rank": [int(rk[(1 << j) - 1:(1 << (j + 1)) - 1].max()) for j in range(kap)],
+                "paper_s (laptop, one core)": dict(zip(["assembly", "factor", "solve", "det"], paper[table][d]))}
+    print(json.dumps({"dimension_tables": out}))
+
+
 def main():
     global N, COMPRESSION
     ap = argparse.ArgumentParser()
@@ -1172,6 +1221,8 @@ def main():
                     help="-1: both forms (default), 0: FP64 only, 1: mixed only")
     ap.add_argument("--compression", default="aca", choices=["aca", "chebyshev"],
                     help="compression of the timed evaluations (profiling captures)")
+    ap.add_argument("--dimension-tables", action="store_true",
+                    help="the d-dimensional Gaussian tables at n = 5000, d = 1 ... 64 (about a minute)")
     ap.add_argument("--dense-3d-column", action="store_true",
                     help="the 3-D Gaussian column at n = 20 000, 50 000, 100 000 (about a minute)")
     ap.add_argument("--profile-dense-row", choices=["d3", "d4"], default=None,
@@ -1184,6 +1235,11 @@ def main():
     COMPRESSION = args.compression
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.dimension_tables:
+        from paper_1403_6015_gb300 import build_lib
+        build_lib.build()
+        dimension_tables()
+        return
     if args.dense_3d_column:
         from paper_1403_6015_gb300 import build_lib
         build_lib.build()
