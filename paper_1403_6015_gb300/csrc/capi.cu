@@ -683,8 +683,8 @@ hodlr_status hodlr_factor_solve(hodlr_ctx* ctx, const double* y, double* x, int 
   if (!y || !x || nrhs < 1 || nrhs > c->max_nrhs || ld < c->n)
     return fail(c, HODLR_EINVAL, "factor_solve: bad y/x/nrhs/ld");
   if (c->factored) return fail(c, HODLR_ESTATE, "already factored (rebuild first)");
-  const double* yd;
-  int64_t ldd;
+  const double* yd = nullptr;
+  int64_t ldd = 0;
   hodlr_status s = stage_in(c, y, nrhs, ld, &yd, &ldd);
   if (s != HODLR_OK) return s;
   TRY_CUDA(c, gather_rhs(c, yd, ldd, nrhs), "gather");
@@ -702,8 +702,8 @@ hodlr_status hodlr_solve(hodlr_ctx* ctx, const double* y, double* x, int nrhs, i
   if (!y || !x || nrhs < 1 || ld < c->n) return fail(c, HODLR_EINVAL, "solve: bad y/x/nrhs/ld");
   for (int c0 = 0; c0 < nrhs; c0 += c->max_nrhs) {
     int nb = std::min(c->max_nrhs, nrhs - c0);
-    const double* yd;
-    int64_t ldd;
+    const double* yd = nullptr;
+    int64_t ldd = 0;
     hodlr_status s = stage_in(c, y + (int64_t)c0 * ld, nb, ld, &yd, &ldd);
     if (s != HODLR_OK) return s;
     cudaEventRecord(c->ev[4], c->stream);
@@ -753,8 +753,8 @@ hodlr_status hodlr_loglik(hodlr_ctx* ctx, const double* y, double* out) {
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!c || !y || !out) return HODLR_EINVAL;
   if (c->indefinite) return fail(c, HODLR_EINVAL, "loglik: the kernel's C is indefinite (not a covariance)");
-  const double* yd;
-  int64_t ldd;
+  const double* yd = nullptr;
+  int64_t ldd = 0;
   hodlr_status s = stage_in(c, y, 1, c->n, &yd, &ldd);
   if (s != HODLR_OK) return s;
   TRY_CUDA(c, gather_rhs(c, yd, ldd, 1), "gather");
@@ -1201,8 +1201,8 @@ hodlr_status hodlr_matvec(hodlr_ctx* ctx, const double* x, double* y) {
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!c || !x || !y) return HODLR_EINVAL;
   if (!c->compressed) return fail(c, HODLR_ESTATE, "matvec before build");
-  const double* xd;
-  int64_t ldd;
+  const double* xd = nullptr;
+  int64_t ldd = 0;
   hodlr_status s = stage_in(c, x, 1, c->n, &xd, &ldd);
   if (s != HODLR_OK) return s;
   // sorted x into ysort, product into Y[:, 0], then back to caller order
@@ -1251,8 +1251,8 @@ hodlr_status hodlr_autotune(hodlr_ctx* ctx, const double* y, int reps, hodlr_tun
   if (!c || !y || reps < 1 || reps > 100) return HODLR_EINVAL;
   if (!c->compressed) return fail(c, HODLR_ESTATE, "autotune: compress (build or rebuild) first");
   if (capturing(c)) return fail(c, HODLR_ESTATE, "autotune: not under stream capture");
-  const double* yd;
-  int64_t ldd;
+  const double* yd = nullptr;
+  int64_t ldd = 0;
   hodlr_status s = stage_in(c, y, 1, c->n, &yd, &ldd);
   if (s != HODLR_OK) return s;
   // candidates: (leaf_threads, leaf_kernel); the tensor-core leaf kernel has one CTA size
@@ -1339,8 +1339,8 @@ hodlr_status hodlr_predict(hodlr_ctx* ctx, const double* xtest, int64_t m, const
   auto run = [&]() -> hodlr_status {
     TRY_CUDA(c, cudaMemcpyAsync(xt, xtest, sizeof(double) * m * c->d, cudaMemcpyDefault, c->stream), "xtest");
     // alpha = C^-1 y with the stored factor (tree order)
-    const double* yd;
-    int64_t ldd;
+    const double* yd = nullptr;
+    int64_t ldd = 0;
     hodlr_status s = stage_in(c, y, 1, c->n, &yd, &ldd);
     if (s != HODLR_OK) return s;
     TRY_CUDA(c, hodlr::launch_gather_rhs(*c, yd, ldd, 1), "gather");

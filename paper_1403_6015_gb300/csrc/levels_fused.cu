@@ -17,10 +17,10 @@
 namespace hodlr {
 namespace {
 
-// Tile shapes of the fused sweep: leaves per block and threads per block.
+// Tile shapes of the fused sweep: leaves per block (kTileG); the threads per block of
+// shapes 0..6 are 256, 128, 256, 512, 64, 64 and 128 (the launch switch below).
 constexpr int kSweepTiles = 7;
 constexpr int kTileG[kSweepTiles] = {4, 2, 8, 8, 2, 1, 1};
-constexpr int kTileT[kSweepTiles] = {256, 128, 256, 512, 64, 64, 128};
 
 struct FusedArgs {
   const int32_t* nb;
