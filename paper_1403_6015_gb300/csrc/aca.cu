@@ -876,9 +876,10 @@ __global__ void k_aca_pivot_col(AcaArgs a) {
 // ---- wide nodes: rank cap above kWideRank ----------------------------------------------
 // Work items of kWideTile rows, so that a block of a top-level node spreads over many CTAs.
 // The sum over the cross's earlier vectors is split over the warps (warp w takes l = w,
-// w + 8, ...; the eight partial sums are added in warp order); the dot products u_l.u and
-// v_l.v of a tile run with threads over l and the tile's rows in order. FP64 arithmetic in
-// both forms (the mixed form's double-float columns are converted on load and store).
+// w + 8, ...; the warps' partial sums are added in warp order); the dot products u_l.u and
+// v_l.v of a tile run with threads over l and the tile's rows in order. The FP64 form
+// computes in FP64; the mixed form as its 1024-row kernels do: residuals in double-float
+// on the FP32 pipe, dot products and norms from the high words in FP32.
 static_assert(kWideTile == 32, "one row of a wide item per lane");
 constexpr int kCrossL = 128;  // l values per CTA of the wide cross term
 constexpr int kWideThreads = 512;  // CTA of the wide row and column kernels (16 warps)
@@ -929,30 +930,66 @@ __global__ void __launch_bounds__(kWideThreads) k_aca_row_wide(AcaArgs a, int it
   double* raw = a.raw + a.raw_off[level_of(id)];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = a.item_start[item] + lane;
-  double acc = 0.0;
-  for (int l0 = 0; l0 < k; l0 += kRankChunk) {
-    const int l1 = min(k, l0 + kRankChunk);
+  if constexpr (kFF) {
+    // mixed form: double-float sums on the FP32 pipe, the argmax on the high words (as in
+    // k_aca_row<true>); the pivot value is the stored double-float
+    const ff* rawf = reinterpret_cast<const ff*>(raw);
+    ff* uf = reinterpret_cast<ff*>(uik);
+    ff* rf = reinterpret_cast<ff*>(&red[0][0]);
+    ff acc = {0.0f, 0.0f};
+    for (int l0 = 0; l0 < k; l0 += kRankChunk) {
+      const int l1 = min(k, l0 + kRankChunk);
+      __syncthreads();
+      for (int l = l0 + threadIdx.x; l < l1; l += kWideThreads) uf[l - l0] = rawf[l * n + bl + i];
+      __syncthreads();
+      if (b < mr)
+        for (int l = l0 + w; l < l1; l += kW) acc = ff_fma(acc, uf[l - l0], rawf[l * n + br + b]);
+    }
+    rf[w * kWideTile + lane] = acc;
     __syncthreads();
-    for (int l = l0 + threadIdx.x; l < l1; l += kWideThreads) uik[l - l0] = rld<kFF>(raw, l * n + bl + i);
+    if (w != 0) return;
+    float bv = 0.0f;
+    int bi = -1;
+    if (b < mr) {
+      ff sum = rf[lane];
+      for (int q = 1; q < kW; ++q) sum = ff_add(sum, rf[q * kWideTile + lane]);
+      const ff v = ff_sub(block_entry_ff<kGen>(a, level_of(id), bl + i, br + b, tab, cf), sum);
+      reinterpret_cast<ff*>(raw)[(int64_t)k * n + br + b] = v;
+      amax_merge_f(bv, bi, v.hi, b);
+    }
+    warp_amax_f(bv, bi);
+    __syncwarp();  // the winning lane's store is visible to lane 0
+    if (lane == 0) {
+      a.part[(int64_t)item * a.part_stride + 0] = bi >= 0 ? ff_to_double(rawf[(int64_t)k * n + br + bi]) : 0.0;
+      a.part[(int64_t)item * a.part_stride + 1] = (double)bi;
+    }
+  } else {
+    double acc = 0.0;
+    for (int l0 = 0; l0 < k; l0 += kRankChunk) {
+      const int l1 = min(k, l0 + kRankChunk);
+      __syncthreads();
+      for (int l = l0 + threadIdx.x; l < l1; l += kWideThreads) uik[l - l0] = raw[l * n + bl + i];
+      __syncthreads();
+      if (b < mr)
+        for (int l = l0 + w; l < l1; l += kW) acc += uik[l - l0] * raw[l * n + br + b];
+    }
+    red[w][lane] = acc;
     __syncthreads();
-    if (b < mr)
-      for (int l = l0 + w; l < l1; l += kW) acc += uik[l - l0] * rld<kFF>(raw, l * n + br + b);
-  }
-  red[w][lane] = acc;
-  __syncthreads();
-  if (w != 0) return;
-  double bv = 0.0;
-  int bi = -1;
-  if (b < mr) {
-    double s = 0.0;
-    for (int q = 0; q < kW; ++q) s += red[q][lane];
-    const double v = rst<kFF>(raw, (int64_t)k * n + br + b, entry_wide<kFF, kGen>(a, cov, id, bl + i, br + b, tab, cf) - s);
-    amax_merge(bv, bi, v, b);
-  }
-  warp_amax(bv, bi);
-  if (lane == 0) {
-    a.part[(int64_t)item * a.part_stride + 0] = bv;
-    a.part[(int64_t)item * a.part_stride + 1] = (double)bi;
+    if (w != 0) return;
+    double bv = 0.0;
+    int bi = -1;
+    if (b < mr) {
+      double s = 0.0;
+      for (int q = 0; q < kW; ++q) s += red[q][lane];
+      const double v = block_entry<false, kGen>(a, cov, bl + i, br + b, tab, cf) - s;
+      raw[(int64_t)k * n + br + b] = v;
+      amax_merge(bv, bi, v, b);
+    }
+    warp_amax(bv, bi);
+    if (lane == 0) {
+      a.part[(int64_t)item * a.part_stride + 0] = bv;
+      a.part[(int64_t)item * a.part_stride + 1] = (double)bi;
+    }
   }
 }
 
@@ -996,67 +1033,146 @@ __global__ void __launch_bounds__(kWideThreads) k_aca_col_wide(AcaArgs a, int it
     for (int q = w; q < s1; q += kW) f |= used_s[q] == t;
     if (f) isu_s[lane] = 1;
   }
-  double acc = 0.0;
-  for (int l0 = 0; l0 < k; l0 += kRankChunk) {
-    const int l1 = min(k, l0 + kRankChunk);
-    __syncthreads();
-    for (int l = l0 + threadIdx.x; l < l1; l += kWideThreads) vjk[l - l0] = rld<kFF>(raw, l * n + br + j);
-    __syncthreads();
-    if (t < ml)
-      for (int l = l0 + w; l < l1; l += kW) acc += rld<kFF>(raw, l * n + bl + t) * vjk[l - l0];
-  }
-  red[w][lane] = acc;
-  __syncthreads();
-  double* out = a.part + (int64_t)item * a.part_stride;
-  if (w == 0) {
-    double u = 0.0, v = 0.0, bv = 0.0;
-    int bi = -1;
-    if (t < ml) {
-      double s = 0.0;
-      for (int q = 0; q < kW; ++q) s += red[q][lane];
-      u = rst<kFF>(raw, (int64_t)k * n + bl + t, entry_wide<kFF, kGen>(a, cov, id, bl + t, br + j, tab, cf) - s);
-      if (!isu_s[lane]) amax_merge(bv, bi, u, t);
+  if constexpr (kFF) {
+    // mixed form: the residual column in double-float on the FP32 pipe, the norms and the
+    // dot products from the high words in FP32 (combined in FP64 by the norm update), the
+    // argmax on the high words: as in k_aca_col<true>
+    const ff* rawf = reinterpret_cast<const ff*>(raw);
+    ff* vf = reinterpret_cast<ff*>(vjk);
+    ff* rf = reinterpret_cast<ff*>(&red[0][0]);
+    __shared__ ff inv_s;  // 1 / delta, converted by one thread (FP64 pipe)
+    __shared__ float ush[kWideTile], vsh[kWideTile];
+    if (threadIdx.x == 0) inv_s = ff_rcp(ff_from_double(delta));
+    ff acc = {0.0f, 0.0f};
+    for (int l0 = 0; l0 < k; l0 += kRankChunk) {
+      const int l1 = min(k, l0 + kRankChunk);
+      __syncthreads();
+      for (int l = l0 + threadIdx.x; l < l1; l += kWideThreads) vf[l - l0] = rawf[l * n + br + j];
+      __syncthreads();
+      if (t < ml)
+        for (int l = l0 + w; l < l1; l += kW) acc = ff_fma(acc, rawf[l * n + bl + t], vf[l - l0]);
     }
-    if (t < mr) {
-      const int64_t e = (int64_t)k * n + br + t;
-      v = rst<kFF>(raw, e, rld<kFF>(raw, e) * (1.0 / delta));
+    rf[w * kWideTile + lane] = acc;
+    __syncthreads();
+    double* out = a.part + (int64_t)item * a.part_stride;
+    if (w == 0) {
+      float uh = 0.0f, vh = 0.0f, bv = 0.0f;
+      int bi = -1;
+      if (t < ml) {
+        ff sum = rf[lane];
+        for (int q = 1; q < kW; ++q) sum = ff_add(sum, rf[q * kWideTile + lane]);
+        const ff u = ff_sub(block_entry_ff<kGen>(a, level_of(id), bl + t, br + j, tab, cf), sum);
+        reinterpret_cast<ff*>(raw)[(int64_t)k * n + bl + t] = u;
+        uh = u.hi;
+        if (!isu_s[lane]) amax_merge_f(bv, bi, u.hi, t);
+      }
+      if (t < mr) {
+        const int64_t e = (int64_t)k * n + br + t;
+        const ff v = ff_mul(rawf[e], inv_s);
+        reinterpret_cast<ff*>(raw)[e] = v;
+        vh = v.hi;
+      }
+      ush[lane] = uh;
+      vsh[lane] = vh;
+      const double nu2 = warp_sum((double)(uh * uh)), nv2 = warp_sum((double)(vh * vh));
+      warp_amax_f(bv, bi);
+      if (lane == 0) {
+        out[0] = bv;
+        out[1] = (double)bi;
+        out[2] = nu2;
+        out[3] = nv2;
+      }
     }
-    us[lane] = u;
-    vs[lane] = v;
-    const double nu2 = warp_sum(u * u), nv2 = warp_sum(v * v);
-    warp_amax(bv, bi);
-    if (lane == 0) {
-      out[0] = bv;
-      out[1] = (double)bi;
-      out[2] = nu2;
-      out[3] = nv2;
+    // u_l.u and v_l.v from the high words: the tile's columns staged as FP32 (coalesced
+    // 32-row loads), thread l summing its column in row order
+    extern __shared__ double tile[];
+    float* tf = reinterpret_cast<float*>(tile);
+    constexpr int kLd = kWideTile + 1;
+    const int tu = min(kWideTile, ml - start), tv = min(kWideTile, mr - start);
+    for (int lb = 0; lb < k; lb += kWideThreads) {
+      const int nl = min(kWideThreads, k - lb);
+      const int l = lb + threadIdx.x;
+      __syncthreads();
+      for (int ll = w; ll < nl; ll += kW)
+        tf[ll * kLd + lane] = lane < tu ? rawf[(int64_t)(lb + ll) * n + bl + start + lane].hi : 0.0f;
+      __syncthreads();
+      float du = 0.0f;
+      if (threadIdx.x < nl)
+        for (int q = 0; q < tu; ++q) du += tf[threadIdx.x * kLd + q] * ush[q];
+      __syncthreads();
+      for (int ll = w; ll < nl; ll += kW)
+        tf[ll * kLd + lane] = lane < tv ? rawf[(int64_t)(lb + ll) * n + br + start + lane].hi : 0.0f;
+      __syncthreads();
+      if (threadIdx.x < nl) {
+        float dv = 0.0f;
+        for (int q = 0; q < tv; ++q) dv += tf[threadIdx.x * kLd + q] * vsh[q];
+        out[4 + l] = du;
+        out[4 + a.max_rank + l] = dv;
+      }
     }
-  }
-  // u_l.u and v_l.v over this tile's rows: kWideThreads values of l at a time, their columns
-  // staged through shared memory (each warp loads whole 32-row columns, coalesced), then
-  // thread l sums its column in row order
-  extern __shared__ double tile[];  // kWideThreads x (kWideTile + 1)
-  constexpr int kLd = kWideTile + 1;
-  const int tu = min(kWideTile, ml - start), tv = min(kWideTile, mr - start);
-  for (int lb = 0; lb < k; lb += kWideThreads) {
-    const int nl = min(kWideThreads, k - lb);
-    const int l = lb + threadIdx.x;
+  } else {
+    double acc = 0.0;
+    for (int l0 = 0; l0 < k; l0 += kRankChunk) {
+      const int l1 = min(k, l0 + kRankChunk);
+      __syncthreads();
+      for (int l = l0 + threadIdx.x; l < l1; l += kWideThreads) vjk[l - l0] = rld<false>(raw, l * n + br + j);
+      __syncthreads();
+      if (t < ml)
+        for (int l = l0 + w; l < l1; l += kW) acc += rld<false>(raw, l * n + bl + t) * vjk[l - l0];
+    }
+    red[w][lane] = acc;
     __syncthreads();
-    for (int ll = w; ll < nl; ll += kW)
-      tile[ll * kLd + lane] = lane < tu ? rld<kFF>(raw, (int64_t)(lb + ll) * n + bl + start + lane) : 0.0;
-    __syncthreads();
-    double du = 0.0;
-    if (threadIdx.x < nl)
-      for (int q = 0; q < tu; ++q) du += tile[threadIdx.x * kLd + q] * us[q];
-    __syncthreads();
-    for (int ll = w; ll < nl; ll += kW)
-      tile[ll * kLd + lane] = lane < tv ? rld<kFF>(raw, (int64_t)(lb + ll) * n + br + start + lane) : 0.0;
-    __syncthreads();
-    if (threadIdx.x < nl) {
-      double dv = 0.0;
-      for (int q = 0; q < tv; ++q) dv += tile[threadIdx.x * kLd + q] * vs[q];
-      out[4 + l] = du;
-      out[4 + a.max_rank + l] = dv;
+    double* out = a.part + (int64_t)item * a.part_stride;
+    if (w == 0) {
+      double u = 0.0, v = 0.0, bv = 0.0;
+      int bi = -1;
+      if (t < ml) {
+        double s = 0.0;
+        for (int q = 0; q < kW; ++q) s += red[q][lane];
+        u = rst<false>(raw, (int64_t)k * n + bl + t, entry_wide<false, kGen>(a, cov, id, bl + t, br + j, tab, cf) - s);
+        if (!isu_s[lane]) amax_merge(bv, bi, u, t);
+      }
+      if (t < mr) {
+        const int64_t e = (int64_t)k * n + br + t;
+        v = rst<false>(raw, e, rld<false>(raw, e) * (1.0 / delta));
+      }
+      us[lane] = u;
+      vs[lane] = v;
+      const double nu2 = warp_sum(u * u), nv2 = warp_sum(v * v);
+      warp_amax(bv, bi);
+      if (lane == 0) {
+        out[0] = bv;
+        out[1] = (double)bi;
+        out[2] = nu2;
+        out[3] = nv2;
+      }
+    }
+    // u_l.u and v_l.v over this tile's rows: kWideThreads values of l at a time, their columns
+    // staged through shared memory (each warp loads whole 32-row columns, coalesced), then
+    // thread l sums its column in row order
+    extern __shared__ double tile[];  // kWideThreads x (kWideTile + 1)
+    constexpr int kLd = kWideTile + 1;
+    const int tu = min(kWideTile, ml - start), tv = min(kWideTile, mr - start);
+    for (int lb = 0; lb < k; lb += kWideThreads) {
+      const int nl = min(kWideThreads, k - lb);
+      const int l = lb + threadIdx.x;
+      __syncthreads();
+      for (int ll = w; ll < nl; ll += kW)
+        tile[ll * kLd + lane] = lane < tu ? rld<false>(raw, (int64_t)(lb + ll) * n + bl + start + lane) : 0.0;
+      __syncthreads();
+      double du = 0.0;
+      if (threadIdx.x < nl)
+        for (int q = 0; q < tu; ++q) du += tile[threadIdx.x * kLd + q] * us[q];
+      __syncthreads();
+      for (int ll = w; ll < nl; ll += kW)
+        tile[ll * kLd + lane] = lane < tv ? rld<false>(raw, (int64_t)(lb + ll) * n + br + start + lane) : 0.0;
+      __syncthreads();
+      if (threadIdx.x < nl) {
+        double dv = 0.0;
+        for (int q = 0; q < tv; ++q) dv += tile[threadIdx.x * kLd + q] * vs[q];
+        out[4 + l] = du;
+        out[4 + a.max_rank + l] = dv;
+      }
     }
   }
 }

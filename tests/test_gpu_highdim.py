@@ -62,9 +62,9 @@ def test_high_dim_vs_oracle_and_dense(H, n, d, half, precision):
     # In [-3, 3]^32 the off-diagonal entries lie between about exp(-50) and exp(-192): the
     # FP64 form compresses them to eps of their own norm; the mixed form's double-floats
     # (FP32 exponent range) lose their low words there or hold them as zero, so its ranks
-    # are not the FP64 form's (the 1024-row tiles' FP32 norms underflow and stop at rank 0,
-    # the 32-row tiles of nodes with a rank cap above 256 take FP64 norms and see the
-    # entries' rounding). Either is exact to rounding against 2I: the checks below.
+    # are not the FP64 form's (its FP32 norms of the high words underflow there, so a
+    # block can stop at rank 0, or see the entries' rounding). Either is exact to rounding
+    # against 2I: the checks below.
     sol_d, ld_d = O.dense_solve(x, "se", th, S2, y)
     print(f"d {d} prec {precision}: ranks {lv.tolist()} logdet vs oracle {rel(ld, ld_o):.2e} "
           f"vs dense {rel(ld, ld_d):.2e}, solution vs dense "
