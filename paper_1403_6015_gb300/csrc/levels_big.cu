@@ -576,10 +576,19 @@ cudaError_t big_setup(Ctx& c) {
   int occ = 0;
   HODLR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lu_panel, kPanelThreads, smem));
   c.coop_cap = std::max(1, occ) * c.sms;
+  // HODLR_TEST_COOP_CAP=k: at most k co-resident CTAs per panel launch, so that a test can
+  // run a level's nodes over several launches (a smaller cap only splits launches)
+  if (const char* ev = getenv("HODLR_TEST_COOP_CAP")) c.coop_cap = std::max(1, std::min(c.coop_cap, atoi(ev)));
   return cudaSuccess;
 }
 
-int64_t big_slot_elems(int coop_cap) { return (int64_t)4 * coop_cap * kSlot; }
+// Published panel candidates per launch: 2 parities x (G + 1) slots for each of its cnt
+// nodes, cnt <= max(1, coop_cap / G), so at most 4 max(coop_cap, G) slots; G is at most
+// the CTAs of a 2 kMaxRank-row panel.
+int64_t big_slot_elems(int coop_cap) {
+  const int g_max = (2 * kMaxRank + kPanelRows - 1) / kPanelRows;
+  return (int64_t)4 * std::max(coop_cap, g_max) * kSlot;
+}
 
 // Node step of level na.j with the blocked LU (factor mode) and the blocked substitution.
 cudaError_t launch_node_blocked(Ctx& c, const NodeArgs& na, bool factor) {

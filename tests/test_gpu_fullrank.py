@@ -199,3 +199,22 @@ def test_full_rank_sweep_and_batched_lanes(H):
     torch.cuda.synchronize()
     assert (st2.cpu().numpy() == 0).all(), st2
     np.testing.assert_allclose(out2.cpu().numpy(), ref, rtol=1e-12, atol=0)
+
+
+def test_panel_launches_split_over_nodes(H, monkeypatch):
+    """A level's nodes go into one cooperative panel launch while their CTAs fit on the GPU
+    at once, else into several. HODLR_TEST_COOP_CAP=2 forces the split (one or two nodes per
+    launch on every level here); each node's arithmetic is the same in either grouping, so
+    the results must be identical bit for bit."""
+    n, d = 1000, 8
+    x = I.uniform_points(n, d, -3.0 / np.sqrt(8.0), 3.0 / np.sqrt(8.0), 2140)
+    y = I.normal(n, 2141)
+    th = [ELL, 1.0]
+    ref = H.Hodlr(x, "se", th, S2, 128, EPS, max_rank=n // 2)
+    sol_ref = ref.factor_solve(y)
+    monkeypatch.setenv("HODLR_TEST_COOP_CAP", "2")
+    h = H.Hodlr(x, "se", th, S2, 128, EPS, max_rank=n // 2)
+    sol = h.factor_solve(y)
+    monkeypatch.delenv("HODLR_TEST_COOP_CAP")
+    assert h.logdet() == ref.logdet()
+    np.testing.assert_array_equal(sol, sol_ref)
