@@ -60,8 +60,9 @@ struct AcaArgs {
   int32_t* active;
   int nint;
   int pre[32];         // presized rank of each level (0: adaptive)
-  int wide0, wide1;    // item range of the wide nodes (rank cap above kWideRank)
-  const int32_t* wide_nodes;  // their ids
+  const int32_t* node_witem0;  // per node: first wide item (-1: none), one past the last
+  const int32_t* node_witem1;
+  const int32_t* wide_nodes;   // the nodes with wide items
 };
 
 // Entry k(x_i, x_j) of an off-diagonal block: FP64, or (mixed form) double-float
@@ -105,6 +106,13 @@ __device__ __forceinline__ ff block_entry_ff(const AcaArgs& a, int lev, int i, i
 }
 
 __device__ __forceinline__ int level_of(int id) { return 31 - __clz(id + 1); }
+
+// Node id's cross runs on its 32-row wide items once its rank has reached kWideRank (the
+// rank changes only at the end of a step, so every kernel of a step agrees), before that on
+// its 1024-row tiles.
+__device__ __forceinline__ bool wide_now(const AcaArgs& a, int id) {
+  return a.node_witem0[id] >= 0 && a.rank[id] >= kWideRank;
+}
 
 // Squared distance of point i to point s, accumulated coordinate by coordinate without
 // fused multiply-adds (the same operations, in the same order, as the oracle's restart
@@ -195,7 +203,7 @@ template <bool kFF, bool kGen>
 __global__ void __launch_bounds__(kAcaThreads) k_aca_row(AcaArgs a) {
   int item = blockIdx.x;
   int id = a.item_node[item];
-  if (a.done[id]) return;
+  if (a.done[id] || wide_now(a, id)) return;
   __shared__ double dsm[kRankChunk];  // u_l(i) for a chunk of l
   __shared__ ff tab[64];
   __shared__ double wv[kAcaThreads / 32];
@@ -301,7 +309,8 @@ __global__ void k_aca_pivot_row(AcaArgs a) {
   int id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (id >= a.nint || a.done[id]) return;
-  int i0 = a.node_item0[id], i1 = a.node_item1[id];
+  const bool wd = wide_now(a, id);
+  int i0 = wd ? a.node_witem0[id] : a.node_item0[id], i1 = wd ? a.node_witem1[id] : a.node_item1[id];
   double bv = 0.0;
   int bi = -1;
   for (int it = i0 + lane; it < i1; it += 32) {
@@ -375,7 +384,7 @@ template <bool kFF, bool kGen>
 __global__ void __launch_bounds__(kAcaThreads) k_aca_col(AcaArgs a) {
   int item = blockIdx.x;
   int id = a.item_node[item];
-  if (a.done[id] || !a.phase[id]) return;
+  if (a.done[id] || !a.phase[id] || wide_now(a, id)) return;
   constexpr int kW = kAcaThreads / 32;
   __shared__ double vjk_s[kRankChunk];           // v_l(j) for a chunk of l
   __shared__ int used_s[kUsedChunk];             // a chunk of the used rows
@@ -813,17 +822,13 @@ __device__ void col_decide(const AcaArgs& a, int id, int k, int bi, double nu2, 
   atomicAdd(a.active, 1);
 }
 
-__device__ __forceinline__ bool is_wide(const AcaArgs& a, int id) {
-  const int i0 = a.node_item0[id];
-  return i0 >= a.wide0 && i0 < a.wide1;
-}
 
 // D: one warp per node combines the tiles, updates the norm estimate and decides (wide
 // nodes: k_aca_pivot_col_wide).
 __global__ void k_aca_pivot_col(AcaArgs a) {
   int id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (id >= a.nint || is_wide(a, id) || a.done[id]) return;
+  if (id >= a.nint || a.done[id] || wide_now(a, id)) return;
   if (!a.phase[id]) {
     if (lane == 0) atomicAdd(a.active, 1);
     return;
@@ -914,7 +919,7 @@ __global__ void __launch_bounds__(kWideThreads) k_aca_row_wide(AcaArgs a, int it
   constexpr int kW = kWideThreads / 32;
   const int item = item0 + blockIdx.x;
   const int id = a.item_node[item];
-  if (a.done[id]) return;
+  if (a.done[id] || a.rank[id] < kWideRank) return;
   __shared__ double uik[kRankChunk];
   __shared__ double red[kW][kWideTile];
   __shared__ ff tab[64];
@@ -1000,7 +1005,7 @@ __global__ void __launch_bounds__(kWideThreads) k_aca_col_wide(AcaArgs a, int it
   constexpr int kW = kWideThreads / 32;
   const int item = item0 + blockIdx.x;
   const int id = a.item_node[item];
-  if (a.done[id] || !a.phase[id]) return;
+  if (a.done[id] || !a.phase[id] || a.rank[id] < kWideRank) return;
   __shared__ double vjk[kRankChunk];
   __shared__ int used_s[kUsedChunk];
   __shared__ double red[kW][kWideTile];
@@ -1182,11 +1187,11 @@ __global__ void __launch_bounds__(kWideThreads) k_aca_col_wide(AcaArgs a, int it
 // (u_l.u)(v_l.v) over its l's (warp sums, then the warps in order) into cross_part.
 __global__ void __launch_bounds__(kCrossL) k_aca_cross_wide(AcaArgs a, double* cross_part, int nchunk) {
   const int id = a.wide_nodes[blockIdx.y];
-  if (a.done[id] || !a.phase[id]) return;
+  if (a.done[id] || !a.phase[id] || a.rank[id] < kWideRank) return;
   const int k = a.rank[id];
   const int l = blockIdx.x * kCrossL + threadIdx.x;
   if (blockIdx.x * kCrossL >= k) return;
-  const int i0 = a.node_item0[id], i1 = a.node_item1[id];
+  const int i0 = a.node_witem0[id], i1 = a.node_witem1[id];
   double c = 0.0;
   if (l < k) {
     double du = 0.0, dv = 0.0;
@@ -1212,14 +1217,14 @@ __global__ void __launch_bounds__(kCrossL) k_aca_cross_wide(AcaArgs a, double* c
 // from k_aca_cross_wide's chunks in order.
 __global__ void __launch_bounds__(32) k_aca_pivot_col_wide(AcaArgs a, const double* cross_part, int nchunk) {
   const int id = a.wide_nodes[blockIdx.x];
-  if (a.done[id]) return;
+  if (a.done[id] || a.rank[id] < kWideRank) return;  // k_aca_pivot_col's node
   const int lane = threadIdx.x;
   if (!a.phase[id]) {
     if (lane == 0) atomicAdd(a.active, 1);
     return;
   }
   const int k = a.rank[id];
-  const int i0 = a.node_item0[id], i1 = a.node_item1[id];
+  const int i0 = a.node_witem0[id], i1 = a.node_witem1[id];
   double bv = 0.0, nu2 = 0.0, nv2 = 0.0;
   int bi = -1;
   for (int it = i0 + lane; it < i1; it += 32) {
@@ -1331,8 +1336,8 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
   a.xrel = reinterpret_cast<const ff*>(c.xrel);
   a.active = c.active;
   a.nint = nint;
-  a.wide0 = (int)c.n_big_items;
-  a.wide1 = (int)(c.n_big_items + c.n_wide_items);
+  a.node_witem0 = c.node_witem0;
+  a.node_witem1 = c.node_witem1;
   a.wide_nodes = c.wide_nodes;
   k_aca_init<<<(nint + 255) / 256, 256, 0, c.stream>>>(a);
   ++c.launches;
@@ -1361,7 +1366,8 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
       ACA_LAUNCH(k_aca_row, (unsigned)nbig, smem_row, a);
       ++c.launches;
     }
-    if (nwide > 0) {
+    const bool wide_step = nwide > 0 && s >= kWideRank;  // a rank grows by one per step at most
+    if (wide_step) {
       ACA_LAUNCH_T(k_aca_row_wide, (unsigned)nwide, kWideThreads, 0, a, (int)nbig);
       ++c.launches;
     }
@@ -1374,7 +1380,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
       ACA_LAUNCH(k_aca_col, (unsigned)nbig, smem_col, a);
       ++c.launches;
     }
-    if (nwide > 0) {
+    if (wide_step) {
       ACA_LAUNCH_T(k_aca_col_wide, (unsigned)nwide, kWideThreads, smem_wide, a, (int)nbig);
       ++c.launches;
     }
@@ -1383,7 +1389,7 @@ cudaError_t launch_aca(Ctx& c, int* steps_out) {
       ++c.launches;
     }
     k_aca_pivot_col<<<wblocks, 256, 0, c.stream>>>(a);
-    if (c.n_wide_nodes > 0) {
+    if (wide_step) {
       k_aca_cross_wide<<<dim3((unsigned)nchunk, (unsigned)c.n_wide_nodes), kCrossL, 0, c.stream>>>(a, c.wide_cross, nchunk);
       k_aca_pivot_col_wide<<<(unsigned)c.n_wide_nodes, 32, 0, c.stream>>>(a, c.wide_cross, nchunk);
       c.launches += 2;

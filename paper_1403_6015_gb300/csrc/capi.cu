@@ -77,14 +77,14 @@ void free_factor_buffers(Ctx* c) {
 void free_all(Ctx* c) {
   free_factor_buffers(c);
   dfree(c->nodes); dfree(c->xs); dfree(c->perm);
-  dfree(c->item_node); dfree(c->item_start); dfree(c->wide_nodes); dfree(c->wide_cross); dfree(c->node_item0); dfree(c->node_item1); dfree(c->raw);
+  dfree(c->item_node); dfree(c->item_start); dfree(c->wide_nodes); dfree(c->wide_cross); dfree(c->node_witem0); dfree(c->node_witem1); dfree(c->node_item0); dfree(c->node_item1); dfree(c->raw);
   dfree(c->cheb_q); dfree(c->cheb_coef);
   dfree(c->st_rank); dfree(c->st_row); dfree(c->st_col); dfree(c->st_done); dfree(c->st_ok);
   dfree(c->st_zero); dfree(c->st_phase); dfree(c->st_nused); dfree(c->st_used);
   dfree(c->st_delta); dfree(c->st_s2); dfree(c->aca_part); dfree(c->active);
   dfree(c->Y); dfree(c->ysort); dfree(c->leafL); dfree(c->leaf_logdet); dfree(c->node_logdet); dfree(c->leaf_perm);
   dfree(c->scal); dfree(c->dflags); dfree(c->tmpvec); dfree(c->ry); dfree(c->rw); dfree(c->exp_tab); dfree(c->xrel); dfree(c->Mlu); dfree(c->Mpiv);
-  dfree(c->big_i32); dfree(c->big_slots); dfree(c->big_perm);
+  dfree(c->big_i32); dfree(c->big_slots); dfree(c->big_perm); dfree(c->split_buf);
   dfree(c->hyp);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
@@ -131,10 +131,12 @@ hodlr_status setup_aca(Ctx* c) {
   const int32_t* nb = c->h_nodes.data();
   const int32_t* ns = nb + ((int64_t)2 << K);
   // work items: first the kAcaTile-row tiles of the nodes with a child above kSmallNode
-  // points (one block each), then the kWideTile-row tiles of the wide nodes (rank cap above
-  // kWideRank), then one item per small node (one warp each); node id owns items
-  // [i0[id], i1[id])
+  // points (one block each), node id owning items [i0[id], i1[id]); then, for the nodes
+  // whose rank cap exceeds kWideRank, kWideTile-row tiles [wi0[id], wi1[id]) too, which take
+  // over from the 1024-row tiles once the node's rank reaches kWideRank; then one item per
+  // small node (one warp each)
   std::vector<int32_t> inode, istart, i0(nint + 1), i1(nint + 1, 0), wide;
+  std::vector<int32_t> wi0(nint + 1, -1), wi1(nint + 1, -1);
   for (int pass = 0; pass < 3; ++pass) {
     if (pass == 1) c->n_big_items = (int64_t)inode.size();
     if (pass == 2) c->n_wide_items = (int64_t)inode.size() - c->n_big_items;
@@ -142,16 +144,16 @@ hodlr_status setup_aca(Ctx* c) {
       int32_t m = std::max(ns[2 * id + 1], ns[2 * id + 2]);
       bool small = m <= hodlr::kSmallNode;
       bool wd = !small && std::min(std::min(ns[2 * id + 1], ns[2 * id + 2]), c->max_rank) > hodlr::kWideRank;
-      if ((pass == 0 && (small || wd)) || (pass == 1 && !wd) || (pass == 2 && !small)) continue;
-      if (wd) wide.push_back(id);
-      const int tile = wd ? hodlr::kWideTile : hodlr::kAcaTile;
-      i0[id] = (int32_t)inode.size();
+      if ((pass == 0 && small) || (pass == 1 && !wd) || (pass == 2 && !small)) continue;
+      if (pass == 1) wide.push_back(id);
+      const int tile = pass == 1 ? hodlr::kWideTile : hodlr::kAcaTile;
+      (pass == 1 ? wi0 : i0)[id] = (int32_t)inode.size();
       for (int32_t s = 0; s < m || s == 0; s += tile) {
         inode.push_back(id);
         istart.push_back(s);
         if (small) break;
       }
-      i1[id] = (int32_t)inode.size();
+      (pass == 1 ? wi1 : i1)[id] = (int32_t)inode.size();
     }
   }
   c->n_wide_nodes = (int)wide.size();
@@ -186,6 +188,8 @@ hodlr_status setup_aca(Ctx* c) {
   TRY_CUDA(c, dalloc(&c->st_s2, nint), "alloc aca state");
   TRY_CUDA(c, dalloc(&c->aca_part, c->n_items * (4 + 2 * c->max_rank)), "alloc aca partials");
   TRY_CUDA(c, dalloc(&c->wide_nodes, (int64_t)wide.size()), "alloc items");
+  TRY_CUDA(c, dalloc(&c->node_witem0, nint + 1), "alloc items");
+  TRY_CUDA(c, dalloc(&c->node_witem1, nint + 1), "alloc items");
   TRY_CUDA(c, dalloc(&c->wide_cross, (int64_t)wide.size() * ((c->max_rank + 127) / 128)), "alloc items");
   if (!wide.empty())
     TRY_CUDA(c, cudaMemcpyAsync(c->wide_nodes, wide.data(), 4 * wide.size(), cudaMemcpyHostToDevice, c->stream), "upload");
@@ -197,6 +201,8 @@ hodlr_status setup_aca(Ctx* c) {
   TRY_CUDA(c, cudaMemcpyAsync(c->item_start, istart.data(), 4 * istart.size(), cudaMemcpyHostToDevice, c->stream), "upload");
   TRY_CUDA(c, cudaMemcpyAsync(c->node_item0, i0.data(), 4 * i0.size(), cudaMemcpyHostToDevice, c->stream), "upload");
   TRY_CUDA(c, cudaMemcpyAsync(c->node_item1, i1.data(), 4 * i1.size(), cudaMemcpyHostToDevice, c->stream), "upload");
+  TRY_CUDA(c, cudaMemcpyAsync(c->node_witem0, wi0.data(), 4 * wi0.size(), cudaMemcpyHostToDevice, c->stream), "upload");
+  TRY_CUDA(c, cudaMemcpyAsync(c->node_witem1, wi1.data(), 4 * wi1.size(), cudaMemcpyHostToDevice, c->stream), "upload");
   TRY_CUDA(c, cudaStreamSynchronize(c->stream), "upload");
   ++c->syncs;
   return HODLR_OK;
@@ -217,7 +223,7 @@ hodlr_status size_buffers(Ctx* c) {
   bool big = false;
   for (int j = 0; j < K; ++j) {
     const int64_t rw = (int64_t)c->h_rl[j] * (c->h_coff[j] + c->h_rl[j] + c->max_nrhs);
-    if (j + 1 < K && hodlr::gemm_step(c->h_rl, j + 1)) direct_el = std::max(direct_el, rw << (j + 1));
+    if (j + 1 < K && hodlr::gemm_step(*c, j + 1)) direct_el = std::max(direct_el, rw << (j + 1));
     else pstride = std::max(pstride, rw);
     big |= c->h_rl[j] > hodlr::kSmemRank;  // a blocked node step (levels_big.cu)
   }
@@ -270,6 +276,22 @@ hodlr_status size_buffers(Ctx* c) {
       c->big_nodes = std::max<int64_t>(nleaf / 2, 1);
       TRY_CUDA(c, dalloc(&c->big_i32, 2 * c->big_nodes), "alloc large-rank scratch");
       TRY_CUDA(c, dalloc(&c->big_slots, hodlr::big_slot_elems(c->coop_cap)), "alloc large-rank scratch");
+    }
+    // split-K partial half sums: every width the sweep steps in product form can use
+    // (factor mode with 1 .. max_nrhs right-hand sides, solve mode)
+    int64_t split_el = 0;
+    for (int u = 1; u < K; ++u) {
+      if (!hodlr::gemm_step(*c, u)) continue;
+      for (int nr = 1; nr <= c->max_nrhs; ++nr)
+        for (int w : {c->h_coff[u] + nr, nr}) {
+          const int S = hodlr::half_sum_splits(*c, u, w);
+          if (S > 1) split_el = std::max<int64_t>(split_el, ((int64_t)S << u) * c->h_rl[u - 1] * w);
+        }
+    }
+    if (c->split_cap < split_el) {
+      dfree(c->split_buf);
+      TRY_CUDA(c, dalloc(&c->split_buf, split_el), "alloc split sums");
+      c->split_cap = split_el;
     }
     if (c->big_perm_cap < perm_el) {
       dfree(c->big_perm);

@@ -29,7 +29,8 @@ constexpr int kBlockRank = 128;    // ranks from this up: the sweep in product f
 constexpr int kAcaTile = 1024;     // columns (rows) of one ACA work item
 constexpr int kSmallNode = 256;    // nodes whose children both fit: one warp per node
 constexpr int kWideRank = 256;     // nodes whose rank cap min(m_left, m_right, max_rank)
-constexpr int kWideTile = 32;      // exceeds this: ACA work items of 32 rows (one per lane)
+constexpr int kWideTile = 32;      // exceeds this also get ACA work items of 32 rows (one
+                                   // per lane), used once their rank reaches kWideRank
 
 // ---------------------------------------------------------------------------------------
 // Covariance functions (Table 1 with length scale ell and amplitude a; Matern nu = 3/2 and
@@ -188,12 +189,6 @@ __device__ __forceinline__ double dist(const Pts& p, int i, int j) {
   return sqrt(s);
 }
 
-// Sweep step of level u (update of level u, half-node sums of level u - 1) in product form:
-// when either level's rank is large. Level j's half sums then come straight from step j + 1,
-// without per-leaf partials.
-inline bool gemm_step(const std::vector<int>& rl, int u) {
-  return rl[u] >= kBlockRank || (u >= 1 && rl[u - 1] >= kBlockRank);
-}
 
 // Device error word bits (ctx->dflags).
 // kFlagNegDet: parity of the negative block determinants of an indefinite C (the sign of
@@ -258,6 +253,8 @@ struct Ctx {
   int64_t n_big_items = 0;        // items [0, n_big_items): tiles of kAcaTile rows; then
   int64_t n_wide_items = 0;       // n_wide_items tiles of kWideTile rows; the rest: small nodes
   int32_t* wide_nodes = nullptr;  // ids of the nodes with wide items
+  int32_t* node_witem0 = nullptr; // per node: its first wide item (-1: none), then one past
+  int32_t* node_witem1 = nullptr; // its last
   double* wide_cross = nullptr;   // their cross-term chunks, ceil(max_rank / 128) each
   int n_wide_nodes = 0;
   std::vector<int64_t> h_raw_off; // offset (in doubles) of level j's raw panel
@@ -316,6 +313,8 @@ struct Ctx {
   int32_t* big_perm = nullptr;
   int64_t big_perm_cap = 0;
   int coop_cap = 0;               // co-resident CTAs of the cooperative panel launch
+  double* split_buf = nullptr;    // split-K partial half-node sums of the product-form sweep
+  int64_t split_cap = 0;
   int64_t fused_work = 0;         // largest per-block reduction of the fused sweep (values)
   int64_t half_elems = 0;
   double* scal = nullptr;         // [0] logdet, [1] quad, [2] loglik
@@ -357,6 +356,29 @@ struct Ctx {
   std::string last_error;
 };
 
+// Sweep step of level u (update of level u, half-node sums of level u - 1) in product form,
+// when either level's rank is large. Level j's half sums then come straight from step j + 1,
+// without per-leaf partials. The FP64 form always takes it there: its batched FP64 products
+// run near the FP64 peak, while the per-leaf kernel spends about 8 FP64 instructions per
+// dot product. The mixed form's per-leaf kernel works in double-float on the FP32 pipe and
+// is faster at moderate ranks (2-D, n = 2^20, ranks up to 225: 1.52 against 2.01 s per
+// evaluation) but far slower at ranks in the thousands (factor of the d = 4, n = 5000
+// Gaussian row: 2.30 against 0.54 s), where it also loops over thousands of coarser panel
+// columns per leaf. So it takes the product form from rank 512 or 1024 panel columns, or
+// where its per-leaf partials would need more than 8 GB.
+constexpr int kMixedProductRank = 512;
+constexpr int kMixedProductCols = 1024;
+inline bool gemm_step(const Ctx& c, int u) {
+  const std::vector<int>& rl = c.h_rl;
+  if (!(rl[u] >= kBlockRank || (u >= 1 && rl[u - 1] >= kBlockRank))) return false;
+  if (c.precision == 0) return true;
+  if (rl[u] >= kMixedProductRank || (u >= 1 && rl[u - 1] >= kMixedProductRank)) return true;
+  if (c.h_coff[u] >= kMixedProductCols) return true;
+  if (u < 1) return false;
+  const double bytes = 8.0 * (double)((int64_t)1 << c.kappa) * rl[u - 1] * (c.h_coff[u] + c.max_nrhs);
+  return bytes > 8e9;
+}
+
 // Launch wrappers (each .cu file defines its own); all are stream-ordered on ctx.stream.
 cudaError_t launch_sort_1d(Ctx& c, const double* x_dev_rowmajor);
 cudaError_t launch_sort_kd(Ctx& c, const double* x_dev_rowmajor);
@@ -392,6 +414,7 @@ cudaError_t big_setup(Ctx& c);
 int64_t big_slot_elems(int coop_cap);
 cudaError_t launch_node_blocked(Ctx& c, const NodeArgs& na, bool factor);
 cudaError_t launch_sweep_gemm(Ctx& c, int u, int nrhs, bool factor_mode);
+int half_sum_splits(const Ctx& c, int u, int w);
 cudaError_t launch_logdet_sum(Ctx& c);
 cudaError_t launch_quad_loglik(Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double* xin_sorted, double* yout_sorted);

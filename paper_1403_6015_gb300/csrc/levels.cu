@@ -407,7 +407,7 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
     int cP = factor_mode ? cj + r : 0;  // panel columns in the level-j partials
     int w = cP + nrhs;
     int h = 1 << (K - j - 1);
-    const bool direct = j + 1 < K && gemm_step(c.h_rl, j + 1);
+    const bool direct = j + 1 < K && gemm_step(c, j + 1);
     if (!direct)
       HODLR_CUDA_TRY(segsum(c.part, c.part_stride, r * w, nleaf, h, c.part2, c.half, c.stream, &c.launches));
     NodeArgs na;
@@ -456,7 +456,7 @@ cudaError_t launch_levels(Ctx& c, int nrhs, bool factor_mode) {
     sa.part_stride = c.part_stride;
     sa.n = c.n;
     if (sa.cP + nrhs == 0) continue;  // nothing left to update (root level, no right-hand side)
-    if (gemm_step(c.h_rl, j)) {
+    if (gemm_step(c, j)) {
       HODLR_CUDA_TRY(launch_sweep_gemm(c, j, nrhs, factor_mode));
       continue;
     }

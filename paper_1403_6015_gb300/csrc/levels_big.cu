@@ -58,6 +58,8 @@ struct GemmArgs {
   int id0;
   int sh;                   // kNodeRows: problems per Z block's node = 2^sh
   int64_t z_stride, z_side; // kNodeRows: Z of node (t >> sh), side ((t >> (sh-1)) & 1)
+  int ksplit;               // kHalfRows: blockIdx.z = t ksplit + s, split s summing rows
+  int kchunk;               // [s kchunk, (s + 1) kchunk) of the half-node into its own C
 };
 
 __device__ __forceinline__ double ldv(const double* p, int64_t i) { return p[i]; }
@@ -70,7 +72,7 @@ __device__ __forceinline__ void stv(ff* p, int64_t i, double v) { p[i] = ff_from
 // and is then subtracted from C (kSub) or stored.
 template <class TA, class TB, class TC, bool kSub>
 __global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
-  const int t = blockIdx.z;
+  int t = blockIdx.z;
   int m = g.m, K = g.k;
   int64_t oa = (int64_t)t * g.a_bs, ob = (int64_t)t * g.b_bs, oc = (int64_t)t * g.c_bs;
   if (g.mode == kNodeRows) {
@@ -81,11 +83,14 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
     oc = b;
     ob = (int64_t)(t >> g.sh) * g.z_stride + (int64_t)((t >> (g.sh - 1)) & 1) * g.z_side;
   } else if (g.mode == kHalfRows) {
+    const int sp = t % g.ksplit;  // C = problem slot t ksplit + sp (its own partial sum)
+    t /= g.ksplit;
     const int id = g.id0 + t;
-    const int b = g.nb[id];
-    K = g.ns[id];
+    const int b = g.nb[id] + sp * g.kchunk;
+    K = min(g.kchunk, g.ns[id] - sp * g.kchunk);
     oa = b;
     ob = b;
+    oc = (int64_t)blockIdx.z * g.c_bs;
   }
   const int i0 = blockIdx.y * kBM, j0 = blockIdx.x * kBN;
   if (i0 >= m || j0 >= g.n) return;
@@ -559,6 +564,17 @@ __global__ void k_z_toff(double* Zall, int64_t z_stride, int m2, int wz, int cj)
   }
 }
 
+// half[t][e] = sum over s < S of part[(t S + s)][e], e < E, in split order.
+__global__ void k_split_sum(const double* __restrict__ part, int S, int64_t E, double* __restrict__ half) {
+  const int t = blockIdx.y;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const double* p = part + (int64_t)t * S * E + e;
+    double v = 0.0;
+    for (int q = 0; q < S; ++q) v += p[(int64_t)q * E];
+    half[(int64_t)t * E + e] = v;
+  }
+}
+
 unsigned grid_for(int64_t elems, int per_block) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((elems + per_block - 1) / per_block, 4096));
 }
@@ -588,6 +604,19 @@ cudaError_t big_setup(Ctx& c) {
 int64_t big_slot_elems(int coop_cap) {
   const int g_max = (2 * kMaxRank + kPanelRows - 1) / kPanelRows;
   return (int64_t)4 * std::max(coop_cap, g_max) * kSlot;
+}
+
+// Splits of the half-node sums of level u - 1 (sweep step u, product form): enough that the
+// products fill the GPU twice (tiles of the rl x w outputs of the 2^u half-nodes times the
+// splits), each split at least 2048 rows, at most 64.
+int half_sum_splits(const Ctx& c, int u, int w) {
+  if (u < 1) return 1;
+  const int rl = c.h_rl[u - 1];
+  const int64_t tiles = (int64_t)((rl + kBM - 1) / kBM) * ((w + kBN - 1) / kBN) << u;
+  int mh = 0;
+  for (int t = 0; t < (1 << u); ++t) mh = std::max(mh, c.h_nodes[((size_t)2 << c.kappa) + (1 << u) - 1 + t]);
+  const int64_t want = (2 * (int64_t)c.sms + tiles - 1) / std::max<int64_t>(tiles, 1);
+  return (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)mh / 2048, 64}));
 }
 
 // Node step of level na.j with the blocked LU (factor mode) and the blocked substitution.
@@ -694,6 +723,8 @@ cudaError_t launch_node_blocked(Ctx& c, const NodeArgs& na, bool factor) {
   return cudaGetLastError();
 }
 
+static int ns_host(const Ctx& c, int id) { return c.h_nodes[((size_t)2 << c.kappa) + id]; }
+
 // Sweep step of level u in product form: the rows of each half of a level-u node
 // P -= Ut Z_side (panel columns [0, cP) and the right-hand sides), then, for u > 0, the
 // half-node sums of level u - 1,
@@ -760,18 +791,31 @@ static cudaError_t sweep_gemm_t(Ctx& c, int u, int nrhs, bool factor_mode) {
     h.nb = nb;
     h.ns = ns;
     h.id0 = (1 << u) - 1;
+    // split-K when the 2^u half-nodes' outputs are too few tiles for the GPU: each split's
+    // sum into its own slot of the split buffer, then the splits added in order
+    const int S = half_sum_splits(c, u, wz);
+    int mh = 0;
+    for (int t = 0; t < (1 << u); ++t) mh = std::max(mh, ns_host(c, h.id0 + t));
+    h.ksplit = S;
+    h.kchunk = (mh + S - 1) / S;
+    double* dst = S > 1 ? c.split_buf : c.half;
     if (cP > 0) {
       h.b = pan;
-      h.c = c.half;
+      h.c = dst;
       h.n = cP;
-      HODLR_CUDA_TRY((gemm<T, T, double, false>(h, rl, 1 << u, c.stream)));
+      HODLR_CUDA_TRY((gemm<T, T, double, false>(h, rl, S << u, c.stream)));
       ++c.launches;
     }
     if (nrhs > 0) {
       h.b = c.Y;
-      h.c = c.half + cP;
+      h.c = dst + cP;
       h.n = nrhs;
-      HODLR_CUDA_TRY((gemm<T, double, double, false>(h, rl, 1 << u, c.stream)));
+      HODLR_CUDA_TRY((gemm<T, double, double, false>(h, rl, S << u, c.stream)));
+      ++c.launches;
+    }
+    if (S > 1) {
+      const int64_t E = (int64_t)rl * wz;
+      k_split_sum<<<dim3(grid_for(E, 256), 1u << u), 256, 0, c.stream>>>(c.split_buf, S, E, c.half);
       ++c.launches;
     }
   }
