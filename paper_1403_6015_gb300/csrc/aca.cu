@@ -889,30 +889,6 @@ static_assert(kWideTile == 32, "one row of a wide item per lane");
 constexpr int kCrossL = 128;  // l values per CTA of the wide cross term
 constexpr int kWideThreads = 512;  // CTA of the wide row and column kernels (16 warps)
 
-template <bool kFF>
-__device__ __forceinline__ double rld(const double* raw, int64_t i) {
-  return kFF ? ff_to_double(reinterpret_cast<const ff*>(raw)[i]) : raw[i];
-}
-
-// Stores v and returns the value stored (the mixed form rounds it to a double-float).
-template <bool kFF>
-__device__ __forceinline__ double rst(double* raw, int64_t i, double v) {
-  if (!kFF) {
-    raw[i] = v;
-    return v;
-  }
-  const ff f = ff_from_double(v);
-  reinterpret_cast<ff*>(raw)[i] = f;
-  return ff_to_double(f);
-}
-
-template <bool kFF, bool kGen>
-__device__ __forceinline__ double entry_wide(const AcaArgs& a, const Cov& cov, int id, int i,
-                                             int j, const ff* tab, const CovFF& cf) {
-  if (kFF) return ff_to_double(block_entry_ff<kGen>(a, level_of(id), i, j, tab, cf));
-  return block_entry<false, kGen>(a, cov, i, j, tab, cf);
-}
-
 // A for a wide item: residual row entries b = start + lane of the right child.
 template <bool kFF, bool kGen>
 __global__ void __launch_bounds__(kWideThreads) k_aca_row_wide(AcaArgs a, int item0) {
@@ -1120,10 +1096,10 @@ __global__ void __launch_bounds__(kWideThreads) k_aca_col_wide(AcaArgs a, int it
     for (int l0 = 0; l0 < k; l0 += kRankChunk) {
       const int l1 = min(k, l0 + kRankChunk);
       __syncthreads();
-      for (int l = l0 + threadIdx.x; l < l1; l += kWideThreads) vjk[l - l0] = rld<false>(raw, l * n + br + j);
+      for (int l = l0 + threadIdx.x; l < l1; l += kWideThreads) vjk[l - l0] = raw[l * n + br + j];
       __syncthreads();
       if (t < ml)
-        for (int l = l0 + w; l < l1; l += kW) acc += rld<false>(raw, l * n + bl + t) * vjk[l - l0];
+        for (int l = l0 + w; l < l1; l += kW) acc += raw[l * n + bl + t] * vjk[l - l0];
     }
     red[w][lane] = acc;
     __syncthreads();
@@ -1134,12 +1110,14 @@ __global__ void __launch_bounds__(kWideThreads) k_aca_col_wide(AcaArgs a, int it
       if (t < ml) {
         double s = 0.0;
         for (int q = 0; q < kW; ++q) s += red[q][lane];
-        u = rst<false>(raw, (int64_t)k * n + bl + t, entry_wide<false, kGen>(a, cov, id, bl + t, br + j, tab, cf) - s);
+        u = block_entry<false, kGen>(a, cov, bl + t, br + j, tab, cf) - s;
+        raw[(int64_t)k * n + bl + t] = u;
         if (!isu_s[lane]) amax_merge(bv, bi, u, t);
       }
       if (t < mr) {
         const int64_t e = (int64_t)k * n + br + t;
-        v = rst<false>(raw, e, rld<false>(raw, e) * (1.0 / delta));
+        v = raw[e] * (1.0 / delta);
+        raw[e] = v;
       }
       us[lane] = u;
       vs[lane] = v;
@@ -1163,14 +1141,14 @@ __global__ void __launch_bounds__(kWideThreads) k_aca_col_wide(AcaArgs a, int it
       const int l = lb + threadIdx.x;
       __syncthreads();
       for (int ll = w; ll < nl; ll += kW)
-        tile[ll * kLd + lane] = lane < tu ? rld<false>(raw, (int64_t)(lb + ll) * n + bl + start + lane) : 0.0;
+        tile[ll * kLd + lane] = lane < tu ? raw[(int64_t)(lb + ll) * n + bl + start + lane] : 0.0;
       __syncthreads();
       double du = 0.0;
       if (threadIdx.x < nl)
         for (int q = 0; q < tu; ++q) du += tile[threadIdx.x * kLd + q] * us[q];
       __syncthreads();
       for (int ll = w; ll < nl; ll += kW)
-        tile[ll * kLd + lane] = lane < tv ? rld<false>(raw, (int64_t)(lb + ll) * n + br + start + lane) : 0.0;
+        tile[ll * kLd + lane] = lane < tv ? raw[(int64_t)(lb + ll) * n + br + start + lane] : 0.0;
       __syncthreads();
       if (threadIdx.x < nl) {
         double dv = 0.0;
